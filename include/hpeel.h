@@ -1,0 +1,163 @@
+/*
+ * hpeel.h -- C ABI of the GB300 (sm_103a) hypergraph peeling and MWHC
+ * minimal-perfect-hash library.
+ *
+ * The operations follow "Cache-Oblivious Peeling of Random Hypergraphs"
+ * (Belazzougui, Boldi, Ottaviano, Venturini, Vigna):
+ *   - peeling order and 2-core ................. sec. 1 (Introduction)
+ *   - hash functions, MWHC system, MPHF ........ sec. 3 (MWHC technique)
+ *   - packed incidence lists (XOR trick) ....... sec. 4.1
+ *   - layered (round-synchronous) peeling ...... sec. 4.2
+ *   - r-partite hashing, reverse-layer assign .. sec. 4.3
+ *   - broadword rank ........................... sec. 5
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are device memory owned by the caller; the library
+ *     never frees or keeps them after the call returns.  h_* pointers are
+ *     host memory owned by the caller.
+ *   - Work is issued on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream).  Calls that must decide on
+ *     the host (how many rounds, whether to retry) synchronise that stream
+ *     before returning; each call says whether it does.
+ *   - Scratch memory is a caller-provided workspace d_ws of at least the
+ *     size the matching *_workspace_size() function returns, 256-byte
+ *     aligned.  The library allocates no device memory.
+ *   - Every call returns an hpeel_status; no C++ exception crosses the ABI.
+ *     On failure hpeel_last_error() (per host thread) holds a message.
+ *   - Edge ids and vertex ids are uint32: n < 2^32 and m < 2^32.
+ *   - All results are exact and deterministic: the same inputs give the
+ *     same bytes on every run and in every launch configuration.
+ */
+#ifndef HPEEL_H
+#define HPEEL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hpeel_status {
+    HPEEL_OK = 0,
+    HPEEL_ERR_INVALID_ARG = 1,        /* bad size, NULL or misaligned pointer */
+    HPEEL_ERR_CUDA = 2,               /* a CUDA runtime call failed */
+    HPEEL_ERR_WORKSPACE_TOO_SMALL = 3,
+    HPEEL_ERR_TIMEOUT = 4,            /* a bounded device-side wait gave up */
+    HPEEL_ERR_DEVICE_CHECK = 5,       /* a kernel found an invalid input */
+    HPEEL_ERR_CORE_NONEMPTY = 6,      /* MPHF: the hypergraph did not peel */
+    HPEEL_ERR_RETRIES_EXHAUSTED = 7,  /* MPHF: no seed tried gave a peel */
+    HPEEL_ERR_CAPACITY = 8            /* more rounds than the library supports */
+} hpeel_status;
+
+/* Per-call results, written to host memory by the calls that take one. */
+typedef struct hpeel_stats {
+    uint64_t n_peeled;      /* edges in the peeling order (sum of layer sizes) */
+    uint32_t rounds;        /* R: number of non-empty layers */
+    uint32_t core_nonempty; /* 1 if n_peeled < n (a 2-core is left) */
+    uint64_t seed_used;     /* MPHF: hash seed of the successful attempt */
+    uint32_t attempts;      /* MPHF: hash seeds tried */
+    uint32_t device_err;    /* non-zero: code a kernel raised (see status) */
+} hpeel_stats;
+
+/* Largest number of rounds a single peel supports (claim words keep the
+ * round in 30 bits; the layer tables are sized to this bound). */
+#define HPEEL_MAX_ROUNDS (1u << 20)
+/* Claim word of an edge that was not peeled (a 2-core edge). */
+#define HPEEL_UNCLAIMED 0xFFFFFFFFu
+
+/* Static description of a status code. */
+const char *hpeel_status_str(hpeel_status s);
+/* Message of the last failure on this host thread ("" if none). */
+const char *hpeel_last_error(void);
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int hpeel_version(void);
+
+/*
+ * Number of vertices m for n edges at sparsity gamma = gamma_milli / 1000,
+ * r-partite: m = r * ceil(ceil(gamma n) / r)  (sec. 3: gamma n vertices;
+ * sec. 4.3: r equal parts).  Returns 0 for n == 0.  Pure host function.
+ */
+uint64_t hpeel_num_vertices(uint64_t n, uint32_t gamma_milli, uint32_t r);
+
+/*
+ * Key -> edge hashing (sec. 3 hash functions h_0..h_{r-1}; sec. 4.3 each h_j
+ * maps into its own part [j m/r, (j+1) m/r)).
+ *   d_keys  [n] uint64 keys.
+ *   d_edges [n][r] uint32 output, row-major: d_edges[i*r + j] =
+ *           (mix64(key_i ^ (seed + j)) mod (m/r)) + j*(m/r), mix64 being the
+ *           SplitMix64 output function.
+ *   2 <= r <= 4, m a positive multiple of r, m < 2^32.
+ * Asynchronous on stream.  Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_CUDA.
+ */
+hpeel_status hpeel_hash_edges(const uint64_t *d_keys, uint64_t n, uint64_t m,
+                              uint32_t r, uint64_t seed, uint32_t *d_edges,
+                              void *stream);
+
+/* Workspace bytes hpeel_peel needs for (n, m, r). */
+size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r);
+
+/*
+ * Round-synchronous peel of an r-partite r-hypergraph (sec. 4.2, with the
+ * packed incidence lists of sec. 4.1).  Round t removes every edge that has
+ * a vertex of degree 1 in the graph left by rounds 0..t-1; an edge reached
+ * from several degree-1 vertices is removed once.
+ *   d_edges     [n][r] uint32, vertex j of every edge in [j m/r, (j+1) m/r)
+ *               (what hpeel_hash_edges produces).  Not modified.
+ *   d_order     [n] uint32 output: the canonical order -- layer 0 in
+ *               ascending edge id, then layer 1 ascending, ..., then the
+ *               2-core edges (not peeled) in ascending id.  The first
+ *               n_peeled entries are a peeling order (sec. 1).
+ *   d_claim     [n] uint32 output or NULL: (round << 2) | hinge for a peeled
+ *               edge, hinge = smallest position j whose vertex had degree 1
+ *               in that round; HPEEL_UNCLAIMED for a 2-core edge.
+ *   d_layer_off [max_layers + 1] uint64 output or NULL: start of layer t in
+ *               d_order for t < R, then n_peeled at index R.
+ *   h_stats     host output or NULL: n_peeled, rounds, core_nonempty.
+ *   2 <= r <= 4.  n = 0 is valid (empty order, no round).
+ * Synchronises stream (the number of rounds is decided on the device and
+ * read back).  Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL,
+ * HPEEL_ERR_CAPACITY (R > max_layers or R > HPEEL_MAX_ROUNDS),
+ * HPEEL_ERR_DEVICE_CHECK (a vertex id outside its part), HPEEL_ERR_CUDA.
+ */
+hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m,
+                        uint32_t r, uint32_t *d_order, uint32_t *d_claim,
+                        uint64_t *d_layer_off, uint32_t max_layers,
+                        hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
+                        void *stream);
+
+/* Workspace bytes hpeel_mphf_build needs for n keys at gamma_milli. */
+size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli);
+
+/*
+ * MWHC minimal perfect hash build, r = 3 (sec. 3): hash the keys into a
+ * 3-partite hypergraph with m = hpeel_num_vertices(n, gamma_milli, 3)
+ * vertices, peel it, solve g in reverse layer order (sec. 4.3 "Avoiding
+ * backward scans") so that g[h_0(x)] + g[h_1(x)] + g[h_2(x)] = i (mod 3),
+ * where h_i(x) is the hinge of x's edge, then build the rank directory
+ * (sec. 3 ranking structure, sec. 5 broadword counting).  If the hypergraph
+ * keeps a 2-core, the build is retried with hash seed seed+1, seed+2, ...
+ * (at most max_tries seeds in total).
+ *   d_keys    [n] uint64, distinct keys (duplicates can never peel).
+ *   d_G       [ceil(m/32)] uint64 output: 2 bits per vertex, vertex v at bits
+ *             2(v mod 32), 2(v mod 32)+1 of word v/32; 0 = unassigned,
+ *             1, 2 = g, 3 = g value 0 of an assigned (hinge) vertex.
+ *   d_rank_dir [ceil(m/512) + 1] uint64 output: d_rank_dir[b] = number of
+ *             non-zero 2-bit values among vertices [0, 512 b).
+ *   MPHF(x) = d_rank_dir[v/512] + non-zero values in [512 (v/512), v), with
+ *   v = h_i(x), i = (G[h_0(x)] + G[h_1(x)] + G[h_2(x)]) mod 3.
+ *   h_stats   host output or NULL (seed_used, attempts, rounds).
+ * Synchronises stream.  Errors: HPEEL_ERR_INVALID_ARG,
+ * HPEEL_ERR_WORKSPACE_TOO_SMALL, HPEEL_ERR_RETRIES_EXHAUSTED,
+ * HPEEL_ERR_CAPACITY, HPEEL_ERR_CUDA.
+ */
+hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
+                              uint32_t gamma_milli, uint32_t max_tries,
+                              uint64_t *d_G, uint64_t *d_rank_dir,
+                              hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
+                              void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPEEL_H */

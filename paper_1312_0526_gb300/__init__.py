@@ -1,0 +1,212 @@
+"""GB300 (sm_103a) hypergraph peeling and MWHC minimal perfect hashing.
+
+Thin Python binding over the C ABI in ``include/hpeel.h`` (library
+``_build/libhpeel.so``, built by ``paper_1312_0526_gb300.build``).  The
+functions here only marshal arguments: torch tensors provide device memory
+and the current CUDA stream, and every step runs in the library's kernels.
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+
+Tensor conventions (torch has no full unsigned support, so unsigned data is
+carried in signed tensors of the same width, bit for bit):
+  keys      int64 [n]       (uint64 keys)
+  edges     int32 [n, r]    (uint32 vertex ids)
+  order     int32 [n]       (uint32 edge ids)
+  claim     int32 [n]       (uint32 claim words, -1 = HPEEL_UNCLAIMED)
+  layer_off int64 [R + 1]
+  G         int64 [ceil(m/32)], rank_dir int64 [ceil(m/512) + 1]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhpeel.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hpeel.h")
+
+UNCLAIMED = 0xFFFFFFFF
+MAX_ROUNDS = 1 << 20
+
+STATUS = {
+    0: "HPEEL_OK", 1: "HPEEL_ERR_INVALID_ARG", 2: "HPEEL_ERR_CUDA",
+    3: "HPEEL_ERR_WORKSPACE_TOO_SMALL", 4: "HPEEL_ERR_TIMEOUT", 5: "HPEEL_ERR_DEVICE_CHECK",
+    6: "HPEEL_ERR_CORE_NONEMPTY", 7: "HPEEL_ERR_RETRIES_EXHAUSTED", 8: "HPEEL_ERR_CAPACITY",
+}
+
+
+class HpeelError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_peeled", ctypes.c_uint64), ("rounds", ctypes.c_uint32),
+                ("core_nonempty", ctypes.c_uint32), ("seed_used", ctypes.c_uint64),
+                ("attempts", ctypes.c_uint32), ("device_err", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1312_0526_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        u64, u32, p, sz = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t
+        st = ctypes.c_int
+        L.hpeel_status_str.restype = ctypes.c_char_p
+        L.hpeel_status_str.argtypes = [st]
+        L.hpeel_last_error.restype = ctypes.c_char_p
+        L.hpeel_last_error.argtypes = []
+        L.hpeel_version.restype = ctypes.c_int
+        L.hpeel_num_vertices.restype = u64
+        L.hpeel_num_vertices.argtypes = [u64, u32, u32]
+        L.hpeel_hash_edges.restype = st
+        L.hpeel_hash_edges.argtypes = [p, u64, u64, u32, u64, p, p]
+        L.hpeel_peel_workspace_size.restype = sz
+        L.hpeel_peel_workspace_size.argtypes = [u64, u64, u32]
+        L.hpeel_peel.restype = st
+        L.hpeel_peel.argtypes = [p, u64, u64, u32, p, p, p, u32, ctypes.POINTER(Stats), p, sz, p]
+        L.hpeel_mphf_workspace_size.restype = sz
+        L.hpeel_mphf_workspace_size.argtypes = [u64, u32]
+        L.hpeel_mphf_build.restype = st
+        L.hpeel_mphf_build.argtypes = [p, u64, u64, u32, u32, p, p, ctypes.POINTER(Stats), p, sz, p]
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise HpeelError(rc, lib().hpeel_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_ptr(t, name, dtype=None, ndim=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimensions")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _workspace(nbytes: int, device):
+    torch = _torch()
+    # 256-byte alignment: the caching allocator hands out 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def num_vertices(n: int, gamma_milli: int = 1230, r: int = 3) -> int:
+    """m = r * ceil(ceil(gamma n) / r) (sec. 3, sec. 4.3)."""
+    return int(lib().hpeel_num_vertices(n, gamma_milli, r))
+
+
+def hash_edges(keys, m: int, r: int = 3, seed: int = 1, out=None):
+    """Edges int32[n, r] of the keys (sec. 3 hashing, sec. 4.3 r parts)."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    n = keys.shape[0]
+    if out is None:
+        out = torch.empty((n, r), dtype=torch.int32, device=keys.device)
+    ep = _dev_ptr(out, "out", torch.int32)
+    if out.numel() != n * r:
+        raise ValueError("out must hold n * r entries")
+    _check(lib().hpeel_hash_edges(kp, n, m, r, seed, ep, _stream()))
+    return out
+
+
+@dataclass
+class PeelResult:
+    order: object      # int32 [n]
+    claim: object      # int32 [n]
+    layer_off: object  # int64 [rounds + 1]
+    rounds: int
+    n_peeled: int
+
+    @property
+    def core_nonempty(self) -> bool:
+        return self.n_peeled < self.order.shape[0]
+
+
+def peel_workspace_size(n: int, m: int, r: int = 3) -> int:
+    return int(lib().hpeel_peel_workspace_size(n, m, r))
+
+
+def peel(edges, m: int, workspace=None, max_layers: int = 4096) -> PeelResult:
+    """Round-synchronous peel with canonical order (sec. 4.2); see hpeel_peel."""
+    torch = _torch()
+    ep = _dev_ptr(edges, "edges", torch.int32, 2)
+    n, r = edges.shape
+    dev = edges.device
+    order = torch.empty(n, dtype=torch.int32, device=dev)
+    claim = torch.empty(n, dtype=torch.int32, device=dev)
+    loff = torch.empty(max_layers + 1, dtype=torch.int64, device=dev)
+    need = peel_workspace_size(n, m, r)
+    ws = workspace if workspace is not None else _workspace(need, dev)
+    wp = _dev_ptr(ws, "workspace", torch.uint8)
+    st = Stats()
+    _check(lib().hpeel_peel(ep, n, m, r, _dev_ptr(order, "order"), _dev_ptr(claim, "claim"),
+                            _dev_ptr(loff, "layer_off"), max_layers, ctypes.byref(st), wp,
+                            ws.numel(), _stream()))
+    R = int(st.rounds)
+    return PeelResult(order, claim, loff[:R + 1], R, int(st.n_peeled))
+
+
+@dataclass
+class MphfResult:
+    G: object
+    rank_dir: object
+    m: int
+    stats: dict
+
+
+def mphf_workspace_size(n: int, gamma_milli: int = 1230) -> int:
+    return int(lib().hpeel_mphf_workspace_size(n, gamma_milli))
+
+
+def mphf_build(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
+               workspace=None, G=None, rank_dir=None) -> MphfResult:
+    """MWHC MPHF build (sec. 3) with reseed-and-retry; see hpeel_mphf_build."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    n = keys.shape[0]
+    dev = keys.device
+    m = num_vertices(n, gamma_milli, 3)
+    if G is None:
+        G = torch.empty(max((m + 31) // 32, 1), dtype=torch.int64, device=dev)
+    if rank_dir is None:
+        rank_dir = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device=dev)
+    ws = workspace if workspace is not None else _workspace(mphf_workspace_size(n, gamma_milli), dev)
+    st = Stats()
+    _check(lib().hpeel_mphf_build(kp, n, seed, gamma_milli, max_tries,
+                                  _dev_ptr(G, "G", torch.int64), _dev_ptr(rank_dir, "rank_dir",
+                                                                          torch.int64),
+                                  ctypes.byref(st), _dev_ptr(ws, "workspace", torch.uint8),
+                                  ws.numel(), _stream()))
+    return MphfResult(G[:(m + 31) // 32], rank_dir, m, st.as_dict())

@@ -1,0 +1,386 @@
+// api.cu -- the C ABI (include/hpeel.h): argument checks, workspace layout,
+// the round loop and the MPHF retry loop.  Every step of the path runs in the
+// kernels of hash.cu, peel.cu, emit.cu and mphf.cu; this file only orders
+// them and reads back the few scalars the host has to decide on.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "kernels.cuh"
+
+using namespace hp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hpeel_status fail(hpeel_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+hpeel_status fail(hpeel_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define HP_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(HPEEL_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                     \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+#define HP_TRY(expr)                                                                        \
+    do {                                                                                    \
+        hpeel_status s_ = (expr);                                                           \
+        if (s_ != HPEEL_OK) return s_;                                                      \
+    } while (0)
+
+hpeel_status check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(HPEEL_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return HPEEL_OK;
+}
+
+hpeel_status make_launch(void *stream, Launch *L) {
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static int sms_cache[64] = {0};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 64 && sms_cache[dev] == 0) {
+            int sms = 0;
+            cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess)
+                return fail(HPEEL_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+            sms_cache[dev] = sms;
+        }
+        L->sms = dev < 64 ? sms_cache[dev] : 148;
+    }
+    L->stream = (cudaStream_t)stream;
+    return HPEEL_OK;
+}
+
+// Small pinned host buffer for the per-round control-block read-back.
+Ctl *pinned_ctl() {
+    thread_local Ctl *p = nullptr;
+    if (!p) {
+        if (cudaMallocHost((void **)&p, sizeof(Ctl)) != cudaSuccess) p = nullptr;
+    }
+    return p;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct PeelLayout {
+    size_t ctl, state, claim, L, F, loff, foff, hist, scantmp, total;
+    uint32_t max_rounds;
+};
+
+PeelLayout peel_layout(uint64_t n, uint64_t m) {
+    PeelLayout p{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    p.max_rounds = (uint32_t)std::min<uint64_t>(HPEEL_MAX_ROUNDS, n + 1);
+    p.ctl = take(sizeof(Ctl));
+    p.state = take(8 * m);
+    p.claim = take(4 * n);
+    p.L = take(4 * n);
+    p.F = take(4 * m);
+    p.loff = take(4 * ((size_t)p.max_rounds + 2));
+    p.foff = take(4 * ((size_t)p.max_rounds + 2));
+    const uint64_t tiles = (n + kEmitTile - 1) / kEmitTile;
+    p.hist = take(4 * kEmitBins * tiles);
+    p.scantmp = take(4 * scan_tmp_words(kEmitBins * tiles));
+    p.total = off;
+    return p;
+}
+
+struct MphfLayout {
+    size_t edges, order, claim, rank_cnt, rank_scan, rank_tmp, peel, total;
+    uint64_t m;
+};
+
+MphfLayout mphf_layout(uint64_t n, uint32_t gamma_milli) {
+    MphfLayout p{};
+    p.m = hpeel_num_vertices(n, gamma_milli, 3);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const uint64_t blocks = (p.m + 511) / 512;
+    p.edges = take(12 * n);
+    p.order = take(4 * n);
+    p.claim = take(4 * n);
+    p.rank_cnt = take(4 * blocks + 4);
+    p.rank_scan = take(4 * blocks + 4);
+    p.rank_tmp = take(4 * scan_tmp_words(blocks));
+    p.peel = off;
+    p.total = off + peel_layout(n, p.m).total;
+    return p;
+}
+
+struct PeelOut {
+    uint32_t rounds;
+    uint64_t n_peeled;
+    uint32_t *loff;  // device layer table (uint32[rounds + 1])
+};
+
+// Round-synchronous peel of device edges into order/claim (sec. 4.2).
+hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t m, uint32_t r,
+                       uint32_t *order, uint32_t *claim_user, char *ws, PeelOut *out) {
+    const PeelLayout lay = peel_layout(n, m);
+    Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
+    uint32_t *state = reinterpret_cast<uint32_t *>(ws + lay.state);
+    uint32_t *claim = claim_user ? claim_user : reinterpret_cast<uint32_t *>(ws + lay.claim);
+    uint32_t *Ll = reinterpret_cast<uint32_t *>(ws + lay.L);
+    uint32_t *F = reinterpret_cast<uint32_t *>(ws + lay.F);
+    uint32_t *loff = reinterpret_cast<uint32_t *>(ws + lay.loff);
+    uint32_t *foff = reinterpret_cast<uint32_t *>(ws + lay.foff);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + lay.hist);
+    uint32_t *scantmp = reinterpret_cast<uint32_t *>(ws + lay.scantmp);
+    const uint32_t P = m / r;
+    Ctl *hctl = pinned_ctl();
+    if (!hctl) return fail(HPEEL_ERR_CUDA, "cudaMallocHost of the control read-back failed");
+
+    HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), L.stream));
+    HP_CUDA(cudaMemsetAsync(loff, 0, 2 * sizeof(uint32_t), L.stream));
+    HP_CUDA(cudaMemsetAsync(foff, 0, 2 * sizeof(uint32_t), L.stream));
+    launch_fill_u32(L, state, 2ull * m, 0u);
+    launch_build_incidence(L, edges, n, r, P, state, claim, ctl);
+    launch_round0(L, state, m, r, P, n, claim, Ll, ctl);
+    HP_TRY(check_launch("build/round0"));
+
+    uint32_t t = 0;
+    for (;;) {
+        if (t + 1 >= lay.max_rounds)
+            return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds - 1);
+        launch_update(L, edges, r, m, claim, state, Ll, F, loff, foff, ctl);
+        HP_TRY(check_launch("update"));
+        HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        if (hctl->err)
+            return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u (round %u)",
+                        hctl->err, t);
+        if (!hctl->more) break;
+        launch_claim(L, state, r, P, n, claim, F, Ll, foff, ctl);
+        HP_TRY(check_launch("claim"));
+        t++;
+    }
+    const uint32_t R = hctl->last_layer ? t + 1 : t;
+    const uint64_t peeled = hctl->lcur;
+    out->rounds = R;
+    out->n_peeled = peeled;
+    out->loff = loff;
+
+    // Canonical order: stable sort by key = round, core edges key R.
+    const uint32_t nkeys = R + 1;
+    uint32_t base = 0, seg = 0;
+    const uint32_t *src = nullptr;
+    uint32_t *loff_h = nullptr;
+    std::string loff_store;
+    for (;;) {
+        const uint32_t count = n - seg;
+        const uint32_t nb = std::min<uint32_t>(nkeys - base, kEmitBins);
+        const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
+        launch_emit_hist(L, src, count, claim, base, R, nb, hist);
+        launch_scan_u32(L, hist, hist, (uint64_t)nb * tiles, scantmp);
+        launch_emit_scatter(L, src, count, claim, base, R, nb, hist, order + seg);
+        HP_TRY(check_launch("emit"));
+        if (nkeys - base <= kEmitBins) break;
+        // keys >= base + nb - 1 landed in the last bin: sort that tail again
+        if (!loff_h) {
+            loff_store.resize(4 * ((size_t)R + 1));
+            loff_h = reinterpret_cast<uint32_t *>(&loff_store[0]);
+            HP_CUDA(cudaMemcpyAsync(loff_h, loff, 4 * ((size_t)R + 1), cudaMemcpyDeviceToHost,
+                                    L.stream));
+            HP_CUDA(cudaStreamSynchronize(L.stream));
+        }
+        base += nb - 1;
+        seg = loff_h[base];
+        HP_CUDA(cudaMemcpyAsync(Ll + seg, order + seg, 4 * (size_t)(n - seg),
+                                cudaMemcpyDeviceToDevice, L.stream));
+        src = Ll + seg;
+    }
+    return HPEEL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hpeel_status_str(hpeel_status s) {
+    switch (s) {
+    case HPEEL_OK: return "ok";
+    case HPEEL_ERR_INVALID_ARG: return "invalid argument";
+    case HPEEL_ERR_CUDA: return "CUDA error";
+    case HPEEL_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case HPEEL_ERR_TIMEOUT: return "device wait timed out";
+    case HPEEL_ERR_DEVICE_CHECK: return "device-side input check failed";
+    case HPEEL_ERR_CORE_NONEMPTY: return "hypergraph has a non-empty 2-core";
+    case HPEEL_ERR_RETRIES_EXHAUSTED: return "no hash seed gave a peelable hypergraph";
+    case HPEEL_ERR_CAPACITY: return "capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char *hpeel_last_error(void) { return g_last_error.c_str(); }
+
+int hpeel_version(void) { return 100; }
+
+uint64_t hpeel_num_vertices(uint64_t n, uint32_t gamma_milli, uint32_t r) {
+    if (r == 0) return 0;
+    const uint64_t gn = (n * gamma_milli + 999u) / 1000u;  // ceil(gamma n)
+    return (gn + r - 1) / r * r;
+}
+
+hpeel_status hpeel_hash_edges(const uint64_t *d_keys, uint64_t n, uint64_t m, uint32_t r,
+                              uint64_t seed, uint32_t *d_edges, void *stream) {
+    g_last_error.clear();
+    if (r < 2 || r > 4) return fail(HPEEL_ERR_INVALID_ARG, "r = %u, need 2 <= r <= 4", r);
+    if (n == 0) return HPEEL_OK;
+    if (m == 0 || m % r != 0 || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of r below 2^32",
+                    (unsigned long long)m);
+    if (!d_keys || !d_edges) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    launch_hash_edges(L, d_keys, n, r, make_fastmod(m / r), seed, d_edges);
+    return check_launch("hash_edges");
+}
+
+size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r) {
+    (void)r;
+    return peel_layout(n, m).total;
+}
+
+hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
+                        uint32_t *d_order, uint32_t *d_claim, uint64_t *d_layer_off,
+                        uint32_t max_layers, hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
+                        void *stream) {
+    g_last_error.clear();
+    if (h_stats) memset(h_stats, 0, sizeof *h_stats);
+    if (r < 2 || r > 4) return fail(HPEEL_ERR_INVALID_ARG, "r = %u, need 2 <= r <= 4", r);
+    if (n >= (1ull << 32) || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    if (n == 0) {
+        if (d_layer_off) HP_CUDA(cudaMemsetAsync(d_layer_off, 0, sizeof(uint64_t), L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        return HPEEL_OK;
+    }
+    if (m == 0 || m % r != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of r",
+                    (unsigned long long)m);
+    if (!d_edges || !d_order || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_ws & 255u) != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < peel_layout(n, m).total)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
+                    peel_layout(n, m).total);
+    PeelOut po{};
+    HP_TRY(peel_core(L, d_edges, (uint32_t)n, (uint32_t)m, r, d_order, d_claim, (char *)d_ws, &po));
+    if (d_layer_off) {
+        if (po.rounds > max_layers)
+            return fail(HPEEL_ERR_CAPACITY, "%u rounds > max_layers %u", po.rounds, max_layers);
+        launch_layer_off(L, po.loff, po.rounds, d_layer_off);
+        HP_TRY(check_launch("layer_off"));
+    }
+    HP_CUDA(cudaStreamSynchronize(L.stream));
+    if (h_stats) {
+        h_stats->n_peeled = po.n_peeled;
+        h_stats->rounds = po.rounds;
+        h_stats->core_nonempty = po.n_peeled < n;
+    }
+    return HPEEL_OK;
+}
+
+size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli) {
+    return mphf_layout(n, gamma_milli).total;
+}
+
+hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
+                              uint32_t gamma_milli, uint32_t max_tries, uint64_t *d_G,
+                              uint64_t *d_rank_dir, hpeel_stats *h_stats, void *d_ws,
+                              size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (h_stats) memset(h_stats, 0, sizeof *h_stats);
+    if (gamma_milli == 0) return fail(HPEEL_ERR_INVALID_ARG, "gamma_milli must be positive");
+    const MphfLayout lay = mphf_layout(n, gamma_milli);
+    const uint64_t m = lay.m;
+    if (n >= (1ull << 32) || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    if (max_tries == 0) return fail(HPEEL_ERR_INVALID_ARG, "max_tries must be positive");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    const uint64_t blocks = (m + 511) / 512;
+    if (n == 0) {
+        if (d_rank_dir) HP_CUDA(cudaMemsetAsync(d_rank_dir, 0, sizeof(uint64_t), L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        if (h_stats) h_stats->seed_used = seed;
+        return HPEEL_OK;
+    }
+    if (!d_keys || !d_G || !d_rank_dir || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_ws & 255u) != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < lay.total)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
+                    lay.total);
+    char *ws = (char *)d_ws;
+    uint32_t *edges = reinterpret_cast<uint32_t *>(ws + lay.edges);
+    uint32_t *order = reinterpret_cast<uint32_t *>(ws + lay.order);
+    uint32_t *claim = reinterpret_cast<uint32_t *>(ws + lay.claim);
+    const FastMod fm = make_fastmod(m / 3);
+    for (uint32_t a = 0; a < max_tries; a++) {
+        const uint64_t s = seed + a;
+        launch_hash_edges(L, d_keys, n, 3, fm, s, edges);
+        HP_TRY(check_launch("hash_edges"));
+        PeelOut po{};
+        HP_TRY(peel_core(L, edges, (uint32_t)n, (uint32_t)m, 3, order, claim, ws + lay.peel, &po));
+        if (h_stats) {
+            h_stats->attempts = a + 1;
+            h_stats->rounds = po.rounds;
+            h_stats->n_peeled = po.n_peeled;
+            h_stats->core_nonempty = po.n_peeled < n;
+        }
+        if (po.n_peeled < n) continue;
+        // a8: reverse layer order
+        const uint64_t words = (m + 31) / 32;
+        HP_CUDA(cudaMemsetAsync(d_G, 0, 8 * words, L.stream));
+        for (int64_t t = (int64_t)po.rounds - 1; t >= 0; t--)
+            launch_assign_layer(L, edges, claim, order, po.loff, (uint32_t)t, d_G);
+        HP_TRY(check_launch("assign"));
+        // a9: rank directory
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(ws + lay.rank_cnt);
+        uint32_t *scn = reinterpret_cast<uint32_t *>(ws + lay.rank_scan);
+        uint32_t *tmp = reinterpret_cast<uint32_t *>(ws + lay.rank_tmp);
+        launch_rank_counts(L, d_G, m, cnt);
+        launch_scan_u32(L, cnt, scn, blocks, tmp);
+        launch_widen_dir(L, scn, cnt, blocks, d_rank_dir);
+        HP_TRY(check_launch("rank"));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        if (h_stats) h_stats->seed_used = s;
+        return HPEEL_OK;
+    }
+    return fail(HPEEL_ERR_RETRIES_EXHAUSTED, "2-core non-empty for seeds %llu..%llu",
+                (unsigned long long)seed, (unsigned long long)(seed + max_tries - 1));
+}
+
+}  // extern "C"

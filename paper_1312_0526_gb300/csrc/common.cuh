@@ -1,0 +1,89 @@
+// common.cuh -- device helpers shared by the hpeel kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hpeel.h"
+
+namespace hp {
+
+constexpr uint32_t kUnclaimed = 0xFFFFFFFFu;
+
+// Device error word codes (hpeel_stats.device_err).
+enum : uint32_t {
+    kDevOk = 0,
+    kDevBadVertex = 1,   // a vertex id outside its part (input violates sec. 4.3)
+    kDevBadEdge = 2,     // an edge id >= n read off a record (inconsistent state)
+    kDevCapacity = 3,    // a round-table bound was exceeded
+    kDevTimeout = 4,     // a bounded wait gave up
+};
+
+// Device-side control block of one peel (lives in the workspace).
+struct Ctl {
+    uint32_t lcur;       // append cursor of the layer list L (L_0 | L_1 | ...)
+    uint32_t fcur;       // append cursor of the frontier list F (F_1 | F_2 | ...)
+    uint32_t round;      // index t of the round being run
+    uint32_t done;       // blocks finished in the current update launch
+    uint32_t err;        // first device error code (0 = none)
+    uint32_t more;       // 1 while the next frontier is non-empty
+    uint32_t last_layer; // size of the layer the last update launch deleted
+    uint32_t pad;
+};
+
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): two
+// xorshift-multiply steps and a final xorshift, modulo 2^64.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Remainder by a runtime divisor P < 2^32 with a precomputed reciprocal
+// (Barrett reduction, P. Barrett, CRYPTO 1986).  With M = floor((2^64-1)/P)
+// the estimate q = floor(x M / 2^64) satisfies Q - 2 <= q <= Q for the true
+// quotient Q = floor(x / P), so x - q P lies in [0, 3P) and at most two
+// corrective subtractions give x mod P exactly.
+struct FastMod {
+    uint64_t P;
+    uint64_t M;
+};
+
+inline FastMod make_fastmod(uint64_t P) { return FastMod{P, P ? (~0ull) / P : 0}; }
+
+__device__ __forceinline__ uint64_t fastmod(uint64_t x, const FastMod f) {
+    uint64_t q = __umul64hi(x, f.M);
+    uint64_t r = x - q * f.P;
+    if (r >= f.P) r -= f.P;
+    if (r >= f.P) r -= f.P;
+    return r;
+}
+
+// Position (part index) of vertex v in an r-partite graph with part size P:
+// the number of part boundaries at or below v.
+template <int R>
+__device__ __forceinline__ uint32_t part_of(uint32_t v, uint32_t P) {
+    uint32_t j = 0;
+#pragma unroll
+    for (int k = 1; k < R; k++) j += (v >= (uint32_t)k * P) ? 1u : 0u;
+    return j;
+}
+
+__device__ __forceinline__ void raise_err(Ctl *ctl, uint32_t code) {
+    atomicCAS(&ctl->err, 0u, code);
+}
+
+// Warp-aggregated append: every lane of the warp calls this (convergent);
+// lanes with pred get consecutive slots of list, one atomicAdd per warp.
+__device__ __forceinline__ void warp_append(uint32_t *cursor, uint32_t *list, bool pred,
+                                            uint32_t value) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, pred);
+    if (ballot == 0) return;
+    uint32_t base = 0;
+    const uint32_t leader = __ffs(ballot) - 1;
+    if (lane == leader) base = atomicAdd(cursor, (uint32_t)__popc(ballot));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = value;
+}
+
+}  // namespace hp

@@ -1,0 +1,211 @@
+// emit.cu -- canonical peeling order: a stable counting sort of edge ids by
+// the round in their claim word, layers in round order and ascending id
+// inside a layer (sec. 4.2 leaves the intra-layer order free; ascending id
+// makes it unique), then the 2-core edges ascending.
+//
+// One pass sorts by up to kEmitBins keys: key k of an edge (round, or
+// core_key for an unclaimed edge) goes to bin min(k - base, nbins - 1).  The
+// host runs further passes on the last bin when there are more rounds.
+//   hist    -- per tile of kEmitTile consecutive inputs, bin counts, stored
+//              bin-major: hist[b * tiles + tile];
+//   scan    -- one exclusive prefix sum over hist gives, for every (bin,
+//              tile), where that tile's edges of that bin start;
+//   scatter -- each warp ranks its 512 inputs in input order (match_any
+//              peers + per-warp running counts), so equal keys keep the
+//              input order: the sort is stable.
+#include "kernels.cuh"
+
+namespace hp {
+
+__device__ __forceinline__ uint32_t emit_bin(uint32_t c, uint32_t base, uint32_t core_key,
+                                             uint32_t nbins) {
+    const uint32_t k = (c == kUnclaimed) ? core_key : (c >> 2);
+    const uint32_t d = k - base;  // k >= base for every input of the pass
+    return d < nbins - 1 ? d : nbins - 1;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_emit_hist(const uint32_t *__restrict__ src, uint32_t count, const uint32_t *__restrict__ claim,
+            uint32_t base, uint32_t core_key, uint32_t nbins, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[kEmitBins];
+    const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
+    for (uint32_t b = threadIdx.x; b < nbins; b += kThreads) h[b] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * kEmitTile;
+#pragma unroll 4
+    for (uint32_t q = 0; q < kEmitItems; q++) {
+        const uint64_t i = t0 + (uint64_t)q * kThreads + threadIdx.x;
+        if (i < count) {
+            const uint32_t e = src ? src[i] : (uint32_t)i;
+            atomicAdd(&h[emit_bin(claim[e], base, core_key, nbins)], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nbins; b += kThreads)
+        hist[(uint64_t)b * tiles + blockIdx.x] = h[b];
+}
+
+void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, const uint32_t *claim,
+                      uint32_t base, uint32_t core_key, uint32_t nbins, uint32_t *hist) {
+    if (count == 0) return;
+    const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
+    k_emit_hist<<<tiles, kThreads, 0, L.stream>>>(src, count, claim, base, core_key, nbins, hist);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
+               const uint32_t *__restrict__ claim, uint32_t base, uint32_t core_key,
+               uint32_t nbins, const uint32_t *__restrict__ offs, uint32_t *__restrict__ out) {
+    __shared__ uint32_t wc[kEmitWarps][kEmitBins];
+    const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t b = lane; b < kEmitBins; b += 32) wc[warp][b] = 0;
+    __syncwarp();
+    // this warp's contiguous run of the tile, kEmitItems groups of 32
+    const uint64_t w0 = (uint64_t)blockIdx.x * kEmitTile + (uint64_t)warp * 32 * kEmitItems;
+    uint32_t bin[kEmitItems], eid[kEmitItems];
+#pragma unroll
+    for (int g = 0; g < kEmitItems; g++) {
+        const uint64_t i = w0 + (uint64_t)g * 32 + lane;
+        const bool valid = i < count;
+        eid[g] = valid ? (src ? src[i] : (uint32_t)i) : 0u;
+        bin[g] = valid ? emit_bin(claim[eid[g]], base, core_key, nbins) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin[g]);
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) wc[warp][bin[g]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per bin: warps' starts = tile start of the bin + counts of earlier warps
+    for (uint32_t b = threadIdx.x; b < nbins; b += kThreads) {
+        uint32_t run = offs[(uint64_t)b * tiles + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kEmitWarps; w++) {
+            const uint32_t c = wc[w][b];
+            wc[w][b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < kEmitItems; g++) {
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin[g]);
+        if (bin[g] != 0xFFFFFFFFu) {
+            out[wc[warp][bin[g]] + __popc(peers & lt)] = eid[g];
+        }
+        __syncwarp();
+        if (bin[g] != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
+            wc[warp][bin[g]] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+void launch_emit_scatter(const Launch &L, const uint32_t *src, uint32_t count,
+                         const uint32_t *claim, uint32_t base, uint32_t core_key, uint32_t nbins,
+                         const uint32_t *offs, uint32_t *out) {
+    if (count == 0) return;
+    const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
+    k_emit_scatter<<<tiles, kThreads, 0, L.stream>>>(src, count, claim, base, core_key, nbins,
+                                                     offs, out);
+}
+
+__global__ void k_layer_off(const uint32_t *__restrict__ loff, uint32_t rounds,
+                            uint64_t *__restrict__ out) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t <= rounds;
+         t += gridDim.x * blockDim.x)
+        out[t] = loff[t];
+}
+
+void launch_layer_off(const Launch &L, const uint32_t *loff, uint32_t rounds, uint64_t *out) {
+    k_layer_off<<<grid_for(L, (uint64_t)rounds + 1, 1, 4), kThreads, 0, L.stream>>>(loff, rounds,
+                                                                                   out);
+}
+
+// ------------------------------------------------------------------ scan --
+// Exclusive prefix sum, reduce-then-scan: level sums of 4096-element blocks
+// are scanned recursively, then each block rescans its elements.
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr uint64_t kScanBlock = (uint64_t)kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t ws[kScanThreads / 32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t s = ws[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, d);
+            if (lane >= (uint32_t)d) s += y;
+        }
+        ws[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = (warp ? ws[warp - 1] : 0u) + x - v;
+    if (total) *total = ws[kScanThreads / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce(const uint32_t *__restrict__ in, uint64_t count, uint32_t *__restrict__ sums) {
+    const uint64_t b0 = (uint64_t)blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++)
+        if (b0 + k < count) s += in[b0 + k];
+    uint32_t total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_down(const uint32_t *in, uint32_t *out, uint64_t count, const uint32_t *__restrict__ offs) {
+    const uint64_t b0 = (uint64_t)blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        v[k] = (b0 + k < count) ? in[b0 + k] : 0u;
+        s += v[k];
+    }
+    uint32_t run = block_excl_scan(s, nullptr) + (offs ? offs[blockIdx.x] : 0u);
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        if (b0 + k < count) out[b0 + k] = run;
+        run += v[k];
+    }
+}
+
+size_t scan_tmp_words(uint64_t count) {
+    size_t words = 0;
+    while (count > kScanBlock) {
+        count = (count + kScanBlock - 1) / kScanBlock;
+        words += count;
+    }
+    return words + 1;
+}
+
+void launch_scan_u32(const Launch &L, const uint32_t *in, uint32_t *out, uint64_t count,
+                     uint32_t *tmp) {
+    if (count == 0) return;
+    if (count <= kScanBlock) {
+        k_scan_down<<<1, kScanThreads, 0, L.stream>>>(in, out, count, nullptr);
+        return;
+    }
+    const uint64_t blocks = (count + kScanBlock - 1) / kScanBlock;
+    uint32_t *sums = tmp;
+    k_scan_reduce<<<(unsigned)blocks, kScanThreads, 0, L.stream>>>(in, count, sums);
+    launch_scan_u32(L, sums, sums, blocks, tmp + blocks);
+    k_scan_down<<<(unsigned)blocks, kScanThreads, 0, L.stream>>>(in, out, count, sums);
+}
+
+}  // namespace hp

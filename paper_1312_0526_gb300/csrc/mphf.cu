@@ -1,0 +1,97 @@
+// mphf.cu -- MWHC assignment and rank directory (r = 3).
+//
+// sec. 3: find u with u[h_0(x)] + u[h_1(x)] + u[h_2(x)] = f(x) (mod 3), where
+// f(x) = i for the hinge h_i(x) of x's edge; then h_{f(x)} is a perfect hash
+// and a rank over the non-zero u makes it minimal.  sec. 4.3 ("Avoiding
+// backward scans"): layers are solved from the last to the first, and the
+// order inside a layer is free.  Inside one layer no edge reads a 2-bit
+// value another edge of the layer writes (a hinge has degree 1 in its round,
+// so it belongs to no other edge alive then), so one launch per layer solves
+// the whole layer in parallel; edges that share a 64-bit word of G combine
+// their bits with atomicOr.
+// sec. 5: the rank counts non-zero 2-bit pairs of a word with a broadword
+// expression instead of a bit loop.
+#include "kernels.cuh"
+
+namespace hp {
+
+__device__ __forceinline__ uint32_t g_get(const uint64_t *G, uint32_t v) {
+    return (uint32_t)(__ldcg(G + (v >> 5)) >> (2u * (v & 31u))) & 3u;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_assign(const uint32_t *__restrict__ edges, const uint32_t *__restrict__ claim,
+         const uint32_t *__restrict__ order, const uint32_t *__restrict__ loff, uint32_t t,
+         uint64_t *G) {
+    const uint32_t lb = loff[t], le = loff[t + 1];
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t i = lb + (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < le; i += stride) {
+        const uint32_t e = order[i];
+        const uint32_t h = claim[e] & 3u;
+        const uint32_t *row = edges + (uint64_t)e * 3;
+        const uint32_t v0 = row[0], v1 = row[1], v2 = row[2];
+        const uint32_t vh = h == 0 ? v0 : (h == 1 ? v1 : v2);
+        const uint32_t s = (h == 0 ? 0u : g_get(G, v0)) + (h == 1 ? 0u : g_get(G, v1)) +
+                           (h == 2 ? 0u : g_get(G, v2));
+        const uint32_t val = (h + 6u - s) % 3u;  // s <= 6
+        const uint64_t code = val ? val : 3u;
+        atomicOr((unsigned long long *)(G + (vh >> 5)),
+                 (unsigned long long)(code << (2u * (vh & 31u))));
+    }
+}
+
+void launch_assign_layer(const Launch &L, const uint32_t *edges, const uint32_t *claim,
+                         const uint32_t *order, const uint32_t *loff, uint32_t t, uint64_t *G) {
+    k_assign<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(edges, claim, order, loff, t, G);
+}
+
+// Non-zero 2-bit values of a word: a pair is non-zero when either bit is set.
+__device__ __forceinline__ uint32_t nonzero_pairs(uint64_t w) {
+    return (uint32_t)__popcll((w | (w >> 1)) & 0x5555555555555555ull);
+}
+
+// One thread per 512 vertices (8 words of G).
+__global__ void k_rank_counts(const uint64_t *__restrict__ G, uint64_t words, uint64_t blocks,
+                              uint32_t *__restrict__ cnt) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < blocks; b += stride) {
+        uint32_t c = 0;
+        const uint64_t w0 = b * 8;
+        if (w0 + 8 <= words && ((((uintptr_t)G) & 15u) == 0)) {
+            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(G + w0);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const ulonglong2 x = p[q];
+                c += nonzero_pairs(x.x) + nonzero_pairs(x.y);
+            }
+        } else {
+            for (uint64_t w = w0; w < words && w < w0 + 8; w++) c += nonzero_pairs(G[w]);
+        }
+        cnt[b] = c;
+    }
+}
+
+void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt) {
+    const uint64_t words = (m + 31) / 32, blocks = (m + 511) / 512;
+    if (blocks == 0) return;
+    k_rank_counts<<<grid_for(L, blocks, 1, 8), kThreads, 0, L.stream>>>(G, words, blocks, cnt);
+}
+
+__global__ void k_widen_dir(const uint32_t *__restrict__ scanned, const uint32_t *__restrict__ cnt,
+                            uint64_t blocks, uint64_t *__restrict__ dir) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= blocks; b += stride) {
+        if (b < blocks)
+            dir[b] = scanned[b];
+        else
+            dir[b] = blocks ? (uint64_t)scanned[blocks - 1] + cnt[blocks - 1] : 0ull;
+    }
+}
+
+void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,
+                      uint64_t blocks, uint64_t *dir) {
+    k_widen_dir<<<grid_for(L, blocks + 1, 1, 8), kThreads, 0, L.stream>>>(scanned, cnt, blocks,
+                                                                          dir);
+}
+
+}  // namespace hp

@@ -1,0 +1,80 @@
+"""The C ABI library builds, loads without a GPU and exports every symbol the
+headers in include/ declare.  No compute call is made here."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1312_0526_gb300 as hp
+from paper_1312_0526_gb300 import build as hpbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(hpeel_\w+)\s*\(", src):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    hpbuild.build()
+    return hp.lib()
+
+
+def test_headers_declare_the_boundary():
+    names = _declared_functions()
+    for want in ("hpeel_hash_edges", "hpeel_peel", "hpeel_mphf_build",
+                 "hpeel_peel_workspace_size", "hpeel_mphf_workspace_size",
+                 "hpeel_num_vertices", "hpeel_status_str", "hpeel_last_error"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    raw = ctypes.CDLL(hp.LIB_PATH)
+    missing = [n for n in _declared_functions() if not hasattr(raw, n)]
+    assert missing == []
+
+
+def test_host_only_calls(lib):
+    assert lib.hpeel_version() >= 100
+    assert lib.hpeel_status_str(0) == b"ok"
+    assert b"2-core" in lib.hpeel_status_str(6)
+    # vertex counts of the workloads (hand-computed, see the oracle pins)
+    assert hp.num_vertices(100_000, 1230, 3) == 123_000
+    assert hp.num_vertices(10**9, 1222, 3) == 1_222_000_002
+    assert hp.num_vertices(10**8, 1300, 4) == 130_000_000
+    assert hp.num_vertices(0, 1230, 3) == 0
+
+
+def test_workspace_sizes_grow_with_n(lib):
+    a = hp.peel_workspace_size(1000, 1230, 3)
+    b = hp.peel_workspace_size(100_000, 123_000, 3)
+    assert 0 < a < b
+    # 8 B record + 4 B frontier per vertex, 4 B claim + 4 B layer per edge
+    assert b >= 12 * 123_000 + 8 * 100_000
+    assert hp.mphf_workspace_size(100_000) > b
+
+
+def test_binding_rejects_host_tensors(lib):
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        hp.hash_edges(torch.zeros(4, dtype=torch.int64), 6, 3, 1)
+    with pytest.raises(ValueError):
+        hp.peel(torch.zeros((4, 3), dtype=torch.int32), 6)
+
+
+def test_oracle_is_not_imported_by_the_product():
+    # the product package never imports the oracle
+    for f in glob.glob(os.path.join(ROOT, "paper_1312_0526_gb300", "**", "*.py"), recursive=True):
+        src = open(f).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+    for f in glob.glob(os.path.join(ROOT, "paper_1312_0526_gb300", "csrc", "*")):
+        assert "hpeel_oracle" not in open(f).read(), f

@@ -1,0 +1,205 @@
+"""GPU path vs CPU oracle, element by element (bit-exact: all integer work).
+
+Every call goes through the C ABI (via the ctypes binding).  Inputs come from
+the seeded generators in paper_1312_0526_gb300.inputs; expected values come
+only from the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1312_0526_gb300 import inputs
+from tests import golden_io
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1312_0526_gb300 as hp  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1312_0526_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _dev(a: np.ndarray):
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    elif a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+# ------------------------------------------------------------------- hash --
+
+@pytest.mark.parametrize("n", [1, 2, 3, 255, 256, 257, 4095, 4097, 100_000, 1_000_003])
+@pytest.mark.parametrize("r", [3, 4])
+def test_hash_edges_parity(n, r):
+    keys = inputs.keys(n, 1)
+    m = oracle.num_vertices(n, 1230, r)
+    want = oracle.hash_edges(keys, m, r, 1)
+    got = _u32(hp.hash_edges(_dev(keys), m, r, 1)).reshape(n, r)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 1000, 41_000, 2**31 - 1, 1_431_655_765])
+def test_hash_edges_fastmod_extreme_divisors(P):
+    # keys that push mix64 outputs over the whole 64-bit range, with part
+    # sizes up to the largest m < 2^32 allows
+    keys = np.concatenate([inputs.keys(20_000, 77),
+                           np.array([0, 1, 2**63, 2**64 - 1, 2**64 - 2], dtype=np.uint64)])
+    m = 3 * P
+    want = oracle.hash_edges(keys, m, 3, 12345)
+    got = _u32(hp.hash_edges(_dev(keys), m, 3, 12345)).reshape(-1, 3)
+    assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------------------- peel --
+
+def _check_peel(edges: np.ndarray, m: int, max_layers=4096):
+    want = oracle.peel_rounds(edges, m)
+    got = hp.peel(_dev(edges), m, max_layers=max_layers)
+    assert got.rounds == want.rounds
+    assert got.n_peeled == want.n_peeled
+    assert np.array_equal(_u32(got.order), want.order)
+    assert np.array_equal(_u32(got.claim), want.claim)
+    assert np.array_equal(_u64(got.layer_off), want.layer_off)
+    return want
+
+
+@pytest.mark.parametrize("name", [n for n in golden_io.all_names()
+                                  if golden_io.load(n)["edges"].shape[0] > 0])
+def test_peel_goldens(name):
+    g = golden_io.load(name)
+    got = hp.peel(_dev(g["edges"]), g["m"])
+    assert np.array_equal(_u32(got.order), g["order"])
+    assert np.array_equal(_u32(got.claim), g["claim"])
+    assert np.array_equal(_u64(got.layer_off), g["layer_off"])
+    assert got.n_peeled == g["n_peeled"]
+
+
+@pytest.mark.parametrize("n,gamma,r", [
+    (1, 1230, 3), (2, 1230, 3), (5, 1230, 3), (100, 1230, 3), (4095, 1230, 3),
+    (4097, 1230, 3), (100_000, 1230, 3), (100_000, 1222, 3), (100_000, 1200, 3),
+    (100_000, 1300, 4), (54_321, 1400, 3), (30_001, 1100, 3), (300_000, 1230, 3),
+])
+def test_peel_parity(n, gamma, r):
+    m = oracle.num_vertices(n, gamma, r)
+    edges = oracle.hash_edges(inputs.keys(n, 1), m, r, 1)
+    want = _check_peel(edges, m)
+    if gamma <= 1200 and n > 1000:
+        assert want.core_nonempty
+
+
+def test_peel_random_small_graphs_with_cores():
+    rng = np.random.default_rng(5)
+    for trial in range(40):
+        r = 3 if trial % 2 == 0 else 4
+        P = int(rng.integers(1, 6))
+        n = int(rng.integers(1, 40))
+        edges = np.stack([rng.integers(0, P, n) + j * P for j in range(r)], axis=1).astype(np.uint32)
+        _check_peel(edges, r * P)
+
+
+def _chain(n):
+    """A band-shaped 3-hypergraph where every vertex has degree 2 except near
+    the ends: it peels from the two ends inwards, a few edges per round."""
+    P = n
+    e = np.zeros((n, 3), dtype=np.uint32)
+    for i in range(n):
+        k, q = divmod(i, 4)
+        e[i] = ((i + 1) // 2, P + i // 2, 2 * P + 2 * k + (q % 2))
+    return e, 3 * P
+
+
+@pytest.mark.parametrize("n", [1200, 1203, 2500])
+def test_peel_many_rounds_multi_pass_emit(n):
+    # more rounds than one emit pass has bins (256): the canonical order
+    # needs the multi-pass sort
+    e, m = _chain(n)
+    want = oracle.peel_rounds(e, m)
+    assert want.rounds > 300
+    _check_peel(e, m, max_layers=4096)
+
+
+def test_peel_deterministic_across_runs():
+    n = 200_000
+    m = oracle.num_vertices(n, 1230, 3)
+    edges = _dev(oracle.hash_edges(inputs.keys(n, 3), m, 3, 1))
+    a = hp.peel(edges, m)
+    for _ in range(3):
+        b = hp.peel(edges, m)
+        assert torch.equal(a.order, b.order) and torch.equal(a.claim, b.claim)
+
+
+def test_peel_empty_input():
+    got = hp.peel(torch.empty((0, 3), dtype=torch.int32, device="cuda"), 0)
+    assert got.rounds == 0 and got.n_peeled == 0 and got.order.numel() == 0
+    assert _u64(got.layer_off).tolist() == [0]
+
+
+def test_peel_rejects_vertex_outside_its_part():
+    e = np.array([[0, 3, 6], [1, 1, 7]], dtype=np.uint32)  # vertex 1 at position 1
+    with pytest.raises(hp.HpeelError, match="DEVICE_CHECK"):
+        hp.peel(_dev(e), 9)
+
+
+def test_peel_rejects_small_workspace():
+    e = np.array([[0, 3, 6]], dtype=np.uint32)
+    ws = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hp.HpeelError, match="WORKSPACE"):
+        hp.peel(_dev(e), 9, workspace=ws)
+
+
+def test_peel_layer_capacity_error():
+    e, m = _chain(1200)
+    with pytest.raises(hp.HpeelError, match="CAPACITY"):
+        hp.peel(_dev(e), m, max_layers=8)
+
+
+# ------------------------------------------------------------------- MPHF --
+
+@pytest.mark.parametrize("n", [1, 17, 1000, 4097, 100_000, 250_000])
+def test_mphf_parity(n):
+    keys = inputs.keys(n, 1)
+    want = oracle.mphf_build(keys, seed=1, max_tries=32)
+    got = hp.mphf_build(_dev(keys), seed=1, max_tries=32)
+    assert got.stats["seed_used"] == want.seed_used
+    assert got.stats["rounds"] == want.rounds
+    assert np.array_equal(_u64(got.G), want.G)
+    assert np.array_equal(_u64(got.rank_dir), want.dir)
+
+
+def test_mphf_retries_exhausted_on_duplicate_keys():
+    keys = np.array([5, 5, 6, 7], dtype=np.uint64)
+    with pytest.raises(hp.HpeelError, match="RETRIES_EXHAUSTED"):
+        hp.mphf_build(_dev(keys), seed=1, max_tries=3)
+
+
+def test_mphf_reseed_matches_oracle():
+    # find key sets whose first hash seed leaves a 2-core; both sides retry
+    found = 0
+    for s in range(300):
+        k = inputs.keys(60, 2000 + s)
+        m = oracle.num_vertices(60, 1230, 3)
+        if oracle.peel_rounds(oracle.hash_edges(k, m, 3, 1), m).core_nonempty:
+            want = oracle.mphf_build(k, seed=1, max_tries=64)
+            got = hp.mphf_build(_dev(k), seed=1, max_tries=64)
+            assert got.stats["seed_used"] == want.seed_used > 1
+            assert np.array_equal(_u64(got.G), want.G)
+            assert np.array_equal(_u64(got.rank_dir), want.dir)
+            found += 1
+            if found == 3:
+                break
+    assert found == 3
