@@ -50,22 +50,22 @@ __device__ __forceinline__ uint32_t nonzero_pairs(uint64_t w) {
     return (uint32_t)__popcll((w | (w >> 1)) & 0x5555555555555555ull);
 }
 
-// One thread per 512 vertices (8 words of G).
+// One thread per 512 vertices (16 words of G, 32 vertices per word).
 __global__ void k_rank_counts(const uint64_t *__restrict__ G, uint64_t words, uint64_t blocks,
                               uint32_t *__restrict__ cnt) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < blocks; b += stride) {
         uint32_t c = 0;
-        const uint64_t w0 = b * 8;
-        if (w0 + 8 <= words && ((((uintptr_t)G) & 15u) == 0)) {
+        const uint64_t w0 = b * 16;
+        if (w0 + 16 <= words && ((((uintptr_t)G) & 15u) == 0)) {
             const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(G + w0);
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
+            for (int q = 0; q < 8; q++) {
                 const ulonglong2 x = p[q];
                 c += nonzero_pairs(x.x) + nonzero_pairs(x.y);
             }
         } else {
-            for (uint64_t w = w0; w < words && w < w0 + 8; w++) c += nonzero_pairs(G[w]);
+            for (uint64_t w = w0; w < words && w < w0 + 16; w++) c += nonzero_pairs(G[w]);
         }
         cnt[b] = c;
     }
