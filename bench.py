@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 MWHC MPHF build hot path.
+
+One step = one whole pass of the hot path over one key set: key -> edge
+hashing, packed-incidence build, round-synchronous peel with canonical order,
+reverse-layer g assignment and rank directory (hpeel_mphf_build), on the
+n = 1e8, r = 3, gamma = 1.23 workload (SplitMix64 keys, seed 1).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU: every rank builds
+its own independent key set (seed 1 + rank) -- weak scaling, no collective on
+the data path; a barrier and a max-reduction of the timings only.
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_KEYS = 10**8
+GAMMA_MILLI = 1230
+R = 3
+KEY_SEED = 1
+HASH_SEED = 1
+METRIC = "peeled edges/sec (Medges/s)"
+UNIT = "Medges/s"
+CPU_SAMPLE_KEYS = 10**7        # cpu_baseline: one oracle build of this many keys
+REF_STEP_KEYS = 10**6          # --impl reference: keys per oracle step
+
+# Algorithmic bytes per unit of work, per step of the path (r = 3).  "sector"
+# charges one 32-byte sector per random access (64 bytes for a read-modify-
+# write), "word" charges only the bytes the method reads and writes.
+# Units: n edges (hash, build, emit, assign), m vertices (fill), round-0
+# vertices m plus first-layer edges (round0), peeled edges (update), frontier
+# vertices of rounds >= 1 (claim).
+def byte_model(step, n, m, st):
+    L0, Fr, peeled = st["first_layer"], st["frontier"], st["n_peeled"]
+    later = peeled - L0
+    if step == "hash_edges":
+        return {"units": n, "word": 20 * n, "sector": 20 * n}
+    if step == "fill":
+        return {"units": m, "word": 8 * m, "sector": 8 * m}
+    if step == "build_incidence":
+        return {"units": n, "word": (12 + 4 + R * 16) * n, "sector": (12 + 4 + R * 64) * n}
+    if step == "round0":
+        return {"units": m, "word": 8 * m + (8 + 4) * L0, "sector": 8 * m + (64 + 4) * L0}
+    if step == "update":
+        return {"units": peeled, "word": (4 + 4 + 12 + (R - 1) * 16) * peeled + 4 * Fr,
+                "sector": (4 + 32 + 32 + (R - 1) * 64) * peeled + 4 * Fr}
+    if step == "claim":
+        return {"units": Fr, "word": (4 + 8 + 8) * Fr + 4 * later,
+                "sector": (4 + 32 + 64) * Fr + 4 * later}
+    if step == "emit_scatter":
+        return {"units": n, "word": 12 * n, "sector": 12 * n}
+    if step == "emit_hist":
+        return {"units": n, "word": 4 * n, "sector": 4 * n}
+    if step == "assign":
+        return {"units": n, "word": (4 + 4 + 12 + 2 * 8 + 16) * n,
+                "sector": (4 + 32 + 32 + 2 * 32 + 64) * n}
+    return None
+
+
+# DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# for a kernel version, keyed by the sha256 of the source file the kernel
+# lives in; stale entries are ignored.  Filled from the summaries in profiles/.
+NCU_TRAFFIC = {
+    # step: (source file, sha256 prefix, bytes per unit)
+}
+
+
+def src_hash(rel):
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline():
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from paper_1312_0526_gb300 import inputs
+    keys = inputs.keys(CPU_SAMPLE_KEYS, KEY_SEED)
+    oracle.build()
+    t0 = time.perf_counter()
+    res = oracle.mphf_build(keys, HASH_SEED, GAMMA_MILLI)
+    dt = time.perf_counter() - t0
+    return {"value": CPU_SAMPLE_KEYS / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one single-threaded oracle MPHF build (hash+peel+assign+rank) of the "
+                      f"first {CPU_SAMPLE_KEYS:.0e} keys of the same stream, {dt:.2f} s, "
+                      f"{res.rounds} rounds"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1312_0526_gb300 import inputs
+    oracle.build()
+    keys = inputs.keys(REF_STEP_KEYS, KEY_SEED)
+    for _ in range(args.warmup):
+        oracle.mphf_build(keys, HASH_SEED, GAMMA_MILLI)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mphf_build(keys, HASH_SEED, GAMMA_MILLI)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = REF_STEP_KEYS / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "mphf-build r=3 gamma=1.23, SplitMix64 keys seed 1; "
+                               f"oracle steps on the first {REF_STEP_KEYS:.0e} keys",
+                   "n": N_KEYS, "gamma": GAMMA_MILLI / 1000, "r": R},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step one single-threaded oracle MPHF build of "
+                                   f"{REF_STEP_KEYS:.0e} keys"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_KEYS, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import build as hpbuild
+    from paper_1312_0526_gb300 import inputs
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
+    if rank == 0:
+        hpbuild.build()
+    if dist:
+        dist.barrier()
+    hp.lib()
+
+    n = args.n
+    m = hp.num_vertices(n, GAMMA_MILLI, R)
+    keys_h = torch.from_numpy(inputs.keys(n, KEY_SEED + rank).view(np.int64)).pin_memory()
+    keys = keys_h.to("cuda", non_blocking=False)
+    ws = torch.empty(hp.mphf_workspace_size(n, GAMMA_MILLI), dtype=torch.uint8, device="cuda")
+    G = torch.empty((m + 31) // 32, dtype=torch.int64, device="cuda")
+    D = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return hp.mphf_build(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D)
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(max(args.warmup, 0)):
+        res = step()
+    sync_all()
+
+    # ---- timed region: device-resident keys, K full steps
+    hp.profile_reset()
+    hp.profile_enable(True)
+    l0 = hp.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        sync_all()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        sync_all()
+    launches = hp.kernel_launches() - l0
+    hp.profile_enable(False)
+    prof = hp.profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms)
+    st = res.stats
+    value = n * world / (ms / 1e3) / 1e6
+
+    # ---- roofline of the dominant step
+    peak, peak_kind = measured_peaks()
+    ranked = sorted(((v[1], k) for k, v in prof.items()), reverse=True)
+    roof = None
+    for tot_ms, name in ranked:
+        model = byte_model(name, n, m, st)
+        if model is None:
+            continue
+        per_step_ms = tot_ms / args.steps
+        launches_per_step = prof[name][0] / args.steps
+        achieved = model["sector"] / (per_step_ms / 1e3) / 1e9
+        traffic = None
+        if name in NCU_TRAFFIC:
+            src, h, per_unit = NCU_TRAFFIC[name]
+            if src_hash(src) == h:
+                traffic = per_unit * model["units"] / max(launches_per_step, 1)
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "model": "sector", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_step": model["sector"],
+                "word_model_gbs": model["word"] / (per_step_ms / 1e3) / 1e9,
+                "launches_per_step": launches_per_step,
+                "ms_per_step": per_step_ms, "share": tot_ms / sum(v[1] for v in prof.values())}
+        break
+
+    # ---- end to end through the public API with host buffers
+    G_h = torch.empty_like(G, device="cpu").pin_memory()
+    D_h = torch.empty_like(D, device="cpu").pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    sync_all()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        keys.copy_(keys_h, non_blocking=True)
+        step()
+        G_h.copy_(G, non_blocking=True)
+        D_h.copy_(D, non_blocking=True)
+    e1.record(stream)
+    sync_all()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"mphf-build n={n:.0e} r=3 gamma=1.23, SplitMix64 keys seed "
+                               f"1+rank, hash seed 1 (hash, incidence, peel, canonical "
+                               f"order, g assignment, rank)",
+                   "n": n, "m": m, "gamma": GAMMA_MILLI / 1000, "r": R,
+                   "parallelism": f"{world} independent key sets (one per GPU)",
+                   "l2": "inputs larger than L2: 0.8 GB keys, 1.0 GB vertex state, "
+                         "1.2 GB edges per step"},
+        "rounds": st["rounds"], "seed_used": st["seed_used"],
+        "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "clocks": clk.summary(),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": n * world / (e2e_ms / 1e3) / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": keys.numel() * 8,
+                "d2h_bytes_per_step": (G.numel() + D.numel()) * 8, "ms_per_step": e2e_ms},
+        "steps_ms": {k: v[1] / args.steps for k, v in sorted(prof.items())},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -58,6 +58,9 @@ typedef struct hpeel_stats {
     uint64_t seed_used;     /* MPHF: hash seed of the successful attempt */
     uint32_t attempts;      /* MPHF: hash seeds tried */
     uint32_t device_err;    /* non-zero: code a kernel raised (see status) */
+    uint64_t first_layer;   /* |L_0|: edges peeled in round 0 */
+    uint64_t frontier;      /* sum over t >= 1 of |F_t|: vertices that fell to
+                               degree 1 after round 0 (work of later rounds) */
 } hpeel_stats;
 
 /* Largest number of rounds a single peel supports (claim words keep the
@@ -156,6 +159,25 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
                               uint64_t *d_G, uint64_t *d_rank_dir,
                               hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
                               void *stream);
+
+/*
+ * Instrumentation (no counterpart in the paper; used to measure the path).
+ *   hpeel_kernel_launches  total number of kernels this library has launched
+ *                          in the process (all devices, all threads).
+ *   hpeel_profile_enable   1: every step of every later call records a CUDA
+ *                          event pair on the call's stream; the elapsed times
+ *                          are added up per step name when the call returns.
+ *                          0 (default): no events are recorded.
+ *   hpeel_profile_reset    clears the per-step totals.
+ *   hpeel_profile_read     writes "name launches total_ms" lines (one per
+ *                          step name) into buf (at most len bytes, always
+ *                          NUL-terminated when len > 0); returns the size
+ *                          needed including the NUL.
+ */
+uint64_t hpeel_kernel_launches(void);
+void hpeel_profile_enable(int on);
+void hpeel_profile_reset(void);
+size_t hpeel_profile_read(char *buf, size_t len);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,8 @@ class HpeelError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("n_peeled", ctypes.c_uint64), ("rounds", ctypes.c_uint32),
                 ("core_nonempty", ctypes.c_uint32), ("seed_used", ctypes.c_uint64),
-                ("attempts", ctypes.c_uint32), ("device_err", ctypes.c_uint32)]
+                ("attempts", ctypes.c_uint32), ("device_err", ctypes.c_uint32),
+                ("first_layer", ctypes.c_uint64), ("frontier", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -85,6 +86,14 @@ def lib():
         L.hpeel_mphf_workspace_size.argtypes = [u64, u32]
         L.hpeel_mphf_build.restype = st
         L.hpeel_mphf_build.argtypes = [p, u64, u64, u32, u32, p, p, ctypes.POINTER(Stats), p, sz, p]
+        L.hpeel_kernel_launches.restype = u64
+        L.hpeel_kernel_launches.argtypes = []
+        L.hpeel_profile_enable.restype = None
+        L.hpeel_profile_enable.argtypes = [ctypes.c_int]
+        L.hpeel_profile_reset.restype = None
+        L.hpeel_profile_reset.argtypes = []
+        L.hpeel_profile_read.restype = sz
+        L.hpeel_profile_read.argtypes = [ctypes.c_char_p, sz]
         _lib = L
         return L
 
@@ -175,7 +184,9 @@ def peel(edges, m: int, workspace=None, max_layers: int = 4096) -> PeelResult:
                             _dev_ptr(loff, "layer_off"), max_layers, ctypes.byref(st), wp,
                             ws.numel(), _stream()))
     R = int(st.rounds)
-    return PeelResult(order, claim, loff[:R + 1], R, int(st.n_peeled))
+    res = PeelResult(order, claim, loff[:R + 1], R, int(st.n_peeled))
+    res.stats = st.as_dict()
+    return res
 
 
 @dataclass
@@ -210,3 +221,29 @@ def mphf_build(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
                                   ctypes.byref(st), _dev_ptr(ws, "workspace", torch.uint8),
                                   ws.numel(), _stream()))
     return MphfResult(G[:(m + 31) // 32], rank_dir, m, st.as_dict())
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process."""
+    return int(lib().hpeel_kernel_launches())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Per-step CUDA-event timing of every later call (see hpeel.h)."""
+    lib().hpeel_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    lib().hpeel_profile_reset()
+
+
+def profile_read() -> dict:
+    """{step name: (launch groups, total ms)} accumulated since the last reset."""
+    need = int(lib().hpeel_profile_read(None, 0))
+    buf = ctypes.create_string_buffer(need + 16)
+    lib().hpeel_profile_read(buf, len(buf))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out

@@ -139,6 +139,8 @@ MphfLayout mphf_layout(uint64_t n, uint32_t gamma_milli) {
 struct PeelOut {
     uint32_t rounds;
     uint64_t n_peeled;
+    uint64_t first_layer;
+    uint64_t frontier;
     uint32_t *loff;  // device layer table (uint32[rounds + 1])
 };
 
@@ -162,24 +164,40 @@ hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint3
     HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), L.stream));
     HP_CUDA(cudaMemsetAsync(loff, 0, 2 * sizeof(uint32_t), L.stream));
     HP_CUDA(cudaMemsetAsync(foff, 0, 2 * sizeof(uint32_t), L.stream));
-    launch_fill_u32(L, state, 2ull * m, 0u);
-    launch_build_incidence(L, edges, n, r, P, state, claim, ctl);
-    launch_round0(L, state, m, r, P, n, claim, Ll, ctl);
+    {
+        ProfScope ps(L, "fill");
+        launch_fill_u32(L, state, 2ull * m, 0u);
+    }
+    {
+        ProfScope ps(L, "build_incidence");
+        launch_build_incidence(L, edges, n, r, P, state, claim, ctl);
+    }
+    {
+        ProfScope ps(L, "round0");
+        launch_round0(L, state, m, r, P, n, claim, Ll, ctl);
+    }
     HP_TRY(check_launch("build/round0"));
 
     uint32_t t = 0;
     for (;;) {
         if (t + 1 >= lay.max_rounds)
             return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds - 1);
-        launch_update(L, edges, r, m, claim, state, Ll, F, loff, foff, ctl);
+        {
+            ProfScope ps(L, "update");
+            launch_update(L, edges, r, m, claim, state, Ll, F, loff, foff, ctl);
+        }
         HP_TRY(check_launch("update"));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
         if (hctl->err)
             return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u (round %u)",
                         hctl->err, t);
+        if (t == 0) out->first_layer = hctl->last_layer;
         if (!hctl->more) break;
-        launch_claim(L, state, r, P, n, claim, F, Ll, foff, ctl);
+        {
+            ProfScope ps(L, "claim");
+            launch_claim(L, state, r, P, n, claim, F, Ll, foff, ctl);
+        }
         HP_TRY(check_launch("claim"));
         t++;
     }
@@ -187,6 +205,7 @@ hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint3
     const uint64_t peeled = hctl->lcur;
     out->rounds = R;
     out->n_peeled = peeled;
+    out->frontier = hctl->fcur;
     out->loff = loff;
 
     // Canonical order: stable sort by key = round, core edges key R.
@@ -199,9 +218,18 @@ hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint3
         const uint32_t count = n - seg;
         const uint32_t nb = std::min<uint32_t>(nkeys - base, kEmitBins);
         const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
-        launch_emit_hist(L, src, count, claim, base, R, nb, hist);
-        launch_scan_u32(L, hist, hist, (uint64_t)nb * tiles, scantmp);
-        launch_emit_scatter(L, src, count, claim, base, R, nb, hist, order + seg);
+        {
+            ProfScope ps(L, "emit_hist");
+            launch_emit_hist(L, src, count, claim, base, R, nb, hist);
+        }
+        {
+            ProfScope ps(L, "emit_scan");
+            launch_scan_u32(L, hist, hist, (uint64_t)nb * tiles, scantmp);
+        }
+        {
+            ProfScope ps(L, "emit_scatter");
+            launch_emit_scatter(L, src, count, claim, base, R, nb, hist, order + seg);
+        }
         HP_TRY(check_launch("emit"));
         if (nkeys - base <= kEmitBins) break;
         // keys >= base + nb - 1 landed in the last bin: sort that tail again
@@ -261,7 +289,10 @@ hpeel_status hpeel_hash_edges(const uint64_t *d_keys, uint64_t n, uint64_t m, ui
     if (!d_keys || !d_edges) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
     Launch L;
     HP_TRY(make_launch(stream, &L));
-    launch_hash_edges(L, d_keys, n, r, make_fastmod(m / r), seed, d_edges);
+    {
+        ProfScope ps(L, "hash_edges");
+        launch_hash_edges(L, d_keys, n, r, make_fastmod(m / r), seed, d_edges);
+    }
     return check_launch("hash_edges");
 }
 
@@ -304,10 +335,13 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
         HP_TRY(check_launch("layer_off"));
     }
     HP_CUDA(cudaStreamSynchronize(L.stream));
+    prof_flush();
     if (h_stats) {
         h_stats->n_peeled = po.n_peeled;
         h_stats->rounds = po.rounds;
         h_stats->core_nonempty = po.n_peeled < n;
+        h_stats->first_layer = po.first_layer;
+        h_stats->frontier = po.frontier;
     }
     return HPEEL_OK;
 }
@@ -350,7 +384,10 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
     const FastMod fm = make_fastmod(m / 3);
     for (uint32_t a = 0; a < max_tries; a++) {
         const uint64_t s = seed + a;
-        launch_hash_edges(L, d_keys, n, 3, fm, s, edges);
+        {
+            ProfScope ps(L, "hash_edges");
+            launch_hash_edges(L, d_keys, n, 3, fm, s, edges);
+        }
         HP_TRY(check_launch("hash_edges"));
         PeelOut po{};
         HP_TRY(peel_core(L, edges, (uint32_t)n, (uint32_t)m, 3, order, claim, ws + lay.peel, &po));
@@ -359,23 +396,31 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
             h_stats->rounds = po.rounds;
             h_stats->n_peeled = po.n_peeled;
             h_stats->core_nonempty = po.n_peeled < n;
+            h_stats->first_layer = po.first_layer;
+            h_stats->frontier = po.frontier;
         }
         if (po.n_peeled < n) continue;
         // a8: reverse layer order
         const uint64_t words = (m + 31) / 32;
         HP_CUDA(cudaMemsetAsync(d_G, 0, 8 * words, L.stream));
-        for (int64_t t = (int64_t)po.rounds - 1; t >= 0; t--)
+        for (int64_t t = (int64_t)po.rounds - 1; t >= 0; t--) {
+            ProfScope ps(L, "assign");
             launch_assign_layer(L, edges, claim, order, po.loff, (uint32_t)t, d_G);
+        }
         HP_TRY(check_launch("assign"));
         // a9: rank directory
         uint32_t *cnt = reinterpret_cast<uint32_t *>(ws + lay.rank_cnt);
         uint32_t *scn = reinterpret_cast<uint32_t *>(ws + lay.rank_scan);
         uint32_t *tmp = reinterpret_cast<uint32_t *>(ws + lay.rank_tmp);
-        launch_rank_counts(L, d_G, m, cnt);
-        launch_scan_u32(L, cnt, scn, blocks, tmp);
-        launch_widen_dir(L, scn, cnt, blocks, d_rank_dir);
+        {
+            ProfScope ps(L, "rank");
+            launch_rank_counts(L, d_G, m, cnt);
+            launch_scan_u32(L, cnt, scn, blocks, tmp);
+            launch_widen_dir(L, scn, cnt, blocks, d_rank_dir);
+        }
         HP_TRY(check_launch("rank"));
         HP_CUDA(cudaStreamSynchronize(L.stream));
+        prof_flush();
         if (h_stats) h_stats->seed_used = s;
         return HPEEL_OK;
     }

@@ -86,4 +86,43 @@ __device__ __forceinline__ void warp_append(uint32_t *cursor, uint32_t *list, bo
     if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = value;
 }
 
+// Block-aggregated append: every thread of the block calls this (it holds
+// barriers) with K candidates; the block reserves all its slots with a single
+// atomicAdd, so the shared cursor sees one atomic per K * blockDim items.
+// The order of the appended values inside the list is unspecified.
+template <int K, int THREADS>
+__device__ __forceinline__ void block_append(uint32_t *cursor, uint32_t *list, const bool (&pred)[K],
+                                             const uint32_t (&val)[K]) {
+    __shared__ uint32_t warp_base[THREADS / 32];
+    __shared__ uint32_t block_base;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) cnt += pred[k] ? 1u : 0u;
+    uint32_t x = cnt;  // inclusive warp scan
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    if (lane == 31) warp_base[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < THREADS / 32; w++) {
+            const uint32_t c = warp_base[w];
+            warp_base[w] = s;
+            s += c;
+        }
+        block_base = s ? atomicAdd(cursor, s) : 0u;
+    }
+    __syncthreads();
+    uint32_t pos = block_base + warp_base[warp] + x - cnt;
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        if (pred[k]) list[pos++] = val[k];
+    __syncthreads();
+}
+
 }  // namespace hp

@@ -49,6 +49,7 @@ void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, cons
                       uint32_t base, uint32_t core_key, uint32_t nbins, uint32_t *hist) {
     if (count == 0) return;
     const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
+    count_launch();
     k_emit_hist<<<tiles, kThreads, 0, L.stream>>>(src, count, claim, base, core_key, nbins, hist);
 }
 
@@ -105,6 +106,7 @@ void launch_emit_scatter(const Launch &L, const uint32_t *src, uint32_t count,
                          const uint32_t *offs, uint32_t *out) {
     if (count == 0) return;
     const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
+    count_launch();
     k_emit_scatter<<<tiles, kThreads, 0, L.stream>>>(src, count, claim, base, core_key, nbins,
                                                      offs, out);
 }
@@ -117,6 +119,7 @@ __global__ void k_layer_off(const uint32_t *__restrict__ loff, uint32_t rounds,
 }
 
 void launch_layer_off(const Launch &L, const uint32_t *loff, uint32_t rounds, uint64_t *out) {
+    count_launch();
     k_layer_off<<<grid_for(L, (uint64_t)rounds + 1, 1, 4), kThreads, 0, L.stream>>>(loff, rounds,
                                                                                    out);
 }
@@ -198,13 +201,16 @@ void launch_scan_u32(const Launch &L, const uint32_t *in, uint32_t *out, uint64_
                      uint32_t *tmp) {
     if (count == 0) return;
     if (count <= kScanBlock) {
+        count_launch();
         k_scan_down<<<1, kScanThreads, 0, L.stream>>>(in, out, count, nullptr);
         return;
     }
     const uint64_t blocks = (count + kScanBlock - 1) / kScanBlock;
     uint32_t *sums = tmp;
+    count_launch();
     k_scan_reduce<<<(unsigned)blocks, kScanThreads, 0, L.stream>>>(in, count, sums);
     launch_scan_u32(L, sums, sums, blocks, tmp + blocks);
+    count_launch();
     k_scan_down<<<(unsigned)blocks, kScanThreads, 0, L.stream>>>(in, out, count, sums);
 }
 

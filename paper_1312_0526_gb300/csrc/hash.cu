@@ -47,9 +47,9 @@ void launch_hash_edges(const Launch &L, const uint64_t *keys, uint64_t n, uint32
     if (n == 0) return;
     const unsigned grid = grid_for(L, n, 1, 8);
     switch (r) {
-    case 2: k_hash_edges<2><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
-    case 3: k_hash_edges<3><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
-    case 4: k_hash_edges<4><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
+    case 2: count_launch(); k_hash_edges<2><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
+    case 3: count_launch(); k_hash_edges<3><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
+    case 4: count_launch(); k_hash_edges<4><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
     }
 }
 

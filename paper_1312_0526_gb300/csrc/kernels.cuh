@@ -20,6 +20,18 @@ struct Launch {
     int sms;  // multiprocessors of the current device
 };
 
+// Instrumentation (prof.cu): every kernel launch is counted; when profiling
+// is on, a ProfScope brackets a step with CUDA events on its stream.
+void count_launch(uint32_t kernels = 1);
+struct ProfScope {
+    ProfScope(const Launch &L, const char *name);
+    ~ProfScope();
+    const Launch &L;
+    const char *name;
+    void *a;
+};
+void prof_flush();  // after a stream synchronisation: accumulate timings
+
 // Persistent grid size for grid-stride kernels over device-sized ranges.
 inline unsigned grid_fixed(const Launch &L, int per_sm) { return (unsigned)(L.sms * per_sm); }
 inline unsigned grid_for(const Launch &L, uint64_t work, int per_thread, int per_sm) {

@@ -42,6 +42,7 @@ k_assign(const uint32_t *__restrict__ edges, const uint32_t *__restrict__ claim,
 
 void launch_assign_layer(const Launch &L, const uint32_t *edges, const uint32_t *claim,
                          const uint32_t *order, const uint32_t *loff, uint32_t t, uint64_t *G) {
+    count_launch();
     k_assign<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(edges, claim, order, loff, t, G);
 }
 
@@ -74,6 +75,7 @@ __global__ void k_rank_counts(const uint64_t *__restrict__ G, uint64_t words, ui
 void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt) {
     const uint64_t words = (m + 31) / 32, blocks = (m + 511) / 512;
     if (blocks == 0) return;
+    count_launch();
     k_rank_counts<<<grid_for(L, blocks, 1, 8), kThreads, 0, L.stream>>>(G, words, blocks, cnt);
 }
 
@@ -90,6 +92,7 @@ __global__ void k_widen_dir(const uint32_t *__restrict__ scanned, const uint32_t
 
 void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,
                       uint64_t blocks, uint64_t *dir) {
+    count_launch();
     k_widen_dir<<<grid_for(L, blocks + 1, 1, 8), kThreads, 0, L.stream>>>(scanned, cnt, blocks,
                                                                           dir);
 }

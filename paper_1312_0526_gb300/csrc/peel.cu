@@ -42,6 +42,7 @@ __global__ void k_fill_u32(uint32_t *__restrict__ p, uint64_t count, uint32_t va
 
 void launch_fill_u32(const Launch &L, uint32_t *p, uint64_t count, uint32_t value) {
     if (count == 0) return;
+    count_launch();
     k_fill_u32<<<grid_for(L, count, 16, 8), kThreads, 0, L.stream>>>(p, count, value);
 }
 
@@ -100,79 +101,97 @@ void launch_build_incidence(const Launch &L, const uint32_t *edges, uint32_t n, 
     if (n == 0) return;
     const unsigned grid = grid_for(L, ((uint64_t)n + 3) / 4, 1, 8);
     switch (r) {
-    case 2: k_build<2><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
-    case 3: k_build<3><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
-    case 4: k_build<4><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
+    case 2: count_launch(); k_build<2><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
+    case 3: count_launch(); k_build<3><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
+    case 4: count_launch(); k_build<4><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
     }
 }
 
 // ---------------------------------------------------------------- round 0 --
+// kR0Items vertices per thread per block step, strided by the block size so
+// every record load is coalesced; one block-aggregated append per step.
+constexpr int kR0Items = 4;
+
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_round0(const uint2 *__restrict__ st, uint32_t m, uint32_t P, uint32_t n,
          uint32_t *__restrict__ claim, uint32_t *__restrict__ Llist, Ctl *ctl) {
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t base = (uint64_t)blockIdx.x * kThreads; base < m; base += stride) {
-        const uint64_t v = base + threadIdx.x;
-        bool take = false;
-        uint32_t e = 0;
-        if (v < m) {
-            const uint2 s = st[v];
-            if (s.x == 1u) {
-                e = s.y;
-                if (e < n) {
-                    const uint32_t j = part_of<R>((uint32_t)v, P);
-                    take = atomicMin(claim + e, j) == kUnclaimed;
-                } else {
-                    raise_err(ctl, kDevBadEdge);
+    constexpr uint32_t kStep = kThreads * kR0Items;
+    const uint64_t stride = (uint64_t)gridDim.x * kStep;
+    for (uint64_t base = (uint64_t)blockIdx.x * kStep; base < m; base += stride) {
+        bool take[kR0Items];
+        uint32_t e[kR0Items];
+#pragma unroll
+        for (int k = 0; k < kR0Items; k++) {
+            const uint64_t v = base + (uint64_t)k * kThreads + threadIdx.x;
+            take[k] = false;
+            e[k] = 0;
+            if (v < m) {
+                const uint2 s = __ldcs(st + v);
+                if (s.x == 1u) {
+                    e[k] = s.y;
+                    if (s.y < n) {
+                        const uint32_t j = part_of<R>((uint32_t)v, P);
+                        take[k] = atomicMin(claim + s.y, j) == kUnclaimed;
+                    } else {
+                        raise_err(ctl, kDevBadEdge);
+                    }
                 }
             }
         }
-        warp_append(&ctl->lcur, Llist, take, e);
+        block_append<kR0Items, kThreads>(&ctl->lcur, Llist, take, e);
     }
 }
 
 void launch_round0(const Launch &L, const uint32_t *state, uint32_t m, uint32_t r, uint32_t P,
                    uint32_t n, uint32_t *claim, uint32_t *Llist, Ctl *ctl) {
     if (m == 0) return;
-    const unsigned grid = grid_for(L, m, 1, 8);
+    const unsigned grid = grid_for(L, m, kR0Items, 8);
     const uint2 *st = reinterpret_cast<const uint2 *>(state);
     switch (r) {
-    case 2: k_round0<2><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
-    case 3: k_round0<3><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
-    case 4: k_round0<4><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
+    case 2: count_launch(); k_round0<2><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
+    case 3: count_launch(); k_round0<3><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
+    case 4: count_launch(); k_round0<4><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
     }
 }
 
 // ---------------------------------------------------------------- claim --
+constexpr int kClaimItems = 4;
+
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_claim(const uint2 *__restrict__ st, uint32_t P, uint32_t n, uint32_t *__restrict__ claim,
         const uint32_t *__restrict__ F, uint32_t *__restrict__ Llist, uint32_t *__restrict__ foff,
         Ctl *ctl) {
+    constexpr uint32_t kStep = kThreads * kClaimItems;
     const uint32_t t = *(volatile uint32_t *)&ctl->round;
     const uint32_t fb = foff[t];
     const uint32_t fe = *(volatile uint32_t *)&ctl->fcur;
     if (blockIdx.x == 0 && threadIdx.x == 0) foff[t + 1] = fe;  // F_{t+1} starts here
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t base = fb + (uint64_t)blockIdx.x * kThreads; base < fe; base += stride) {
-        const uint64_t i = base + threadIdx.x;
-        bool take = false;
-        uint32_t e = 0;
-        if (i < fe) {
-            const uint32_t v = F[i];
-            const uint2 s = st[v];
-            if (s.x == 1u) {
-                e = s.y;
-                if (e < n) {
-                    const uint32_t tag = (t << 2) | part_of<R>(v, P);
-                    take = atomicMin(claim + e, tag) == kUnclaimed;
-                } else {
-                    raise_err(ctl, kDevBadEdge);
+    const uint64_t stride = (uint64_t)gridDim.x * kStep;
+    for (uint64_t base = fb + (uint64_t)blockIdx.x * kStep; base < fe; base += stride) {
+        bool take[kClaimItems];
+        uint32_t e[kClaimItems];
+#pragma unroll
+        for (int k = 0; k < kClaimItems; k++) {
+            const uint64_t i = base + (uint64_t)k * kThreads + threadIdx.x;
+            take[k] = false;
+            e[k] = 0;
+            if (i < fe) {
+                const uint32_t v = F[i];
+                const uint2 s = st[v];
+                if (s.x == 1u) {
+                    e[k] = s.y;
+                    if (s.y < n) {
+                        const uint32_t tag = (t << 2) | part_of<R>(v, P);
+                        take[k] = atomicMin(claim + s.y, tag) == kUnclaimed;
+                    } else {
+                        raise_err(ctl, kDevBadEdge);
+                    }
                 }
             }
         }
-        warp_append(&ctl->lcur, Llist, take, e);
+        block_append<kClaimItems, kThreads>(&ctl->lcur, Llist, take, e);
     }
 }
 
@@ -182,53 +201,60 @@ void launch_claim(const Launch &L, const uint32_t *state, uint32_t r, uint32_t P
     const unsigned grid = grid_fixed(L, 8);
     const uint2 *st = reinterpret_cast<const uint2 *>(state);
     switch (r) {
-    case 2: k_claim<2><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
-    case 3: k_claim<3><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
-    case 4: k_claim<4><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
+    case 2: count_launch(); k_claim<2><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
+    case 3: count_launch(); k_claim<3><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
+    case 4: count_launch(); k_claim<4><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
     }
 }
 
 // ---------------------------------------------------------------- update --
+constexpr int kUpdItems = 2;  // edges per thread per block step
+
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_update(const uint32_t *__restrict__ edges, uint32_t m, const uint32_t *__restrict__ claim,
          uint32_t *__restrict__ st, const uint32_t *__restrict__ Llist, uint32_t *__restrict__ F,
          uint32_t *__restrict__ loff, const uint32_t *__restrict__ foff, Ctl *ctl) {
+    constexpr uint32_t kStep = kThreads * kUpdItems;
+    constexpr int K = kUpdItems * (R - 1);
     const uint32_t t = *(volatile uint32_t *)&ctl->round;
     const uint32_t lb = loff[t];
     const uint32_t le = *(volatile uint32_t *)&ctl->lcur;
     if (blockIdx.x == 0 && threadIdx.x == 0) loff[t + 1] = le;  // L_t = [lb, le)
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t base = lb + (uint64_t)blockIdx.x * kThreads; base < le; base += stride) {
-        const uint64_t i = base + threadIdx.x;
-        bool app[R - 1];
-        uint32_t wv[R - 1];
+    const uint64_t stride = (uint64_t)gridDim.x * kStep;
+    for (uint64_t base = lb + (uint64_t)blockIdx.x * kStep; base < le; base += stride) {
+        bool app[K];
+        uint32_t wv[K];
 #pragma unroll
-        for (int k = 0; k < R - 1; k++) {
-            app[k] = false;
-            wv[k] = 0;
-        }
-        if (i < le) {
-            const uint32_t e = Llist[i];
-            const uint32_t h = claim[e] & 3u;
-            int k = 0;
+        for (int q = 0; q < kUpdItems; q++) {
+            const uint64_t i = base + (uint64_t)q * kThreads + threadIdx.x;
+            uint32_t e = 0, h = 0xFFu;
+            uint32_t w[R];
+            if (i < le) {
+                e = Llist[i];
+                h = claim[e] & 3u;
 #pragma unroll
-            for (int j = 0; j < R; j++) {
-                if ((uint32_t)j == h) continue;
-                const uint32_t w = edges[(uint64_t)e * R + j];
-                if (w < m) {
-                    const uint32_t old = atomicSub(st + 2ull * w, 1u);
-                    atomicXor(st + 2ull * w + 1, e);
-                    app[k] = (old == 2u);
-                    wv[k] = w;
+                for (int j = 0; j < R; j++) w[j] = edges[(uint64_t)e * R + j];
+            }
+#pragma unroll
+            for (int k = 0; k < R - 1; k++) {
+                app[q * (R - 1) + k] = false;
+                wv[q * (R - 1) + k] = 0;
+                if (h == 0xFFu) continue;
+                // k-th non-hinge position: positions after the hinge shift by one
+                const int j = k + ((uint32_t)k >= h ? 1 : 0);
+                const uint32_t x = w[j];
+                if (x < m) {
+                    const uint32_t old = atomicSub(st + 2ull * x, 1u);
+                    atomicXor(st + 2ull * x + 1, e);
+                    app[q * (R - 1) + k] = (old == 2u);
+                    wv[q * (R - 1) + k] = x;
                 } else {
                     raise_err(ctl, kDevBadVertex);
                 }
-                k++;
             }
         }
-#pragma unroll
-        for (int k = 0; k < R - 1; k++) warp_append(&ctl->fcur, F, app[k], wv[k]);
+        block_append<K, kThreads>(&ctl->fcur, F, app, wv);
     }
     // The last block to finish closes the round: F_{t+1} = [foff[t+1], fcur).
     __syncthreads();
@@ -251,9 +277,9 @@ void launch_update(const Launch &L, const uint32_t *edges, uint32_t r, uint32_t 
                    uint32_t *loff, const uint32_t *foff, Ctl *ctl) {
     const unsigned grid = grid_fixed(L, 8);
     switch (r) {
-    case 2: k_update<2><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
-    case 3: k_update<3><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
-    case 4: k_update<4><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
+    case 2: count_launch(); k_update<2><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
+    case 3: count_launch(); k_update<3><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
+    case 4: count_launch(); k_update<4><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
     }
 }
 
