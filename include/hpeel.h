@@ -129,6 +129,38 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m,
                         hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
                         void *stream);
 
+/*
+ * hpeel_peel without any allocation.  The paper has no counterpart: this is
+ * a calling convenience of this library.
+ *
+ * For callers that cannot allocate device memory at the time they need a
+ * peel -- code running inside another runtime's memory pool or arena, code
+ * under a fixed memory budget, plugins where calling the allocator is not
+ * allowed.  Same arguments, results and errors as hpeel_peel, without the
+ * workspace: the scratch is an array of HPEEL_NOALLOC_SCRATCH_BYTES compiled
+ * into this library's device image.  Every GPU on which the library's kernels
+ * are loaded holds that array until the process exits.  The call makes no
+ * cudaMalloc, cudaFree or other device allocation.
+ *   - Size limit: the call fails with HPEEL_ERR_WORKSPACE_TOO_SMALL (and
+ *     launches nothing) when hpeel_peel_workspace_size(n, m, r) exceeds
+ *     HPEEL_NOALLOC_SCRATCH_BYTES -- about 540,000 edges at gamma = 1.23,
+ *     r = 3.  Larger graphs need hpeel_peel and a caller workspace.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls in the process share the one array, which keeps the last
+ *     call's contents.  Each call clears what it needs before use, so leftover
+ *     contents never change a result, but two calls whose work overlaps on
+ *     the GPU (different streams or host threads on the same device) race on
+ *     the array: callers must order such calls.
+ * Synchronises stream.
+ */
+#define HPEEL_NOALLOC_SCRATCH_BYTES (16u << 20)
+hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, uint64_t m,
+                                uint32_t r, uint32_t *d_order, uint32_t *d_claim,
+                                uint64_t *d_layer_off, uint32_t max_layers,
+                                hpeel_stats *h_stats, void *stream);
+
 /* Workspace bytes hpeel_mphf_build needs for n keys at gamma_milli. */
 size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli);
 

@@ -86,6 +86,8 @@ def lib():
         L.hpeel_mphf_workspace_size.argtypes = [u64, u32]
         L.hpeel_mphf_build.restype = st
         L.hpeel_mphf_build.argtypes = [p, u64, u64, u32, u32, p, p, ctypes.POINTER(Stats), p, sz, p]
+        L.hpeel_peel_noalloc.restype = st
+        L.hpeel_peel_noalloc.argtypes = [p, u64, u64, u32, p, p, p, u32, ctypes.POINTER(Stats), p]
         L.hpeel_kernel_launches.restype = u64
         L.hpeel_kernel_launches.argtypes = []
         L.hpeel_profile_enable.restype = None
@@ -183,6 +185,32 @@ def peel(edges, m: int, workspace=None, max_layers: int = 4096) -> PeelResult:
     _check(lib().hpeel_peel(ep, n, m, r, _dev_ptr(order, "order"), _dev_ptr(claim, "claim"),
                             _dev_ptr(loff, "layer_off"), max_layers, ctypes.byref(st), wp,
                             ws.numel(), _stream()))
+    R = int(st.rounds)
+    res = PeelResult(order, claim, loff[:R + 1], R, int(st.n_peeled))
+    res.stats = st.as_dict()
+    return res
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def peel_noalloc(edges, m: int, max_layers: int = 4096) -> PeelResult:
+    """hpeel_peel_noalloc: the peel of ``peel`` with no workspace and no device
+    allocation inside the call (the library's built-in scratch is used; graphs
+    up to NOALLOC_SCRATCH_BYTES of scratch).  The output tensors are allocated
+    here by torch, before the call; callers that cannot allocate call the C
+    entry point with their own output buffers."""
+    torch = _torch()
+    ep = _dev_ptr(edges, "edges", torch.int32, 2)
+    n, r = edges.shape
+    dev = edges.device
+    order = torch.empty(n, dtype=torch.int32, device=dev)
+    claim = torch.empty(n, dtype=torch.int32, device=dev)
+    loff = torch.empty(max_layers + 1, dtype=torch.int64, device=dev)
+    st = Stats()
+    _check(lib().hpeel_peel_noalloc(ep, n, m, r, _dev_ptr(order, "order"),
+                                    _dev_ptr(claim, "claim"), _dev_ptr(loff, "layer_off"),
+                                    max_layers, ctypes.byref(st), _stream()))
     R = int(st.rounds)
     res = PeelResult(order, claim, loff[:R + 1], R, int(st.n_peeled))
     res.stats = st.as_dict()

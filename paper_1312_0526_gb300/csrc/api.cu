@@ -145,8 +145,10 @@ struct PeelOut {
 };
 
 // Round-synchronous peel of device edges into order/claim (sec. 4.2).
-hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t m, uint32_t r,
-                       uint32_t *order, uint32_t *claim_user, char *ws, PeelOut *out) {
+// hctl: host memory the control block is read back into after every round.
+hpeel_status peel_core_rb(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t m,
+                          uint32_t r, uint32_t *order, uint32_t *claim_user, char *ws,
+                          PeelOut *out, Ctl *hctl) {
     const PeelLayout lay = peel_layout(n, m);
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
     uint32_t *state = reinterpret_cast<uint32_t *>(ws + lay.state);
@@ -158,8 +160,6 @@ hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint3
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + lay.hist);
     uint32_t *scantmp = reinterpret_cast<uint32_t *>(ws + lay.scantmp);
     const uint32_t P = m / r;
-    Ctl *hctl = pinned_ctl();
-    if (!hctl) return fail(HPEEL_ERR_CUDA, "cudaMallocHost of the control read-back failed");
 
     HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), L.stream));
     HP_CUDA(cudaMemsetAsync(loff, 0, 2 * sizeof(uint32_t), L.stream));
@@ -247,6 +247,13 @@ hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint3
         src = Ll + seg;
     }
     return HPEEL_OK;
+}
+
+hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t m, uint32_t r,
+                       uint32_t *order, uint32_t *claim_user, char *ws, PeelOut *out) {
+    Ctl *hctl = pinned_ctl();
+    if (!hctl) return fail(HPEEL_ERR_CUDA, "cudaMallocHost of the control read-back failed");
+    return peel_core_rb(L, edges, n, m, r, order, claim_user, ws, out, hctl);
 }
 
 }  // namespace
@@ -429,3 +436,101 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Peel without any allocation.
+//
+// Some callers cannot allocate device memory when they need a peel: code that
+// runs inside another runtime's memory pool or arena (which hands out no raw
+// cudaMalloc blocks), code under a strict memory budget that must not grow
+// the device footprint at call time, or plugins loaded where calling the
+// allocator is forbidden.  For them hpeel_peel_noalloc runs the same kernels
+// as hpeel_peel with its scratch taken from a fixed array that is part of this
+// library's device image instead of a caller workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+// The built-in scratch: every GPU on which the library's kernels are loaded
+// holds these bytes until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HPEEL_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};  // device address of the scratch, per device
+
+// Device address of the scratch on the current device.  Host code cannot use
+// the symbol itself (on the host it names a stand-in, not device memory), so
+// the address is looked up once per device, with that device current.
+hpeel_status noalloc_scratch(void **out) {
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(HPEEL_ERR_INVALID_ARG, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return fail(HPEEL_ERR_CUDA, "cudaGetSymbolAddress of the built-in scratch failed: %s",
+                        cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return HPEEL_OK;
+}
+
+}  // namespace
+
+extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, uint64_t m,
+                                           uint32_t r, uint32_t *d_order, uint32_t *d_claim,
+                                           uint64_t *d_layer_off, uint32_t max_layers,
+                                           hpeel_stats *h_stats, void *stream) {
+    g_last_error.clear();
+    if (h_stats) memset(h_stats, 0, sizeof *h_stats);
+    if (r < 2 || r > 4) return fail(HPEEL_ERR_INVALID_ARG, "r = %u, need 2 <= r <= 4", r);
+    if (n >= (1ull << 32) || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    if (n > 0 && (m == 0 || m % r != 0))
+        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of r",
+                    (unsigned long long)m);
+    const size_t need = n ? peel_layout(n, m).total : 0;
+    if (need > (size_t)HPEEL_NOALLOC_SCRATCH_BYTES)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL,
+                    "n = %llu, m = %llu needs %zu bytes of scratch; the built-in scratch holds "
+                    "%zu bytes -- use hpeel_peel with a caller workspace",
+                    (unsigned long long)n, (unsigned long long)m, need,
+                    (size_t)HPEEL_NOALLOC_SCRATCH_BYTES);
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    void *scratch = nullptr;
+    HP_TRY(noalloc_scratch(&scratch));
+    if (n == 0) {
+        if (d_layer_off) HP_CUDA(cudaMemsetAsync(d_layer_off, 0, sizeof(uint64_t), L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        return HPEEL_OK;
+    }
+    if (!d_edges || !d_order) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    // Every value the peel reads from the scratch is written earlier in the
+    // same call (the control block, the first layer/frontier offsets and the
+    // vertex records are cleared first), so what a previous call left there
+    // does not matter.  The control block is read back into ordinary host
+    // memory, which needs no pinned allocation.
+    thread_local Ctl readback;
+    PeelOut po{};
+    HP_TRY(peel_core_rb(L, d_edges, (uint32_t)n, (uint32_t)m, r, d_order, d_claim, (char *)scratch,
+                        &po, &readback));
+    if (d_layer_off) {
+        if (po.rounds > max_layers)
+            return fail(HPEEL_ERR_CAPACITY, "%u rounds > max_layers %u", po.rounds, max_layers);
+        launch_layer_off(L, po.loff, po.rounds, d_layer_off);
+        HP_TRY(check_launch("layer_off"));
+    }
+    HP_CUDA(cudaStreamSynchronize(L.stream));
+    prof_flush();
+    if (h_stats) {
+        h_stats->n_peeled = po.n_peeled;
+        h_stats->rounds = po.rounds;
+        h_stats->core_nonempty = po.n_peeled < n;
+        h_stats->first_layer = po.first_layer;
+        h_stats->frontier = po.frontier;
+    }
+    return HPEEL_OK;
+}
