@@ -40,34 +40,40 @@ REF_STEP_KEYS = 10**6          # --impl reference: keys per oracle step
 
 # Algorithmic bytes per unit of work, per step of the path (r = 3).  "sector"
 # charges one 32-byte sector per random access (64 bytes for a read-modify-
-# write), "word" charges only the bytes the method reads and writes.
-# Units: n edges (hash, build, emit, assign), m vertices (fill), round-0
-# vertices m plus first-layer edges (round0), peeled edges (update), frontier
-# vertices of rounds >= 1 (claim).
+# write), "word" charges only the bytes the method reads and writes.  Units:
+# edges (hash, build, extract, emit, assign), vertices (fill, round0),
+# deleted edges (rounds).  A round that streams all records also reads 16 B
+# per edge; a vertex that falls to degree 1 claims its last edge (one random
+# read-modify-write) and may append it (4 B).
 def byte_model(step, n, m, st):
-    L0, Fr, peeled = st["first_layer"], st["frontier"], st["n_peeled"]
-    later = peeled - L0
+    L0, peeled = st["first_layer"], st["n_peeled"]
+    cross, dcross = st["frontier"], st["dense_cross"]
+    dedges, drounds = st["dense_edges"], st["dense_rounds"]
+    sedges, scross = peeled - dedges, cross - dcross
     if step == "hash_edges":
-        return {"units": n, "word": 20 * n, "sector": 20 * n}
+        return {"units": n, "word": 24 * n, "sector": 24 * n}
     if step == "fill":
         return {"units": m, "word": 8 * m, "sector": 8 * m}
     if step == "build_incidence":
-        return {"units": n, "word": (12 + 4 + R * 16) * n, "sector": (12 + 4 + R * 64) * n}
+        return {"units": n, "word": (16 + R * 16) * n, "sector": (16 + R * 64) * n}
     if step == "round0":
-        return {"units": m, "word": 8 * m + (8 + 4) * L0, "sector": 8 * m + (64 + 4) * L0}
-    if step == "update":
-        return {"units": peeled, "word": (4 + 4 + 12 + (R - 1) * 16) * peeled + 4 * Fr,
-                "sector": (4 + 32 + 32 + (R - 1) * 64) * peeled + 4 * Fr}
-    if step == "claim":
-        return {"units": Fr, "word": (4 + 8 + 8) * Fr + 4 * later,
-                "sector": (4 + 32 + 64) * Fr + 4 * later}
+        return {"units": m, "word": 8 * m + 8 * L0, "sector": 8 * m + 64 * L0}
+    if step == "round_dense":
+        return {"units": dedges,
+                "word": 16 * n * drounds + dedges * ((R - 1) * 16 + 16) + dcross * 12,
+                "sector": 16 * n * drounds + dedges * ((R - 1) * 64 + 16) + dcross * 68}
+    if step == "round_sparse":
+        return {"units": sedges,
+                "word": sedges * (4 + 16 + (R - 1) * 16 + 16) + scross * 12,
+                "sector": sedges * (4 + 32 + (R - 1) * 64 + 16) + scross * 68}
+    if step == "extract_claim":
+        return {"units": n, "word": 20 * n, "sector": 20 * n}
     if step == "emit_scatter":
         return {"units": n, "word": 12 * n, "sector": 12 * n}
     if step == "emit_hist":
         return {"units": n, "word": 4 * n, "sector": 4 * n}
     if step == "assign":
-        return {"units": n, "word": (4 + 4 + 12 + 2 * 8 + 16) * n,
-                "sector": (4 + 32 + 32 + 2 * 32 + 64) * n}
+        return {"units": n, "word": (16 + 2 * 8 + 16) * n, "sector": (16 + 2 * 32 + 64) * n}
     return None
 
 
@@ -236,10 +242,12 @@ def main():
     ws = torch.empty(hp.mphf_workspace_size(n, GAMMA_MILLI), dtype=torch.uint8, device="cuda")
     G = torch.empty((m + 31) // 32, dtype=torch.int64, device="cuda")
     D = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device="cuda")
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step():
-        return hp.mphf_build(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D)
+        return hp.mphf_build(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D,
+                             order=order)
 
     def sync_all():
         torch.cuda.synchronize()

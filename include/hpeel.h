@@ -59,8 +59,13 @@ typedef struct hpeel_stats {
     uint32_t attempts;      /* MPHF: hash seeds tried */
     uint32_t device_err;    /* non-zero: code a kernel raised (see status) */
     uint64_t first_layer;   /* |L_0|: edges peeled in round 0 */
-    uint64_t frontier;      /* sum over t >= 1 of |F_t|: vertices that fell to
-                               degree 1 after round 0 (work of later rounds) */
+    uint64_t frontier;      /* vertices that fell from degree 2 to 1 in some
+                               round (the frontiers F_1, F_2, ...) */
+    uint64_t dense_edges;   /* edges deleted by rounds that streamed all edge
+                               records (the others read the layer list) */
+    uint64_t dense_cross;   /* the part of 'frontier' found by those rounds */
+    uint32_t dense_rounds;  /* rounds that streamed all edge records */
+    uint32_t reserved;
 } hpeel_stats;
 
 /* Largest number of rounds a single peel supports (claim words keep the
@@ -68,6 +73,30 @@ typedef struct hpeel_stats {
 #define HPEEL_MAX_ROUNDS (1u << 20)
 /* Claim word of an edge that was not peeled (a 2-core edge). */
 #define HPEEL_UNCLAIMED 0xFFFFFFFFu
+
+/*
+ * Tuning knobs (process-wide; no counterpart in the paper -- they pick among
+ * equivalent schedules and never change a result).
+ *   bucket_shift        log2 of the vertices per chunk of the L2-blocked
+ *                       incidence build (default 22: 32 MiB of vertex
+ *                       records per chunk, about a quarter of GB300's L2).
+ *   bucket_min_vertices graphs with at least this many vertices use the
+ *                       L2-blocked build (default 8 Mi); smaller ones update
+ *                       the vertex records directly.
+ *   dense_div           a round whose layer has more than n / dense_div
+ *                       edges streams all edge records instead of reading
+ *                       the layer list (default 12).
+ * hpeel_set_tuning(NULL) restores the defaults.  Workspace sizes depend on
+ * the tuning: query them after setting it.  Errors: HPEEL_ERR_INVALID_ARG.
+ */
+typedef struct hpeel_tuning {
+    uint32_t bucket_shift;
+    uint32_t bucket_min_vertices;
+    uint32_t dense_div;
+    uint32_t reserved[5];
+} hpeel_tuning;
+hpeel_status hpeel_set_tuning(const hpeel_tuning *t);
+void hpeel_get_tuning(hpeel_tuning *t);
 
 /* Static description of a status code. */
 const char *hpeel_status_str(hpeel_status s);
@@ -143,7 +172,7 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m,
  * cudaMalloc, cudaFree or other device allocation.
  *   - Size limit: the call fails with HPEEL_ERR_WORKSPACE_TOO_SMALL (and
  *     launches nothing) when hpeel_peel_workspace_size(n, m, r) exceeds
- *     HPEEL_NOALLOC_SCRATCH_BYTES -- about 540,000 edges at gamma = 1.23,
+ *     HPEEL_NOALLOC_SCRATCH_BYTES -- about 440,000 edges at gamma = 1.23,
  *     r = 3.  Larger graphs need hpeel_peel and a caller workspace.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before
@@ -181,6 +210,9 @@ size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli);
  *             non-zero 2-bit values among vertices [0, 512 b).
  *   MPHF(x) = d_rank_dir[v/512] + non-zero values in [512 (v/512), v), with
  *   v = h_i(x), i = (G[h_0(x)] + G[h_1(x)] + G[h_2(x)]) mod 3.
+ *   d_order   [n] uint32 output or NULL: the canonical peeling order of the
+ *             successful attempt's hypergraph (as hpeel_peel gives it), so
+ *             the whole path can be checked; NULL skips that sort.
  *   h_stats   host output or NULL (seed_used, attempts, rounds).
  * Synchronises stream.  Errors: HPEEL_ERR_INVALID_ARG,
  * HPEEL_ERR_WORKSPACE_TOO_SMALL, HPEEL_ERR_RETRIES_EXHAUSTED,
@@ -188,7 +220,7 @@ size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli);
  */
 hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
                               uint32_t gamma_milli, uint32_t max_tries,
-                              uint64_t *d_G, uint64_t *d_rank_dir,
+                              uint64_t *d_G, uint64_t *d_rank_dir, uint32_t *d_order,
                               hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
                               void *stream);
 

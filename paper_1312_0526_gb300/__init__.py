@@ -43,11 +43,18 @@ class HpeelError(RuntimeError):
         self.status = status
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("bucket_shift", ctypes.c_uint32), ("bucket_min_vertices", ctypes.c_uint32),
+                ("dense_div", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("n_peeled", ctypes.c_uint64), ("rounds", ctypes.c_uint32),
                 ("core_nonempty", ctypes.c_uint32), ("seed_used", ctypes.c_uint64),
                 ("attempts", ctypes.c_uint32), ("device_err", ctypes.c_uint32),
-                ("first_layer", ctypes.c_uint64), ("frontier", ctypes.c_uint64)]
+                ("first_layer", ctypes.c_uint64), ("frontier", ctypes.c_uint64),
+                ("dense_edges", ctypes.c_uint64), ("dense_cross", ctypes.c_uint64),
+                ("dense_rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -85,9 +92,14 @@ def lib():
         L.hpeel_mphf_workspace_size.restype = sz
         L.hpeel_mphf_workspace_size.argtypes = [u64, u32]
         L.hpeel_mphf_build.restype = st
-        L.hpeel_mphf_build.argtypes = [p, u64, u64, u32, u32, p, p, ctypes.POINTER(Stats), p, sz, p]
+        L.hpeel_mphf_build.argtypes = [p, u64, u64, u32, u32, p, p, p, ctypes.POINTER(Stats), p,
+                                       sz, p]
         L.hpeel_peel_noalloc.restype = st
         L.hpeel_peel_noalloc.argtypes = [p, u64, u64, u32, p, p, p, u32, ctypes.POINTER(Stats), p]
+        L.hpeel_set_tuning.restype = st
+        L.hpeel_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
+        L.hpeel_get_tuning.restype = None
+        L.hpeel_get_tuning.argtypes = [ctypes.POINTER(Tuning)]
         L.hpeel_kernel_launches.restype = u64
         L.hpeel_kernel_launches.argtypes = []
         L.hpeel_profile_enable.restype = None
@@ -230,7 +242,7 @@ def mphf_workspace_size(n: int, gamma_milli: int = 1230) -> int:
 
 
 def mphf_build(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
-               workspace=None, G=None, rank_dir=None) -> MphfResult:
+               workspace=None, G=None, rank_dir=None, order=None) -> MphfResult:
     """MWHC MPHF build (sec. 3) with reseed-and-retry; see hpeel_mphf_build."""
     torch = _torch()
     kp = _dev_ptr(keys, "keys", torch.int64, 1)
@@ -243,12 +255,19 @@ def mphf_build(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
         rank_dir = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device=dev)
     ws = workspace if workspace is not None else _workspace(mphf_workspace_size(n, gamma_milli), dev)
     st = Stats()
+    op = None
+    if order is not None:
+        op = _dev_ptr(order, "order", torch.int32, 1)
+        if order.numel() != n:
+            raise ValueError("order must hold n entries")
     _check(lib().hpeel_mphf_build(kp, n, seed, gamma_milli, max_tries,
                                   _dev_ptr(G, "G", torch.int64), _dev_ptr(rank_dir, "rank_dir",
                                                                           torch.int64),
-                                  ctypes.byref(st), _dev_ptr(ws, "workspace", torch.uint8),
+                                  op, ctypes.byref(st), _dev_ptr(ws, "workspace", torch.uint8),
                                   ws.numel(), _stream()))
-    return MphfResult(G[:(m + 31) // 32], rank_dir, m, st.as_dict())
+    res = MphfResult(G[:(m + 31) // 32], rank_dir, m, st.as_dict())
+    res.order = order
+    return res
 
 
 def kernel_launches() -> int:
@@ -275,3 +294,21 @@ def profile_read() -> dict:
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out
+
+
+def get_tuning() -> dict:
+    t = Tuning()
+    lib().hpeel_get_tuning(ctypes.byref(t))
+    return {"bucket_shift": t.bucket_shift, "bucket_min_vertices": t.bucket_min_vertices,
+            "dense_div": t.dense_div}
+
+
+def set_tuning(**kw) -> None:
+    """Set tuning knobs (see hpeel_set_tuning); no arguments restores defaults."""
+    if not kw:
+        _check(lib().hpeel_set_tuning(None))
+        return
+    cur = get_tuning()
+    cur.update(kw)
+    t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["dense_div"])
+    _check(lib().hpeel_set_tuning(ctypes.byref(t)))

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -83,12 +84,28 @@ Ctl *pinned_ctl() {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct PeelLayout {
-    size_t ctl, state, claim, L, F, loff, foff, hist, scantmp, total;
+    size_t ctl, rec, state, claim, L, S, pairs, fill, loff, hist, scantmp, total;
     uint32_t max_rounds;
+    bool bucketed;
+    BucketPlan plan;
 };
 
-PeelLayout peel_layout(uint64_t n, uint64_t m) {
+// Process-wide tuning (hpeel_set_tuning); read by layouts and launches.
+hpeel_tuning g_tuning = {22u, 8u << 20, 12u, {0, 0, 0, 0, 0}};
+std::mutex g_tuning_mu;
+
+hpeel_tuning tuning() {
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    return g_tuning;
+}
+
+// Workspace of one peel: edge records, vertex records, claim words, layer
+// list, optional MWHC solve records, incidence buckets of the L2-blocked
+// build (sharing space with the layer list and solve records, which are
+// written only after the build), layer table, order-sort scratch.
+PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool with_s) {
     PeelLayout p{};
+    const hpeel_tuning tu = tuning();
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -96,13 +113,20 @@ PeelLayout peel_layout(uint64_t n, uint64_t m) {
         return o;
     };
     p.max_rounds = (uint32_t)std::min<uint64_t>(HPEEL_MAX_ROUNDS, n + 1);
+    p.bucketed = n > 0 && m >= tu.bucket_min_vertices;
+    if (p.bucketed) p.plan = bucket_plan(n, m, r, tu.bucket_shift);
     p.ctl = take(sizeof(Ctl));
+    p.rec = take((r == 4 ? 32 : 16) * n);
     p.state = take(8 * m);
     p.claim = take(4 * n);
-    p.L = take(4 * n);
-    p.F = take(4 * m);
-    p.loff = take(4 * ((size_t)p.max_rounds + 2));
-    p.foff = take(4 * ((size_t)p.max_rounds + 2));
+    const size_t ls = align256(4 * n) + (with_s ? 16 * n : 0);
+    const size_t shared = std::max<size_t>(ls, p.bucketed ? p.plan.pair_bytes : 0);
+    const size_t region = take(shared);
+    p.L = region;
+    p.S = region + align256(4 * n);
+    p.pairs = region;
+    p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks : 0);
+    p.loff = take(4 * ((size_t)p.max_rounds + 3));
     const uint64_t tiles = (n + kEmitTile - 1) / kEmitTile;
     p.hist = take(4 * kEmitBins * tiles);
     p.scantmp = take(4 * scan_tmp_words(kEmitBins * tiles));
@@ -111,7 +135,7 @@ PeelLayout peel_layout(uint64_t n, uint64_t m) {
 }
 
 struct MphfLayout {
-    size_t edges, order, claim, rank_cnt, rank_scan, rank_tmp, peel, total;
+    size_t rank_cnt, rank_scan, rank_tmp, peel, total;
     uint64_t m;
 };
 
@@ -125,14 +149,11 @@ MphfLayout mphf_layout(uint64_t n, uint32_t gamma_milli) {
         return o;
     };
     const uint64_t blocks = (p.m + 511) / 512;
-    p.edges = take(12 * n);
-    p.order = take(4 * n);
-    p.claim = take(4 * n);
     p.rank_cnt = take(4 * blocks + 4);
     p.rank_scan = take(4 * blocks + 4);
     p.rank_tmp = take(4 * scan_tmp_words(blocks));
     p.peel = off;
-    p.total = off + peel_layout(n, p.m).total;
+    p.total = off + peel_layout(n, p.m, 3, true).total;
     return p;
 }
 
@@ -141,74 +162,121 @@ struct PeelOut {
     uint64_t n_peeled;
     uint64_t first_layer;
     uint64_t frontier;
-    uint32_t *loff;  // device layer table (uint32[rounds + 1])
+    uint64_t dense_edges;
+    uint64_t dense_cross;
+    uint32_t dense_rounds;
+    uint32_t *loff;  // device layer table (uint32[rounds + 2])
+    uint4 *S;        // device solve records (MPHF, sparse layers)
+    uint4 *rec;      // device edge records
+    std::vector<uint8_t> dense;  // per round: layer deleted by a record stream
 };
 
-// Round-synchronous peel of device edges into order/claim (sec. 4.2).
+// What a peel starts from and what it must produce.
+struct PeelIO {
+    const uint32_t *edges = nullptr;  // row-major [n][r] input, or
+    const uint64_t *keys = nullptr;   // keys hashed with (seed, fm) into records
+    uint64_t seed = 0;
+    FastMod fm{0, 0};
+    uint32_t *order = nullptr;  // canonical order output (nullptr: not needed)
+    uint32_t *claim = nullptr;  // claim-word output (nullptr: workspace)
+    bool with_s = false;        // write MWHC solve records (r = 3)
+};
+
+// A layer is deleted by streaming all edge records once it holds more than
+// n / kDenseDiv edges (a random record access costs about as much as
+// streaming 12 records).
+
+// Round-synchronous peel (sec. 4.2) of n edges on m vertices.
 // hctl: host memory the control block is read back into after every round.
-hpeel_status peel_core_rb(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t m,
-                          uint32_t r, uint32_t *order, uint32_t *claim_user, char *ws,
-                          PeelOut *out, Ctl *hctl) {
-    const PeelLayout lay = peel_layout(n, m);
+hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_t m, uint32_t r,
+                          char *ws, PeelOut *out, Ctl *hctl) {
+    const PeelLayout lay = peel_layout(n, m, r, io.with_s);
+    const hpeel_tuning tu = tuning();
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
-    uint32_t *state = reinterpret_cast<uint32_t *>(ws + lay.state);
-    uint32_t *claim = claim_user ? claim_user : reinterpret_cast<uint32_t *>(ws + lay.claim);
+    uint4 *rec = reinterpret_cast<uint4 *>(ws + lay.rec);
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(ws + lay.state);
+    uint32_t *claim = io.claim ? io.claim : reinterpret_cast<uint32_t *>(ws + lay.claim);
     uint32_t *Ll = reinterpret_cast<uint32_t *>(ws + lay.L);
-    uint32_t *F = reinterpret_cast<uint32_t *>(ws + lay.F);
+    uint4 *S = io.with_s ? reinterpret_cast<uint4 *>(ws + lay.S) : nullptr;
     uint32_t *loff = reinterpret_cast<uint32_t *>(ws + lay.loff);
-    uint32_t *foff = reinterpret_cast<uint32_t *>(ws + lay.foff);
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + lay.hist);
     uint32_t *scantmp = reinterpret_cast<uint32_t *>(ws + lay.scantmp);
     const uint32_t P = m / r;
 
     HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), L.stream));
-    HP_CUDA(cudaMemsetAsync(loff, 0, 2 * sizeof(uint32_t), L.stream));
-    HP_CUDA(cudaMemsetAsync(foff, 0, 2 * sizeof(uint32_t), L.stream));
     {
         ProfScope ps(L, "fill");
-        launch_fill_u32(L, state, 2ull * m, 0u);
+        launch_fill_u32(L, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
     }
-    {
+    if (lay.bucketed) {
+        uint2 *pairs = reinterpret_cast<uint2 *>(ws + lay.pairs);
+        uint32_t *fill = reinterpret_cast<uint32_t *>(ws + lay.fill);
+        HP_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)lay.plan.chunks, L.stream));
+        ProfScope ps(L, io.keys ? "hash_bucket" : "records_bucket");
+        launch_build_bucketed(L, lay.plan, io.keys, io.edges, n, r, io.fm, io.seed, P, rec, pairs,
+                              fill, st, ctl);
+    } else {
+        if (io.keys) {
+            ProfScope ps(L, "hash_edges");
+            launch_hash_records(L, io.keys, n, r, io.fm, io.seed, rec);
+        } else {
+            ProfScope ps(L, "records");
+            launch_records(L, io.edges, n, r, P, rec, ctl);
+        }
         ProfScope ps(L, "build_incidence");
-        launch_build_incidence(L, edges, n, r, P, state, claim, ctl);
+        launch_build_incidence(L, rec, n, r, m, st, ctl);
     }
     {
         ProfScope ps(L, "round0");
-        launch_round0(L, state, m, r, P, n, claim, Ll, ctl);
+        launch_round0(L, st, m, r, P, n, rec, loff, ctl);
     }
     HP_TRY(check_launch("build/round0"));
+    HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
+    HP_CUDA(cudaStreamSynchronize(L.stream));
+    if (hctl->err)
+        return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u (build)", hctl->err);
+    out->first_layer = hctl->next_size;
 
-    uint32_t t = 0;
-    for (;;) {
-        if (t + 1 >= lay.max_rounds)
-            return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds - 1);
+    uint32_t R = 0;
+    for (uint32_t t = 0; hctl->more; t++) {
+        if (t + 2 >= lay.max_rounds + 3)
+            return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds);
+        const bool dense = t == 0 || hctl->next_size > n / std::max(1u, tu.dense_div);
+        const uint32_t layer = hctl->next_size, cross0 = hctl->cross;
         {
-            ProfScope ps(L, "update");
-            launch_update(L, edges, r, m, claim, state, Ll, F, loff, foff, ctl);
+            ProfScope ps(L, dense ? "round_dense" : "round_sparse");
+            launch_round(L, dense, io.with_s, r, Ll, loff, n, st, rec, S, ctl);
         }
-        HP_TRY(check_launch("update"));
+        HP_TRY(check_launch("round"));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
         if (hctl->err)
             return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u (round %u)",
                         hctl->err, t);
-        if (t == 0) out->first_layer = hctl->last_layer;
-        if (!hctl->more) break;
-        {
-            ProfScope ps(L, "claim");
-            launch_claim(L, state, r, P, n, claim, F, Ll, foff, ctl);
+        out->dense.push_back(dense ? 1 : 0);
+        if (dense) {
+            out->dense_rounds += 1;
+            out->dense_edges += layer;
+            out->dense_cross += hctl->cross - cross0;
         }
-        HP_TRY(check_launch("claim"));
-        t++;
+        R = t + 1;
     }
-    const uint32_t R = hctl->last_layer ? t + 1 : t;
-    const uint64_t peeled = hctl->lcur;
     out->rounds = R;
-    out->n_peeled = peeled;
-    out->frontier = hctl->fcur;
+    out->n_peeled = hctl->lcur;
+    out->frontier = hctl->cross;
     out->loff = loff;
+    out->S = S;
+    out->rec = rec;
+
+    if (!io.order && !io.claim) return HPEEL_OK;
+    {
+        ProfScope ps(L, "extract_claim");
+        launch_extract_claim(L, rec, n, r, claim);
+    }
+    if (!io.order) return check_launch("extract_claim");
 
     // Canonical order: stable sort by key = round, core edges key R.
+    uint32_t *order = io.order;
     const uint32_t nkeys = R + 1;
     uint32_t base = 0, seg = 0;
     const uint32_t *src = nullptr;
@@ -249,11 +317,11 @@ hpeel_status peel_core_rb(const Launch &L, const uint32_t *edges, uint32_t n, ui
     return HPEEL_OK;
 }
 
-hpeel_status peel_core(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t m, uint32_t r,
-                       uint32_t *order, uint32_t *claim_user, char *ws, PeelOut *out) {
+hpeel_status peel_core(const Launch &L, const PeelIO &io, uint32_t n, uint32_t m, uint32_t r,
+                       char *ws, PeelOut *out) {
     Ctl *hctl = pinned_ctl();
     if (!hctl) return fail(HPEEL_ERR_CUDA, "cudaMallocHost of the control read-back failed");
-    return peel_core_rb(L, edges, n, m, r, order, claim_user, ws, out, hctl);
+    return peel_core_rb(L, io, n, m, r, ws, out, hctl);
 }
 
 }  // namespace
@@ -276,6 +344,24 @@ const char *hpeel_status_str(hpeel_status s) {
 }
 
 const char *hpeel_last_error(void) { return g_last_error.c_str(); }
+
+hpeel_status hpeel_set_tuning(const hpeel_tuning *t) {
+    g_last_error.clear();
+    hpeel_tuning v = {22u, 8u << 20, 12u, {0, 0, 0, 0, 0}};
+    if (t) {
+        if (t->bucket_shift < 8 || t->bucket_shift > 30)
+            return fail(HPEEL_ERR_INVALID_ARG, "bucket_shift %u outside [8, 30]", t->bucket_shift);
+        if (t->dense_div == 0) return fail(HPEEL_ERR_INVALID_ARG, "dense_div must be positive");
+        v = *t;
+    }
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    g_tuning = v;
+    return HPEEL_OK;
+}
+
+void hpeel_get_tuning(hpeel_tuning *t) {
+    if (t) *t = tuning();
+}
 
 int hpeel_version(void) { return 100; }
 
@@ -304,8 +390,7 @@ hpeel_status hpeel_hash_edges(const uint64_t *d_keys, uint64_t n, uint64_t m, ui
 }
 
 size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r) {
-    (void)r;
-    return peel_layout(n, m).total;
+    return peel_layout(n, m, r, false).total;
 }
 
 hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
@@ -330,11 +415,15 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
     if (!d_edges || !d_order || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
     if (((uintptr_t)d_ws & 255u) != 0)
         return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    if (ws_bytes < peel_layout(n, m).total)
-        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
-                    peel_layout(n, m).total);
+    const size_t need = peel_layout(n, m, r, false).total;
+    if (ws_bytes < need)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes, need);
     PeelOut po{};
-    HP_TRY(peel_core(L, d_edges, (uint32_t)n, (uint32_t)m, r, d_order, d_claim, (char *)d_ws, &po));
+    PeelIO io;
+    io.edges = d_edges;
+    io.order = d_order;
+    io.claim = d_claim;
+    HP_TRY(peel_core(L, io, (uint32_t)n, (uint32_t)m, r, (char *)d_ws, &po));
     if (d_layer_off) {
         if (po.rounds > max_layers)
             return fail(HPEEL_ERR_CAPACITY, "%u rounds > max_layers %u", po.rounds, max_layers);
@@ -349,6 +438,9 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
         h_stats->core_nonempty = po.n_peeled < n;
         h_stats->first_layer = po.first_layer;
         h_stats->frontier = po.frontier;
+        h_stats->dense_edges = po.dense_edges;
+        h_stats->dense_cross = po.dense_cross;
+        h_stats->dense_rounds = po.dense_rounds;
     }
     return HPEEL_OK;
 }
@@ -359,8 +451,8 @@ size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli) {
 
 hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
                               uint32_t gamma_milli, uint32_t max_tries, uint64_t *d_G,
-                              uint64_t *d_rank_dir, hpeel_stats *h_stats, void *d_ws,
-                              size_t ws_bytes, void *stream) {
+                              uint64_t *d_rank_dir, uint32_t *d_order, hpeel_stats *h_stats,
+                              void *d_ws, size_t ws_bytes, void *stream) {
     g_last_error.clear();
     if (h_stats) memset(h_stats, 0, sizeof *h_stats);
     if (gamma_milli == 0) return fail(HPEEL_ERR_INVALID_ARG, "gamma_milli must be positive");
@@ -385,19 +477,17 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
         return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
                     lay.total);
     char *ws = (char *)d_ws;
-    uint32_t *edges = reinterpret_cast<uint32_t *>(ws + lay.edges);
-    uint32_t *order = reinterpret_cast<uint32_t *>(ws + lay.order);
-    uint32_t *claim = reinterpret_cast<uint32_t *>(ws + lay.claim);
     const FastMod fm = make_fastmod(m / 3);
     for (uint32_t a = 0; a < max_tries; a++) {
         const uint64_t s = seed + a;
-        {
-            ProfScope ps(L, "hash_edges");
-            launch_hash_edges(L, d_keys, n, 3, fm, s, edges);
-        }
-        HP_TRY(check_launch("hash_edges"));
         PeelOut po{};
-        HP_TRY(peel_core(L, edges, (uint32_t)n, (uint32_t)m, 3, order, claim, ws + lay.peel, &po));
+        PeelIO io;
+        io.keys = d_keys;
+        io.seed = s;
+        io.fm = fm;
+        io.order = d_order;
+        io.with_s = true;
+        HP_TRY(peel_core(L, io, (uint32_t)n, (uint32_t)m, 3, ws + lay.peel, &po));
         if (h_stats) {
             h_stats->attempts = a + 1;
             h_stats->rounds = po.rounds;
@@ -405,6 +495,9 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
             h_stats->core_nonempty = po.n_peeled < n;
             h_stats->first_layer = po.first_layer;
             h_stats->frontier = po.frontier;
+        h_stats->dense_edges = po.dense_edges;
+        h_stats->dense_cross = po.dense_cross;
+        h_stats->dense_rounds = po.dense_rounds;
         }
         if (po.n_peeled < n) continue;
         // a8: reverse layer order
@@ -412,7 +505,8 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
         HP_CUDA(cudaMemsetAsync(d_G, 0, 8 * words, L.stream));
         for (int64_t t = (int64_t)po.rounds - 1; t >= 0; t--) {
             ProfScope ps(L, "assign");
-            launch_assign_layer(L, edges, claim, order, po.loff, (uint32_t)t, d_G);
+            launch_assign_layer(L, po.dense[t] != 0, po.S, po.rec, (uint32_t)n, po.loff,
+                                (uint32_t)t, d_G);
         }
         HP_TRY(check_launch("assign"));
         // a9: rank directory
@@ -491,7 +585,7 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
     if (n > 0 && (m == 0 || m % r != 0))
         return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of r",
                     (unsigned long long)m);
-    const size_t need = n ? peel_layout(n, m).total : 0;
+    const size_t need = n ? peel_layout(n, m, r, false).total : 0;
     if (need > (size_t)HPEEL_NOALLOC_SCRATCH_BYTES)
         return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL,
                     "n = %llu, m = %llu needs %zu bytes of scratch; the built-in scratch holds "
@@ -515,8 +609,11 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
     // memory, which needs no pinned allocation.
     thread_local Ctl readback;
     PeelOut po{};
-    HP_TRY(peel_core_rb(L, d_edges, (uint32_t)n, (uint32_t)m, r, d_order, d_claim, (char *)scratch,
-                        &po, &readback));
+    PeelIO io;
+    io.edges = d_edges;
+    io.order = d_order;
+    io.claim = d_claim;
+    HP_TRY(peel_core_rb(L, io, (uint32_t)n, (uint32_t)m, r, (char *)scratch, &po, &readback));
     if (d_layer_off) {
         if (po.rounds > max_layers)
             return fail(HPEEL_ERR_CAPACITY, "%u rounds > max_layers %u", po.rounds, max_layers);
@@ -531,6 +628,9 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
         h_stats->core_nonempty = po.n_peeled < n;
         h_stats->first_layer = po.first_layer;
         h_stats->frontier = po.frontier;
+        h_stats->dense_edges = po.dense_edges;
+        h_stats->dense_cross = po.dense_cross;
+        h_stats->dense_rounds = po.dense_rounds;
     }
     return HPEEL_OK;
 }

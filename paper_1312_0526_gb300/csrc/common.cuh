@@ -25,9 +25,11 @@ struct Ctl {
     uint32_t round;      // index t of the round being run
     uint32_t done;       // blocks finished in the current update launch
     uint32_t err;        // first device error code (0 = none)
-    uint32_t more;       // 1 while the next frontier is non-empty
-    uint32_t last_layer; // size of the layer the last update launch deleted
-    uint32_t pad;
+    uint32_t more;       // 1 while the next layer is non-empty
+    uint32_t next_size;  // size of the layer the next round deletes
+    uint32_t scur;       // solve-record cursor of a dense round
+    uint32_t cross;      // vertices that fell from degree 2 to 1 (all rounds)
+    uint32_t pad[6];
 };
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): two
@@ -86,6 +88,75 @@ __device__ __forceinline__ void warp_append(uint32_t *cursor, uint32_t *list, bo
     if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = value;
 }
 
+// ---- edge records ------------------------------------------------------
+// Edge e: one uint4 {v_0, v_1, v_2, claim} for r <= 3 (v_2 = 0 when r = 2),
+// two uint4 {v_0..v_3}, {claim, 0, 0, 0} for r = 4.
+template <int R>
+__device__ __forceinline__ uint32_t *claim_ptr(uint4 *rec, uint64_t e) {
+    return R == 4 ? &rec[2 * e + 1].x : &rec[e].w;
+}
+
+template <int R>
+__device__ __forceinline__ void store_record(uint4 *rec, uint64_t e, const uint32_t (&v)[4],
+                                             bool valid) {
+    // an invalid edge keeps vertex 0 everywhere: memory-safe, flagged by the caller
+    const uint32_t a = valid ? v[0] : 0u, b = valid ? v[1] : 0u;
+    const uint32_t c = valid ? v[2] : 0u, d = valid ? v[3] : 0u;
+    if (R == 4) {
+        rec[2 * e] = make_uint4(a, b, c, d);
+        rec[2 * e + 1] = make_uint4(kUnclaimed, 0u, 0u, 0u);
+    } else {
+        rec[e] = make_uint4(a, b, R == 3 ? c : 0u, kUnclaimed);
+    }
+}
+
+// Vertices only (immutable once written): streaming load.
+template <int R>
+__device__ __forceinline__ void load_vertices(const uint4 *rec, uint64_t e, uint32_t (&v)[4]) {
+    const uint4 q = __ldcs(rec + (R == 4 ? 2 * e : e));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+
+// Vertices and claim word (random access).
+template <int R>
+__device__ __forceinline__ uint32_t load_record(const uint4 *rec, uint64_t e, uint32_t (&v)[4]) {
+    if (R == 4) {
+        const uint4 q = rec[2 * e], c = rec[2 * e + 1];
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        return c.x;
+    }
+    const uint4 q = rec[e];
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = 0u;
+    return q.w;
+}
+
+// Same, for a pass that streams every record once.
+template <int R>
+__device__ __forceinline__ uint32_t load_record_stream(const uint4 *rec, uint64_t e,
+                                                       uint32_t (&v)[4]) {
+    if (R == 4) {
+        const uint4 q = __ldcs(rec + 2 * e), c = __ldcs(rec + 2 * e + 1);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        return c.x;
+    }
+    const uint4 q = __ldcs(rec + e);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = 0u;
+    return q.w;
+}
+
+// MWHC solve record of a peeled edge (r = 3): {v_hinge, v_a, v_b, hinge},
+// a < b the two other positions.
+__device__ __forceinline__ uint4 solve_record(uint32_t c, const uint32_t (&v)[4]) {
+    const uint32_t h = c & 3u;
+    const uint32_t vh = h == 0 ? v[0] : (h == 1 ? v[1] : v[2]);
+    const uint32_t va = h == 0 ? v[1] : v[0];
+    const uint32_t vb = h == 2 ? v[1] : v[2];
+    return make_uint4(vh, va, vb, h);
+}
+
 // Block-aggregated append: every thread of the block calls this (it holds
 // barriers) with K candidates; the block reserves all its slots with a single
 // atomicAdd, so the shared cursor sees one atomic per K * blockDim items.
@@ -123,6 +194,67 @@ __device__ __forceinline__ void block_append(uint32_t *cursor, uint32_t *list, c
     for (int k = 0; k < K; k++)
         if (pred[k]) list[pos++] = val[k];
     __syncthreads();
+}
+
+// Per-warp staging buffer in shared memory for list appends: lanes push
+// values (warp-synchronous), and the warp reserves space in the global list
+// with one atomicAdd per CAP values (flush when full and at the end), so the
+// shared list cursor sees few atomics however many values are appended.  The
+// order of the values in the list is unspecified.
+template <int CAP>
+struct WarpStage {
+    uint32_t *buf;  // this warp's CAP slots in shared memory
+    uint32_t cnt;   // values staged (warp-uniform)
+
+    __device__ __forceinline__ void flush(uint32_t *cursor, uint32_t *list) {
+        __syncwarp();
+        if (cnt == 0) return;
+        const uint32_t lane = threadIdx.x & 31u;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(cursor, cnt);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        for (uint32_t i = lane; i < cnt; i += 32) list[base + i] = buf[i];
+        cnt = 0;
+        __syncwarp();
+    }
+    // every lane of the warp calls push (convergent)
+    __device__ __forceinline__ void push(bool pred, uint32_t val, uint32_t *cursor,
+                                         uint32_t *list) {
+        const uint32_t lane = threadIdx.x & 31u;
+        const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, pred);
+        if (ballot == 0) return;
+        const uint32_t k = __popc(ballot);
+        if (cnt + k > CAP) flush(cursor, list);
+        if (pred) buf[cnt + __popc(ballot & ((1u << lane) - 1u))] = val;
+        cnt += k;
+        __syncwarp();
+    }
+};
+
+// Block-aggregated reservation of one slot per thread with pred: returns the
+// slot (unspecified order) for those threads; one atomicAdd per block call.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_reserve(uint32_t *cursor, bool pred) {
+    __shared__ uint32_t warp_base[THREADS / 32];
+    __shared__ uint32_t block_base;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, pred);
+    if (lane == 0) warp_base[warp] = __popc(ballot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < THREADS / 32; w++) {
+            const uint32_t c = warp_base[w];
+            warp_base[w] = s;
+            s += c;
+        }
+        block_base = s ? atomicAdd(cursor, s) : 0u;
+    }
+    __syncthreads();
+    const uint32_t pos = block_base + warp_base[warp] + __popc(ballot & ((1u << lane) - 1u));
+    __syncthreads();
+    return pos;
 }
 
 }  // namespace hp

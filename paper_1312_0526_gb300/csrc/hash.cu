@@ -53,4 +53,33 @@ void launch_hash_edges(const Launch &L, const uint64_t *keys, uint64_t n, uint32
     }
 }
 
+// Keys -> edge records {v_0, v_1, v_2, unclaimed} (the MPHF path keeps its
+// edges only as records): one 16-byte coalesced store per key.
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_hash_records(const uint64_t *__restrict__ keys, uint64_t n, FastMod fm, uint64_t seed,
+               uint4 *__restrict__ rec) {
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    const uint32_t P = (uint32_t)fm.P;
+    for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = __ldcs(keys + i);
+        uint32_t v[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < R; j++)
+            v[j] = (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) + (uint32_t)j * P;
+        store_record<R>(rec, i, v, true);
+    }
+}
+
+void launch_hash_records(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
+                         FastMod fm, uint64_t seed, uint4 *rec) {
+    if (n == 0) return;
+    const unsigned grid = grid_for(L, n, 1, 8);
+    switch (r) {
+    case 2: count_launch(); k_hash_records<2><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, rec); break;
+    case 3: count_launch(); k_hash_records<3><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, rec); break;
+    case 4: count_launch(); k_hash_records<4><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, rec); break;
+    }
+}
+
 }  // namespace hp

@@ -42,33 +42,54 @@ inline unsigned grid_for(const Launch &L, uint64_t work, int per_thread, int per
     return (unsigned)blocks;
 }
 
-// a1: keys -> r-partite edges.
+// a1: keys -> r-partite edges (row-major rows, or edge records).
 void launch_hash_edges(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
                        FastMod fm, uint64_t seed, uint32_t *edges);
+void launch_hash_records(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
+                         FastMod fm, uint64_t seed, uint4 *rec);
 
 // fill count 32-bit words with value.
 void launch_fill_u32(const Launch &L, uint32_t *p, uint64_t count, uint32_t value);
 
-// a2: degree / XOR-of-edge-ids records (state[2v] = deg, state[2v+1] = xor),
-// claim[e] = unclaimed.
-void launch_build_incidence(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t r,
-                            uint32_t P, uint32_t *state, uint32_t *claim, Ctl *ctl);
+// Row-major edges -> edge records (checks the r-partite ranges).
+void launch_records(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t r, uint32_t P,
+                    uint4 *rec, Ctl *ctl);
 
-// a3 + a4 for round 0: scan all vertices, claim the edge of every degree-1
-// vertex, append first claims to L.
-void launch_round0(const Launch &L, const uint32_t *state, uint32_t m, uint32_t r, uint32_t P,
-                   uint32_t n, uint32_t *claim, uint32_t *Llist, Ctl *ctl);
+// a2: vertex records {deg, sum of incident edge ids} from the edge records.
+void launch_build_incidence(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                            uint32_t m, unsigned long long *st, Ctl *ctl);
 
-// a4 for round t >= 1 (t read on the device): claim edges of F_t.
-void launch_claim(const Launch &L, const uint32_t *state, uint32_t r, uint32_t P, uint32_t n,
-                  uint32_t *claim, const uint32_t *F, uint32_t *Llist, uint32_t *foff,
+// a2, L2-blocked (build.cu): records + incidences bucketed by vertex chunk,
+// then the buckets applied chunk by chunk.
+struct BucketPlan {
+    uint32_t shift;            // log2 vertices per chunk
+    uint32_t chunks_per_part;
+    uint32_t chunks;
+    uint32_t cap;              // incidences per bucket
+    uint64_t pair_bytes;       // bucket storage
+    size_t smem;               // dynamic shared memory of the bucketing kernel
+};
+BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift);
+void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
+                           const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
+                           uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
+                           unsigned long long *st, Ctl *ctl);
+
+// a3 + a4 of round 0: scan all vertices, claim the edge of every degree-1
+// vertex; publishes loff[0..1].
+void launch_round0(const Launch &L, const unsigned long long *st, uint32_t m, uint32_t r,
+                   uint32_t P, uint32_t n, uint4 *rec, uint32_t *loff, Ctl *ctl);
+
+// a5 + a4 of the next round + a6: delete layer t (t read on the device),
+// claim and list layer t+1, close the round.  with_s: write MWHC solve
+// records (r = 3).
+void launch_round(const Launch &L, bool dense, bool with_s, uint32_t r, uint32_t *Llist,
+                  uint32_t *loff, uint32_t n, unsigned long long *st, uint4 *rec, uint4 *S,
                   Ctl *ctl);
 
-// a5 + a6: delete the edges of L_t from their non-hinge vertices, append
-// vertices that fall to degree 1 to F_{t+1}; the last block advances t.
-void launch_update(const Launch &L, const uint32_t *edges, uint32_t r, uint32_t m,
-                   const uint32_t *claim, uint32_t *state, const uint32_t *Llist, uint32_t *F,
-                   uint32_t *loff, const uint32_t *foff, Ctl *ctl);
+// claim[e] = claim word of record e.
+void launch_extract_claim(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                          uint32_t *claim);
 
 // a7: one pass of the stable counting sort of edge ids by round.
 void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, const uint32_t *claim,
@@ -83,9 +104,10 @@ size_t scan_tmp_words(uint64_t count);
 void launch_scan_u32(const Launch &L, const uint32_t *in, uint32_t *out, uint64_t count,
                      uint32_t *tmp);
 
-// a8: MWHC assignment of one layer t (host loop runs t = R-1 .. 0).
-void launch_assign_layer(const Launch &L, const uint32_t *edges, const uint32_t *claim,
-                         const uint32_t *order, const uint32_t *loff, uint32_t t, uint64_t *G);
+// a8: MWHC assignment of one layer t from its solve records (host loop runs
+// t = R-1 .. 0).
+void launch_assign_layer(const Launch &L, bool dense, const uint4 *S, const uint4 *rec,
+                         uint32_t n, const uint32_t *loff, uint32_t t, uint64_t *G);
 // a9: per-512-vertex counts of non-zero 2-bit values, then the directory.
 void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt);
 void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,

@@ -1,25 +1,37 @@
 // peel.cu -- packed incidence build and round-synchronous peeling.
 //
-// State: one 8-byte record per vertex, {deg, xor of incident edge ids}
-// (sec. 4.1, the labelled packed incidence list with the edge id as label).
-// Round t (sec. 4.2):
-//   claim  -- every vertex v of the frontier F_t that still has degree 1
-//             retrieves its edge e = xor[v] and writes (t << 2) | j into
-//             claim[e] with atomicMin, j = position of v in the edge.  The
-//             minimum is the hinge (smallest position), whatever the order
-//             of the atomics; the one thread that sees the unclaimed value
-//             appends e to the layer L_t, so an edge enters L_t once (the
-//             deduplication of D_i into P_i).
-//   update -- every edge of L_t is deleted (DeleteEdge) from its non-hinge
-//             vertices: atomicSub on deg, atomicXor on xor.  The hinge keeps
-//             its record: its only edge is gone and it is in no later
-//             frontier, so nothing reads it again.  A vertex whose degree
-//             drops from 2 to 1 is appended to F_{t+1}; each vertex crosses
-//             that step at most once, so the frontiers F_1, F_2, ... fit in
-//             one list of m entries and the layers in one list of n.
-// Round 0 scans all m records instead of a list (F_0 is never stored).
-// Kernels read t and the list bounds from the device control block, so the
-// host loop needs no per-round arguments.
+// Edge records.  Edge e is one 16-byte record {v_0, v_1, v_2, claim} (r <= 3;
+// 32 bytes with the claim in the second half for r = 4): one random access
+// reads the vertices of an edge together with its claim word, where claim =
+// (round << 2) | hinge once the edge is peeled and 0xFFFFFFFF before.
+//
+// Vertex records (sec. 4.1, packed incidence list with the edge id as label).
+// The record of a vertex is one 64-bit word: degree in the low half, and in
+// the high half the sum modulo 2^32 of the ids of its incident edges.  The
+// paper combines the ids with XOR; any group operation has the property the
+// XOR trick uses (with one edge left, the accumulator is that edge's id), and
+// with addition one 64-bit atomicAdd updates degree and accumulator together
+// and returns both.  AddEdge adds (e << 32) + 1, DeleteEdge subtracts it;
+// the degree never goes below zero, so the low half never borrows from the
+// high half.
+//
+// Rounds (sec. 4.2).  Layer L_t is the set of edges with a vertex of degree
+// 1 after rounds 0..t-1.  The kernel of round t deletes every edge of L_t
+// from its non-hinge vertices (the hinge keeps its record: its only edge is
+// gone and no later round looks at it).  The atomic that takes a vertex from
+// degree 2 to 1 returns the remaining edge f (old sum - e): that vertex is in
+// the next frontier, and it claims f for round t+1 right away with atomicMin
+// on f's claim word.  If f is itself in L_t, its claim already holds round t
+// and the min leaves it unchanged; so the claims reaching an edge for round
+// t+1 are exactly those of its degree-1 vertices after round t, the minimum
+// is the hinge (smallest position) whatever the order of the atomics, and
+// the single claimer that sees the unclaimed value appends f to L_{t+1} (the
+// deduplication of D_i into P_i).  One kernel per round; the frontier is
+// never stored.  (A vertex keeps its position j in every edge: the graph is
+// r-partite, sec. 4.3.)
+// Round 0 claims from a scan of all vertex records; a layer is deleted either
+// from the list L (sparse) or by streaming all edge records and keeping those
+// of the round (dense, for layers that are a large fraction of the edges).
 #include "kernels.cuh"
 
 namespace hp {
@@ -46,240 +58,312 @@ void launch_fill_u32(const Launch &L, uint32_t *p, uint64_t count, uint32_t valu
     k_fill_u32<<<grid_for(L, count, 16, 8), kThreads, 0, L.stream>>>(p, count, value);
 }
 
-// ---------------------------------------------------------------- build --
-// Four edges per thread: r uint4 loads hold 4 whole rows (coalesced).
+// ------------------------------------------------------------ records --
+// Row-major [n][R] edges -> records, with the r-partite check of sec. 4.3.
 template <int R>
 __global__ void __launch_bounds__(kThreads)
-k_build(const uint32_t *__restrict__ edges, uint32_t n, uint32_t P, uint32_t *__restrict__ st,
-        uint32_t *__restrict__ claim, Ctl *ctl) {
-    const uint64_t groups = ((uint64_t)n + 3) / 4;
+k_records(const uint32_t *__restrict__ edges, uint32_t n, uint32_t P, uint4 *__restrict__ rec,
+          Ctl *ctl) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const bool aligned = ((((uintptr_t)edges) | ((uintptr_t)claim)) & 15u) == 0;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride) {
-        const uint32_t e0 = (uint32_t)(g * 4);
-        const uint32_t cnt = min(4u, n - e0);
-        uint32_t w[4 * R];
-        if (cnt == 4 && aligned) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(edges + (uint64_t)e0 * R);
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        uint32_t v[4] = {0, 0, 0, 0};
+        bool ok = true;
 #pragma unroll
-            for (int q = 0; q < R; q++) {
-                const uint4 t = __ldcs(p + q);
-                w[4 * q + 0] = t.x;
-                w[4 * q + 1] = t.y;
-                w[4 * q + 2] = t.z;
-                w[4 * q + 3] = t.w;
-            }
-            *reinterpret_cast<uint4 *>(claim + e0) =
-                make_uint4(kUnclaimed, kUnclaimed, kUnclaimed, kUnclaimed);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4 * R; q++)
-                w[q] = (q / R < (int)cnt) ? edges[(uint64_t)e0 * R + q] : 0u;
-            for (uint32_t k = 0; k < cnt; k++) claim[e0 + k] = kUnclaimed;
+        for (int j = 0; j < R; j++) {
+            v[j] = edges[e * R + j];
+            ok &= (v[j] - (uint32_t)j * P) < P;
         }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (k < (int)cnt) {
-                const uint32_t e = e0 + k;
-#pragma unroll
-                for (int j = 0; j < R; j++) {
-                    const uint32_t v = w[k * R + j];
-                    if (v - (uint32_t)j * P >= P) {  // outside part j
-                        raise_err(ctl, kDevBadVertex);
-                        continue;
-                    }
-                    atomicAdd(st + 2ull * v, 1u);
-                    atomicXor(st + 2ull * v + 1, e);
-                }
-            }
-        }
+        if (!ok) raise_err(ctl, kDevBadVertex);
+        store_record<R>(rec, e, v, ok);
     }
 }
 
-void launch_build_incidence(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t r,
-                            uint32_t P, uint32_t *state, uint32_t *claim, Ctl *ctl) {
+void launch_records(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t r, uint32_t P,
+                    uint4 *rec, Ctl *ctl) {
     if (n == 0) return;
-    const unsigned grid = grid_for(L, ((uint64_t)n + 3) / 4, 1, 8);
+    const unsigned grid = grid_for(L, n, 1, 8);
     switch (r) {
-    case 2: count_launch(); k_build<2><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
-    case 3: count_launch(); k_build<3><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
-    case 4: count_launch(); k_build<4><<<grid, kThreads, 0, L.stream>>>(edges, n, P, state, claim, ctl); break;
+    case 2: count_launch(); k_records<2><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl); break;
+    case 3: count_launch(); k_records<3><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl); break;
+    case 4: count_launch(); k_records<4><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl); break;
     }
 }
 
-// ---------------------------------------------------------------- round 0 --
-// kR0Items vertices per thread per block step, strided by the block size so
-// every record load is coalesced; one block-aggregated append per step.
-constexpr int kR0Items = 4;
-
+// ---------------------------------------------------------------- build --
+// AddEdge of every edge on its r vertices: one 64-bit reduction each.
 template <int R>
 __global__ void __launch_bounds__(kThreads)
-k_round0(const uint2 *__restrict__ st, uint32_t m, uint32_t P, uint32_t n,
-         uint32_t *__restrict__ claim, uint32_t *__restrict__ Llist, Ctl *ctl) {
-    constexpr uint32_t kStep = kThreads * kR0Items;
-    const uint64_t stride = (uint64_t)gridDim.x * kStep;
-    for (uint64_t base = (uint64_t)blockIdx.x * kStep; base < m; base += stride) {
-        bool take[kR0Items];
-        uint32_t e[kR0Items];
+k_build(const uint4 *__restrict__ rec, uint32_t n, uint32_t m,
+        unsigned long long *__restrict__ st, Ctl *ctl) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        uint32_t v[4];
+        load_vertices<R>(rec, e, v);
+        const unsigned long long add = ((unsigned long long)e << 32) | 1ull;
 #pragma unroll
-        for (int k = 0; k < kR0Items; k++) {
-            const uint64_t v = base + (uint64_t)k * kThreads + threadIdx.x;
-            take[k] = false;
-            e[k] = 0;
-            if (v < m) {
-                const uint2 s = __ldcs(st + v);
-                if (s.x == 1u) {
-                    e[k] = s.y;
-                    if (s.y < n) {
-                        const uint32_t j = part_of<R>((uint32_t)v, P);
-                        take[k] = atomicMin(claim + s.y, j) == kUnclaimed;
-                    } else {
-                        raise_err(ctl, kDevBadEdge);
-                    }
-                }
-            }
+        for (int j = 0; j < R; j++) {
+            if (v[j] < m)
+                atomicAdd(st + v[j], add);
+            else
+                raise_err(ctl, kDevBadVertex);
         }
-        block_append<kR0Items, kThreads>(&ctl->lcur, Llist, take, e);
     }
 }
 
-void launch_round0(const Launch &L, const uint32_t *state, uint32_t m, uint32_t r, uint32_t P,
-                   uint32_t n, uint32_t *claim, uint32_t *Llist, Ctl *ctl) {
-    if (m == 0) return;
-    const unsigned grid = grid_for(L, m, kR0Items, 8);
-    const uint2 *st = reinterpret_cast<const uint2 *>(state);
+void launch_build_incidence(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                            uint32_t m, unsigned long long *st, Ctl *ctl) {
+    if (n == 0) return;
+    const unsigned grid = grid_for(L, n, 1, 8);
     switch (r) {
-    case 2: count_launch(); k_round0<2><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
-    case 3: count_launch(); k_round0<3><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
-    case 4: count_launch(); k_round0<4><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, claim, Llist, ctl); break;
+    case 2: count_launch(); k_build<2><<<grid, kThreads, 0, L.stream>>>(rec, n, m, st, ctl); break;
+    case 3: count_launch(); k_build<3><<<grid, kThreads, 0, L.stream>>>(rec, n, m, st, ctl); break;
+    case 4: count_launch(); k_build<4><<<grid, kThreads, 0, L.stream>>>(rec, n, m, st, ctl); break;
     }
 }
 
-// ---------------------------------------------------------------- claim --
-constexpr int kClaimItems = 4;
-
-template <int R>
-__global__ void __launch_bounds__(kThreads)
-k_claim(const uint2 *__restrict__ st, uint32_t P, uint32_t n, uint32_t *__restrict__ claim,
-        const uint32_t *__restrict__ F, uint32_t *__restrict__ Llist, uint32_t *__restrict__ foff,
-        Ctl *ctl) {
-    constexpr uint32_t kStep = kThreads * kClaimItems;
-    const uint32_t t = *(volatile uint32_t *)&ctl->round;
-    const uint32_t fb = foff[t];
-    const uint32_t fe = *(volatile uint32_t *)&ctl->fcur;
-    if (blockIdx.x == 0 && threadIdx.x == 0) foff[t + 1] = fe;  // F_{t+1} starts here
-    const uint64_t stride = (uint64_t)gridDim.x * kStep;
-    for (uint64_t base = fb + (uint64_t)blockIdx.x * kStep; base < fe; base += stride) {
-        bool take[kClaimItems];
-        uint32_t e[kClaimItems];
-#pragma unroll
-        for (int k = 0; k < kClaimItems; k++) {
-            const uint64_t i = base + (uint64_t)k * kThreads + threadIdx.x;
-            take[k] = false;
-            e[k] = 0;
-            if (i < fe) {
-                const uint32_t v = F[i];
-                const uint2 s = st[v];
-                if (s.x == 1u) {
-                    e[k] = s.y;
-                    if (s.y < n) {
-                        const uint32_t tag = (t << 2) | part_of<R>(v, P);
-                        take[k] = atomicMin(claim + s.y, tag) == kUnclaimed;
-                    } else {
-                        raise_err(ctl, kDevBadEdge);
-                    }
-                }
-            }
-        }
-        block_append<kClaimItems, kThreads>(&ctl->lcur, Llist, take, e);
-    }
-}
-
-void launch_claim(const Launch &L, const uint32_t *state, uint32_t r, uint32_t P, uint32_t n,
-                  uint32_t *claim, const uint32_t *F, uint32_t *Llist, uint32_t *foff,
-                  Ctl *ctl) {
-    const unsigned grid = grid_fixed(L, 8);
-    const uint2 *st = reinterpret_cast<const uint2 *>(state);
-    switch (r) {
-    case 2: count_launch(); k_claim<2><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
-    case 3: count_launch(); k_claim<3><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
-    case 4: count_launch(); k_claim<4><<<grid, kThreads, 0, L.stream>>>(st, P, n, claim, F, Llist, foff, ctl); break;
-    }
-}
-
-// ---------------------------------------------------------------- update --
-constexpr int kUpdItems = 2;  // edges per thread per block step
-
-template <int R>
-__global__ void __launch_bounds__(kThreads)
-k_update(const uint32_t *__restrict__ edges, uint32_t m, const uint32_t *__restrict__ claim,
-         uint32_t *__restrict__ st, const uint32_t *__restrict__ Llist, uint32_t *__restrict__ F,
-         uint32_t *__restrict__ loff, const uint32_t *__restrict__ foff, Ctl *ctl) {
-    constexpr uint32_t kStep = kThreads * kUpdItems;
-    constexpr int K = kUpdItems * (R - 1);
-    const uint32_t t = *(volatile uint32_t *)&ctl->round;
-    const uint32_t lb = loff[t];
-    const uint32_t le = *(volatile uint32_t *)&ctl->lcur;
-    if (blockIdx.x == 0 && threadIdx.x == 0) loff[t + 1] = le;  // L_t = [lb, le)
-    const uint64_t stride = (uint64_t)gridDim.x * kStep;
-    for (uint64_t base = lb + (uint64_t)blockIdx.x * kStep; base < le; base += stride) {
-        bool app[K];
-        uint32_t wv[K];
-#pragma unroll
-        for (int q = 0; q < kUpdItems; q++) {
-            const uint64_t i = base + (uint64_t)q * kThreads + threadIdx.x;
-            uint32_t e = 0, h = 0xFFu;
-            uint32_t w[R];
-            if (i < le) {
-                e = Llist[i];
-                h = claim[e] & 3u;
-#pragma unroll
-                for (int j = 0; j < R; j++) w[j] = edges[(uint64_t)e * R + j];
-            }
-#pragma unroll
-            for (int k = 0; k < R - 1; k++) {
-                app[q * (R - 1) + k] = false;
-                wv[q * (R - 1) + k] = 0;
-                if (h == 0xFFu) continue;
-                // k-th non-hinge position: positions after the hinge shift by one
-                const int j = k + ((uint32_t)k >= h ? 1 : 0);
-                const uint32_t x = w[j];
-                if (x < m) {
-                    const uint32_t old = atomicSub(st + 2ull * x, 1u);
-                    atomicXor(st + 2ull * x + 1, e);
-                    app[q * (R - 1) + k] = (old == 2u);
-                    wv[q * (R - 1) + k] = x;
-                } else {
-                    raise_err(ctl, kDevBadVertex);
-                }
-            }
-        }
-        block_append<K, kThreads>(&ctl->fcur, F, app, wv);
-    }
-    // The last block to finish closes the round: F_{t+1} = [foff[t+1], fcur).
+// ------------------------------------------------------- round epilogue --
+// Every block adds its counts; the last block of the launch to finish
+// closes round t: layer L_{t+1} is [loff[t+1], lcur) now that every append
+// of the launch is done.  No block waits for another.
+__device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t,
+                                            uint32_t crossings) {
+    __shared__ uint32_t s_cross;
+    if (threadIdx.x == 0) s_cross = 0;
+    __syncthreads();
+    if (crossings) atomicAdd(&s_cross, crossings);
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (s_cross) atomicAdd(&ctl->cross, s_cross);
         __threadfence();
         const uint32_t d = atomicAdd(&ctl->done, 1u);
         if (d == gridDim.x - 1) {
             __threadfence();
-            const uint32_t fe = atomicAdd(&ctl->fcur, 0u);
-            ctl->more = (fe > foff[t + 1] && le > lb) ? 1u : 0u;
-            ctl->last_layer = le - lb;
+            const uint32_t end = atomicAdd(&ctl->lcur, 0u);
+            const uint32_t beg = loff[t + 1];
+            loff[t + 2] = end;
+            ctl->next_size = end - beg;
+            ctl->more = end > beg ? 1u : 0u;
+            ctl->scur = beg;
             ctl->done = 0;
             ctl->round = t + 1;
         }
     }
 }
 
-void launch_update(const Launch &L, const uint32_t *edges, uint32_t r, uint32_t m,
-                   const uint32_t *claim, uint32_t *state, const uint32_t *Llist, uint32_t *F,
-                   uint32_t *loff, const uint32_t *foff, Ctl *ctl) {
-    const unsigned grid = grid_fixed(L, 8);
+// ---------------------------------------------------------------- round 0 --
+// Claims of round 0 from a scan of all vertex records (F_0 is never stored).
+// Layer 0 is not listed: the round-0 deletion pass is dense.  L_1 starts at
+// index |L_0| of the layer list.
+constexpr int kR0Items = 4;
+
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_round0(const unsigned long long *__restrict__ st, uint32_t m, uint32_t P, uint32_t n,
+         uint4 *__restrict__ rec, uint32_t *__restrict__ loff, Ctl *ctl) {
+    constexpr uint32_t kStep = kThreads * kR0Items;
+    const uint64_t stride = (uint64_t)gridDim.x * kStep;
+    uint32_t first = 0;
+    for (uint64_t base = (uint64_t)blockIdx.x * kStep; base < m; base += stride) {
+#pragma unroll
+        for (int k = 0; k < kR0Items; k++) {
+            const uint64_t v = base + (uint64_t)k * kThreads + threadIdx.x;
+            if (v < m) {
+                const unsigned long long s = __ldcs(st + v);
+                if ((uint32_t)s == 1u) {
+                    const uint32_t e = (uint32_t)(s >> 32);
+                    if (e < n) {
+                        const uint32_t j = part_of<R>((uint32_t)v, P);
+                        first += atomicMin(claim_ptr<R>(rec, e), j) == kUnclaimed ? 1u : 0u;
+                    } else {
+                        raise_err(ctl, kDevBadEdge);
+                    }
+                }
+            }
+        }
+    }
+    // |L_0| = number of first claims; the last block publishes it as loff[1]
+    __shared__ uint32_t s_first;
+    if (threadIdx.x == 0) s_first = 0;
+    __syncthreads();
+    if (first) atomicAdd(&s_first, first);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_first) atomicAdd(&ctl->lcur, s_first);
+        __threadfence();
+        const uint32_t d = atomicAdd(&ctl->done, 1u);
+        if (d == gridDim.x - 1) {
+            __threadfence();
+            const uint32_t end = atomicAdd(&ctl->lcur, 0u);
+            loff[0] = 0;
+            loff[1] = end;
+            ctl->next_size = end;
+            ctl->more = end > 0 ? 1u : 0u;
+            ctl->scur = 0;
+            ctl->done = 0;
+            ctl->round = 0;
+        }
+    }
+}
+
+void launch_round0(const Launch &L, const unsigned long long *st, uint32_t m, uint32_t r,
+                   uint32_t P, uint32_t n, uint4 *rec, uint32_t *loff, Ctl *ctl) {
+    const unsigned grid = grid_for(L, m ? m : 1, kR0Items, 8);
     switch (r) {
-    case 2: count_launch(); k_update<2><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
-    case 3: count_launch(); k_update<3><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
-    case 4: count_launch(); k_update<4><<<grid, kThreads, 0, L.stream>>>(edges, m, claim, state, Llist, F, loff, foff, ctl); break;
+    case 2: count_launch(); k_round0<2><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl); break;
+    case 3: count_launch(); k_round0<3><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl); break;
+    case 4: count_launch(); k_round0<4><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl); break;
+    }
+}
+
+// ---------------------------------------------------------------- rounds --
+// Delete edge e (claim word c, vertices v) of layer t from its non-hinge
+// vertices; claim for round t+1 the remaining edge of every vertex that falls
+// to degree 1.  Returns how many fell; take/f receive the first claims.
+template <int R>
+__device__ __forceinline__ uint32_t delete_edge(uint32_t e, uint32_t c, const uint32_t (&v)[4],
+                                                uint32_t t, uint32_t n,
+                                                unsigned long long *st, uint4 *rec, Ctl *ctl,
+                                                bool (&take)[R - 1], uint32_t (&f)[R - 1]) {
+    const uint32_t h = c & 3u;
+    const unsigned long long sub = 0ull - (((unsigned long long)e << 32) | 1ull);
+    uint32_t cross = 0;
+#pragma unroll
+    for (int k = 0; k < R - 1; k++) {
+        const int j = k + ((uint32_t)k >= h ? 1 : 0);  // k-th non-hinge position
+        const unsigned long long old = atomicAdd(st + v[j], sub);
+        if ((uint32_t)old == 2u) {
+            cross++;
+            const uint32_t g = (uint32_t)(old >> 32) - e;  // the one edge left
+            if (g < n) {
+                const uint32_t tag = ((t + 1) << 2) | (uint32_t)j;
+                take[k] = atomicMin(claim_ptr<R>(rec, g), tag) == kUnclaimed;
+                f[k] = g;
+            } else {
+                raise_err(ctl, kDevBadEdge);
+            }
+        }
+    }
+    return cross;
+}
+
+constexpr int kStageCap = 256;  // staged appends per warp
+
+// Sparse round: the edges of L_t from the list; solve record i of L_t.
+template <int R, bool WITH_S>
+__global__ void __launch_bounds__(kThreads)
+k_round_sparse(uint32_t *__restrict__ Llist, uint32_t *__restrict__ loff, uint32_t n,
+               unsigned long long *__restrict__ st, uint4 *__restrict__ rec,
+               uint4 *__restrict__ S, Ctl *ctl) {
+    __shared__ uint32_t stage_buf[kThreads / 32][kStageCap];
+    WarpStage<kStageCap> stage{stage_buf[threadIdx.x >> 5], 0};
+    const uint32_t t = *(volatile uint32_t *)&ctl->round;
+    const uint32_t lb = loff[t], le = loff[t + 1];
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    uint32_t cross = 0;
+    // warp-uniform trip count: whole warps step together
+    for (uint64_t base = lb + ((uint64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u));
+         base < le; base += stride) {
+        const uint64_t i = base + (threadIdx.x & 31u);
+        bool take[R - 1];
+        uint32_t f[R - 1];
+#pragma unroll
+        for (int k = 0; k < R - 1; k++) {
+            take[k] = false;
+            f[k] = 0;
+        }
+        if (i < le) {
+            const uint32_t e = Llist[i];
+            uint32_t v[4];
+            const uint32_t c = load_record<R>(rec, e, v);
+            cross += delete_edge<R>(e, c, v, t, n, st, rec, ctl, take, f);
+            if (WITH_S) S[i] = solve_record(c, v);
+        }
+#pragma unroll
+        for (int k = 0; k < R - 1; k++) stage.push(take[k], f[k], &ctl->lcur, Llist);
+    }
+    stage.flush(&ctl->lcur, Llist);
+    close_round(ctl, loff, t, cross);
+}
+
+// Dense round: stream all edge records, keep those claimed in round t (no
+// solve records: a dense layer is assigned from a record stream as well).
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_round_dense(uint32_t *__restrict__ Llist, uint32_t *__restrict__ loff, uint32_t n,
+              unsigned long long *__restrict__ st, uint4 *__restrict__ rec, Ctl *ctl) {
+    __shared__ uint32_t stage_buf[kThreads / 32][kStageCap];
+    WarpStage<kStageCap> stage{stage_buf[threadIdx.x >> 5], 0};
+    const uint32_t t = *(volatile uint32_t *)&ctl->round;
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    uint32_t cross = 0;
+    for (uint64_t base = (uint64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u); base < n;
+         base += stride) {
+        const uint64_t e = base + (threadIdx.x & 31u);
+        bool take[R - 1];
+        uint32_t f[R - 1];
+#pragma unroll
+        for (int k = 0; k < R - 1; k++) {
+            take[k] = false;
+            f[k] = 0;
+        }
+        if (e < n) {
+            uint32_t v[4];
+            const uint32_t c = load_record_stream<R>(rec, e, v);
+            if (c != kUnclaimed && (c >> 2) == t)
+                cross += delete_edge<R>((uint32_t)e, c, v, t, n, st, rec, ctl, take, f);
+        }
+#pragma unroll
+        for (int k = 0; k < R - 1; k++) stage.push(take[k], f[k], &ctl->lcur, Llist);
+    }
+    stage.flush(&ctl->lcur, Llist);
+    close_round(ctl, loff, t, cross);
+}
+
+void launch_round(const Launch &L, bool dense, bool with_s, uint32_t r, uint32_t *Llist,
+                  uint32_t *loff, uint32_t n, unsigned long long *st, uint4 *rec, uint4 *S,
+                  Ctl *ctl) {
+    const unsigned grid = dense ? grid_for(L, n ? n : 1, 1, 8) : grid_fixed(L, 8);
+#define HP_ROUND(RR, WS)                                                                      \
+    do {                                                                                      \
+        count_launch();                                                                       \
+        if (dense)                                                                            \
+            k_round_dense<RR><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, st, rec, ctl); \
+        else                                                                                  \
+            k_round_sparse<RR, WS><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, st, rec,  \
+                                                                    S, ctl);                  \
+    } while (0)
+    if (with_s) {
+        HP_ROUND(3, true);  // solve records exist for the r = 3 MPHF only
+    } else {
+        switch (r) {
+        case 2: HP_ROUND(2, false); break;
+        case 3: HP_ROUND(3, false); break;
+        case 4: HP_ROUND(4, false); break;
+        }
+    }
+#undef HP_ROUND
+}
+
+// --------------------------------------------------------------- claims --
+// Compact claim array: the API output and the key of the order sort.
+template <int R>
+__global__ void k_extract_claim(const uint4 *__restrict__ rec, uint32_t n,
+                                uint32_t *__restrict__ claim) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        uint32_t v[4];
+        claim[e] = load_record_stream<R>(rec, e, v);
+    }
+}
+
+void launch_extract_claim(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                          uint32_t *claim) {
+    if (n == 0) return;
+    const unsigned grid = grid_for(L, n, 1, 8);
+    switch (r) {
+    case 2: count_launch(); k_extract_claim<2><<<grid, kThreads, 0, L.stream>>>(rec, n, claim); break;
+    case 3: count_launch(); k_extract_claim<3><<<grid, kThreads, 0, L.stream>>>(rec, n, claim); break;
+    case 4: count_launch(); k_extract_claim<4><<<grid, kThreads, 0, L.stream>>>(rec, n, claim); break;
     }
 }
 

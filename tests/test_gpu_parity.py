@@ -174,11 +174,16 @@ def test_peel_layer_capacity_error():
 def test_mphf_parity(n):
     keys = inputs.keys(n, 1)
     want = oracle.mphf_build(keys, seed=1, max_tries=32)
-    got = hp.mphf_build(_dev(keys), seed=1, max_tries=32)
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    got = hp.mphf_build(_dev(keys), seed=1, max_tries=32, order=order)
     assert got.stats["seed_used"] == want.seed_used
     assert got.stats["rounds"] == want.rounds
     assert np.array_equal(_u64(got.G), want.G)
     assert np.array_equal(_u64(got.rank_dir), want.dir)
+    # the whole path: the canonical order of the successful attempt's graph
+    m = oracle.num_vertices(n, 1230, 3)
+    pw = oracle.peel_rounds(oracle.hash_edges(keys, m, 3, want.seed_used), m)
+    assert np.array_equal(_u32(order), pw.order)
 
 
 def test_mphf_retries_exhausted_on_duplicate_keys():
@@ -203,3 +208,68 @@ def test_mphf_reseed_matches_oracle():
             if found == 3:
                 break
     assert found == 3
+
+
+# ----------------------------------------------- L2-blocked incidence build --
+
+@pytest.fixture
+def small_buckets():
+    """Route small graphs through the L2-blocked build with 1024-vertex
+    chunks (many buckets), restoring the defaults afterwards."""
+    hp.set_tuning(bucket_shift=10, bucket_min_vertices=0)
+    yield
+    hp.set_tuning()
+
+
+@pytest.mark.parametrize("n,gamma,r", [(100_000, 1230, 3), (100_003, 1200, 3),
+                                       (50_000, 1300, 4), (20_000, 1500, 2), (1, 1230, 3),
+                                       (1025, 1230, 3)])
+def test_peel_parity_bucketed(small_buckets, n, gamma, r):
+    m = oracle.num_vertices(n, gamma, r)
+    edges = oracle.hash_edges(inputs.keys(n, 5), m, r, 1)
+    _check_peel(edges, m)
+
+
+def test_peel_bucket_overflow_falls_back(small_buckets):
+    # every vertex in the first 1024 of its part: the buckets sized for a
+    # uniform spread overflow, and the overflowing incidences are applied
+    # directly
+    n, P = 60_000, 40_000
+    rng = np.random.default_rng(9)
+    edges = np.stack([rng.integers(0, 1024, n) + j * P for j in range(3)], axis=1).astype(np.uint32)
+    _check_peel(edges, 3 * P)
+
+
+@pytest.mark.parametrize("n", [1000, 100_000])
+def test_mphf_parity_bucketed(small_buckets, n):
+    keys = inputs.keys(n, 4)
+    want = oracle.mphf_build(keys, seed=1, max_tries=32)
+    got = hp.mphf_build(_dev(keys), seed=1, max_tries=32)
+    assert got.stats["seed_used"] == want.seed_used
+    assert np.array_equal(_u64(got.G), want.G)
+    assert np.array_equal(_u64(got.rank_dir), want.dir)
+
+
+def test_tuning_rejects_bad_values():
+    with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
+        hp.set_tuning(bucket_shift=3)
+    with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
+        hp.set_tuning(dense_div=0)
+    hp.set_tuning()
+    assert hp.get_tuning()["bucket_shift"] == 22
+
+
+@pytest.mark.slow
+def test_peel_and_mphf_parity_1e7_default_tuning():
+    # default tuning: m = 12.3M vertices takes the L2-blocked build and dense
+    # rounds; the whole output is compared with the oracle
+    n = 10_000_000
+    keys = inputs.keys(n, 1)
+    m = oracle.num_vertices(n, 1230, 3)
+    edges = oracle.hash_edges(keys, m, 3, 1)
+    _check_peel(edges, m)
+    want = oracle.mphf_build(keys, seed=1)
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    got = hp.mphf_build(_dev(keys), seed=1, order=order)
+    assert np.array_equal(_u64(got.G), want.G)
+    assert np.array_equal(_u64(got.rank_dir), want.dir)

@@ -42,7 +42,7 @@ def test_noalloc_matches_workspace_peel_on_two_calls_in_a_row():
     # first a larger graph that fills most of the scratch, then a smaller one
     # with a 2-core: stale contents of the first call must not leak into the
     # second
-    e1, m1 = _edges(500_000, 1230, 1)
+    e1, m1 = _edges(400_000, 1230, 1)
     e2, m2 = _edges(60_000, 1200, 2)
     want1 = hp.peel(e1, m1)
     want2 = hp.peel(e2, m2)
