@@ -225,6 +225,62 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
                               void *stream);
 
 /*
+ * Batched peel of many independent bucket hypergraphs (the bucketed layout of
+ * sec. 3 "Practical workarounds (HEM)": one small MWHC hypergraph per bucket),
+ * r = 3.  Bucket b holds keys d_keys[off[b] .. off[b+1]) (n_b of them, at most
+ * 65,536); it is hashed with seed b into m_b = hpeel_num_vertices(n_b,
+ * gamma_milli, 3) vertices and peeled as hpeel_peel would (sec. 4.2).
+ *   d_bucket_off    [B + 1] uint64, non-decreasing, off[0] = 0.
+ *   d_order         [off[B]] uint32 output: for every bucket, at its keys'
+ *                   positions, the canonical order of its edges in local ids
+ *                   (edge i = key off[b] + i): layers ascending by round, ids
+ *                   ascending inside a layer, then the 2-core edges ascending.
+ *   d_bucket_rounds [B] uint32 output or NULL: rounds of each bucket.
+ *   d_bucket_status [B] uint32 output or NULL: 0 = peeled completely, 1 = a
+ *                   2-core is left, 2 = more than 65,536 keys (the bucket's
+ *                   outputs are not written).
+ *   d_G, d_G_off    both NULL, or: d_G_off [B + 1] word offsets (from
+ *                   hpeel_batched_g_offsets) and d_G [d_G_off[B]] uint64 output,
+ *                   the MWHC g values of bucket b at d_G + d_G_off[b] in the
+ *                   layout of hpeel_mphf_build's d_G (all zero for a bucket that
+ *                   kept a 2-core).
+ *   tuning          NULL for the defaults, or the launch shape (see
+ *                   hpeel_batch_tuning); results never depend on it.
+ *   1000 <= gamma_milli <= 1999 (the largest bucket's vertex ids must fit 17
+ *   bits).
+ * Asynchronous: no host synchronisation, no allocation -- the call can be
+ * captured into a CUDA graph.  Errors: HPEEL_ERR_INVALID_ARG,
+ * HPEEL_ERR_WORKSPACE_TOO_SMALL, HPEEL_ERR_CUDA.
+ */
+typedef struct hpeel_batch_tuning {
+    uint32_t threads;      /* threads per block (multiple of 32, 64..1024; 0: 256) */
+    uint32_t ctas_per_sm;  /* blocks per SM (grid = SMs x this; 0: 2) */
+    uint32_t smem_bytes;   /* shared memory per block for bucket state (0: the SM's
+                              shared memory split between the blocks); buckets
+                              that do not fit use the workspace instead */
+    uint32_t reserved[5];
+} hpeel_batch_tuning;
+
+size_t hpeel_batched_workspace_size(uint32_t B, uint32_t gamma_milli,
+                                    const hpeel_batch_tuning *tuning);
+
+/* d_G_off[b] = sum over c < b of ceil(m_c / 32): where bucket b's g words
+ * start in d_G (B + 1 entries).  Uses the first part of a batched workspace
+ * (hpeel_batched_workspace_size(B, gamma_milli, NULL) bytes suffice).
+ * Asynchronous.  Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL,
+ * HPEEL_ERR_CUDA. */
+hpeel_status hpeel_batched_g_offsets(const uint64_t *d_bucket_off, uint32_t B,
+                                     uint32_t gamma_milli, uint64_t *d_G_off,
+                                     void *d_ws, size_t ws_bytes, void *stream);
+
+hpeel_status hpeel_peel_batched(const uint64_t *d_keys, const uint64_t *d_bucket_off,
+                                uint32_t B, uint32_t gamma_milli, uint32_t *d_order,
+                                uint32_t *d_bucket_rounds, uint32_t *d_bucket_status,
+                                uint64_t *d_G, const uint64_t *d_G_off,
+                                const hpeel_batch_tuning *tuning, void *d_ws,
+                                size_t ws_bytes, void *stream);
+
+/*
  * Instrumentation (no counterpart in the paper; used to measure the path).
  *   hpeel_kernel_launches  total number of kernels this library has launched
  *                          in the process (all devices, all threads).

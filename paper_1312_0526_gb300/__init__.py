@@ -25,6 +25,12 @@ from dataclasses import dataclass
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhpeel.so")
+
+
+def _build_dir() -> str:
+    d = os.path.join(_HERE, "_build")
+    os.makedirs(d, exist_ok=True)
+    return d
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "hpeel.h")
 
 UNCLAIMED = 0xFFFFFFFF
@@ -46,6 +52,11 @@ class HpeelError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("bucket_shift", ctypes.c_uint32), ("bucket_min_vertices", ctypes.c_uint32),
                 ("dense_div", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("smem_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
 
 
 class Stats(ctypes.Structure):
@@ -100,6 +111,13 @@ def lib():
         L.hpeel_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
         L.hpeel_get_tuning.restype = None
         L.hpeel_get_tuning.argtypes = [ctypes.POINTER(Tuning)]
+        L.hpeel_batched_workspace_size.restype = sz
+        L.hpeel_batched_workspace_size.argtypes = [u32, u32, ctypes.POINTER(BatchTuning)]
+        L.hpeel_batched_g_offsets.restype = st
+        L.hpeel_batched_g_offsets.argtypes = [p, u32, u32, p, p, sz, p]
+        L.hpeel_peel_batched.restype = st
+        L.hpeel_peel_batched.argtypes = [p, p, u32, u32, p, p, p, p, p,
+                                         ctypes.POINTER(BatchTuning), p, sz, p]
         L.hpeel_kernel_launches.restype = u64
         L.hpeel_kernel_launches.argtypes = []
         L.hpeel_profile_enable.restype = None
@@ -312,3 +330,66 @@ def set_tuning(**kw) -> None:
     cur.update(kw)
     t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["dense_div"])
     _check(lib().hpeel_set_tuning(ctypes.byref(t)))
+
+
+def _batch_tuning(tuning):
+    if tuning is None:
+        return None
+    t = BatchTuning(int(tuning.get("threads", 0)), int(tuning.get("ctas_per_sm", 0)),
+                    int(tuning.get("smem_bytes", 0)))
+    return ctypes.byref(t)
+
+
+def batched_workspace_size(B: int, gamma_milli: int = 1230, tuning=None) -> int:
+    return int(lib().hpeel_batched_workspace_size(B, gamma_milli, _batch_tuning(tuning)))
+
+
+@dataclass
+class BatchedResult:
+    order: object     # int32 [total]: per-bucket canonical orders (local ids)
+    rounds: object    # int32 [B]
+    status: object    # int32 [B]: 0 peeled, 1 2-core left, 2 too large
+    G: object         # int64 [G_off[B]] or None
+    G_off: object     # int64 [B + 1] or None
+
+
+def batched_g_offsets(bucket_off, gamma_milli: int = 1230, workspace=None):
+    """Word offsets of the per-bucket g arrays (hpeel_batched_g_offsets)."""
+    torch = _torch()
+    op = _dev_ptr(bucket_off, "bucket_off", torch.int64, 1)
+    B = bucket_off.shape[0] - 1
+    ws = workspace if workspace is not None else _workspace(
+        batched_workspace_size(B, gamma_milli), bucket_off.device)
+    G_off = torch.empty(B + 1, dtype=torch.int64, device=bucket_off.device)
+    _check(lib().hpeel_batched_g_offsets(op, B, gamma_milli, _dev_ptr(G_off, "G_off"),
+                                         _dev_ptr(ws, "workspace", torch.uint8), ws.numel(),
+                                         _stream()))
+    return G_off
+
+
+def peel_batched(keys, bucket_off, gamma_milli: int = 1230, with_g: bool = False,
+                 tuning=None, workspace=None, out=None) -> BatchedResult:
+    """Peel every bucket of keys (bucket b = keys[off[b]:off[b+1]], hash seed b)
+    in one persistent launch (hpeel_peel_batched).  Asynchronous."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    op = _dev_ptr(bucket_off, "bucket_off", torch.int64, 1)
+    B = bucket_off.shape[0] - 1
+    dev = keys.device
+    need = batched_workspace_size(B, gamma_milli, tuning)
+    ws = workspace if workspace is not None else _workspace(need, dev)
+    if out is None:
+        out = BatchedResult(torch.empty(keys.shape[0], dtype=torch.int32, device=dev),
+                            torch.empty(B, dtype=torch.int32, device=dev),
+                            torch.empty(B, dtype=torch.int32, device=dev), None, None)
+        if with_g:
+            out.G_off = batched_g_offsets(bucket_off, gamma_milli, ws)
+            words = int(out.G_off[-1].item())
+            out.G = torch.empty(max(words, 1), dtype=torch.int64, device=dev)
+    gp = _dev_ptr(out.G, "G") if out.G is not None else None
+    gop = _dev_ptr(out.G_off, "G_off") if out.G_off is not None else None
+    _check(lib().hpeel_peel_batched(kp, op, B, gamma_milli, _dev_ptr(out.order, "order"),
+                                    _dev_ptr(out.rounds, "rounds"), _dev_ptr(out.status, "status"),
+                                    gp, gop, _batch_tuning(tuning),
+                                    _dev_ptr(ws, "workspace", torch.uint8), ws.numel(), _stream()))
+    return out

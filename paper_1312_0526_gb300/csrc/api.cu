@@ -12,65 +12,16 @@
 #include <string>
 #include <vector>
 
+#include "host.h"
 #include "kernels.cuh"
 
 using namespace hp;
 
-namespace {
-
+namespace hp {
 thread_local std::string g_last_error;
-
-hpeel_status fail(hpeel_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
-hpeel_status fail(hpeel_status s, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    g_last_error = buf;
-    return s;
 }
 
-#define HP_CUDA(call)                                                                       \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess)                                                              \
-            return fail(HPEEL_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                     \
-                        cudaGetErrorString(e_), __FILE__, __LINE__);                        \
-    } while (0)
-
-#define HP_TRY(expr)                                                                        \
-    do {                                                                                    \
-        hpeel_status s_ = (expr);                                                           \
-        if (s_ != HPEEL_OK) return s_;                                                      \
-    } while (0)
-
-hpeel_status check_launch(const char *what) {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return fail(HPEEL_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
-    return HPEEL_OK;
-}
-
-hpeel_status make_launch(void *stream, Launch *L) {
-    int dev = 0;
-    HP_CUDA(cudaGetDevice(&dev));
-    static std::mutex mu;
-    static int sms_cache[64] = {0};
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (dev < 64 && sms_cache[dev] == 0) {
-            int sms = 0;
-            cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess)
-                return fail(HPEEL_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-            sms_cache[dev] = sms;
-        }
-        L->sms = dev < 64 ? sms_cache[dev] : 148;
-    }
-    L->stream = (cudaStream_t)stream;
-    return HPEEL_OK;
-}
+namespace {
 
 // Small pinned host buffer for the per-round control-block read-back.
 Ctl *pinned_ctl() {
@@ -80,8 +31,6 @@ Ctl *pinned_ctl() {
     }
     return p;
 }
-
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct PeelLayout {
     size_t ctl, rec, state, claim, L, S, pairs, fill, loff, hist, scantmp, total;

@@ -99,6 +99,16 @@ void launch_emit_scatter(const Launch &L, const uint32_t *src, uint32_t count,
                          const uint32_t *offs, uint32_t *out);
 void launch_layer_off(const Launch &L, const uint32_t *loff, uint32_t rounds, uint64_t *out);
 
+// a10: batched bucket peel (batched.cu).
+size_t batched_scratch_bytes(uint32_t gamma_milli);
+uint32_t batched_max_gamma_milli();
+void launch_batched(const Launch &L, const uint64_t *keys, const uint64_t *off, uint32_t B,
+                    uint32_t gamma_milli, uint32_t *order, uint32_t *rounds, uint32_t *status,
+                    uint64_t *G, const uint64_t *G_off, uint32_t threads, uint32_t ctas,
+                    uint32_t smem_bytes, uint32_t *sched, uint32_t *next, char *scratch);
+void launch_batch_g_offsets(const Launch &L, const uint64_t *off, uint32_t B, uint32_t gamma_milli,
+                            uint32_t *words, uint32_t *scanned, uint32_t *tmp, uint64_t *G_off);
+
 // Exclusive prefix sum of count 32-bit values (out may alias in).
 size_t scan_tmp_words(uint64_t count);
 void launch_scan_u32(const Launch &L, const uint32_t *in, uint32_t *out, uint64_t count,
