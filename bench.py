@@ -50,22 +50,29 @@ def byte_model(step, n, m, st):
     cross, dcross = st["frontier"], st["dense_cross"]
     dedges, drounds = st["dense_edges"], st["dense_rounds"]
     sedges, scross = peeled - dedges, cross - dcross
+    if step == "hash_bucket":
+        # key read, edge record write, 3 incidences written to and read back
+        # from the chunk buckets; the vertex records are written once (the
+        # updates hit L2)
+        w = (8 + 16 + 2 * R * 8) * n + 8 * m
+        return {"units": n, "word": w, "sector": w}
     if step == "hash_edges":
         return {"units": n, "word": 24 * n, "sector": 24 * n}
     if step == "fill":
         return {"units": m, "word": 8 * m, "sector": 8 * m}
     if step == "build_incidence":
         return {"units": n, "word": (16 + R * 16) * n, "sector": (16 + R * 64) * n}
-    if step == "round0":
-        return {"units": m, "word": 8 * m + 8 * L0, "sector": 8 * m + 64 * L0}
-    if step == "round_dense":
-        return {"units": dedges,
-                "word": 16 * n * drounds + dedges * ((R - 1) * 16 + 16) + dcross * 12,
-                "sector": 16 * n * drounds + dedges * ((R - 1) * 64 + 16) + dcross * 68}
-    if step == "round_sparse":
-        return {"units": sedges,
-                "word": sedges * (4 + 16 + (R - 1) * 16 + 16) + scross * 12,
-                "sector": sedges * (4 + 32 + (R - 1) * 64 + 16) + scross * 68}
+    if step == "rounds":
+        # round 0 scan and claims, then every round: dense rounds stream all
+        # records; every deleted edge updates its r-1 non-hinge vertices; a
+        # sparse round also reads the list entry, gathers the record and
+        # writes a solve record; a vertex falling to degree 1 claims its last
+        # edge and may append it
+        word = (8 * m + 8 * L0 + 16 * n * drounds + dedges * ((R - 1) * 16)
+                + sedges * (4 + 16 + (R - 1) * 16 + 16) + cross * 12)
+        sector = (8 * m + 64 * L0 + 16 * n * drounds + dedges * ((R - 1) * 64)
+                  + sedges * (4 + 32 + (R - 1) * 64 + 16) + cross * 68)
+        return {"units": peeled, "word": word, "sector": sector}
     if step == "extract_claim":
         return {"units": n, "word": 20 * n, "sector": 20 * n}
     if step == "emit_scatter":
@@ -372,6 +379,8 @@ def main():
             continue
         per_step_ms = tot_ms / args.steps
         launches_per_step = prof[name][0] / args.steps
+        if name == "rounds":  # round 0 + the round kernel's graph iterations
+            launches_per_step = 1 + st["rounds"]
         achieved = model["sector"] / (per_step_ms / 1e3) / 1e9
         traffic = None
         if name in NCU_TRAFFIC:

@@ -86,6 +86,11 @@ typedef struct hpeel_stats {
  *   dense_div           a round whose layer has more than n / dense_div
  *                       edges streams all edge records instead of reading
  *                       the layer list (default 12).
+ *   host_round_loop     0 (default): the rounds run back to back on the
+ *                       device (a CUDA graph whose while node repeats the
+ *                       round kernel until a layer is empty); 1: the host
+ *                       launches every round and reads the round's outcome
+ *                       back before the next.
  * hpeel_set_tuning(NULL) restores the defaults.  Workspace sizes depend on
  * the tuning: query them after setting it.  Errors: HPEEL_ERR_INVALID_ARG.
  */
@@ -93,7 +98,8 @@ typedef struct hpeel_tuning {
     uint32_t bucket_shift;
     uint32_t bucket_min_vertices;
     uint32_t dense_div;
-    uint32_t reserved[5];
+    uint32_t host_round_loop;
+    uint32_t reserved[4];
 } hpeel_tuning;
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t);
 void hpeel_get_tuning(hpeel_tuning *t);

@@ -51,7 +51,8 @@ class HpeelError(RuntimeError):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("bucket_shift", ctypes.c_uint32), ("bucket_min_vertices", ctypes.c_uint32),
-                ("dense_div", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("dense_div", ctypes.c_uint32), ("host_round_loop", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -318,7 +319,7 @@ def get_tuning() -> dict:
     t = Tuning()
     lib().hpeel_get_tuning(ctypes.byref(t))
     return {"bucket_shift": t.bucket_shift, "bucket_min_vertices": t.bucket_min_vertices,
-            "dense_div": t.dense_div}
+            "dense_div": t.dense_div, "host_round_loop": t.host_round_loop}
 
 
 def set_tuning(**kw) -> None:
@@ -328,7 +329,8 @@ def set_tuning(**kw) -> None:
         return
     cur = get_tuning()
     cur.update(kw)
-    t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["dense_div"])
+    t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["dense_div"],
+               cur["host_round_loop"])
     _check(lib().hpeel_set_tuning(ctypes.byref(t)))
 
 

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -40,7 +41,7 @@ struct PeelLayout {
 };
 
 // Process-wide tuning (hpeel_set_tuning); read by layouts and launches.
-hpeel_tuning g_tuning = {22u, 8u << 20, 12u, {0, 0, 0, 0, 0}};
+hpeel_tuning g_tuning = {22u, 8u << 20, 12u, 0u, {0, 0, 0, 0}};
 std::mutex g_tuning_mu;
 
 hpeel_tuning tuning() {
@@ -135,6 +136,78 @@ struct PeelIO {
 // n / kDenseDiv edges (a random record access costs about as much as
 // streaming 12 records).
 
+// Executable graphs of the round loop, cached by their parameters: round 0,
+// then a while node whose body is one round kernel.  The round kernel's last
+// block sets the while condition (next layer non-empty, table not full).
+struct RoundGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_graph_mu;
+std::map<std::string, RoundGraph> g_graphs;
+std::vector<std::string> g_graph_order;
+
+hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool with_s,
+                                unsigned long long *st, uint32_t m, uint32_t P, uint32_t n,
+                                uint4 *rec, uint32_t *loff, Ctl *ctl, uint32_t *Ll,
+                                uint32_t dense_div, uint4 *S, uint32_t max_rounds) {
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    const RoundLaunch k0 = round0_launch(L, r, m);
+    const RoundLaunch k1 = round_launch(L, with_s, r);
+    char keybuf[256];
+    snprintf(keybuf, sizeof keybuf, "%d|%p|%p|%p|%u|%u|%u|%p|%p|%p|%p|%u|%p|%u|%u|%u", dev, k0.fn,
+             k1.fn, (void *)st, m, P, n, (void *)rec, (void *)loff, (void *)ctl, (void *)Ll,
+             dense_div, (void *)S, max_rounds, k0.grid, k1.grid);
+    const std::string key(keybuf);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) {
+        RoundGraph rg;
+        HP_CUDA(cudaGraphCreate(&rg.graph, 0));
+        cudaGraphConditionalHandle h = 0;
+        HP_CUDA(cudaGraphConditionalHandleCreate(&h, rg.graph, 0, 0));
+        const unsigned long long *st_c = st;
+        void *a0[] = {(void *)&st_c, &m, &P, &n, &rec, &loff, &ctl, &h};
+        cudaKernelNodeParams p0{};
+        p0.func = k0.fn;
+        p0.gridDim = dim3(k0.grid);
+        p0.blockDim = dim3(k0.block);
+        p0.kernelParams = a0;
+        cudaGraphNode_t n0, nw, n1;
+        HP_CUDA(cudaGraphAddKernelNode(&n0, rg.graph, nullptr, 0, &p0));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        HP_CUDA(cudaGraphAddNode(&nw, rg.graph, &n0, nullptr, 1, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        void *a1[] = {&Ll, &loff, &n, &dense_div, &st, &rec, &S, &ctl, &max_rounds, &h};
+        cudaKernelNodeParams p1{};
+        p1.func = k1.fn;
+        p1.gridDim = dim3(k1.grid);
+        p1.blockDim = dim3(k1.block);
+        p1.kernelParams = a1;
+        HP_CUDA(cudaGraphAddKernelNode(&n1, body, nullptr, 0, &p1));
+        HP_CUDA(cudaGraphInstantiate(&rg.exec, rg.graph, 0));
+        if (g_graph_order.size() >= 16) {  // keep the 16 most recent
+            auto old = g_graphs.find(g_graph_order.front());
+            if (old != g_graphs.end()) {
+                cudaGraphExecDestroy(old->second.exec);
+                cudaGraphDestroy(old->second.graph);
+                g_graphs.erase(old);
+            }
+            g_graph_order.erase(g_graph_order.begin());
+        }
+        it = g_graphs.emplace(key, rg).first;
+        g_graph_order.push_back(key);
+    }
+    count_launch(1);  // round 0; the caller counts the round kernel's iterations
+    HP_CUDA(cudaGraphLaunch(it->second.exec, L.stream));
+    return HPEEL_OK;
+}
+
 // Round-synchronous peel (sec. 4.2) of n edges on m vertices.
 // hctl: host memory the control block is read back into after every round.
 hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_t m, uint32_t r,
@@ -175,47 +248,63 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         ProfScope ps(L, "build_incidence");
         launch_build_incidence(L, rec, n, r, m, st, ctl);
     }
-    {
-        ProfScope ps(L, "round0");
-        launch_round0(L, st, m, r, P, n, rec, loff, ctl);
-    }
-    HP_TRY(check_launch("build/round0"));
-    HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
-    HP_CUDA(cudaStreamSynchronize(L.stream));
-    if (hctl->err)
-        return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u (build)", hctl->err);
-    out->first_layer = hctl->next_size;
-
-    uint32_t R = 0;
-    for (uint32_t t = 0; hctl->more; t++) {
-        if (t + 2 >= lay.max_rounds + 3)
-            return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds);
-        const bool dense = t == 0 || hctl->next_size > n / std::max(1u, tu.dense_div);
-        const uint32_t layer = hctl->next_size, cross0 = hctl->cross;
+    HP_TRY(check_launch("build"));
+    const uint32_t dense_div = std::max(1u, tu.dense_div);
+    if (tu.host_round_loop) {
+        // one launch per round, the control block read back after each
         {
-            ProfScope ps(L, dense ? "round_dense" : "round_sparse");
-            launch_round(L, dense, io.with_s, r, Ll, loff, n, st, rec, S, ctl);
+            ProfScope ps(L, "round0");
+            launch_round0(L, st, m, r, P, n, rec, loff, ctl);
         }
-        HP_TRY(check_launch("round"));
+        HP_TRY(check_launch("round0"));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
-        if (hctl->err)
-            return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u (round %u)",
-                        hctl->err, t);
-        out->dense.push_back(dense ? 1 : 0);
-        if (dense) {
-            out->dense_rounds += 1;
-            out->dense_edges += layer;
-            out->dense_cross += hctl->cross - cross0;
+        while (hctl->more && !hctl->err) {
+            {
+                ProfScope ps(L, "rounds");
+                launch_round(L, io.with_s, r, Ll, loff, n, dense_div, st, rec, S, ctl,
+                             lay.max_rounds);
+            }
+            HP_TRY(check_launch("round"));
+            HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
+            HP_CUDA(cudaStreamSynchronize(L.stream));
         }
-        R = t + 1;
+    } else {
+        // round 0 and a CUDA-graph while node around the round kernel: the
+        // rounds run back to back on the device, one read-back at the end
+        ProfScope ps(L, "rounds");
+        HP_TRY(launch_round_graph(L, r, io.with_s, st, m, P, n, rec, loff, ctl, Ll, dense_div, S,
+                                  lay.max_rounds));
+        HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        count_launch(hctl->round + (hctl->more ? 1 : 0));
     }
+    if (hctl->err == kDevCapacity)
+        return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds - 1);
+    if (hctl->err)
+        return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u", hctl->err);
+    const uint32_t R = hctl->more ? hctl->round + 1 : hctl->round;
+    out->first_layer = hctl->first_layer;
     out->rounds = R;
     out->n_peeled = hctl->lcur;
     out->frontier = hctl->cross;
+    out->dense_rounds = hctl->dense_rounds;
+    out->dense_edges = hctl->dense_edges;
+    out->dense_cross = hctl->dense_cross;
     out->loff = loff;
     out->S = S;
     out->rec = rec;
+    // which layers were deleted from a record stream (their MWHC assignment
+    // streams the records too): the kernel's rule, from the layer sizes
+    if (io.with_s && R > 0) {
+        std::vector<uint32_t> lh(R + 1);
+        HP_CUDA(cudaMemcpyAsync(lh.data(), loff, 4 * ((size_t)R + 1), cudaMemcpyDeviceToHost,
+                                L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        out->dense.resize(R);
+        for (uint32_t t = 0; t < R; t++)
+            out->dense[t] = (t == 0 || lh[t + 1] - lh[t] > n / dense_div) ? 1 : 0;
+    }
 
     if (!io.order && !io.claim) return HPEEL_OK;
     {
@@ -296,7 +385,7 @@ const char *hpeel_last_error(void) { return g_last_error.c_str(); }
 
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t) {
     g_last_error.clear();
-    hpeel_tuning v = {22u, 8u << 20, 12u, {0, 0, 0, 0, 0}};
+    hpeel_tuning v = {22u, 8u << 20, 12u, 0u, {0, 0, 0, 0}};
     if (t) {
         if (t->bucket_shift < 8 || t->bucket_shift > 30)
             return fail(HPEEL_ERR_INVALID_ARG, "bucket_shift %u outside [8, 30]", t->bucket_shift);

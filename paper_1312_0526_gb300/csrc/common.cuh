@@ -29,7 +29,11 @@ struct Ctl {
     uint32_t next_size;  // size of the layer the next round deletes
     uint32_t scur;       // solve-record cursor of a dense round
     uint32_t cross;      // vertices that fell from degree 2 to 1 (all rounds)
-    uint32_t pad[6];
+    uint32_t first_layer;   // |L_0|
+    uint32_t dense_rounds;  // rounds that streamed all edge records
+    uint32_t dense_edges;   // edges those rounds deleted
+    uint32_t dense_cross;   // degree 2 -> 1 falls in those rounds
+    uint32_t pad[2];
 };
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): two

@@ -75,17 +75,25 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
                            unsigned long long *st, Ctl *ctl);
 
+// A kernel of the round loop and its launch shape, for graph nodes.
+struct RoundLaunch {
+    void *fn;
+    unsigned grid, block;
+};
+
 // a3 + a4 of round 0: scan all vertices, claim the edge of every degree-1
 // vertex; publishes loff[0..1].
 void launch_round0(const Launch &L, const unsigned long long *st, uint32_t m, uint32_t r,
                    uint32_t P, uint32_t n, uint4 *rec, uint32_t *loff, Ctl *ctl);
+RoundLaunch round0_launch(const Launch &L, uint32_t r, uint32_t m);
 
 // a5 + a4 of the next round + a6: delete layer t (t read on the device),
 // claim and list layer t+1, close the round.  with_s: write MWHC solve
 // records (r = 3).
-void launch_round(const Launch &L, bool dense, bool with_s, uint32_t r, uint32_t *Llist,
-                  uint32_t *loff, uint32_t n, unsigned long long *st, uint4 *rec, uint4 *S,
-                  Ctl *ctl);
+void launch_round(const Launch &L, bool with_s, uint32_t r, uint32_t *Llist, uint32_t *loff,
+                  uint32_t n, uint32_t dense_div, unsigned long long *st, uint4 *rec, uint4 *S,
+                  Ctl *ctl, uint32_t max_rounds);
+RoundLaunch round_launch(const Launch &L, bool with_s, uint32_t r);
 
 // claim[e] = claim word of record e.
 void launch_extract_claim(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,

@@ -124,9 +124,14 @@ void launch_build_incidence(const Launch &L, const uint4 *rec, uint32_t n, uint3
 // ------------------------------------------------------- round epilogue --
 // Every block adds its counts; the last block of the launch to finish
 // closes round t: layer L_{t+1} is [loff[t+1], lcur) now that every append
-// of the launch is done.  No block waits for another.
+// of the launch is done.  No block waits for another.  When the launch runs
+// inside a CUDA graph's while node, the last block also sets the node's
+// condition: 1 while the next layer is non-empty and the layer table has
+// room (the loop ends after at most max_rounds launches whatever happens).
 __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t,
-                                            uint32_t crossings) {
+                                            uint32_t crossings, bool dense, uint32_t layer,
+                                            uint32_t max_rounds,
+                                            cudaGraphConditionalHandle cond) {
     __shared__ uint32_t s_cross;
     if (threadIdx.x == 0) s_cross = 0;
     __syncthreads();
@@ -141,11 +146,22 @@ __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t
             const uint32_t end = atomicAdd(&ctl->lcur, 0u);
             const uint32_t beg = loff[t + 1];
             loff[t + 2] = end;
+            uint32_t more = end > beg ? 1u : 0u;
+            if (more && t + 2 >= max_rounds) {  // round t+1 would overflow loff
+                more = 0;
+                atomicCAS(&ctl->err, 0u, (uint32_t)kDevCapacity);
+            }
+            if (dense) {
+                ctl->dense_rounds += 1;
+                ctl->dense_edges += layer;
+                ctl->dense_cross += s_cross;
+            }
             ctl->next_size = end - beg;
-            ctl->more = end > beg ? 1u : 0u;
+            ctl->more = more;
             ctl->scur = beg;
             ctl->done = 0;
             ctl->round = t + 1;
+            if (cond) cudaGraphSetConditional(cond, more);
         }
     }
 }
@@ -159,7 +175,8 @@ constexpr int kR0Items = 4;
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_round0(const unsigned long long *__restrict__ st, uint32_t m, uint32_t P, uint32_t n,
-         uint4 *__restrict__ rec, uint32_t *__restrict__ loff, Ctl *ctl) {
+         uint4 *__restrict__ rec, uint32_t *__restrict__ loff, Ctl *ctl,
+         cudaGraphConditionalHandle cond) {
     constexpr uint32_t kStep = kThreads * kR0Items;
     const uint64_t stride = (uint64_t)gridDim.x * kStep;
     uint32_t first = 0;
@@ -197,21 +214,35 @@ k_round0(const unsigned long long *__restrict__ st, uint32_t m, uint32_t P, uint
             loff[0] = 0;
             loff[1] = end;
             ctl->next_size = end;
+            ctl->first_layer = end;
             ctl->more = end > 0 ? 1u : 0u;
             ctl->scur = 0;
             ctl->done = 0;
             ctl->round = 0;
+            if (cond) cudaGraphSetConditional(cond, end > 0 ? 1u : 0u);
         }
     }
+}
+
+template <int R>
+void *round0_fn() { return (void *)k_round0<R>; }
+
+RoundLaunch round0_launch(const Launch &L, uint32_t r, uint32_t m) {
+    RoundLaunch k{};
+    k.grid = grid_for(L, m ? m : 1, kR0Items, 8);
+    k.block = kThreads;
+    k.fn = r == 2 ? round0_fn<2>() : (r == 3 ? round0_fn<3>() : round0_fn<4>());
+    return k;
 }
 
 void launch_round0(const Launch &L, const unsigned long long *st, uint32_t m, uint32_t r,
                    uint32_t P, uint32_t n, uint4 *rec, uint32_t *loff, Ctl *ctl) {
     const unsigned grid = grid_for(L, m ? m : 1, kR0Items, 8);
+    const cudaGraphConditionalHandle c0 = 0;
     switch (r) {
-    case 2: count_launch(); k_round0<2><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl); break;
-    case 3: count_launch(); k_round0<3><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl); break;
-    case 4: count_launch(); k_round0<4><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl); break;
+    case 2: count_launch(); k_round0<2><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl, c0); break;
+    case 3: count_launch(); k_round0<3><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl, c0); break;
+    case 4: count_launch(); k_round0<4><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl, c0); break;
     }
 }
 
@@ -248,21 +279,28 @@ __device__ __forceinline__ uint32_t delete_edge(uint32_t e, uint32_t c, const ui
 
 constexpr int kStageCap = 256;  // staged appends per warp
 
-// Sparse round: the edges of L_t from the list; solve record i of L_t.
+// Round t: delete layer L_t and list layer L_{t+1}.  A layer holding more
+// than n / dense_div edges is read by streaming all edge records and keeping
+// those claimed in round t (no solve records: such a layer is assigned from a
+// record stream too); a smaller one is read from the list, and its solve
+// record i goes to S[i].  Round 0 is always dense (L_0 is not listed).  The
+// choice depends only on device values all blocks read alike.
 template <int R, bool WITH_S>
 __global__ void __launch_bounds__(kThreads)
-k_round_sparse(uint32_t *__restrict__ Llist, uint32_t *__restrict__ loff, uint32_t n,
-               unsigned long long *__restrict__ st, uint4 *__restrict__ rec,
-               uint4 *__restrict__ S, Ctl *ctl) {
+k_round(uint32_t *__restrict__ Llist, uint32_t *__restrict__ loff, uint32_t n, uint32_t dense_div,
+        unsigned long long *__restrict__ st, uint4 *__restrict__ rec, uint4 *__restrict__ S,
+        Ctl *ctl, uint32_t max_rounds, cudaGraphConditionalHandle cond) {
     __shared__ uint32_t stage_buf[kThreads / 32][kStageCap];
     WarpStage<kStageCap> stage{stage_buf[threadIdx.x >> 5], 0};
     const uint32_t t = *(volatile uint32_t *)&ctl->round;
     const uint32_t lb = loff[t], le = loff[t + 1];
+    const bool dense = t == 0 || (le - lb) > n / dense_div;
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     uint32_t cross = 0;
+    const uint64_t first = dense ? 0 : lb, last = dense ? n : le;
     // warp-uniform trip count: whole warps step together
-    for (uint64_t base = lb + ((uint64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u));
-         base < le; base += stride) {
+    for (uint64_t base = first + ((uint64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u));
+         base < last; base += stride) {
         const uint64_t i = base + (threadIdx.x & 31u);
         bool take[R - 1];
         uint32_t f[R - 1];
@@ -271,77 +309,56 @@ k_round_sparse(uint32_t *__restrict__ Llist, uint32_t *__restrict__ loff, uint32
             take[k] = false;
             f[k] = 0;
         }
-        if (i < le) {
-            const uint32_t e = Llist[i];
+        if (i < last) {
             uint32_t v[4];
-            const uint32_t c = load_record<R>(rec, e, v);
-            cross += delete_edge<R>(e, c, v, t, n, st, rec, ctl, take, f);
-            if (WITH_S) S[i] = solve_record(c, v);
+            if (dense) {
+                const uint32_t c = load_record_stream<R>(rec, i, v);
+                if (c != kUnclaimed && (c >> 2) == t)
+                    cross += delete_edge<R>((uint32_t)i, c, v, t, n, st, rec, ctl, take, f);
+            } else {
+                const uint32_t e = Llist[i];
+                const uint32_t c = load_record<R>(rec, e, v);
+                cross += delete_edge<R>(e, c, v, t, n, st, rec, ctl, take, f);
+                if (WITH_S) S[i] = solve_record(c, v);
+            }
         }
 #pragma unroll
         for (int k = 0; k < R - 1; k++) stage.push(take[k], f[k], &ctl->lcur, Llist);
     }
     stage.flush(&ctl->lcur, Llist);
-    close_round(ctl, loff, t, cross);
+    close_round(ctl, loff, t, cross, dense, le - lb, max_rounds, cond);
 }
 
-// Dense round: stream all edge records, keep those claimed in round t (no
-// solve records: a dense layer is assigned from a record stream as well).
-template <int R>
-__global__ void __launch_bounds__(kThreads)
-k_round_dense(uint32_t *__restrict__ Llist, uint32_t *__restrict__ loff, uint32_t n,
-              unsigned long long *__restrict__ st, uint4 *__restrict__ rec, Ctl *ctl) {
-    __shared__ uint32_t stage_buf[kThreads / 32][kStageCap];
-    WarpStage<kStageCap> stage{stage_buf[threadIdx.x >> 5], 0};
-    const uint32_t t = *(volatile uint32_t *)&ctl->round;
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    uint32_t cross = 0;
-    for (uint64_t base = (uint64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u); base < n;
-         base += stride) {
-        const uint64_t e = base + (threadIdx.x & 31u);
-        bool take[R - 1];
-        uint32_t f[R - 1];
-#pragma unroll
-        for (int k = 0; k < R - 1; k++) {
-            take[k] = false;
-            f[k] = 0;
-        }
-        if (e < n) {
-            uint32_t v[4];
-            const uint32_t c = load_record_stream<R>(rec, e, v);
-            if (c != kUnclaimed && (c >> 2) == t)
-                cross += delete_edge<R>((uint32_t)e, c, v, t, n, st, rec, ctl, take, f);
-        }
-#pragma unroll
-        for (int k = 0; k < R - 1; k++) stage.push(take[k], f[k], &ctl->lcur, Llist);
-    }
-    stage.flush(&ctl->lcur, Llist);
-    close_round(ctl, loff, t, cross);
+template <int R, bool WS>
+void *round_fn() { return (void *)k_round<R, WS>; }
+
+RoundLaunch round_launch(const Launch &L, bool with_s, uint32_t r) {
+    RoundLaunch k{};
+    k.grid = grid_fixed(L, 8);
+    k.block = kThreads;
+    if (with_s)
+        k.fn = round_fn<3, true>();  // solve records exist for the r = 3 MPHF only
+    else
+        k.fn = r == 2 ? round_fn<2, false>() : (r == 3 ? round_fn<3, false>() : round_fn<4, false>());
+    return k;
 }
 
-void launch_round(const Launch &L, bool dense, bool with_s, uint32_t r, uint32_t *Llist,
-                  uint32_t *loff, uint32_t n, unsigned long long *st, uint4 *rec, uint4 *S,
-                  Ctl *ctl) {
-    const unsigned grid = dense ? grid_for(L, n ? n : 1, 1, 8) : grid_fixed(L, 8);
-#define HP_ROUND(RR, WS)                                                                      \
-    do {                                                                                      \
-        count_launch();                                                                       \
-        if (dense)                                                                            \
-            k_round_dense<RR><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, st, rec, ctl); \
-        else                                                                                  \
-            k_round_sparse<RR, WS><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, st, rec,  \
-                                                                    S, ctl);                  \
-    } while (0)
+void launch_round(const Launch &L, bool with_s, uint32_t r, uint32_t *Llist, uint32_t *loff,
+                  uint32_t n, uint32_t dense_div, unsigned long long *st, uint4 *rec, uint4 *S,
+                  Ctl *ctl, uint32_t max_rounds) {
+    const unsigned grid = grid_fixed(L, 8);
+    const cudaGraphConditionalHandle c0 = 0;
+    count_launch();
     if (with_s) {
-        HP_ROUND(3, true);  // solve records exist for the r = 3 MPHF only
-    } else {
-        switch (r) {
-        case 2: HP_ROUND(2, false); break;
-        case 3: HP_ROUND(3, false); break;
-        case 4: HP_ROUND(4, false); break;
-        }
+        k_round<3, true><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S,
+                                                         ctl, max_rounds, c0);
+        return;
     }
-#undef HP_ROUND
+    switch (r) {
+    case 2: k_round<2, false><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S, ctl, max_rounds, c0); break;
+    case 3: k_round<3, false><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S, ctl, max_rounds, c0); break;
+    case 4: k_round<4, false><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S, ctl, max_rounds, c0); break;
+    }
 }
 
 // --------------------------------------------------------------- claims --

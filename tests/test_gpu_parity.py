@@ -273,3 +273,46 @@ def test_peel_and_mphf_parity_1e7_default_tuning():
     got = hp.mphf_build(_dev(keys), seed=1, order=order)
     assert np.array_equal(_u64(got.G), want.G)
     assert np.array_equal(_u64(got.rank_dir), want.dir)
+
+
+# ----------------------------------------------------- round-loop drivers --
+
+@pytest.fixture
+def host_round_loop():
+    """The host launches every round instead of the device-side graph loop."""
+    hp.set_tuning(host_round_loop=1)
+    yield
+    hp.set_tuning()
+
+
+@pytest.mark.parametrize("n,gamma,r", [(100_000, 1230, 3), (100_000, 1200, 3),
+                                       (50_000, 1300, 4), (3, 1230, 3)])
+def test_peel_parity_host_round_loop(host_round_loop, n, gamma, r):
+    m = oracle.num_vertices(n, gamma, r)
+    edges = oracle.hash_edges(inputs.keys(n, 6), m, r, 1)
+    _check_peel(edges, m)
+
+
+def test_mphf_parity_host_round_loop(host_round_loop):
+    keys = inputs.keys(200_000, 8)
+    want = oracle.mphf_build(keys, seed=1)
+    got = hp.mphf_build(_dev(keys), seed=1)
+    assert np.array_equal(_u64(got.G), want.G)
+    assert np.array_equal(_u64(got.rank_dir), want.dir)
+
+
+@pytest.mark.parametrize("dense_div", [1, 2, 1000000])
+def test_peel_parity_dense_threshold(dense_div):
+    # every layer sparse (1), every layer dense (1e6), in between (2)
+    hp.set_tuning(dense_div=dense_div)
+    try:
+        n = 120_000
+        m = oracle.num_vertices(n, 1230, 3)
+        edges = oracle.hash_edges(inputs.keys(n, 12), m, 3, 1)
+        _check_peel(edges, m)
+        keys = inputs.keys(n, 13)
+        want = oracle.mphf_build(keys, seed=1)
+        got = hp.mphf_build(_dev(keys), seed=1)
+        assert np.array_equal(_u64(got.G), want.G)
+    finally:
+        hp.set_tuning()
