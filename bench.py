@@ -179,6 +179,30 @@ def cpu_baseline():
                       f"{res.rounds} rounds"}
 
 
+def lookup_leg(keys, G, D, m, seed):
+    """MPHF lookups of the n build keys (hpeel_mphf_lookup), and the space of
+    the built function."""
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+
+    out = torch.empty(keys.shape[0], dtype=torch.int32, device="cuda")
+    hp.mphf_lookup(keys, seed, m, G, D, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    a.record()
+    for _ in range(reps):
+        hp.mphf_lookup(keys, seed, m, G, D, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    n = keys.shape[0]
+    ok = bool(torch.equal(torch.sort(out)[0], torch.arange(n, dtype=torch.int32, device="cuda")))
+    return {"value": n / ms / 1e3, "unit": "Mlookups/s", "ms": ms, "bijection": ok,
+            "bits_per_key": hp.mphf_bits_per_key(n, GAMMA_MILLI)}
+
+
 BATCH_B = 65536
 
 
@@ -255,6 +279,49 @@ def batched_leg(steps, warmup):
     return out
 
 
+SERVE_REQUESTS = 200
+
+
+def serving_leg():
+    """Serving: MPHF build requests with Poisson arrivals, key-set sizes
+    log-uniform 1e3..1e7 (SplitMix64 keys, seed 1000 + request), gamma 1.23;
+    4 slots, 32 GiB admission budget, keys uploaded from pinned host memory
+    inside each request's latency.  The arrival rate is swept as a fraction
+    of the capacity measured with one slot and every request queued at once."""
+    import numpy as np
+    import torch
+
+    from paper_1312_0526_gb300 import inputs, serve
+
+    unit_arrivals, sizes, seeds = inputs.request_stream(SERVE_REQUESTS, rate_per_s=1.0, seed=4)
+    keysets = [torch.from_numpy(inputs.keys(int(s), int(k)).view(np.int64)).pin_memory()
+               for s, k in zip(sizes, seeds)]
+    srv = serve.MphfServer(slots=1, hbm_budget=32 << 30, keep_results=False, max_tries=32)
+    try:
+        serve.run_stream(srv, keysets[:8], [0.0] * 8)  # warm-up (workspace, graphs)
+        srv.results.clear()
+        res = serve.run_stream(srv, keysets, [0.0] * len(keysets))
+    finally:
+        srv.close()
+    span = max(r.finished for r in res) - min(r.arrival for r in res)
+    capacity = len(res) / span
+    out = {"requests": SERVE_REQUESTS, "mean_keys": float(np.mean(sizes)),
+           "capacity_req_per_s": capacity, "isolated": serve.latency_summary(res), "rates": []}
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.1):
+        rate = frac * capacity
+        srv = serve.MphfServer(slots=4, hbm_budget=32 << 30, keep_results=False,
+                               max_tries=32)
+        try:
+            res = serve.run_stream(srv, keysets, list(unit_arrivals / rate))
+            summ = serve.latency_summary(res)
+            summ.update({"load": frac, "rate_req_per_s": rate,
+                         "max_concurrent": srv.max_running})
+            out["rates"].append(summ)
+        finally:
+            srv.close()
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -295,6 +362,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_KEYS, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-serving", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -422,6 +490,10 @@ def main():
     batched = None
     if world == 1 and not args.no_batched:
         batched = batched_leg(args.steps, args.warmup)
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = serving_leg()
+    lookup = lookup_leg(keys, G, D, m, res.stats["seed_used"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -443,6 +515,8 @@ def main():
                 "d2h_bytes_per_step": (G.numel() + D.numel()) * 8, "ms_per_step": e2e_ms},
         "steps_ms": {k: v[1] / args.steps for k, v in sorted(prof.items())},
         "batched": batched,
+        "serving": serving,
+        "lookup": lookup,
     }
     print(json.dumps(line), flush=True)
     if dist:

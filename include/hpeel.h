@@ -231,6 +231,23 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
                               void *stream);
 
 /*
+ * MPHF lookup (sec. 3; sec. 5 broadword rank): for each query key, hash it
+ * with the build's seed into v_0, v_1, v_2 (as hpeel_hash_edges with r = 3),
+ * take i = (g[v_0] + g[v_1] + g[v_2]) mod 3 (a stored 3 is 0) and return the
+ * rank of v_i among the assigned vertices:
+ *   d_rank_dir[v_i / 512] + non-zero 2-bit values in [512 (v_i / 512), v_i).
+ * For a key of the build set the result is its MPHF value in [0, n) (a
+ * bijection onto [0, n)); for any other key it is some value in [0, n].
+ *   d_keys [nq] uint64; seed = hpeel_stats.seed_used of the build; m =
+ *   hpeel_num_vertices(n, gamma_milli, 3); d_G, d_rank_dir as
+ *   hpeel_mphf_build wrote them; d_out [nq] uint32 output.
+ * Asynchronous.  Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_CUDA.
+ */
+hpeel_status hpeel_mphf_lookup(const uint64_t *d_keys, uint64_t nq, uint64_t seed,
+                               uint64_t m, const uint64_t *d_G, const uint64_t *d_rank_dir,
+                               uint32_t *d_out, void *stream);
+
+/*
  * Batched peel of many independent bucket hypergraphs (the bucketed layout of
  * sec. 3 "Practical workarounds (HEM)": one small MWHC hypergraph per bucket),
  * r = 3.  Bucket b holds keys d_keys[off[b] .. off[b+1]) (n_b of them, at most

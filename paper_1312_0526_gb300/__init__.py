@@ -119,6 +119,8 @@ def lib():
         L.hpeel_peel_batched.restype = st
         L.hpeel_peel_batched.argtypes = [p, p, u32, u32, p, p, p, p, p,
                                          ctypes.POINTER(BatchTuning), p, sz, p]
+        L.hpeel_mphf_lookup.restype = st
+        L.hpeel_mphf_lookup.argtypes = [p, u64, u64, u64, p, p, p, p]
         L.hpeel_kernel_launches.restype = u64
         L.hpeel_kernel_launches.argtypes = []
         L.hpeel_profile_enable.restype = None
@@ -220,6 +222,25 @@ def peel(edges, m: int, workspace=None, max_layers: int = 4096) -> PeelResult:
     res = PeelResult(order, claim, loff[:R + 1], R, int(st.n_peeled))
     res.stats = st.as_dict()
     return res
+
+
+def mphf_lookup(keys, seed: int, m: int, G, rank_dir, out=None):
+    """MPHF values of the query keys (hpeel_mphf_lookup): int32 [nq]."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    if out is None:
+        out = torch.empty(keys.shape[0], dtype=torch.int32, device=keys.device)
+    _check(lib().hpeel_mphf_lookup(kp, keys.shape[0], seed, m, _dev_ptr(G, "G", torch.int64),
+                                   _dev_ptr(rank_dir, "rank_dir", torch.int64),
+                                   _dev_ptr(out, "out", torch.int32), _stream()))
+    return out
+
+
+def mphf_bits_per_key(n: int, gamma_milli: int = 1230) -> float:
+    """Space of the built function: 2 bits per vertex plus a 64-bit rank count
+    per 512 vertices (Table "space" of the paper: 2.61 bits/key at 1.23)."""
+    m = num_vertices(n, gamma_milli, 3)
+    return (64 * ((m + 31) // 32) + 64 * ((m + 511) // 512 + 1)) / max(n, 1)
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -34,7 +34,7 @@ Ctl *pinned_ctl() {
 }
 
 struct PeelLayout {
-    size_t ctl, rec, state, claim, L, S, pairs, fill, loff, hist, scantmp, total;
+    size_t ctl, params, rec, state, claim, L, S, pairs, fill, loff, hist, scantmp, total;
     uint32_t max_rounds;
     bool bucketed;
     BucketPlan plan;
@@ -66,6 +66,7 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool with_s) {
     p.bucketed = n > 0 && m >= tu.bucket_min_vertices;
     if (p.bucketed) p.plan = bucket_plan(n, m, r, tu.bucket_shift);
     p.ctl = take(sizeof(Ctl));
+    p.params = take(sizeof(RoundParams));
     p.rec = take((r == 4 ? 32 : 16) * n);
     p.state = take(8 * m);
     p.claim = take(4 * n);
@@ -148,17 +149,14 @@ std::map<std::string, RoundGraph> g_graphs;
 std::vector<std::string> g_graph_order;
 
 hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool with_s,
-                                unsigned long long *st, uint32_t m, uint32_t P, uint32_t n,
-                                uint4 *rec, uint32_t *loff, Ctl *ctl, uint32_t *Ll,
-                                uint32_t dense_div, uint4 *S, uint32_t max_rounds) {
+                                const RoundParams *prm) {
     int dev = 0;
     HP_CUDA(cudaGetDevice(&dev));
-    const RoundLaunch k0 = round0_launch(L, r, m);
+    const RoundLaunch k0 = round0_launch(L, r);
     const RoundLaunch k1 = round_launch(L, with_s, r);
-    char keybuf[256];
-    snprintf(keybuf, sizeof keybuf, "%d|%p|%p|%p|%u|%u|%u|%p|%p|%p|%p|%u|%p|%u|%u|%u", dev, k0.fn,
-             k1.fn, (void *)st, m, P, n, (void *)rec, (void *)loff, (void *)ctl, (void *)Ll,
-             dense_div, (void *)S, max_rounds, k0.grid, k1.grid);
+    char keybuf[160];
+    snprintf(keybuf, sizeof keybuf, "%d|%p|%p|%p|%u|%u", dev, k0.fn, k1.fn, (const void *)prm,
+             k0.grid, k1.grid);
     const std::string key(keybuf);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = g_graphs.find(key);
@@ -167,13 +165,12 @@ hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool with_s,
         HP_CUDA(cudaGraphCreate(&rg.graph, 0));
         cudaGraphConditionalHandle h = 0;
         HP_CUDA(cudaGraphConditionalHandleCreate(&h, rg.graph, 0, 0));
-        const unsigned long long *st_c = st;
-        void *a0[] = {(void *)&st_c, &m, &P, &n, &rec, &loff, &ctl, &h};
+        void *args[] = {(void *)&prm, &h};
         cudaKernelNodeParams p0{};
         p0.func = k0.fn;
         p0.gridDim = dim3(k0.grid);
         p0.blockDim = dim3(k0.block);
-        p0.kernelParams = a0;
+        p0.kernelParams = args;
         cudaGraphNode_t n0, nw, n1;
         HP_CUDA(cudaGraphAddKernelNode(&n0, rg.graph, nullptr, 0, &p0));
         cudaGraphNodeParams cp{};
@@ -183,12 +180,11 @@ hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool with_s,
         cp.conditional.size = 1;
         HP_CUDA(cudaGraphAddNode(&nw, rg.graph, &n0, nullptr, 1, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
-        void *a1[] = {&Ll, &loff, &n, &dense_div, &st, &rec, &S, &ctl, &max_rounds, &h};
         cudaKernelNodeParams p1{};
         p1.func = k1.fn;
         p1.gridDim = dim3(k1.grid);
         p1.blockDim = dim3(k1.block);
-        p1.kernelParams = a1;
+        p1.kernelParams = args;
         HP_CUDA(cudaGraphAddKernelNode(&n1, body, nullptr, 0, &p1));
         HP_CUDA(cudaGraphInstantiate(&rg.exec, rg.graph, 0));
         if (g_graph_order.size() >= 16) {  // keep the 16 most recent
@@ -250,11 +246,25 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     }
     HP_TRY(check_launch("build"));
     const uint32_t dense_div = std::max(1u, tu.dense_div);
+    RoundParams hp_prm{};
+    hp_prm.st = st;
+    hp_prm.rec = rec;
+    hp_prm.Llist = Ll;
+    hp_prm.loff = loff;
+    hp_prm.S = S;
+    hp_prm.ctl = ctl;
+    hp_prm.n = n;
+    hp_prm.m = m;
+    hp_prm.P = P;
+    hp_prm.dense_div = dense_div;
+    hp_prm.max_rounds = lay.max_rounds;
+    RoundParams *prm = reinterpret_cast<RoundParams *>(ws + lay.params);
+    HP_CUDA(cudaMemcpyAsync(prm, &hp_prm, sizeof hp_prm, cudaMemcpyHostToDevice, L.stream));
     if (tu.host_round_loop) {
         // one launch per round, the control block read back after each
         {
             ProfScope ps(L, "round0");
-            launch_round0(L, st, m, r, P, n, rec, loff, ctl);
+            launch_round0(L, r, prm);
         }
         HP_TRY(check_launch("round0"));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
@@ -262,8 +272,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         while (hctl->more && !hctl->err) {
             {
                 ProfScope ps(L, "rounds");
-                launch_round(L, io.with_s, r, Ll, loff, n, dense_div, st, rec, S, ctl,
-                             lay.max_rounds);
+                launch_round(L, io.with_s, r, prm);
             }
             HP_TRY(check_launch("round"));
             HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
@@ -273,8 +282,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         // round 0 and a CUDA-graph while node around the round kernel: the
         // rounds run back to back on the device, one read-back at the end
         ProfScope ps(L, "rounds");
-        HP_TRY(launch_round_graph(L, r, io.with_s, st, m, P, n, rec, loff, ctl, Ll, dense_div, S,
-                                  lay.max_rounds));
+        HP_TRY(launch_round_graph(L, r, io.with_s, prm));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
         count_launch(hctl->round + (hctl->more ? 1 : 0));
@@ -565,6 +573,22 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
     }
     return fail(HPEEL_ERR_RETRIES_EXHAUSTED, "2-core non-empty for seeds %llu..%llu",
                 (unsigned long long)seed, (unsigned long long)(seed + max_tries - 1));
+}
+
+hpeel_status hpeel_mphf_lookup(const uint64_t *d_keys, uint64_t nq, uint64_t seed,
+                               uint64_t m, const uint64_t *d_G, const uint64_t *d_rank_dir,
+                               uint32_t *d_out, void *stream) {
+    g_last_error.clear();
+    if (nq == 0) return HPEEL_OK;
+    if (m < 3 || m % 3 != 0 || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of 3 below 2^32",
+                    (unsigned long long)m);
+    if (!d_keys || !d_G || !d_rank_dir || !d_out) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    ProfScope ps(L, "lookup");
+    launch_lookup(L, d_keys, nq, make_fastmod(m / 3), seed, d_G, d_rank_dir, d_out);
+    return check_launch("lookup");
 }
 
 }  // extern "C"

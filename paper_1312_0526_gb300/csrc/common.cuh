@@ -36,6 +36,18 @@ struct Ctl {
     uint32_t pad[2];
 };
 
+// Arguments of the round-loop kernels, kept in the workspace so the CUDA
+// graph of a round loop depends only on where the workspace is.
+struct RoundParams {
+    unsigned long long *st;  // vertex records [m]
+    uint4 *rec;              // edge records [n]
+    uint32_t *Llist;         // layer list [n]
+    uint32_t *loff;          // layer starts
+    uint4 *S;                // solve records (or null)
+    Ctl *ctl;
+    uint32_t n, m, P, dense_div, max_rounds, pad[3];
+};
+
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): two
 // xorshift-multiply steps and a final xorshift, modulo 2^64.
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {

@@ -83,16 +83,13 @@ struct RoundLaunch {
 
 // a3 + a4 of round 0: scan all vertices, claim the edge of every degree-1
 // vertex; publishes loff[0..1].
-void launch_round0(const Launch &L, const unsigned long long *st, uint32_t m, uint32_t r,
-                   uint32_t P, uint32_t n, uint4 *rec, uint32_t *loff, Ctl *ctl);
-RoundLaunch round0_launch(const Launch &L, uint32_t r, uint32_t m);
+void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm);
+RoundLaunch round0_launch(const Launch &L, uint32_t r);
 
 // a5 + a4 of the next round + a6: delete layer t (t read on the device),
 // claim and list layer t+1, close the round.  with_s: write MWHC solve
 // records (r = 3).
-void launch_round(const Launch &L, bool with_s, uint32_t r, uint32_t *Llist, uint32_t *loff,
-                  uint32_t n, uint32_t dense_div, unsigned long long *st, uint4 *rec, uint4 *S,
-                  Ctl *ctl, uint32_t max_rounds);
+void launch_round(const Launch &L, bool with_s, uint32_t r, const RoundParams *prm);
 RoundLaunch round_launch(const Launch &L, bool with_s, uint32_t r);
 
 // claim[e] = claim word of record e.
@@ -130,5 +127,8 @@ void launch_assign_layer(const Launch &L, bool dense, const uint4 *S, const uint
 void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt);
 void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,
                       uint64_t blocks, uint64_t *dir);
+// MPHF lookup of nq keys.
+void launch_lookup(const Launch &L, const uint64_t *keys, uint64_t nq, FastMod fm, uint64_t seed,
+                   const uint64_t *G, const uint64_t *dir, uint32_t *out);
 
 }  // namespace hp

@@ -114,4 +114,42 @@ void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *
                                                                           dir);
 }
 
+// ---------------------------------------------------------------- lookup --
+// MPHF value of a key (sec. 3 and sec. 5): hash to h_0..h_2, i = (g[h_0] +
+// g[h_1] + g[h_2]) mod 3 (a stored 3 counts as 0), v = h_i, and the value is
+// the rank of v among the assigned vertices: the directory entry of v's
+// 512-vertex block plus the non-zero pairs before v inside the block,
+// counted a word at a time with the broadword expression.
+__global__ void __launch_bounds__(kThreads)
+k_lookup(const uint64_t *__restrict__ keys, uint64_t nq, FastMod fm, uint64_t seed,
+         const uint64_t *__restrict__ G, const uint64_t *__restrict__ dir,
+         uint32_t *__restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    const uint32_t P = (uint32_t)fm.P;
+    for (uint64_t q = (uint64_t)blockIdx.x * kThreads + threadIdx.x; q < nq; q += stride) {
+        const uint64_t k = __ldcs(keys + q);
+        uint32_t v[3], g = 0;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            v[j] = (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) + (uint32_t)j * P;
+            g += (uint32_t)(__ldg(G + (v[j] >> 5)) >> (2u * (v[j] & 31u))) & 3u;
+        }
+        const uint32_t i = g % 3u;
+        const uint32_t x = i == 0 ? v[0] : (i == 1 ? v[1] : v[2]);
+        const uint32_t blk = x >> 9, w_end = x >> 5;
+        uint64_t rank = __ldg(dir + blk);
+        for (uint32_t w = blk << 4; w < w_end; w++) rank += nonzero_pairs(__ldg(G + w));
+        const uint32_t sh = 2u * (x & 31u);
+        if (sh) rank += nonzero_pairs(__ldg(G + w_end) & ((1ull << sh) - 1ull));
+        out[q] = (uint32_t)rank;
+    }
+}
+
+void launch_lookup(const Launch &L, const uint64_t *keys, uint64_t nq, FastMod fm, uint64_t seed,
+                   const uint64_t *G, const uint64_t *dir, uint32_t *out) {
+    if (nq == 0) return;
+    count_launch();
+    k_lookup<<<grid_for(L, nq, 1, 8), kThreads, 0, L.stream>>>(keys, nq, fm, seed, G, dir, out);
+}
+
 }  // namespace hp

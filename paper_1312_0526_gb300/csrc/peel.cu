@@ -174,9 +174,12 @@ constexpr int kR0Items = 4;
 
 template <int R>
 __global__ void __launch_bounds__(kThreads)
-k_round0(const unsigned long long *__restrict__ st, uint32_t m, uint32_t P, uint32_t n,
-         uint4 *__restrict__ rec, uint32_t *__restrict__ loff, Ctl *ctl,
-         cudaGraphConditionalHandle cond) {
+k_round0(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
+    const unsigned long long *__restrict__ st = prm->st;
+    uint4 *__restrict__ rec = prm->rec;
+    uint32_t *__restrict__ loff = prm->loff;
+    Ctl *ctl = prm->ctl;
+    const uint32_t m = prm->m, P = prm->P, n = prm->n;
     constexpr uint32_t kStep = kThreads * kR0Items;
     const uint64_t stride = (uint64_t)gridDim.x * kStep;
     uint32_t first = 0;
@@ -227,22 +230,22 @@ k_round0(const unsigned long long *__restrict__ st, uint32_t m, uint32_t P, uint
 template <int R>
 void *round0_fn() { return (void *)k_round0<R>; }
 
-RoundLaunch round0_launch(const Launch &L, uint32_t r, uint32_t m) {
+RoundLaunch round0_launch(const Launch &L, uint32_t r) {
     RoundLaunch k{};
-    k.grid = grid_for(L, m ? m : 1, kR0Items, 8);
+    k.grid = grid_fixed(L, 8);
     k.block = kThreads;
     k.fn = r == 2 ? round0_fn<2>() : (r == 3 ? round0_fn<3>() : round0_fn<4>());
     return k;
 }
 
-void launch_round0(const Launch &L, const unsigned long long *st, uint32_t m, uint32_t r,
-                   uint32_t P, uint32_t n, uint4 *rec, uint32_t *loff, Ctl *ctl) {
-    const unsigned grid = grid_for(L, m ? m : 1, kR0Items, 8);
+void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm) {
+    const unsigned grid = grid_fixed(L, 8);
     const cudaGraphConditionalHandle c0 = 0;
+    count_launch();
     switch (r) {
-    case 2: count_launch(); k_round0<2><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl, c0); break;
-    case 3: count_launch(); k_round0<3><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl, c0); break;
-    case 4: count_launch(); k_round0<4><<<grid, kThreads, 0, L.stream>>>(st, m, P, n, rec, loff, ctl, c0); break;
+    case 2: k_round0<2><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
+    case 3: k_round0<3><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
+    case 4: k_round0<4><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
     }
 }
 
@@ -287,9 +290,14 @@ constexpr int kStageCap = 256;  // staged appends per warp
 // choice depends only on device values all blocks read alike.
 template <int R, bool WITH_S>
 __global__ void __launch_bounds__(kThreads)
-k_round(uint32_t *__restrict__ Llist, uint32_t *__restrict__ loff, uint32_t n, uint32_t dense_div,
-        unsigned long long *__restrict__ st, uint4 *__restrict__ rec, uint4 *__restrict__ S,
-        Ctl *ctl, uint32_t max_rounds, cudaGraphConditionalHandle cond) {
+k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
+    uint32_t *__restrict__ Llist = prm->Llist;
+    uint32_t *__restrict__ loff = prm->loff;
+    unsigned long long *__restrict__ st = prm->st;
+    uint4 *__restrict__ rec = prm->rec;
+    uint4 *__restrict__ S = prm->S;
+    Ctl *ctl = prm->ctl;
+    const uint32_t n = prm->n, dense_div = prm->dense_div, max_rounds = prm->max_rounds;
     __shared__ uint32_t stage_buf[kThreads / 32][kStageCap];
     WarpStage<kStageCap> stage{stage_buf[threadIdx.x >> 5], 0};
     const uint32_t t = *(volatile uint32_t *)&ctl->round;
@@ -343,21 +351,18 @@ RoundLaunch round_launch(const Launch &L, bool with_s, uint32_t r) {
     return k;
 }
 
-void launch_round(const Launch &L, bool with_s, uint32_t r, uint32_t *Llist, uint32_t *loff,
-                  uint32_t n, uint32_t dense_div, unsigned long long *st, uint4 *rec, uint4 *S,
-                  Ctl *ctl, uint32_t max_rounds) {
+void launch_round(const Launch &L, bool with_s, uint32_t r, const RoundParams *prm) {
     const unsigned grid = grid_fixed(L, 8);
     const cudaGraphConditionalHandle c0 = 0;
     count_launch();
     if (with_s) {
-        k_round<3, true><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S,
-                                                         ctl, max_rounds, c0);
+        k_round<3, true><<<grid, kThreads, 0, L.stream>>>(prm, c0);
         return;
     }
     switch (r) {
-    case 2: k_round<2, false><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S, ctl, max_rounds, c0); break;
-    case 3: k_round<3, false><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S, ctl, max_rounds, c0); break;
-    case 4: k_round<4, false><<<grid, kThreads, 0, L.stream>>>(Llist, loff, n, dense_div, st, rec, S, ctl, max_rounds, c0); break;
+    case 2: k_round<2, false><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
+    case 3: k_round<3, false><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
+    case 4: k_round<4, false><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
     }
 }
 

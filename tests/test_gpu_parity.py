@@ -316,3 +316,26 @@ def test_peel_parity_dense_threshold(dense_div):
         assert np.array_equal(_u64(got.G), want.G)
     finally:
         hp.set_tuning()
+
+
+# ------------------------------------------------------------------ lookup --
+
+@pytest.mark.parametrize("n", [1, 1000, 100_000])
+def test_mphf_lookup_is_a_bijection_and_matches_oracle(n):
+    keys = inputs.keys(n, 21)
+    dk = _dev(keys)
+    res = hp.mphf_build(dk, seed=1, max_tries=32)
+    seed = res.stats["seed_used"]
+    vals = hp.mphf_lookup(dk, seed, res.m, res.G, res.rank_dir)
+    got = _u32(vals)
+    assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32))
+    Gh, Dh = _u64(res.G), _u64(res.rank_dir)
+    for i in range(0, n, max(1, n // 500)):
+        assert got[i] == oracle.lookup(int(keys[i]), seed, res.m, Gh, Dh)
+    # keys outside the set map into [0, n]
+    other = _u32(hp.mphf_lookup(_dev(inputs.keys(5000, 99)), seed, res.m, res.G, res.rank_dir))
+    assert other.max() <= n
+
+
+def test_bits_per_key_matches_table_space():
+    assert round(hp.mphf_bits_per_key(10**8), 2) == 2.61
