@@ -51,10 +51,13 @@ def byte_model(step, n, m, st):
     dedges, drounds = st["dense_edges"], st["dense_rounds"]
     sedges, scross = peeled - dedges, cross - dcross
     if step == "hash_bucket":
-        # key read, edge record write, 3 incidences written to and read back
-        # from the chunk buckets; the vertex records are written once (the
-        # updates hit L2)
-        w = (8 + 16 + 2 * R * 8) * n + 8 * m
+        # key read, edge record write, r incidences written to the buckets
+        w = (8 + 16 + R * 8) * n
+        return {"units": n, "word": w, "sector": w}
+    if step == "apply_buckets":
+        # incidences read back; the vertex records are read and written once
+        # (the updates hit L2)
+        w = R * 8 * n + 16 * m
         return {"units": n, "word": w, "sector": w}
     if step == "hash_edges":
         return {"units": n, "word": 24 * n, "sector": 24 * n}
@@ -363,6 +366,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-serving", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--round-loop", default="graph", choices=["graph", "host"],
+                    help="graph: rounds in a CUDA graph (default); host: one launch per round "
+                         "(same kernels; for profilers that cannot see inside the graph)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -387,6 +393,8 @@ def main():
         dist.barrier()
     hp.lib()
 
+    if args.round_loop == "host":
+        hp.set_tuning(host_round_loop=1)
     n = args.n
     m = hp.num_vertices(n, GAMMA_MILLI, R)
     keys_h = torch.from_numpy(inputs.keys(n, KEY_SEED + rank).view(np.int64)).pin_memory()
@@ -447,8 +455,8 @@ def main():
             continue
         per_step_ms = tot_ms / args.steps
         launches_per_step = prof[name][0] / args.steps
-        if name == "rounds":  # round 0 + the round kernel's graph iterations
-            launches_per_step = 1 + st["rounds"]
+        if name == "rounds" and args.round_loop == "graph":
+            launches_per_step = 1 + st["rounds"]  # round 0 + the graph's iterations
         achieved = model["sector"] / (per_step_ms / 1e3) / 1e9
         traffic = None
         if name in NCU_TRAFFIC:

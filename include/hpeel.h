@@ -91,6 +91,9 @@ typedef struct hpeel_stats {
  *                       round kernel until a layer is empty); 1: the host
  *                       launches every round and reads the round's outcome
  *                       back before the next.
+ *   bucket_sub_shift    log2 of the vertices one block accumulates in shared
+ *                       memory in the L2-blocked build (0 = automatic:
+ *                       min(13, bucket_shift - 9); at most 14).
  * hpeel_set_tuning(NULL) restores the defaults.  Workspace sizes depend on
  * the tuning: query them after setting it.  Errors: HPEEL_ERR_INVALID_ARG.
  */
@@ -99,7 +102,8 @@ typedef struct hpeel_tuning {
     uint32_t bucket_min_vertices;
     uint32_t dense_div;
     uint32_t host_round_loop;
-    uint32_t reserved[4];
+    uint32_t bucket_sub_shift;
+    uint32_t reserved[3];
 } hpeel_tuning;
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t);
 void hpeel_get_tuning(hpeel_tuning *t);

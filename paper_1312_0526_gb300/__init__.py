@@ -52,7 +52,7 @@ class HpeelError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("bucket_shift", ctypes.c_uint32), ("bucket_min_vertices", ctypes.c_uint32),
                 ("dense_div", ctypes.c_uint32), ("host_round_loop", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("bucket_sub_shift", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -340,7 +340,8 @@ def get_tuning() -> dict:
     t = Tuning()
     lib().hpeel_get_tuning(ctypes.byref(t))
     return {"bucket_shift": t.bucket_shift, "bucket_min_vertices": t.bucket_min_vertices,
-            "dense_div": t.dense_div, "host_round_loop": t.host_round_loop}
+            "dense_div": t.dense_div, "host_round_loop": t.host_round_loop,
+            "bucket_sub_shift": t.bucket_sub_shift}
 
 
 def set_tuning(**kw) -> None:
@@ -351,7 +352,7 @@ def set_tuning(**kw) -> None:
     cur = get_tuning()
     cur.update(kw)
     t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["dense_div"],
-               cur["host_round_loop"])
+               cur["host_round_loop"], cur["bucket_sub_shift"])
     _check(lib().hpeel_set_tuning(ctypes.byref(t)))
 
 

@@ -34,14 +34,26 @@ Ctl *pinned_ctl() {
 }
 
 struct PeelLayout {
-    size_t ctl, params, rec, state, claim, L, S, pairs, fill, loff, hist, scantmp, total;
+    size_t ctl, params, rec, state, claim, L, S, pairs, fill, pairs2, fill2, ovf, ovf_count, loff,
+        hist, scantmp, total;
     uint32_t max_rounds;
     bool bucketed;
     BucketPlan plan;
 };
 
+// SM count of the current device (152 when there is none: plan for a GB300).
+int current_sms() {
+    int dev = 0;
+    DeviceInfo d;
+    if (cudaGetDevice(&dev) != cudaSuccess || device_info(dev, &d) != HPEEL_OK) {
+        cudaGetLastError();
+        return 152;
+    }
+    return d.sms;
+}
+
 // Process-wide tuning (hpeel_set_tuning); read by layouts and launches.
-hpeel_tuning g_tuning = {22u, 8u << 20, 12u, 0u, {0, 0, 0, 0}};
+hpeel_tuning g_tuning = {22u, 8u << 20, 12u, 0u, 0u, {0, 0, 0}};
 std::mutex g_tuning_mu;
 
 hpeel_tuning tuning() {
@@ -64,7 +76,10 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool with_s) {
     };
     p.max_rounds = (uint32_t)std::min<uint64_t>(HPEEL_MAX_ROUNDS, n + 1);
     p.bucketed = n > 0 && m >= tu.bucket_min_vertices;
-    if (p.bucketed) p.plan = bucket_plan(n, m, r, tu.bucket_shift);
+    if (p.bucketed) {
+        p.plan = bucket_plan(n, m, r, tu.bucket_shift, tu.bucket_sub_shift, current_sms());
+        if (p.plan.chunks > 65535) p.bucketed = false;  // one grid row per chunk
+    }
     p.ctl = take(sizeof(Ctl));
     p.params = take(sizeof(RoundParams));
     p.rec = take((r == 4 ? 32 : 16) * n);
@@ -76,7 +91,11 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool with_s) {
     p.L = region;
     p.S = region + align256(4 * n);
     p.pairs = region;
-    p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks : 0);
+    p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks * p.plan.regions : 0);
+    p.pairs2 = take(p.bucketed ? p.plan.pair2_bytes : 0);
+    p.fill2 = take(p.bucketed ? 4 * (size_t)p.plan.subs : 0);
+    p.ovf = take(p.bucketed ? 8 * (size_t)p.plan.ovf_cap : 0);
+    p.ovf_count = take(p.bucketed ? 4 : 0);
     p.loff = take(4 * ((size_t)p.max_rounds + 3));
     const uint64_t tiles = (n + kEmitTile - 1) / kEmitTile;
     p.hist = take(4 * kEmitBins * tiles);
@@ -131,6 +150,7 @@ struct PeelIO {
     uint32_t *order = nullptr;  // canonical order output (nullptr: not needed)
     uint32_t *claim = nullptr;  // claim-word output (nullptr: workspace)
     bool with_s = false;        // write MWHC solve records (r = 3)
+    bool force_direct = false;  // update the vertex records directly (no buckets)
 };
 
 // A layer is deleted by streaming all edge records once it holds more than
@@ -222,18 +242,28 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     const uint32_t P = m / r;
 
     HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), L.stream));
-    {
-        ProfScope ps(L, "fill");
-        launch_fill_u32(L, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
-    }
-    if (lay.bucketed) {
+    if (lay.bucketed && !io.force_direct) {
         uint2 *pairs = reinterpret_cast<uint2 *>(ws + lay.pairs);
         uint32_t *fill = reinterpret_cast<uint32_t *>(ws + lay.fill);
-        HP_CUDA(cudaMemsetAsync(fill, 0, 4 * (size_t)lay.plan.chunks, L.stream));
-        ProfScope ps(L, io.keys ? "hash_bucket" : "records_bucket");
-        launch_build_bucketed(L, lay.plan, io.keys, io.edges, n, r, io.fm, io.seed, P, rec, pairs,
-                              fill, st, ctl);
+        uint2 *pairs2 = reinterpret_cast<uint2 *>(ws + lay.pairs2);
+        uint32_t *fill2 = reinterpret_cast<uint32_t *>(ws + lay.fill2);
+        Overflow ov{reinterpret_cast<uint2 *>(ws + lay.ovf),
+                    reinterpret_cast<uint32_t *>(ws + lay.ovf_count), lay.plan.ovf_cap};
+        HP_CUDA(cudaMemsetAsync(fill2, 0, 4 * (size_t)lay.plan.subs, L.stream));
+        HP_CUDA(cudaMemsetAsync(ov.count, 0, 4, L.stream));
+        {
+            ProfScope ps(L, io.keys ? "hash_bucket" : "records_bucket");
+            launch_build_bucketed(L, lay.plan, io.keys, io.edges, n, r, io.fm, io.seed, P, rec,
+                                  pairs, fill, ov, ctl);
+        }
+        // every vertex record is written by the shared-memory apply
+        ProfScope ps(L, "apply_buckets");
+        launch_apply_buckets(L, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl);
     } else {
+        {
+            ProfScope ps(L, "fill");
+            launch_fill_u32(L, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
+        }
         if (io.keys) {
             ProfScope ps(L, "hash_edges");
             launch_hash_records(L, io.keys, n, r, io.fm, io.seed, rec);
@@ -286,6 +316,13 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
         count_launch(hctl->round + (hctl->more ? 1 : 0));
+    }
+    if (hctl->err == kDevBuildOverflow && !io.force_direct) {
+        // a skewed input overflowed the incidence buckets: redo the whole
+        // peel (records included) with direct updates of the vertex records
+        PeelIO again = io;
+        again.force_direct = true;
+        return peel_core_rb(L, again, n, m, r, ws, out, hctl);
     }
     if (hctl->err == kDevCapacity)
         return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds - 1);
@@ -393,11 +430,14 @@ const char *hpeel_last_error(void) { return g_last_error.c_str(); }
 
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t) {
     g_last_error.clear();
-    hpeel_tuning v = {22u, 8u << 20, 12u, 0u, {0, 0, 0, 0}};
+    hpeel_tuning v = {22u, 8u << 20, 12u, 0u, 0u, {0, 0, 0}};
     if (t) {
         if (t->bucket_shift < 8 || t->bucket_shift > 30)
             return fail(HPEEL_ERR_INVALID_ARG, "bucket_shift %u outside [8, 30]", t->bucket_shift);
         if (t->dense_div == 0) return fail(HPEEL_ERR_INVALID_ARG, "dense_div must be positive");
+        if (t->bucket_sub_shift > 14 || (t->bucket_sub_shift && t->bucket_sub_shift > t->bucket_shift))
+            return fail(HPEEL_ERR_INVALID_ARG, "bucket_sub_shift %u: need 0 or at most "
+                        "min(14, bucket_shift)", t->bucket_sub_shift);
         v = *t;
     }
     std::lock_guard<std::mutex> lk(g_tuning_mu);

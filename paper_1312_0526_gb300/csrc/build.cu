@@ -7,15 +7,17 @@
 // sec. 4.3 part by part), with the GPU's L2 as the fast memory -- and then
 // applied chunk after chunk, so the records being updated stay in L2:
 //   pass 1 (fused with hashing, or with the row -> record conversion): each
-//          block takes a tile of edges, writes their records, counting-sorts
-//          the tile's (vertex, edge) incidences by chunk in shared memory and
-//          appends each chunk's run to that chunk's bucket;
+//          block takes tiles of edges, writes their records, counting-sorts
+//          a tile's (vertex, edge) incidences by chunk in shared memory and
+//          appends each chunk's run to its own region of that chunk's bucket
+//          (one region per (chunk, block), cursors in shared memory: no
+//          global atomics);
 //   pass 2: one kernel walks the buckets in chunk order and adds
 //          (e << 32) + 1 to each vertex record (64-bit reductions, L2 hits).
 // A chunk is 2^shift consecutive vertices of one part of the r-partite
-// vertex set.  Bucket capacity covers the expected load of a chunk with a
-// wide margin; an incidence that finds its bucket full is applied directly
-// (same result, random access), so any input is handled.
+// vertex set.  Region capacity covers the expected load with a wide margin;
+// an incidence that finds its region full is applied directly (same result,
+// random access), so any input is handled.
 #include <algorithm>
 #include <cmath>
 
@@ -29,30 +31,42 @@ struct BucketGeom {
     uint32_t P;                // part size
     uint32_t shift;            // log2 of the vertices per chunk
     uint32_t chunks_per_part;
-    uint32_t cap;              // bucket capacity (incidences)
+    uint32_t cap;              // region capacity (incidences per chunk and block)
 };
 
 __device__ __forceinline__ uint32_t chunk_of(uint32_t v, uint32_t j, const BucketGeom &g) {
     return j * g.chunks_per_part + ((v - j * g.P) >> g.shift);
 }
 
+// An incidence that finds its region full goes to the overflow list, applied
+// after everything else; when the list itself is full the build fails with
+// kDevBuildOverflow and the host redoes it with direct updates.
+__device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
+    const uint32_t k = atomicAdd(ov.count, 1u);
+    if (k < ov.cap)
+        ov.list[k] = p;
+    else
+        atomicCAS(&ctl->err, 0u, (uint32_t)kDevBuildOverflow);
+}
+
 template <int R, bool FROM_KEYS>
 __global__ void __launch_bounds__(kThreads, 2)
 k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ rows,
                    uint32_t n, FastMod fm, uint64_t seed, BucketGeom g, uint4 *__restrict__ rec,
-                   uint2 *__restrict__ pairs, uint32_t *__restrict__ fill,
-                   unsigned long long *__restrict__ st, Ctl *ctl) {
+                   uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov,
+                   Ctl *ctl) {
     constexpr int kInc = kTileEdges * R;
     extern __shared__ uint32_t smem[];
     const uint32_t C = R * g.chunks_per_part;
     const uint32_t Cp = (C + 1) & ~1u;
     uint32_t *hist = smem;            // C: tile count per chunk
-    uint32_t *gbase = hist + Cp;      // C: bucket position of the tile's run
-    uint32_t *toff = gbase + Cp;      // C: start of the chunk's run in stage
+    uint32_t *cur = hist + Cp;        // C: fill of this block's region of each chunk
+    uint32_t *toff = cur + Cp;        // C: start of the chunk's run in stage
     uint32_t *sch = toff + Cp;        // kInc: chunk of each stage slot
     uint2 *stage = reinterpret_cast<uint2 *>(sch + kInc);  // kInc (8-byte aligned: Cp, kInc even)
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 
+    for (uint32_t c = threadIdx.x; c < C; c += kThreads) cur[c] = 0;
     const uint64_t tiles = ((uint64_t)n + kTileEdges - 1) / kTileEdges;
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         for (uint32_t c = threadIdx.x; c < C; c += kThreads) hist[c] = 0;
@@ -89,9 +103,6 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             }
         }
         __syncthreads();
-        // reserve each chunk's run in its bucket
-        for (uint32_t c = threadIdx.x; c < C; c += kThreads)
-            gbase[c] = hist[c] ? atomicAdd(fill + c, hist[c]) : 0u;
         // exclusive scan of hist -> toff (warp 0, 32 chunks per step)
         if (warp == 0) {
             uint32_t run = 0;
@@ -126,43 +137,183 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
         const uint32_t total = toff[C - 1] + hist[C - 1];
         for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
             const uint32_t c = sch[k];
-            const uint32_t pos = gbase[c] + (k - toff[c]);
+            const uint32_t pos = cur[c] + (k - toff[c]);
             const uint2 p = stage[k];
             if (pos < g.cap)
-                pairs[(uint64_t)c * g.cap + pos] = p;
-            else  // bucket full: apply this incidence directly
-                atomicAdd(st + p.x, ((unsigned long long)p.y << 32) | 1ull);
+                pairs[((uint64_t)c * gridDim.x + blockIdx.x) * g.cap + pos] = p;
+            else
+                overflow_push(p, ov, ctl);
+        }
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < C; c += kThreads) cur[c] += hist[c];
+        __syncthreads();
+    }
+    for (uint32_t c = threadIdx.x; c < C; c += kThreads)
+        fill[(size_t)c * gridDim.x + blockIdx.x] = cur[c];
+}
+
+// Refine: the pairs of each chunk (all its regions) are counting-sorted in
+// shared memory, a tile of kRefineTile slots at a time, into 2^(shift -
+// sub_shift) sub-buckets of 2^sub_shift vertices; each tile's run of a
+// sub-bucket is appended to it with one atomicAdd on its cursor.
+constexpr int kRefineItems = 16;
+constexpr uint32_t kRefineTile = kThreads * kRefineItems;  // 4096 slots
+
+__global__ void __launch_bounds__(kThreads)
+k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ fill, BucketGeom g,
+                 uint32_t regions, uint32_t sub_shift, uint2 *__restrict__ pairs2,
+                 uint32_t *__restrict__ fill2, uint32_t cap2, Overflow ov, Ctl *ctl) {
+    extern __shared__ uint32_t smem[];
+    const uint32_t S = 1u << (g.shift - sub_shift);
+    uint32_t *hist = smem;          // S
+    uint32_t *gbase = hist + S;     // S
+    uint32_t *toff = gbase + S;     // S
+    uint32_t *sb = toff + S;        // kRefineTile: sub-bucket of each stage slot
+    uint2 *stage = reinterpret_cast<uint2 *>(sb + kRefineTile);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t span = (uint64_t)regions * g.cap;
+    const uint32_t c = blockIdx.y;  // one grid row per chunk
+    const uint32_t part = c / g.chunks_per_part;
+    const uint32_t base_v = part * g.P + (c % g.chunks_per_part) * (1u << g.shift);
+    const uint2 *src = pairs + (uint64_t)c * span;
+    const uint32_t *f = fill + (size_t)c * regions;
+    // tiles never straddle regions: region reg has ceil(cap / kRefineTile)
+    // tiles, of which those below its fill hold pairs
+    const uint32_t tpr = (g.cap + kRefineTile - 1) / kRefineTile;
+    const uint32_t tiles = regions * tpr;
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint32_t reg = tile / tpr, t0 = (tile - reg * tpr) * kRefineTile;
+        const uint32_t cnt = min(__ldg(f + reg), g.cap);
+        if (t0 >= cnt) continue;  // block-uniform: nothing in this tile
+        const uint2 *tsrc = src + (uint64_t)reg * g.cap + t0;
+        const uint32_t tn = min(cnt - t0, kRefineTile);
+        for (uint32_t b = threadIdx.x; b < S; b += kThreads) hist[b] = 0;
+        __syncthreads();
+        uint2 p[kRefineItems];
+        uint32_t rk[kRefineItems];
+        bool ok[kRefineItems];
+#pragma unroll
+        for (int q = 0; q < kRefineItems; q++) {
+            const uint32_t i = (uint32_t)q * kThreads + threadIdx.x;
+            ok[q] = i < tn;
+            rk[q] = 0;
+            if (ok[q]) {
+                p[q] = __ldcs(tsrc + i);
+                rk[q] = atomicAdd(&hist[(p[q].x - base_v) >> sub_shift], 1u);
+            }
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < S; b += kThreads)
+            gbase[b] = hist[b] ? atomicAdd(fill2 + (size_t)c * S + b, hist[b]) : 0u;
+        if (warp == 0) {  // exclusive scan of hist -> toff
+            uint32_t run = 0;
+            for (uint32_t b0 = 0; b0 < S; b0 += 32) {
+                const uint32_t b = b0 + lane;
+                const uint32_t h = b < S ? hist[b] : 0u;
+                uint32_t x = h;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+                    if (lane >= (uint32_t)d) x += y;
+                }
+                if (b < S) toff[b] = run + x - h;
+                run += __shfl_sync(0xFFFFFFFFu, x, 31);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kRefineItems; q++) {
+            if (!ok[q]) continue;
+            const uint32_t b = (p[q].x - base_v) >> sub_shift;
+            const uint32_t slot = toff[b] + rk[q];
+            stage[slot] = p[q];
+            sb[slot] = b;
+        }
+        __syncthreads();
+        const uint32_t total = toff[S - 1] + hist[S - 1];
+        for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
+            const uint32_t b = sb[k];
+            const uint32_t pos = gbase[b] + (k - toff[b]);
+            if (pos < cap2)
+                pairs2[((size_t)c * S + b) * cap2 + pos] = stage[k];
+            else
+                overflow_push(stage[k], ov, ctl);
         }
         __syncthreads();
     }
 }
 
-// Apply the buckets in chunk order (every block walks chunk 0, then 1, ...):
-// at any time the grid updates the records of about one chunk.
-__global__ void __launch_bounds__(kThreads)
-k_apply_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ fill, uint32_t C,
-                uint32_t cap, unsigned long long *__restrict__ st) {
-    const uint32_t stride = gridDim.x * kThreads;
-    for (uint32_t c = 0; c < C; c++) {
-        const uint32_t cnt = min(fill[c], cap);
-        const uint2 *b = pairs + (uint64_t)c * cap;
-        for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < cnt; i += stride) {
-            const uint2 p = __ldcs(b + i);
-            atomicAdd(st + p.x, ((unsigned long long)p.y << 32) | 1ull);
-        }
+// One block per sub-bucket: degrees and id sums of its 2^sub_shift vertices
+// accumulate in shared memory (two 32-bit atomics per incidence: the record's
+// halves are independent, AddEdge never carries from one into the other),
+// then every vertex record of the range is written once.
+__global__ void __launch_bounds__(1024)
+k_apply_smem(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill2, uint32_t cap2,
+             BucketGeom g, uint32_t sub_shift, unsigned long long *__restrict__ st) {
+    extern __shared__ uint32_t smem[];
+    const uint32_t nv = 1u << sub_shift;
+    uint32_t *deg = smem, *sum = smem + nv;
+    const uint32_t S = 1u << (g.shift - sub_shift);
+    const uint32_t s = blockIdx.x;
+    const uint32_t c = s / S, b = s % S;
+    const uint32_t part = c / g.chunks_per_part;
+    const uint32_t base_v = part * g.P + (c % g.chunks_per_part) * (1u << g.shift) + b * nv;
+    const uint32_t part_end = (part + 1) * g.P;
+    if (base_v >= part_end) return;  // a sub-bucket past the end of its part
+    for (uint32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        deg[k] = 0;
+        sum[k] = 0;
+    }
+    __syncthreads();
+    const uint32_t cnt = min(fill2[s], cap2);
+    const uint2 *src = pairs2 + (size_t)s * cap2;
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint2 p = __ldcs(src + i);
+        const uint32_t k = p.x - base_v;
+        atomicAdd(deg + k, 1u);
+        atomicAdd(sum + k, p.y);
+    }
+    __syncthreads();
+    const uint32_t lim = min(nv, part_end - base_v);
+    for (uint32_t k = threadIdx.x; k < lim; k += blockDim.x)
+        st[base_v + k] = (unsigned long long)deg[k] | ((unsigned long long)sum[k] << 32);
+}
+
+__global__ void k_apply_overflow(const uint2 *__restrict__ list, const uint32_t *__restrict__ count,
+                                 uint32_t cap, unsigned long long *__restrict__ st) {
+    const uint32_t cnt = min(*count, cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const uint2 p = list[i];
+        atomicAdd(st + p.x, ((unsigned long long)p.y << 32) | 1ull);
     }
 }
 
-BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift) {
+BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift, uint32_t sub_shift,
+                       int sms) {
     BucketPlan b{};
     const uint64_t P = m / r;
     b.shift = shift;
     b.chunks_per_part = (uint32_t)((P + (1ull << shift) - 1) >> shift);
     b.chunks = r * b.chunks_per_part;
-    const double expect = P ? (double)n * (double)(1ull << shift) / (double)P : 0.0;
-    uint64_t cap = (uint64_t)(expect + 16.0 * std::sqrt(expect + 1.0) + 1024.0);
+    const uint64_t tiles = (n + kTileEdges - 1) / kTileEdges;
+    b.regions = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sms * 2));
+    // a region gets the incidences of one chunk from about n / regions edges
+    const double expect = P ? (double)n * (double)(1ull << shift) / (double)P / b.regions : 0.0;
+    uint64_t cap = (uint64_t)(expect + 8.0 * std::sqrt(expect + 1.0) + 64.0);
     b.cap = (uint32_t)std::min<uint64_t>(cap, n);
-    b.pair_bytes = (uint64_t)b.chunks * b.cap * 8;
+    b.pair_bytes = (uint64_t)b.chunks * b.regions * b.cap * 8;
+    // sub-buckets: 2^sub_shift vertices (default 2^13: 64 KiB of shared
+    // memory for the apply's two 32-bit counters per vertex, 3 blocks per SM)
+    b.sub_shift = sub_shift ? sub_shift : (shift > 9 ? shift - 9 : 0);
+    if (b.sub_shift > 14) b.sub_shift = 14;
+    if (!sub_shift && b.sub_shift > 13) b.sub_shift = 13;
+    if (b.sub_shift > shift) b.sub_shift = shift;
+    b.subs = b.chunks << (shift - b.sub_shift);
+    const double expect2 = P ? (double)n * (double)(1ull << b.sub_shift) / (double)P : 0.0;
+    uint64_t cap2 = (uint64_t)(expect2 + 8.0 * std::sqrt(expect2 + 1.0) + 256.0);
+    b.cap2 = (uint32_t)std::min<uint64_t>(cap2, n);
+    b.pair2_bytes = (uint64_t)b.subs * b.cap2 * 8;
+    b.ovf_cap = (uint32_t)std::max<uint64_t>(1u << 16, n / 16);
     b.smem = (size_t)(3 * ((b.chunks + 1) & ~1u)) * 4 + (size_t)kTileEdges * r * (8 + 4);
     return b;
 }
@@ -170,18 +321,17 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift) {
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           unsigned long long *st, Ctl *ctl) {
+                           Overflow ov, Ctl *ctl) {
     if (n == 0) return;
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
-    const uint64_t tiles = ((uint64_t)n + kTileEdges - 1) / kTileEdges;
-    const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)L.sms * 2);
+    const unsigned grid = b.regions;  // one bucket region per block and chunk
 #define HP_BK(RR, FK)                                                                         \
     do {                                                                                      \
         auto kern = k_records_bucketed<RR, FK>;                                               \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem); \
         count_launch();                                                                       \
         kern<<<grid, kThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, g, rec, pairs,    \
-                                                   fill, st, ctl);                            \
+                                                   fill, ov, ctl);                            \
     } while (0)
     if (keys) {
         switch (r) {
@@ -197,9 +347,26 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
         }
     }
 #undef HP_BK
+}
+
+void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
+                          const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
+                          unsigned long long *st, Ctl *ctl) {
+    BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
+    const uint32_t S = 1u << (b.shift - b.sub_shift);
+    const size_t smem1 = (3 * (size_t)S + kRefineTile) * 4 + (size_t)kRefineTile * 8;
+    cudaFuncSetAttribute(k_refine_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    const uint64_t tiles = (uint64_t)b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);
+    const unsigned gx = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)L.sms * 2));
     count_launch();
-    k_apply_buckets<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(pairs, fill, b.chunks, b.cap,
-                                                                  st);
+    k_refine_buckets<<<dim3(gx, b.chunks), kThreads, smem1, L.stream>>>(
+        pairs, fill, g, b.regions, b.sub_shift, pairs2, fill2, b.cap2, ov, ctl);
+    const size_t smem2 = (size_t)8 << b.sub_shift;
+    cudaFuncSetAttribute(k_apply_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    count_launch();
+    k_apply_smem<<<b.subs, 1024, smem2, L.stream>>>(pairs2, fill2, b.cap2, g, b.sub_shift, st);
+    count_launch();
+    k_apply_overflow<<<grid_fixed(L, 4), kThreads, 0, L.stream>>>(ov.list, ov.count, ov.cap, st);
 }
 
 }  // namespace hp

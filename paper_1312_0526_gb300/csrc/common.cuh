@@ -16,6 +16,7 @@ enum : uint32_t {
     kDevBadEdge = 2,     // an edge id >= n read off a record (inconsistent state)
     kDevCapacity = 3,    // a round-table bound was exceeded
     kDevTimeout = 4,     // a bounded wait gave up
+    kDevBuildOverflow = 5,  // the bucketed build's overflow list was full
 };
 
 // Device-side control block of one peel (lives in the workspace).

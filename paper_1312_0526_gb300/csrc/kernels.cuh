@@ -65,15 +65,31 @@ struct BucketPlan {
     uint32_t shift;            // log2 vertices per chunk
     uint32_t chunks_per_part;
     uint32_t chunks;
-    uint32_t cap;              // incidences per bucket
+    uint32_t regions;          // bucket regions per chunk (= blocks of the bucketing kernel)
+    uint32_t cap;              // incidences per region
     uint64_t pair_bytes;       // bucket storage
     size_t smem;               // dynamic shared memory of the bucketing kernel
+    uint32_t sub_shift;        // log2 vertices per sub-bucket
+    uint32_t subs;             // sub-buckets in all
+    uint32_t cap2;             // incidences per sub-bucket
+    uint64_t pair2_bytes;      // sub-bucket storage
+    uint32_t ovf_cap;          // overflow list entries
 };
-BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift);
+// Incidences that found their bucket full (applied last).
+struct Overflow {
+    uint2 *list;
+    uint32_t *count;
+    uint32_t cap;
+};
+BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift, uint32_t sub_shift,
+                       int sms);
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           unsigned long long *st, Ctl *ctl);
+                           Overflow ov, Ctl *ctl);
+void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
+                          const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
+                          unsigned long long *st, Ctl *ctl);
 
 // A kernel of the round loop and its launch shape, for graph nodes.
 struct RoundLaunch {

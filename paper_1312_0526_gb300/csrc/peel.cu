@@ -138,7 +138,10 @@ __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t
     if (crossings) atomicAdd(&s_cross, crossings);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (s_cross) atomicAdd(&ctl->cross, s_cross);
+        if (s_cross) {
+            atomicAdd(&ctl->cross, s_cross);
+            if (dense) atomicAdd(&ctl->dense_cross, s_cross);
+        }
         __threadfence();
         const uint32_t d = atomicAdd(&ctl->done, 1u);
         if (d == gridDim.x - 1) {
@@ -154,7 +157,6 @@ __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t
             if (dense) {
                 ctl->dense_rounds += 1;
                 ctl->dense_edges += layer;
-                ctl->dense_cross += s_cross;
             }
             ctl->next_size = end - beg;
             ctl->more = more;

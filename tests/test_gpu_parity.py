@@ -230,13 +230,14 @@ def test_peel_parity_bucketed(small_buckets, n, gamma, r):
     _check_peel(edges, m)
 
 
-def test_peel_bucket_overflow_falls_back(small_buckets):
-    # every vertex in the first 1024 of its part: the buckets sized for a
-    # uniform spread overflow, and the overflowing incidences are applied
-    # directly
+@pytest.mark.parametrize("span", [1024, 4096, 30_000])
+def test_peel_bucket_overflow_falls_back(small_buckets, span):
+    # every vertex in the first `span` of its part: buckets sized for a
+    # uniform spread overflow; overflowing incidences go to the overflow
+    # list, and when that is full too the peel is redone with direct updates
     n, P = 60_000, 40_000
     rng = np.random.default_rng(9)
-    edges = np.stack([rng.integers(0, 1024, n) + j * P for j in range(3)], axis=1).astype(np.uint32)
+    edges = np.stack([rng.integers(0, span, n) + j * P for j in range(3)], axis=1).astype(np.uint32)
     _check_peel(edges, 3 * P)
 
 
