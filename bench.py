@@ -92,6 +92,9 @@ def byte_model(step, n, m, st):
 # lives in; stale entries are ignored.  Filled from the summaries in profiles/.
 NCU_TRAFFIC = {
     # step: (source file, sha256 prefix, bytes per unit)
+    # rounds: k_round0 + k_round of one build at n = 3e7 (host round loop),
+    # 12.62 GB of DRAM traffic for 3e7 peeled edges; profiles/rounds_n3e7_dram.md
+    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "3c03faf2e871eceb", 420.82),
 }
 
 
@@ -458,17 +461,22 @@ def main():
         if name == "rounds" and args.round_loop == "graph":
             launches_per_step = 1 + st["rounds"]  # round 0 + the graph's iterations
         achieved = model["sector"] / (per_step_ms / 1e3) / 1e9
-        traffic = None
+        traffic = traffic_step = None
         if name in NCU_TRAFFIC:
             src, h, per_unit = NCU_TRAFFIC[name]
             if src_hash(src) == h:
-                traffic = per_unit * model["units"] / max(launches_per_step, 1)
+                traffic_step = per_unit * model["units"]
+                traffic = traffic_step / max(launches_per_step, 1)
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "model": "sector", "peak_kind": peak_kind,
                 "algorithmic_bytes_per_step": model["sector"],
                 "word_model_gbs": model["word"] / (per_step_ms / 1e3) / 1e9,
                 "launches_per_step": launches_per_step,
+                "traffic_per_step": traffic_step,
+                "traffic_gbs": traffic_step / (per_step_ms / 1e3) / 1e9 if traffic_step else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at n = 3e7, "
+                                  "scaled by peeled edges" if traffic_step else None,
                 "ms_per_step": per_step_ms, "share": tot_ms / sum(v[1] for v in prof.values())}
         break
 
