@@ -130,21 +130,23 @@ void launch_build_incidence(const Launch &L, const uint4 *rec, uint32_t n, uint3
 // room (the loop ends after at most max_rounds launches whatever happens).
 __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t,
                                             uint32_t crossings, bool dense, uint32_t layer,
-                                            uint32_t max_rounds,
+                                            uint32_t max_rounds, uint32_t active,
                                             cudaGraphConditionalHandle cond) {
-    __shared__ uint32_t s_cross;
-    if (threadIdx.x == 0) s_cross = 0;
-    __syncthreads();
-    if (crossings) atomicAdd(&s_cross, crossings);
+    __shared__ uint32_t s_cross[kThreads / 32];
+    const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, crossings);
+    if ((threadIdx.x & 31u) == 0) s_cross[threadIdx.x >> 5] = wsum;
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (s_cross) {
-            atomicAdd(&ctl->cross, s_cross);
-            if (dense) atomicAdd(&ctl->dense_cross, s_cross);
+        uint32_t bsum = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; w++) bsum += s_cross[w];
+        if (bsum) {
+            atomicAdd(&ctl->cross, bsum);
+            if (dense) atomicAdd(&ctl->dense_cross, bsum);
         }
         __threadfence();
         const uint32_t d = atomicAdd(&ctl->done, 1u);
-        if (d == gridDim.x - 1) {
+        if (d == active - 1) {
             __threadfence();
             const uint32_t end = atomicAdd(&ctl->lcur, 0u);
             const uint32_t beg = loff[t + 1];
@@ -252,36 +254,6 @@ void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm) {
 }
 
 // ---------------------------------------------------------------- rounds --
-// Delete edge e (claim word c, vertices v) of layer t from its non-hinge
-// vertices; claim for round t+1 the remaining edge of every vertex that falls
-// to degree 1.  Returns how many fell; take/f receive the first claims.
-template <int R>
-__device__ __forceinline__ uint32_t delete_edge(uint32_t e, uint32_t c, const uint32_t (&v)[4],
-                                                uint32_t t, uint32_t n,
-                                                unsigned long long *st, uint4 *rec, Ctl *ctl,
-                                                bool (&take)[R - 1], uint32_t (&f)[R - 1]) {
-    const uint32_t h = c & 3u;
-    const unsigned long long sub = 0ull - (((unsigned long long)e << 32) | 1ull);
-    uint32_t cross = 0;
-#pragma unroll
-    for (int k = 0; k < R - 1; k++) {
-        const int j = k + ((uint32_t)k >= h ? 1 : 0);  // k-th non-hinge position
-        const unsigned long long old = atomicAdd(st + v[j], sub);
-        if ((uint32_t)old == 2u) {
-            cross++;
-            const uint32_t g = (uint32_t)(old >> 32) - e;  // the one edge left
-            if (g < n) {
-                const uint32_t tag = ((t + 1) << 2) | (uint32_t)j;
-                take[k] = atomicMin(claim_ptr<R>(rec, g), tag) == kUnclaimed;
-                f[k] = g;
-            } else {
-                raise_err(ctl, kDevBadEdge);
-            }
-        }
-    }
-    return cross;
-}
-
 constexpr int kStageCap = 256;  // staged appends per warp
 
 // Round t: delete layer L_t and list layer L_{t+1}.  A layer holding more
@@ -290,6 +262,11 @@ constexpr int kStageCap = 256;  // staged appends per warp
 // record stream too); a smaller one is read from the list, and its solve
 // record i goes to S[i].  Round 0 is always dense (L_0 is not listed).  The
 // choice depends only on device values all blocks read alike.
+// Each warp takes kRoundU * 32 consecutive entries per step, lane-strided,
+// and issues every gather and atomic of its kRoundU edges before it consumes
+// any result: more memory requests in flight per thread.
+constexpr int kRoundU = 2;
+
 template <int R, bool WITH_S>
 __global__ void __launch_bounds__(kThreads)
 k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
@@ -305,38 +282,91 @@ k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
     const uint32_t t = *(volatile uint32_t *)&ctl->round;
     const uint32_t lb = loff[t], le = loff[t + 1];
     const bool dense = t == 0 || (le - lb) > n / dense_div;
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    uint32_t cross = 0;
     const uint64_t first = dense ? 0 : lb, last = dense ? n : le;
-    // warp-uniform trip count: whole warps step together
-    for (uint64_t base = first + ((uint64_t)blockIdx.x * kThreads + (threadIdx.x & ~31u));
+    constexpr uint32_t kBlockStep = kThreads * kRoundU;
+    // blocks past the end of a small layer have nothing to do and take no
+    // part in closing the round
+    const uint64_t need = (last - first + kBlockStep - 1) / kBlockStep;
+    const uint32_t active = (uint32_t)(need < gridDim.x ? (need ? need : 1) : gridDim.x);
+    if (blockIdx.x >= active) return;
+    const uint64_t stride = (uint64_t)active * kBlockStep;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t cross = 0;
+    const unsigned long long one = 1ull;
+    for (uint64_t base = first + (uint64_t)blockIdx.x * kBlockStep + (uint64_t)warp * 32 * kRoundU;
          base < last; base += stride) {
-        const uint64_t i = base + (threadIdx.x & 31u);
-        bool take[R - 1];
-        uint32_t f[R - 1];
+        uint32_t e[kRoundU], c[kRoundU], v[kRoundU][4];
+        bool mine[kRoundU];
 #pragma unroll
-        for (int k = 0; k < R - 1; k++) {
-            take[k] = false;
-            f[k] = 0;
-        }
-        if (i < last) {
-            uint32_t v[4];
-            if (dense) {
-                const uint32_t c = load_record_stream<R>(rec, i, v);
-                if (c != kUnclaimed && (c >> 2) == t)
-                    cross += delete_edge<R>((uint32_t)i, c, v, t, n, st, rec, ctl, take, f);
-            } else {
-                const uint32_t e = Llist[i];
-                const uint32_t c = load_record<R>(rec, e, v);
-                cross += delete_edge<R>(e, c, v, t, n, st, rec, ctl, take, f);
-                if (WITH_S) S[i] = solve_record(c, v);
+        for (int u = 0; u < kRoundU; u++) {
+            const uint64_t i = base + (uint64_t)u * 32 + lane;
+            mine[u] = false;
+            c[u] = kUnclaimed;
+            e[u] = 0;
+            if (i < last) {
+                if (dense) {
+                    e[u] = (uint32_t)i;
+                    c[u] = load_record_stream<R>(rec, i, v[u]);
+                    mine[u] = c[u] != kUnclaimed && (c[u] >> 2) == t;
+                } else {
+                    e[u] = Llist[i];
+                    mine[u] = true;
+                }
             }
         }
+        if (!dense) {
 #pragma unroll
-        for (int k = 0; k < R - 1; k++) stage.push(take[k], f[k], &ctl->lcur, Llist);
+            for (int u = 0; u < kRoundU; u++)
+                if (mine[u]) c[u] = load_record<R>(rec, e[u], v[u]);
+        }
+        // DeleteEdge on the non-hinge vertices of every edge (issued together)
+        unsigned long long old[kRoundU][R - 1];
+#pragma unroll
+        for (int u = 0; u < kRoundU; u++) {
+            const uint32_t h = c[u] & 3u;
+            const unsigned long long sub = 0ull - (((unsigned long long)e[u] << 32) | one);
+#pragma unroll
+            for (int k = 0; k < R - 1; k++) {
+                old[u][k] = 0;
+                if (mine[u]) {
+                    // k-th non-hinge position is k or k + 1 (static indices keep v in registers)
+                    const uint32_t x = (uint32_t)k >= h ? v[u][k + 1] : v[u][k];
+                    old[u][k] = atomicAdd(st + x, sub);
+                }
+            }
+        }
+        // vertices that fell to degree 1 claim their last edge for round t+1
+        bool take[kRoundU][R - 1];
+        uint32_t f[kRoundU][R - 1];
+#pragma unroll
+        for (int u = 0; u < kRoundU; u++) {
+            const uint32_t h = c[u] & 3u;
+#pragma unroll
+            for (int k = 0; k < R - 1; k++) {
+                take[u][k] = false;
+                f[u][k] = 0;
+                if (mine[u] && (uint32_t)old[u][k] == 2u) {
+                    cross++;
+                    const uint32_t j = (uint32_t)k + ((uint32_t)k >= h ? 1u : 0u);
+                    const uint32_t g = (uint32_t)(old[u][k] >> 32) - e[u];  // the edge left
+                    if (g < n) {
+                        take[u][k] = atomicMin(claim_ptr<R>(rec, g), ((t + 1) << 2) | j) ==
+                                     kUnclaimed;
+                        f[u][k] = g;
+                    } else {
+                        raise_err(ctl, kDevBadEdge);
+                    }
+                }
+            }
+            if (WITH_S && !dense && mine[u]) S[base + (uint64_t)u * 32 + lane] = solve_record(c[u], v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kRoundU; u++)
+#pragma unroll
+            for (int k = 0; k < R - 1; k++) stage.push(take[u][k], f[u][k], &ctl->lcur, Llist);
     }
     stage.flush(&ctl->lcur, Llist);
-    close_round(ctl, loff, t, cross, dense, le - lb, max_rounds, cond);
+    close_round(ctl, loff, t, cross, dense, le - lb, max_rounds, active, cond);
 }
 
 template <int R, bool WS>
