@@ -41,15 +41,15 @@ REF_STEP_KEYS = 10**6          # --impl reference: keys per oracle step
 # Algorithmic bytes per unit of work, per step of the path (r = 3).  "sector"
 # charges one 32-byte sector per random access (64 bytes for a read-modify-
 # write), "word" charges only the bytes the method reads and writes.  Units:
-# edges (hash, build, extract, emit, assign), vertices (fill, round0),
-# deleted edges (rounds).  A round that streams all records also reads 16 B
-# per edge; a vertex that falls to degree 1 claims its last edge (one random
-# read-modify-write) and may append it (4 B).
+# edges (hash, build, extract, emit, assign), vertices (fill), peeled edges
+# (rounds).  Every peeled edge is appended to the layer list once (16 B) and
+# read back once by the round that deletes it, which updates its r-1 other
+# vertices; a vertex that falls to degree 1 marks its record and claims its
+# last edge (one random read-modify-write; the mark and the read of the
+# claimed edge's vertices hit the sectors those atomics just fetched).
 def byte_model(step, n, m, st):
     L0, peeled = st["first_layer"], st["n_peeled"]
-    cross, dcross = st["frontier"], st["dense_cross"]
-    dedges, drounds = st["dense_edges"], st["dense_rounds"]
-    sedges, scross = peeled - dedges, cross - dcross
+    cross, moves = st["frontier"], st["hinge_moves"]
     if step == "hash_bucket":
         # key read, edge record write, r incidences written to the buckets
         w = (8 + 16 + R * 8) * n
@@ -66,15 +66,14 @@ def byte_model(step, n, m, st):
     if step == "build_incidence":
         return {"units": n, "word": (16 + R * 16) * n, "sector": (16 + R * 64) * n}
     if step == "rounds":
-        # round 0 scan and claims, then every round: dense rounds stream all
-        # records; every deleted edge updates its r-1 non-hinge vertices; a
-        # sparse round also reads the list entry, gathers the record and
-        # writes a solve record; a vertex falling to degree 1 claims its last
-        # edge and may append it
-        word = (8 * m + 8 * L0 + 16 * n * drounds + dedges * ((R - 1) * 16)
-                + sedges * (4 + 16 + (R - 1) * 16 + 16) + cross * 12)
-        sector = (8 * m + 64 * L0 + 16 * n * drounds + dedges * ((R - 1) * 64)
-                  + sedges * (4 + 32 + (R - 1) * 64 + 16) + cross * 68)
+        # round 0: scan of the vertex records, mark + claim per degree-1
+        # vertex; then per peeled edge: entry append and read, r-1 DeleteEdge
+        # atomics; per fall to degree 1: mark, claim, vertex read; per moved
+        # hinge: entry rewrite
+        word = (8 * m + L0 * (8 + 8 + 16) + peeled * (32 + (R - 1) * 16)
+                + cross * (4 + 8 + 16) + 16 * moves)
+        sector = (8 * m + L0 * (32 + 64) + peeled * (32 + (R - 1) * 64)
+                  + cross * 64 + 16 * moves)
         return {"units": peeled, "word": word, "sector": sector}
     if step == "extract_claim":
         return {"units": n, "word": 20 * n, "sector": 20 * n}
@@ -83,6 +82,7 @@ def byte_model(step, n, m, st):
     if step == "emit_hist":
         return {"units": n, "word": 4 * n, "sector": 4 * n}
     if step == "assign":
+        # entry stream, two g reads and one g update per edge (G is L2-resident)
         return {"units": n, "word": (16 + 2 * 8 + 16) * n, "sector": (16 + 2 * 32 + 64) * n}
     return None
 
@@ -491,21 +491,52 @@ def main():
                 "ms_per_step": per_step_ms, "share": tot_ms / sum(v[1] for v in prof.values())}
         break
 
-    # ---- end to end through the public API with host buffers
-    G_h = torch.empty_like(G, device="cpu").pin_memory()
-    D_h = torch.empty_like(D, device="cpu").pin_memory()
+    # ---- end to end through the public API with host buffers: every step
+    # copies its keys from pinned host memory and reads its g values and rank
+    # directory back.  The copies run on a second stream, double-buffered, so
+    # step i+1's keys travel while step i builds (a pipelined server).
+    copy_stream = torch.cuda.Stream()
+    kbuf = [keys, torch.empty_like(keys)]
+    Gb, Db = [G, torch.empty_like(G)], [D, torch.empty_like(D)]
+    G_h = [torch.empty_like(G, device="cpu").pin_memory() for _ in range(2)]
+    D_h = [torch.empty_like(D, device="cpu").pin_memory() for _ in range(2)]
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    read = [None, None]
     e2e_steps = max(1, min(args.steps, 5))
     sync_all()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
-        keys.copy_(keys_h, non_blocking=True)
-        step()
-        G_h.copy_(G, non_blocking=True)
-        D_h.copy_(D, non_blocking=True)
+    copy_stream.wait_event(e0)
+    with torch.cuda.stream(copy_stream):
+        kbuf[0].copy_(keys_h, non_blocking=True)
+        ready[0].record(copy_stream)
+    for i in range(e2e_steps):
+        b = i & 1
+        if i + 1 < e2e_steps:
+            # kbuf[1-b] last fed step i-1, which has returned (the build call
+            # synchronises its stream)
+            with torch.cuda.stream(copy_stream):
+                kbuf[1 - b].copy_(keys_h, non_blocking=True)
+                ready[1 - b].record(copy_stream)
+        stream.wait_event(ready[b])
+        if read[b] is not None:
+            stream.wait_event(read[b])  # step i-2's results are on the host
+        hp.mphf_build(kbuf[b], HASH_SEED, GAMMA_MILLI, workspace=ws, G=Gb[b], rank_dir=Db[b],
+                      order=order)
+        built = torch.cuda.Event()
+        built.record(stream)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(built)
+            G_h[b].copy_(Gb[b], non_blocking=True)
+            D_h[b].copy_(Db[b], non_blocking=True)
+            read[b] = torch.cuda.Event()
+            read[b].record(copy_stream)
+    stream.wait_stream(copy_stream)
     e1.record(stream)
     sync_all()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
+    for b in range(min(2, e2e_steps)):  # the pipelined steps built what the timed ones did
+        assert torch.equal(G_h[b], G.cpu()) and torch.equal(D_h[b], D.cpu())
 
     if rank != 0:
         if dist:
@@ -539,7 +570,9 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": aggregate_medges(n, world, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": keys.numel() * 8,
-                "d2h_bytes_per_step": (G.numel() + D.numel()) * 8, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": (G.numel() + D.numel()) * 8, "ms_per_step": e2e_ms,
+                "copies": "pinned host buffers, second stream, next step's keys copied "
+                          "during the current step"},
         "steps_ms": {k: v[1] / args.steps for k, v in sorted(prof.items())},
         "batched": batched,
         "serving": serving,

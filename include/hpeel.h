@@ -61,11 +61,10 @@ typedef struct hpeel_stats {
     uint64_t first_layer;   /* |L_0|: edges peeled in round 0 */
     uint64_t frontier;      /* vertices that fell from degree 2 to 1 in some
                                round (the frontiers F_1, F_2, ...) */
-    uint64_t dense_edges;   /* edges deleted by rounds that streamed all edge
-                               records (the others read the layer list) */
-    uint64_t dense_cross;   /* the part of 'frontier' found by those rounds */
-    uint32_t dense_rounds;  /* rounds that streamed all edge records */
-    uint32_t reserved;
+    uint64_t hinge_moves;   /* peeled edges whose first claim came from a
+                               vertex other than the hinge (a vertex of
+                               smaller position claimed later in the round) */
+    uint64_t reserved[2];
 } hpeel_stats;
 
 /* Largest number of rounds a single peel supports (claim words keep the
@@ -83,9 +82,6 @@ typedef struct hpeel_stats {
  *   bucket_min_vertices graphs with at least this many vertices use the
  *                       L2-blocked build (default 8 Mi); smaller ones update
  *                       the vertex records directly.
- *   dense_div           a round whose layer has more than n / dense_div
- *                       edges streams all edge records instead of reading
- *                       the layer list (default 12).
  *   host_round_loop     0 (default): the rounds run back to back on the
  *                       device (a CUDA graph whose while node repeats the
  *                       round kernel until a layer is empty); 1: the host
@@ -100,10 +96,9 @@ typedef struct hpeel_stats {
 typedef struct hpeel_tuning {
     uint32_t bucket_shift;
     uint32_t bucket_min_vertices;
-    uint32_t dense_div;
     uint32_t host_round_loop;
     uint32_t bucket_sub_shift;
-    uint32_t reserved[3];
+    uint32_t reserved[4];
 } hpeel_tuning;
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t);
 void hpeel_get_tuning(hpeel_tuning *t);
@@ -159,7 +154,8 @@ size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r);
  *   2 <= r <= 4.  n = 0 is valid (empty order, no round).
  * Synchronises stream (the number of rounds is decided on the device and
  * read back).  Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL,
- * HPEEL_ERR_CAPACITY (R > max_layers or R > HPEEL_MAX_ROUNDS),
+ * HPEEL_ERR_CAPACITY (R > max_layers or R > HPEEL_MAX_ROUNDS, or a vertex
+ * of degree 2^31 or more),
  * HPEEL_ERR_DEVICE_CHECK (a vertex id outside its part), HPEEL_ERR_CUDA.
  */
 hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m,
@@ -182,7 +178,7 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m,
  * cudaMalloc, cudaFree or other device allocation.
  *   - Size limit: the call fails with HPEEL_ERR_WORKSPACE_TOO_SMALL (and
  *     launches nothing) when hpeel_peel_workspace_size(n, m, r) exceeds
- *     HPEEL_NOALLOC_SCRATCH_BYTES -- about 440,000 edges at gamma = 1.23,
+ *     HPEEL_NOALLOC_SCRATCH_BYTES -- about 500,000 edges at gamma = 1.23,
  *     r = 3.  Larger graphs need hpeel_peel and a caller workspace.
  *   - The first call on a device looks up the array's device address (once
  *     per device, with that device current); make that first call before
@@ -194,7 +190,7 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m,
  *     the array: callers must order such calls.
  * Synchronises stream.
  */
-#define HPEEL_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define HPEEL_NOALLOC_SCRATCH_BYTES (24u << 20)
 hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, uint64_t m,
                                 uint32_t r, uint32_t *d_order, uint32_t *d_claim,
                                 uint64_t *d_layer_off, uint32_t max_layers,

@@ -51,8 +51,8 @@ class HpeelError(RuntimeError):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("bucket_shift", ctypes.c_uint32), ("bucket_min_vertices", ctypes.c_uint32),
-                ("dense_div", ctypes.c_uint32), ("host_round_loop", ctypes.c_uint32),
-                ("bucket_sub_shift", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("host_round_loop", ctypes.c_uint32), ("bucket_sub_shift", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -65,11 +65,10 @@ class Stats(ctypes.Structure):
                 ("core_nonempty", ctypes.c_uint32), ("seed_used", ctypes.c_uint64),
                 ("attempts", ctypes.c_uint32), ("device_err", ctypes.c_uint32),
                 ("first_layer", ctypes.c_uint64), ("frontier", ctypes.c_uint64),
-                ("dense_edges", ctypes.c_uint64), ("dense_cross", ctypes.c_uint64),
-                ("dense_rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("hinge_moves", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
 
 
 _lib = None
@@ -243,7 +242,7 @@ def mphf_bits_per_key(n: int, gamma_milli: int = 1230) -> float:
     return (64 * ((m + 31) // 32) + 64 * ((m + 511) // 512 + 1)) / max(n, 1)
 
 
-NOALLOC_SCRATCH_BYTES = 16 << 20
+NOALLOC_SCRATCH_BYTES = 24 << 20
 
 
 def peel_noalloc(edges, m: int, max_layers: int = 4096) -> PeelResult:
@@ -340,7 +339,7 @@ def get_tuning() -> dict:
     t = Tuning()
     lib().hpeel_get_tuning(ctypes.byref(t))
     return {"bucket_shift": t.bucket_shift, "bucket_min_vertices": t.bucket_min_vertices,
-            "dense_div": t.dense_div, "host_round_loop": t.host_round_loop,
+            "host_round_loop": t.host_round_loop,
             "bucket_sub_shift": t.bucket_sub_shift}
 
 
@@ -351,8 +350,8 @@ def set_tuning(**kw) -> None:
         return
     cur = get_tuning()
     cur.update(kw)
-    t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["dense_div"],
-               cur["host_round_loop"], cur["bucket_sub_shift"])
+    t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["host_round_loop"],
+               cur["bucket_sub_shift"])
     _check(lib().hpeel_set_tuning(ctypes.byref(t)))
 
 

@@ -34,7 +34,7 @@ Ctl *pinned_ctl() {
 }
 
 struct PeelLayout {
-    size_t ctl, params, rec, state, claim, L, S, pairs, fill, pairs2, fill2, ovf, ovf_count, loff,
+    size_t ctl, params, rec, state, claim, L, pairs, fill, pairs2, fill2, ovf, ovf_count, loff,
         hist, scantmp, total;
     uint32_t max_rounds;
     bool bucketed;
@@ -53,7 +53,7 @@ int current_sms() {
 }
 
 // Process-wide tuning (hpeel_set_tuning); read by layouts and launches.
-hpeel_tuning g_tuning = {22u, 8u << 20, 12u, 0u, 0u, {0, 0, 0}};
+hpeel_tuning g_tuning = {22u, 8u << 20, 0u, 0u, {0, 0, 0, 0}};
 std::mutex g_tuning_mu;
 
 hpeel_tuning tuning() {
@@ -62,10 +62,10 @@ hpeel_tuning tuning() {
 }
 
 // Workspace of one peel: edge records, vertex records, claim words, layer
-// list, optional MWHC solve records, incidence buckets of the L2-blocked
-// build (sharing space with the layer list and solve records, which are
+// list (one entry per edge, the shape of an edge record), incidence buckets
+// of the L2-blocked build (sharing space with the layer list, which is
 // written only after the build), layer table, order-sort scratch.
-PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool with_s) {
+PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r) {
     PeelLayout p{};
     const hpeel_tuning tu = tuning();
     size_t off = 0;
@@ -85,11 +85,10 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool with_s) {
     p.rec = take((r == 4 ? 32 : 16) * n);
     p.state = take(8 * m);
     p.claim = take(4 * n);
-    const size_t ls = align256(4 * n) + (with_s ? 16 * n : 0);
+    const size_t ls = (r == 4 ? 32 : 16) * n;
     const size_t shared = std::max<size_t>(ls, p.bucketed ? p.plan.pair_bytes : 0);
     const size_t region = take(shared);
     p.L = region;
-    p.S = region + align256(4 * n);
     p.pairs = region;
     p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks * p.plan.regions : 0);
     p.pairs2 = take(p.bucketed ? p.plan.pair2_bytes : 0);
@@ -123,7 +122,7 @@ MphfLayout mphf_layout(uint64_t n, uint32_t gamma_milli) {
     p.rank_scan = take(4 * blocks + 4);
     p.rank_tmp = take(4 * scan_tmp_words(blocks));
     p.peel = off;
-    p.total = off + peel_layout(n, p.m, 3, true).total;
+    p.total = off + peel_layout(n, p.m, 3).total;
     return p;
 }
 
@@ -132,13 +131,9 @@ struct PeelOut {
     uint64_t n_peeled;
     uint64_t first_layer;
     uint64_t frontier;
-    uint64_t dense_edges;
-    uint64_t dense_cross;
-    uint32_t dense_rounds;
+    uint64_t moves;
     uint32_t *loff;  // device layer table (uint32[rounds + 2])
-    uint4 *S;        // device solve records (MPHF, sparse layers)
-    uint4 *rec;      // device edge records
-    std::vector<uint8_t> dense;  // per round: layer deleted by a record stream
+    uint4 *list;     // device layer list: entries {v_hinge, others, e}
 };
 
 // What a peel starts from and what it must produce.
@@ -149,31 +144,89 @@ struct PeelIO {
     FastMod fm{0, 0};
     uint32_t *order = nullptr;  // canonical order output (nullptr: not needed)
     uint32_t *claim = nullptr;  // claim-word output (nullptr: workspace)
-    bool with_s = false;        // write MWHC solve records (r = 3)
     bool force_direct = false;  // update the vertex records directly (no buckets)
 };
-
-// A layer is deleted by streaming all edge records once it holds more than
-// n / kDenseDiv edges (a random record access costs about as much as
-// streaming 12 records).
 
 // Executable graphs of the round loop, cached by their parameters: round 0,
 // then a while node whose body is one round kernel.  The round kernel's last
 // block sets the while condition (next layer non-empty, table not full).
+// The cache keeps the kGraphCache most recently used graphs.  A graph may
+// still run on another caller's stream when it is evicted, so every launch
+// records an event after it, and eviction waits for that event before the
+// graph (and the condition handle its kernels set) is destroyed.
 struct RoundGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;  // recorded after the latest launch
 };
+constexpr size_t kGraphCache = 16;
 std::mutex g_graph_mu;
 std::map<std::string, RoundGraph> g_graphs;
-std::vector<std::string> g_graph_order;
+std::vector<std::string> g_graph_lru;  // least recently used first
 
-hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool with_s,
-                                const RoundParams *prm) {
+void destroy_graph(RoundGraph &g) {
+    if (g.done) {
+        cudaEventSynchronize(g.done);
+        cudaEventDestroy(g.done);
+    }
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = RoundGraph{};
+}
+
+hpeel_status build_round_graph(const RoundLaunch &k0, const RoundLaunch &k1,
+                               const RoundParams *prm, RoundGraph *out) {
+    RoundGraph rg;
+    auto cleanup = [&](hpeel_status st) {
+        destroy_graph(rg);
+        return st;
+    };
+    if (cudaGraphCreate(&rg.graph, 0) != cudaSuccess ||
+        cudaEventCreateWithFlags(&rg.done, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(HPEEL_ERR_CUDA, "graph creation failed: %s",
+                            cudaGetErrorString(cudaGetLastError())));
+    cudaGraphConditionalHandle h = 0;
+    void *args[] = {(void *)&prm, &h};
+    cudaKernelNodeParams p0{};
+    p0.func = k0.fn;
+    p0.gridDim = dim3(k0.grid);
+    p0.blockDim = dim3(k0.block);
+    p0.kernelParams = args;
+    p0.sharedMemBytes = k0.smem;
+    cudaGraphNode_t n0, nw, n1;
+    cudaGraphNodeParams cp{};
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, rg.graph, 0, 0);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n0, rg.graph, nullptr, 0, &p0);
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&nw, rg.graph, &n0, nullptr, 1, &cp);
+    }
+    if (e == cudaSuccess) {
+        cudaKernelNodeParams p1{};
+        p1.func = k1.fn;
+        p1.gridDim = dim3(k1.grid);
+        p1.blockDim = dim3(k1.block);
+        p1.kernelParams = args;
+        p1.sharedMemBytes = k1.smem;
+        e = cudaGraphAddKernelNode(&n1, cp.conditional.phGraph_out[0], nullptr, 0, &p1);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&rg.exec, rg.graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(HPEEL_ERR_CUDA, "round graph: %s", cudaGetErrorString(e)));
+    }
+    *out = rg;
+    return HPEEL_OK;
+}
+
+hpeel_status launch_round_graph(const Launch &L, uint32_t r, const RoundParams *prm) {
     int dev = 0;
     HP_CUDA(cudaGetDevice(&dev));
     const RoundLaunch k0 = round0_launch(L, r);
-    const RoundLaunch k1 = round_launch(L, with_s, r);
+    const RoundLaunch k1 = round_launch(L, r);
     char keybuf[160];
     snprintf(keybuf, sizeof keybuf, "%d|%p|%p|%p|%u|%u", dev, k0.fn, k1.fn, (const void *)prm,
              k0.grid, k1.grid);
@@ -181,46 +234,26 @@ hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool with_s,
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
-        RoundGraph rg;
-        HP_CUDA(cudaGraphCreate(&rg.graph, 0));
-        cudaGraphConditionalHandle h = 0;
-        HP_CUDA(cudaGraphConditionalHandleCreate(&h, rg.graph, 0, 0));
-        void *args[] = {(void *)&prm, &h};
-        cudaKernelNodeParams p0{};
-        p0.func = k0.fn;
-        p0.gridDim = dim3(k0.grid);
-        p0.blockDim = dim3(k0.block);
-        p0.kernelParams = args;
-        cudaGraphNode_t n0, nw, n1;
-        HP_CUDA(cudaGraphAddKernelNode(&n0, rg.graph, nullptr, 0, &p0));
-        cudaGraphNodeParams cp{};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        HP_CUDA(cudaGraphAddNode(&nw, rg.graph, &n0, nullptr, 1, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        cudaKernelNodeParams p1{};
-        p1.func = k1.fn;
-        p1.gridDim = dim3(k1.grid);
-        p1.blockDim = dim3(k1.block);
-        p1.kernelParams = args;
-        HP_CUDA(cudaGraphAddKernelNode(&n1, body, nullptr, 0, &p1));
-        HP_CUDA(cudaGraphInstantiate(&rg.exec, rg.graph, 0));
-        if (g_graph_order.size() >= 16) {  // keep the 16 most recent
-            auto old = g_graphs.find(g_graph_order.front());
+        while (g_graph_lru.size() >= kGraphCache) {
+            auto old = g_graphs.find(g_graph_lru.front());
             if (old != g_graphs.end()) {
-                cudaGraphExecDestroy(old->second.exec);
-                cudaGraphDestroy(old->second.graph);
+                destroy_graph(old->second);  // waits for its latest launch
                 g_graphs.erase(old);
             }
-            g_graph_order.erase(g_graph_order.begin());
+            g_graph_lru.erase(g_graph_lru.begin());
         }
+        RoundGraph rg;
+        HP_TRY(build_round_graph(k0, k1, prm, &rg));
         it = g_graphs.emplace(key, rg).first;
-        g_graph_order.push_back(key);
+        g_graph_lru.push_back(key);
+    } else {
+        auto pos = std::find(g_graph_lru.begin(), g_graph_lru.end(), key);
+        if (pos != g_graph_lru.end()) g_graph_lru.erase(pos);
+        g_graph_lru.push_back(key);
     }
     count_launch(1);  // round 0; the caller counts the round kernel's iterations
     HP_CUDA(cudaGraphLaunch(it->second.exec, L.stream));
+    HP_CUDA(cudaEventRecord(it->second.done, L.stream));
     return HPEEL_OK;
 }
 
@@ -228,14 +261,13 @@ hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool with_s,
 // hctl: host memory the control block is read back into after every round.
 hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_t m, uint32_t r,
                           char *ws, PeelOut *out, Ctl *hctl) {
-    const PeelLayout lay = peel_layout(n, m, r, io.with_s);
+    const PeelLayout lay = peel_layout(n, m, r);
     const hpeel_tuning tu = tuning();
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
     uint4 *rec = reinterpret_cast<uint4 *>(ws + lay.rec);
     unsigned long long *st = reinterpret_cast<unsigned long long *>(ws + lay.state);
     uint32_t *claim = io.claim ? io.claim : reinterpret_cast<uint32_t *>(ws + lay.claim);
-    uint32_t *Ll = reinterpret_cast<uint32_t *>(ws + lay.L);
-    uint4 *S = io.with_s ? reinterpret_cast<uint4 *>(ws + lay.S) : nullptr;
+    uint4 *Ll = reinterpret_cast<uint4 *>(ws + lay.L);
     uint32_t *loff = reinterpret_cast<uint32_t *>(ws + lay.loff);
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + lay.hist);
     uint32_t *scantmp = reinterpret_cast<uint32_t *>(ws + lay.scantmp);
@@ -275,18 +307,15 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         launch_build_incidence(L, rec, n, r, m, st, ctl);
     }
     HP_TRY(check_launch("build"));
-    const uint32_t dense_div = std::max(1u, tu.dense_div);
     RoundParams hp_prm{};
     hp_prm.st = st;
     hp_prm.rec = rec;
-    hp_prm.Llist = Ll;
+    hp_prm.L = Ll;
     hp_prm.loff = loff;
-    hp_prm.S = S;
     hp_prm.ctl = ctl;
     hp_prm.n = n;
     hp_prm.m = m;
     hp_prm.P = P;
-    hp_prm.dense_div = dense_div;
     hp_prm.max_rounds = lay.max_rounds;
     RoundParams *prm = reinterpret_cast<RoundParams *>(ws + lay.params);
     HP_CUDA(cudaMemcpyAsync(prm, &hp_prm, sizeof hp_prm, cudaMemcpyHostToDevice, L.stream));
@@ -302,7 +331,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         while (hctl->more && !hctl->err) {
             {
                 ProfScope ps(L, "rounds");
-                launch_round(L, io.with_s, r, prm);
+                launch_round(L, r, prm);
             }
             HP_TRY(check_launch("round"));
             HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
@@ -312,7 +341,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         // round 0 and a CUDA-graph while node around the round kernel: the
         // rounds run back to back on the device, one read-back at the end
         ProfScope ps(L, "rounds");
-        HP_TRY(launch_round_graph(L, r, io.with_s, prm));
+        HP_TRY(launch_round_graph(L, r, prm));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
         count_launch(hctl->round + (hctl->more ? 1 : 0));
@@ -326,6 +355,8 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     }
     if (hctl->err == kDevCapacity)
         return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds - 1);
+    if (hctl->err == kDevDegree)
+        return fail(HPEEL_ERR_CAPACITY, "a vertex has degree 2^31 or more");
     if (hctl->err)
         return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u", hctl->err);
     const uint32_t R = hctl->more ? hctl->round + 1 : hctl->round;
@@ -333,23 +364,9 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     out->rounds = R;
     out->n_peeled = hctl->lcur;
     out->frontier = hctl->cross;
-    out->dense_rounds = hctl->dense_rounds;
-    out->dense_edges = hctl->dense_edges;
-    out->dense_cross = hctl->dense_cross;
+    out->moves = hctl->moves;
     out->loff = loff;
-    out->S = S;
-    out->rec = rec;
-    // which layers were deleted from a record stream (their MWHC assignment
-    // streams the records too): the kernel's rule, from the layer sizes
-    if (io.with_s && R > 0) {
-        std::vector<uint32_t> lh(R + 1);
-        HP_CUDA(cudaMemcpyAsync(lh.data(), loff, 4 * ((size_t)R + 1), cudaMemcpyDeviceToHost,
-                                L.stream));
-        HP_CUDA(cudaStreamSynchronize(L.stream));
-        out->dense.resize(R);
-        for (uint32_t t = 0; t < R; t++)
-            out->dense[t] = (t == 0 || lh[t + 1] - lh[t] > n / dense_div) ? 1 : 0;
-    }
+    out->list = Ll;
 
     if (!io.order && !io.claim) return HPEEL_OK;
     {
@@ -393,9 +410,13 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         }
         base += nb - 1;
         seg = loff_h[base];
-        HP_CUDA(cudaMemcpyAsync(Ll + seg, order + seg, 4 * (size_t)(n - seg),
+        // the edge records are dead once the claims are extracted: their
+        // space holds the tail being re-sorted (the layer list must survive
+        // for the MWHC assignment)
+        uint32_t *tail = reinterpret_cast<uint32_t *>(rec);
+        HP_CUDA(cudaMemcpyAsync(tail + seg, order + seg, 4 * (size_t)(n - seg),
                                 cudaMemcpyDeviceToDevice, L.stream));
-        src = Ll + seg;
+        src = tail + seg;
     }
     return HPEEL_OK;
 }
@@ -430,11 +451,10 @@ const char *hpeel_last_error(void) { return g_last_error.c_str(); }
 
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t) {
     g_last_error.clear();
-    hpeel_tuning v = {22u, 8u << 20, 12u, 0u, 0u, {0, 0, 0}};
+    hpeel_tuning v = {22u, 8u << 20, 0u, 0u, {0, 0, 0, 0}};
     if (t) {
         if (t->bucket_shift < 8 || t->bucket_shift > 30)
             return fail(HPEEL_ERR_INVALID_ARG, "bucket_shift %u outside [8, 30]", t->bucket_shift);
-        if (t->dense_div == 0) return fail(HPEEL_ERR_INVALID_ARG, "dense_div must be positive");
         if (t->bucket_sub_shift > 14 || (t->bucket_sub_shift && t->bucket_sub_shift > t->bucket_shift))
             return fail(HPEEL_ERR_INVALID_ARG, "bucket_sub_shift %u: need 0 or at most "
                         "min(14, bucket_shift)", t->bucket_sub_shift);
@@ -476,7 +496,7 @@ hpeel_status hpeel_hash_edges(const uint64_t *d_keys, uint64_t n, uint64_t m, ui
 }
 
 size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r) {
-    return peel_layout(n, m, r, false).total;
+    return peel_layout(n, m, r).total;
 }
 
 hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
@@ -501,7 +521,7 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
     if (!d_edges || !d_order || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
     if (((uintptr_t)d_ws & 255u) != 0)
         return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    const size_t need = peel_layout(n, m, r, false).total;
+    const size_t need = peel_layout(n, m, r).total;
     if (ws_bytes < need)
         return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes, need);
     PeelOut po{};
@@ -524,9 +544,7 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
         h_stats->core_nonempty = po.n_peeled < n;
         h_stats->first_layer = po.first_layer;
         h_stats->frontier = po.frontier;
-        h_stats->dense_edges = po.dense_edges;
-        h_stats->dense_cross = po.dense_cross;
-        h_stats->dense_rounds = po.dense_rounds;
+        h_stats->hinge_moves = po.moves;
     }
     return HPEEL_OK;
 }
@@ -572,7 +590,6 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
         io.seed = s;
         io.fm = fm;
         io.order = d_order;
-        io.with_s = true;
         HP_TRY(peel_core(L, io, (uint32_t)n, (uint32_t)m, 3, ws + lay.peel, &po));
         if (h_stats) {
             h_stats->attempts = a + 1;
@@ -581,9 +598,7 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
             h_stats->core_nonempty = po.n_peeled < n;
             h_stats->first_layer = po.first_layer;
             h_stats->frontier = po.frontier;
-        h_stats->dense_edges = po.dense_edges;
-        h_stats->dense_cross = po.dense_cross;
-        h_stats->dense_rounds = po.dense_rounds;
+        h_stats->hinge_moves = po.moves;
         }
         if (po.n_peeled < n) continue;
         // a8: reverse layer order
@@ -591,8 +606,7 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
         HP_CUDA(cudaMemsetAsync(d_G, 0, 8 * words, L.stream));
         for (int64_t t = (int64_t)po.rounds - 1; t >= 0; t--) {
             ProfScope ps(L, "assign");
-            launch_assign_layer(L, po.dense[t] != 0, po.S, po.rec, (uint32_t)n, po.loff,
-                                (uint32_t)t, d_G);
+            launch_assign_layer(L, po.list, po.loff, (uint32_t)t, (uint32_t)(m / 3), d_G);
         }
         HP_TRY(check_launch("assign"));
         // a9: rank directory
@@ -687,7 +701,7 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
     if (n > 0 && (m == 0 || m % r != 0))
         return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of r",
                     (unsigned long long)m);
-    const size_t need = n ? peel_layout(n, m, r, false).total : 0;
+    const size_t need = n ? peel_layout(n, m, r).total : 0;
     if (need > (size_t)HPEEL_NOALLOC_SCRATCH_BYTES)
         return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL,
                     "n = %llu, m = %llu needs %zu bytes of scratch; the built-in scratch holds "
@@ -730,9 +744,7 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
         h_stats->core_nonempty = po.n_peeled < n;
         h_stats->first_layer = po.first_layer;
         h_stats->frontier = po.frontier;
-        h_stats->dense_edges = po.dense_edges;
-        h_stats->dense_cross = po.dense_cross;
-        h_stats->dense_rounds = po.dense_rounds;
+        h_stats->hinge_moves = po.moves;
     }
     return HPEEL_OK;
 }

@@ -17,24 +17,21 @@ enum : uint32_t {
     kDevCapacity = 3,    // a round-table bound was exceeded
     kDevTimeout = 4,     // a bounded wait gave up
     kDevBuildOverflow = 5,  // the bucketed build's overflow list was full
+    kDevDegree = 6,      // a vertex degree of 2^31 or more (no room for the mark bit)
 };
 
 // Device-side control block of one peel (lives in the workspace).
 struct Ctl {
     uint32_t lcur;       // append cursor of the layer list L (L_0 | L_1 | ...)
-    uint32_t fcur;       // append cursor of the frontier list F (F_1 | F_2 | ...)
     uint32_t round;      // index t of the round being run
     uint32_t done;       // blocks finished in the current update launch
     uint32_t err;        // first device error code (0 = none)
     uint32_t more;       // 1 while the next layer is non-empty
     uint32_t next_size;  // size of the layer the next round deletes
-    uint32_t scur;       // solve-record cursor of a dense round
     uint32_t cross;      // vertices that fell from degree 2 to 1 (all rounds)
     uint32_t first_layer;   // |L_0|
-    uint32_t dense_rounds;  // rounds that streamed all edge records
-    uint32_t dense_edges;   // edges those rounds deleted
-    uint32_t dense_cross;   // degree 2 -> 1 falls in those rounds
-    uint32_t pad[2];
+    uint32_t moves;      // list entries whose first claimer was not the hinge
+    uint32_t pad[7];
 };
 
 // Arguments of the round-loop kernels, kept in the workspace so the CUDA
@@ -42,11 +39,10 @@ struct Ctl {
 struct RoundParams {
     unsigned long long *st;  // vertex records [m]
     uint4 *rec;              // edge records [n]
-    uint32_t *Llist;         // layer list [n]
+    uint4 *L;                // layer list: one entry per peeled edge
     uint32_t *loff;          // layer starts
-    uint4 *S;                // solve records (or null)
     Ctl *ctl;
-    uint32_t n, m, P, dense_div, max_rounds, pad[3];
+    uint32_t n, m, P, max_rounds;
 };
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): two
@@ -90,6 +86,10 @@ __device__ __forceinline__ uint32_t part_of(uint32_t v, uint32_t P) {
 __device__ __forceinline__ void raise_err(Ctl *ctl, uint32_t code) {
     atomicCAS(&ctl->err, 0u, code);
 }
+
+// Mark bit in the degree half of a vertex record: set once the vertex has
+// degree 1 with its last edge claimed (round 0 scan, or the fall from 2 to 1).
+constexpr uint32_t kMark = 0x80000000u;
 
 // Warp-aggregated append: every lane of the warp calls this (convergent);
 // lanes with pred get consecutive slots of list, one atomicAdd per warp.
@@ -164,14 +164,76 @@ __device__ __forceinline__ uint32_t load_record_stream(const uint4 *rec, uint64_
     return q.w;
 }
 
-// MWHC solve record of a peeled edge (r = 3): {v_hinge, v_a, v_b, hinge},
-// a < b the two other positions.
-__device__ __forceinline__ uint4 solve_record(uint32_t c, const uint32_t (&v)[4]) {
-    const uint32_t h = c & 3u;
-    const uint32_t vh = h == 0 ? v[0] : (h == 1 ? v[1] : v[2]);
-    const uint32_t va = h == 0 ? v[1] : v[0];
-    const uint32_t vb = h == 2 ? v[1] : v[2];
-    return make_uint4(vh, va, vb, h);
+// ---- layer-list entries --------------------------------------------------
+// One entry per peeled edge, in the shape of its edge record with the
+// vertices rotated: word 0 the hinge vertex, then the other vertices in
+// position order, and the edge id where the record keeps its claim word
+// ({v_h, v_a, v_b, e} for r = 3; {v_h, v_a, 0, e} for r = 2; two uint4
+// {v_h, v_a, v_b, v_c}, {e, 0, 0, 0} for r = 4).  The hinge position is the
+// part of word 0 (sec. 4.3), so an entry is also the MWHC solve record of
+// its edge.
+template <int R>
+struct Entry {
+    uint4 w[R == 4 ? 2 : 1];
+};
+
+template <int R>
+__device__ __forceinline__ Entry<R> make_entry(const uint32_t (&v)[4], uint32_t e) {
+    Entry<R> x;
+    if (R == 4) {
+        x.w[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        x.w[R == 4 ? 1 : 0] = make_uint4(e, 0u, 0u, 0u);
+    } else {
+        x.w[0] = make_uint4(v[0], v[1], R == 3 ? v[2] : 0u, e);
+    }
+    return x;
+}
+
+// v[0] = hinge vertex, v[1..R-1] = others in position order; returns e.
+template <int R>
+__device__ __forceinline__ uint32_t load_entry(const uint4 *L, uint64_t i, uint32_t (&v)[4]) {
+    if (R == 4) {
+        const uint4 a = __ldcs(L + 2 * i), b = __ldcs(L + 2 * i + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        return b.x;
+    }
+    const uint4 a = __ldcs(L + i);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = 0u;
+    return a.w;
+}
+
+template <int R>
+__device__ __forceinline__ void store_entry(uint4 *L, uint64_t i, const Entry<R> &x) {
+    if (R == 4) {
+        L[2 * i] = x.w[0];
+        L[2 * i + 1] = x.w[R == 4 ? 1 : 0];
+    } else {
+        L[i] = x.w[0];
+    }
+}
+
+// Rotation of the position-ordered vertices p[0..R-1] around position h:
+// out[0] = p[h], out[1..R-1] = the others in position order.  Static indices
+// only, so the arrays stay in registers.
+template <int R>
+__device__ __forceinline__ void rotate_to(const uint32_t (&p)[4], uint32_t h, uint32_t (&out)[4]) {
+    uint32_t x = p[0];
+#pragma unroll
+    for (int q = 1; q < R; q++) x = h == (uint32_t)q ? p[q] : x;
+    out[0] = x;
+#pragma unroll
+    for (int k = 0; k < R - 1; k++) out[k + 1] = (uint32_t)k >= h ? p[k + 1] : p[k];
+#pragma unroll
+    for (int k = R; k < 4; k++) out[k] = 0u;
+}
+
+// Inverse: position-ordered vertices of an entry whose hinge is at position h.
+template <int R>
+__device__ __forceinline__ void unrotate(const uint32_t (&v)[4], uint32_t h, uint32_t (&p)[4]) {
+#pragma unroll
+    for (int q = 0; q < R; q++) p[q] = (uint32_t)q == h ? v[0] : ((uint32_t)q < h ? v[q + 1] : v[q]);
+#pragma unroll
+    for (int k = R; k < 4; k++) p[k] = 0u;
 }
 
 // Block-aggregated append: every thread of the block calls this (it holds
@@ -218,12 +280,12 @@ __device__ __forceinline__ void block_append(uint32_t *cursor, uint32_t *list, c
 // with one atomicAdd per CAP values (flush when full and at the end), so the
 // shared list cursor sees few atomics however many values are appended.  The
 // order of the values in the list is unspecified.
-template <int CAP>
+template <typename T, int CAP>
 struct WarpStage {
-    uint32_t *buf;  // this warp's CAP slots in shared memory
-    uint32_t cnt;   // values staged (warp-uniform)
+    T *buf;        // this warp's CAP slots in shared memory
+    uint32_t cnt;  // values staged (warp-uniform)
 
-    __device__ __forceinline__ void flush(uint32_t *cursor, uint32_t *list) {
+    __device__ __forceinline__ void flush(uint32_t *cursor, T *list) {
         __syncwarp();
         if (cnt == 0) return;
         const uint32_t lane = threadIdx.x & 31u;
@@ -235,8 +297,7 @@ struct WarpStage {
         __syncwarp();
     }
     // every lane of the warp calls push (convergent)
-    __device__ __forceinline__ void push(bool pred, uint32_t val, uint32_t *cursor,
-                                         uint32_t *list) {
+    __device__ __forceinline__ void push(bool pred, const T &val, uint32_t *cursor, T *list) {
         const uint32_t lane = threadIdx.x & 31u;
         const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, pred);
         if (ballot == 0) return;

@@ -34,6 +34,19 @@ void prof_flush();  // after a stream synchronisation: accumulate timings
 
 // Persistent grid size for grid-stride kernels over device-sized ranges.
 inline unsigned grid_fixed(const Launch &L, int per_sm) { return (unsigned)(L.sms * per_sm); }
+// One wave: as many blocks of kThreads as fit on the device at once (at most
+// cap_per_sm per SM), for grid-stride kernels.
+inline unsigned grid_resident(const Launch &L, const void *fn, int cap_per_sm,
+                              size_t dyn_smem = 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, dyn_smem) != cudaSuccess ||
+        nb <= 0) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    if (nb > cap_per_sm) nb = cap_per_sm;
+    return (unsigned)(L.sms * nb);
+}
 inline unsigned grid_for(const Launch &L, uint64_t work, int per_thread, int per_sm) {
     uint64_t blocks = (work + (uint64_t)kThreads * per_thread - 1) / ((uint64_t)kThreads * per_thread);
     uint64_t cap = (uint64_t)L.sms * per_sm;
@@ -95,6 +108,7 @@ void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, cons
 struct RoundLaunch {
     void *fn;
     unsigned grid, block;
+    unsigned smem;  // dynamic shared memory bytes per block
 };
 
 // a3 + a4 of round 0: scan all vertices, claim the edge of every degree-1
@@ -103,10 +117,9 @@ void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm);
 RoundLaunch round0_launch(const Launch &L, uint32_t r);
 
 // a5 + a4 of the next round + a6: delete layer t (t read on the device),
-// claim and list layer t+1, close the round.  with_s: write MWHC solve
-// records (r = 3).
-void launch_round(const Launch &L, bool with_s, uint32_t r, const RoundParams *prm);
-RoundLaunch round_launch(const Launch &L, bool with_s, uint32_t r);
+// claim and list layer t+1, close the round.
+void launch_round(const Launch &L, uint32_t r, const RoundParams *prm);
+RoundLaunch round_launch(const Launch &L, uint32_t r);
 
 // claim[e] = claim word of record e.
 void launch_extract_claim(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
@@ -137,8 +150,8 @@ void launch_scan_u32(const Launch &L, const uint32_t *in, uint32_t *out, uint64_
 
 // a8: MWHC assignment of one layer t from its solve records (host loop runs
 // t = R-1 .. 0).
-void launch_assign_layer(const Launch &L, bool dense, const uint4 *S, const uint4 *rec,
-                         uint32_t n, const uint32_t *loff, uint32_t t, uint64_t *G);
+void launch_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
+                         uint32_t P, uint64_t *G);
 // a9: per-512-vertex counts of non-zero 2-bit values, then the directory.
 void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt);
 void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,

@@ -19,48 +19,28 @@ __device__ __forceinline__ uint32_t g_get(const uint64_t *G, uint32_t v) {
     return (uint32_t)(__ldcg(G + (v >> 5)) >> (2u * (v & 31u))) & 3u;
 }
 
-// Layer t: solve records S[loff[t] .. loff[t+1]) = {v_hinge, v_a, v_b, hinge},
-// written by the round that deleted the layer, read here as a stream.
+// Layer t: list entries loff[t] .. loff[t+1], each {v_hinge, v_a, v_b, e}
+// with the hinge position the part of v_hinge, read as a stream.
 __global__ void __launch_bounds__(kThreads)
-k_assign(const uint4 *__restrict__ S, const uint32_t *__restrict__ loff, uint32_t t,
-         uint64_t *G) {
+k_assign(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, uint32_t t,
+         uint32_t P, uint64_t *G) {
     const uint32_t lb = loff[t], le = loff[t + 1];
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     for (uint64_t i = lb + (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < le; i += stride) {
-        const uint4 s = __ldcs(S + i);
+        const uint4 s = __ldcs(Lst + i);
+        const uint32_t h = part_of<3>(s.x, P);
         const uint32_t sum = g_get(G, s.y) + g_get(G, s.z);
-        const uint32_t val = (s.w + 6u - sum) % 3u;  // sum <= 6
+        const uint32_t val = (h + 6u - sum) % 3u;  // sum <= 6
         const uint64_t code = val ? val : 3u;
         atomicOr((unsigned long long *)(G + (s.x >> 5)),
                  (unsigned long long)(code << (2u * (s.x & 31u))));
     }
 }
 
-// Layer t of a round that streamed the records: stream them again and solve
-// the edges whose claim word holds round t.
-__global__ void __launch_bounds__(kThreads)
-k_assign_dense(const uint4 *__restrict__ rec, uint32_t n, uint32_t t, uint64_t *G) {
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t e = (uint64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += stride) {
-        const uint4 q = __ldcs(rec + e);
-        if (q.w == kUnclaimed || (q.w >> 2) != t) continue;
-        const uint32_t v[4] = {q.x, q.y, q.z, 0u};
-        const uint4 s = solve_record(q.w, v);
-        const uint32_t sum = g_get(G, s.y) + g_get(G, s.z);
-        const uint32_t val = (s.w + 6u - sum) % 3u;
-        const uint64_t code = val ? val : 3u;
-        atomicOr((unsigned long long *)(G + (s.x >> 5)),
-                 (unsigned long long)(code << (2u * (s.x & 31u))));
-    }
-}
-
-void launch_assign_layer(const Launch &L, bool dense, const uint4 *S, const uint4 *rec,
-                         uint32_t n, const uint32_t *loff, uint32_t t, uint64_t *G) {
+void launch_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
+                         uint32_t P, uint64_t *G) {
     count_launch();
-    if (dense)
-        k_assign_dense<<<grid_for(L, n, 1, 8), kThreads, 0, L.stream>>>(rec, n, t, G);
-    else
-        k_assign<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(S, loff, t, G);
+    k_assign<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(Lst, loff, t, P, G);
 }
 
 // Non-zero 2-bit values of a word: a pair is non-zero when either bit is set.

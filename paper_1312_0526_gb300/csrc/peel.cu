@@ -23,15 +23,32 @@
 // the next frontier, and it claims f for round t+1 right away with atomicMin
 // on f's claim word.  If f is itself in L_t, its claim already holds round t
 // and the min leaves it unchanged; so the claims reaching an edge for round
-// t+1 are exactly those of its degree-1 vertices after round t, the minimum
-// is the hinge (smallest position) whatever the order of the atomics, and
-// the single claimer that sees the unclaimed value appends f to L_{t+1} (the
-// deduplication of D_i into P_i).  One kernel per round; the frontier is
-// never stored.  (A vertex keeps its position j in every edge: the graph is
-// r-partite, sec. 4.3.)
-// Round 0 claims from a scan of all vertex records; a layer is deleted either
-// from the list L (sparse) or by streaming all edge records and keeping those
-// of the round (dense, for layers that are a large fraction of the edges).
+// t+1 are exactly those of its degree-1 vertices after round t, and the
+// minimum is the hinge (smallest position) whatever the order of the
+// atomics.  One kernel per round; the frontier is never stored.  (A vertex
+// keeps its position j in every edge: the graph is r-partite, sec. 4.3.)
+//
+// Layer list.  The claimer that sees the unclaimed value (the deduplication
+// of D_i into P_i) appends one entry for f: f's vertices, read from the
+// record whose sector the claim atomic works on, rotated so
+// that its own vertex comes first, and f's id.  Round t+1 then reads its
+// layer as a sequential stream with no gather of edge records.  The first
+// claimer need not be the hinge: a claimer of a smaller position may come
+// later in the same round.  A later claimer whose atomicMin lowered the
+// claim word therefore sets the mark bit of its vertex's record (kMark); the
+// last of them holds the final minimum.  A vertex whose last edge is in L_t
+// itself never marks (that claim holds round t and stays lower), so no
+// deletion of round t sees a mark.  The round that deletes f takes as hinge
+// the smallest position among the entry's first vertex and the marked
+// vertices its DeleteEdge atomics return (all of them degree-1 vertices of f
+// when round t+1 starts, and among them the true hinge), and rewrites the
+// entry when the hinge moved, so each entry ends up as the solve record of
+// its edge.  Round 0 claims from a scan of all vertex records and lists L_0
+// the same way.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "kernels.cuh"
 
 namespace hp {
@@ -122,31 +139,41 @@ void launch_build_incidence(const Launch &L, const uint4 *rec, uint32_t n, uint3
 }
 
 // ------------------------------------------------------- round epilogue --
-// Every block adds its counts; the last block of the launch to finish
-// closes round t: layer L_{t+1} is [loff[t+1], lcur) now that every append
-// of the launch is done.  No block waits for another.  When the launch runs
-// inside a CUDA graph's while node, the last block also sets the node's
-// condition: 1 while the next layer is non-empty and the layer table has
-// room (the loop ends after at most max_rounds launches whatever happens).
+// Every block of the launch adds its counts; the last block of the launch to
+// finish closes round t: layer L_{t+1} is [loff[t+1], lcur) now that every
+// append of the launch is done.  No block waits for another.  Every block
+// takes part, including blocks with no entries: a block reads the round
+// state (ctl->round, loff) when it starts, and a block of the same launch
+// may start only after others have finished when the GPU is shared with
+// other work, so the round may advance only once every block has read it.
+// When the launch runs inside a CUDA graph's while node, the last block also
+// sets the node's condition: 1 while the next layer is non-empty, the layer
+// table has room and no kernel has raised an error (the loop ends after at
+// most max_rounds launches whatever happens).
 __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t,
-                                            uint32_t crossings, bool dense, uint32_t layer,
-                                            uint32_t max_rounds, uint32_t active,
+                                            uint32_t crossings, uint32_t moves,
+                                            uint32_t max_rounds,
                                             cudaGraphConditionalHandle cond) {
-    __shared__ uint32_t s_cross[kThreads / 32];
-    const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, crossings);
-    if ((threadIdx.x & 31u) == 0) s_cross[threadIdx.x >> 5] = wsum;
+    __shared__ uint32_t s_cnt[2][kThreads / 32];
+    const uint32_t wc = __reduce_add_sync(0xFFFFFFFFu, crossings);
+    const uint32_t wm = __reduce_add_sync(0xFFFFFFFFu, moves);
+    if ((threadIdx.x & 31u) == 0) {
+        s_cnt[0][threadIdx.x >> 5] = wc;
+        s_cnt[1][threadIdx.x >> 5] = wm;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t bsum = 0;
+        uint32_t bc = 0, bm = 0;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; w++) bsum += s_cross[w];
-        if (bsum) {
-            atomicAdd(&ctl->cross, bsum);
-            if (dense) atomicAdd(&ctl->dense_cross, bsum);
+        for (int w = 0; w < kThreads / 32; w++) {
+            bc += s_cnt[0][w];
+            bm += s_cnt[1][w];
         }
+        if (bc) atomicAdd(&ctl->cross, bc);
+        if (bm) atomicAdd(&ctl->moves, bm);
         __threadfence();
         const uint32_t d = atomicAdd(&ctl->done, 1u);
-        if (d == active - 1) {
+        if (d == gridDim.x - 1) {
             __threadfence();
             const uint32_t end = atomicAdd(&ctl->lcur, 0u);
             const uint32_t beg = loff[t + 1];
@@ -156,13 +183,9 @@ __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t
                 more = 0;
                 atomicCAS(&ctl->err, 0u, (uint32_t)kDevCapacity);
             }
-            if (dense) {
-                ctl->dense_rounds += 1;
-                ctl->dense_edges += layer;
-            }
+            if (atomicAdd(&ctl->err, 0u) != 0u) more = 0;  // stop on any device error
             ctl->next_size = end - beg;
             ctl->more = more;
-            ctl->scur = beg;
             ctl->done = 0;
             ctl->round = t + 1;
             if (cond) cudaGraphSetConditional(cond, more);
@@ -170,63 +193,188 @@ __device__ __forceinline__ void close_round(Ctl *ctl, uint32_t *loff, uint32_t t
     }
 }
 
+// Staged list entries: a per-warp buffer in dynamic shared memory, flushed
+// to the list with one atomicAdd on the shared cursor per buffer-full.  The
+// cursor is a single address, so its atomics serialise: the larger the
+// buffer, the fewer of them (8 KiB per warp in the round kernel, 4 KiB in
+// the round-0 scan).
+#ifndef HPEEL_ROUND_STAGE_BYTES
+#define HPEEL_ROUND_STAGE_BYTES 8192
+#endif
+#ifndef HPEEL_ROUND0_STAGE_BYTES
+#define HPEEL_ROUND0_STAGE_BYTES 4096
+#endif
+template <int R, int BYTES>
+constexpr int stage_cap() { return BYTES / (int)sizeof(Entry<R>); }
+
+template <int R, int CAP>
+__device__ __forceinline__ WarpStage<Entry<R>, CAP> warp_stage() {
+    extern __shared__ uint4 dyn_smem[];
+    return WarpStage<Entry<R>, CAP>{reinterpret_cast<Entry<R> *>(dyn_smem) + (threadIdx.x >> 5) * CAP,
+                                    0};
+}
+
+// Grid (one resident wave) and dynamic shared memory of a staged kernel.
+// Above 48 KiB a kernel needs the opt-in attribute, set once per kernel and
+// device (not on every launch: other callers' graphs may be running).
+inline RoundLaunch staged_launch(const Launch &L, void *fn, unsigned stage_bytes) {
+    RoundLaunch k{};
+    k.fn = fn;
+    k.block = kThreads;
+    k.smem = (kThreads / 32) * stage_bytes;
+    if (k.smem > (48u << 10)) {
+        static std::mutex mu;
+        static std::set<std::pair<int, void *>> done;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(mu);
+        if (done.insert({dev, fn}).second)
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+    }
+    k.grid = grid_resident(L, fn, 8, k.smem);
+    return k;
+}
+
+// Claim of edge f with tag (atomicMin on its claim word, returns the old
+// word), and f's vertices in position order.  The vertex words are read
+// first, and the claim's address depends on the loaded word (the select is
+// never taken: a vertex id is below m < 2^32 - 1), so the atomic reaches L2
+// after the load has brought the record's sector in.  Issued independently,
+// the two requests often fetched the same sector from DRAM twice.
+template <int R>
+__device__ __forceinline__ uint32_t claim_and_read(uint4 *rec, uint32_t f, uint32_t tag,
+                                                   uint32_t (&p)[4]) {
+    const uint4 q = __ldcg(rec + (R == 4 ? 2 * (uint64_t)f : (uint64_t)f));
+    p[0] = q.x;
+    p[1] = q.y;
+    p[2] = R >= 3 ? q.z : 0u;
+    p[3] = R == 4 ? q.w : 0u;
+    return atomicMin(claim_ptr<R>(rec, f) + (q.x == 0xFFFFFFFFu ? 1 : 0), tag);
+}
+
 // ---------------------------------------------------------------- round 0 --
-// Claims of round 0 from a scan of all vertex records (F_0 is never stored).
-// Layer 0 is not listed: the round-0 deletion pass is dense.  L_1 starts at
-// index |L_0| of the layer list.
+// Claims of round 0 from a scan of all vertex records (F_0 is never stored):
+// a vertex of degree 1 claims its edge with its position, and the first
+// claimer of an edge lists it in L_0.  About a fifth of the vertices have
+// degree 1, so each warp first queues its degree-1 vertices (vertex, edge)
+// in shared memory and then claims them in full batches of 32, up to
+// kR0Items batches in flight before any result is used.
 constexpr int kR0Items = 4;
+constexpr int kR0Queue = 32 * (kR0Items + 1);  // queued vertices per warp
+
+template <int R>
+__device__ __forceinline__ void round0_claims(int batches, const uint2 *q, uint32_t lane_limit,
+                                              unsigned long long *st, uint4 *rec, uint32_t P,
+                                              WarpStage<Entry<R>, stage_cap<R, HPEEL_ROUND0_STAGE_BYTES>()> &stage,
+                                              Ctl *ctl, Entry<R> *Lst) {
+    const uint32_t lane = threadIdx.x & 31u;
+    bool first[kR0Items], have[kR0Items];
+    uint32_t pv[kR0Items][4], jv[kR0Items], ev[kR0Items];
+#pragma unroll
+    for (int b = 0; b < kR0Items; b++) {
+        first[b] = false;
+        have[b] = false;
+        jv[b] = 0;
+        ev[b] = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) pv[b][k] = 0;
+        if (b < batches) {
+            const uint32_t slot = (uint32_t)b * 32u + lane;
+            have[b] = slot < lane_limit;
+            if (have[b]) {
+                const uint2 it = q[slot];  // {vertex, edge}
+                const uint32_t j = part_of<R>(it.x, P);
+                const uint32_t c = claim_and_read<R>(rec, it.y, j, pv[b]);
+                first[b] = c == kUnclaimed;
+                // a later claimer that lowered the claim marks its vertex;
+                // this kernel is the record's only writer
+                if (!first[b] && j < c) st[it.x] = ((unsigned long long)it.y << 32) | (1u | kMark);
+                jv[b] = j;
+                ev[b] = it.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < kR0Items; b++) {
+        if (b < batches) {
+            uint32_t x[4];
+            rotate_to<R>(pv[b], jv[b], x);
+            stage.push(first[b], make_entry<R>(x, ev[b]), &ctl->lcur, Lst);
+        }
+    }
+}
 
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_round0(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
-    const unsigned long long *__restrict__ st = prm->st;
+    unsigned long long *__restrict__ st = prm->st;
     uint4 *__restrict__ rec = prm->rec;
+    Entry<R> *__restrict__ Lst = reinterpret_cast<Entry<R> *>(prm->L);
     uint32_t *__restrict__ loff = prm->loff;
     Ctl *ctl = prm->ctl;
     const uint32_t m = prm->m, P = prm->P, n = prm->n;
+    constexpr int kCap = stage_cap<R, HPEEL_ROUND0_STAGE_BYTES>();
+    auto stage = warp_stage<R, kCap>();
+    __shared__ uint2 queue[kThreads / 32][kR0Queue];
+    uint2 *q = queue[threadIdx.x >> 5];
+    uint32_t qn = 0;  // warp-uniform queue length
+    const uint32_t lane = threadIdx.x & 31u;
     constexpr uint32_t kStep = kThreads * kR0Items;
     const uint64_t stride = (uint64_t)gridDim.x * kStep;
-    uint32_t first = 0;
+    // whole warps step together: the trip count depends on blockIdx only
     for (uint64_t base = (uint64_t)blockIdx.x * kStep; base < m; base += stride) {
 #pragma unroll
         for (int k = 0; k < kR0Items; k++) {
             const uint64_t v = base + (uint64_t)k * kThreads + threadIdx.x;
+            bool one = false;
+            uint32_t e = 0;
             if (v < m) {
                 const unsigned long long s = __ldcs(st + v);
-                if ((uint32_t)s == 1u) {
-                    const uint32_t e = (uint32_t)(s >> 32);
-                    if (e < n) {
-                        const uint32_t j = part_of<R>((uint32_t)v, P);
-                        first += atomicMin(claim_ptr<R>(rec, e), j) == kUnclaimed ? 1u : 0u;
-                    } else {
-                        raise_err(ctl, kDevBadEdge);
-                    }
+                const uint32_t deg = (uint32_t)s;
+                if (deg & kMark) raise_err(ctl, kDevDegree);
+                e = (uint32_t)(s >> 32);
+                if (deg == 1u) {
+                    one = e < n;
+                    if (!one) raise_err(ctl, kDevBadEdge);
                 }
             }
+            const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, one);
+            if (one) q[qn + __popc(ballot & ((1u << lane) - 1u))] = make_uint2((uint32_t)v, e);
+            qn += __popc(ballot);
+        }
+        __syncwarp();
+        const int full = (int)(qn >> 5);  // < kR0Items + 1 batches
+        if (full) {
+            round0_claims<R>(full, q, (uint32_t)full * 32u, st, rec, P, stage, ctl, Lst);
+            // move the partial batch to the front
+            const uint32_t rest = qn - (uint32_t)full * 32u;
+            uint2 keep = make_uint2(0u, 0u);
+            if (lane < rest) keep = q[(uint32_t)full * 32u + lane];
+            __syncwarp();
+            if (lane < rest) q[lane] = keep;
+            qn = rest;
+            __syncwarp();
         }
     }
-    // |L_0| = number of first claims; the last block publishes it as loff[1]
-    __shared__ uint32_t s_first;
-    if (threadIdx.x == 0) s_first = 0;
-    __syncthreads();
-    if (first) atomicAdd(&s_first, first);
+    if (qn) round0_claims<R>(1, q, qn, st, rec, P, stage, ctl, Lst);
+    stage.flush(&ctl->lcur, Lst);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (s_first) atomicAdd(&ctl->lcur, s_first);
         __threadfence();
         const uint32_t d = atomicAdd(&ctl->done, 1u);
         if (d == gridDim.x - 1) {
             __threadfence();
             const uint32_t end = atomicAdd(&ctl->lcur, 0u);
+            // no round after a device error (the build's included)
+            const uint32_t more = (end > 0 && atomicAdd(&ctl->err, 0u) == 0u) ? 1u : 0u;
             loff[0] = 0;
             loff[1] = end;
             ctl->next_size = end;
             ctl->first_layer = end;
-            ctl->more = end > 0 ? 1u : 0u;
-            ctl->scur = 0;
+            ctl->more = more;
             ctl->done = 0;
             ctl->round = 0;
-            if (cond) cudaGraphSetConditional(cond, end > 0 ? 1u : 0u);
+            if (cond) cudaGraphSetConditional(cond, more);
         }
     }
 }
@@ -235,166 +383,168 @@ template <int R>
 void *round0_fn() { return (void *)k_round0<R>; }
 
 RoundLaunch round0_launch(const Launch &L, uint32_t r) {
-    RoundLaunch k{};
-    k.grid = grid_fixed(L, 8);
-    k.block = kThreads;
-    k.fn = r == 2 ? round0_fn<2>() : (r == 3 ? round0_fn<3>() : round0_fn<4>());
-    return k;
+    return staged_launch(L, r == 2 ? round0_fn<2>() : (r == 3 ? round0_fn<3>() : round0_fn<4>()),
+                         HPEEL_ROUND0_STAGE_BYTES);
 }
 
 void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm) {
-    const unsigned grid = grid_fixed(L, 8);
+    const RoundLaunch k = round0_launch(L, r);
     const cudaGraphConditionalHandle c0 = 0;
     count_launch();
     switch (r) {
-    case 2: k_round0<2><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
-    case 3: k_round0<3><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
-    case 4: k_round0<4><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
+    case 2: k_round0<2><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
+    case 3: k_round0<3><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
+    case 4: k_round0<4><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
     }
 }
 
 // ---------------------------------------------------------------- rounds --
-constexpr int kStageCap = 256;  // staged appends per warp
+// Round t: delete layer L_t, read from the list as a stream, and list layer
+// L_{t+1}.  Each warp takes kRoundU * 32 consecutive entries per step,
+// lane-strided, and issues every atomic of its kRoundU edges before it
+// consumes any result: more memory requests in flight per thread.
+#ifndef HPEEL_ROUND_U
+#define HPEEL_ROUND_U 4
+#endif
+// r = 4 carries more registers per edge: two edges per thread
+template <int R>
+constexpr int round_u() { return R == 4 ? 2 : HPEEL_ROUND_U; }
 
-// Round t: delete layer L_t and list layer L_{t+1}.  A layer holding more
-// than n / dense_div edges is read by streaming all edge records and keeping
-// those claimed in round t (no solve records: such a layer is assigned from a
-// record stream too); a smaller one is read from the list, and its solve
-// record i goes to S[i].  Round 0 is always dense (L_0 is not listed).  The
-// choice depends only on device values all blocks read alike.
-// Each warp takes kRoundU * 32 consecutive entries per step, lane-strided,
-// and issues every gather and atomic of its kRoundU edges before it consumes
-// any result: more memory requests in flight per thread.
-constexpr int kRoundU = 2;
-
-template <int R, bool WITH_S>
+template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
-    uint32_t *__restrict__ Llist = prm->Llist;
+    constexpr int kRoundU = round_u<R>();
+    uint4 *__restrict__ Lw = prm->L;
+    Entry<R> *__restrict__ Lst = reinterpret_cast<Entry<R> *>(prm->L);
     uint32_t *__restrict__ loff = prm->loff;
     unsigned long long *__restrict__ st = prm->st;
     uint4 *__restrict__ rec = prm->rec;
-    uint4 *__restrict__ S = prm->S;
     Ctl *ctl = prm->ctl;
-    const uint32_t n = prm->n, dense_div = prm->dense_div, max_rounds = prm->max_rounds;
-    __shared__ uint32_t stage_buf[kThreads / 32][kStageCap];
-    WarpStage<kStageCap> stage{stage_buf[threadIdx.x >> 5], 0};
+    const uint32_t n = prm->n, P = prm->P, max_rounds = prm->max_rounds;
+    constexpr int kCap = stage_cap<R, HPEEL_ROUND_STAGE_BYTES>();
+    auto stage = warp_stage<R, kCap>();
     const uint32_t t = *(volatile uint32_t *)&ctl->round;
-    const uint32_t lb = loff[t], le = loff[t + 1];
-    const bool dense = t == 0 || (le - lb) > n / dense_div;
-    const uint64_t first = dense ? 0 : lb, last = dense ? n : le;
+    uint32_t lb = loff[t], le = loff[t + 1];
+    if (lb > le || le > n) {  // inconsistent state: report, delete nothing
+        raise_err(ctl, kDevCapacity);
+        lb = le;
+    }
     constexpr uint32_t kBlockStep = kThreads * kRoundU;
-    // blocks past the end of a small layer have nothing to do and take no
-    // part in closing the round
-    const uint64_t need = (last - first + kBlockStep - 1) / kBlockStep;
+    // a small layer is spread over as many blocks as it fills; the others
+    // skip the loop but still take part in closing the round
+    const uint64_t need = ((uint64_t)(le - lb) + kBlockStep - 1) / kBlockStep;
     const uint32_t active = (uint32_t)(need < gridDim.x ? (need ? need : 1) : gridDim.x);
-    if (blockIdx.x >= active) return;
     const uint64_t stride = (uint64_t)active * kBlockStep;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    uint32_t cross = 0;
+    uint32_t cross = 0, moves = 0;
     const unsigned long long one = 1ull;
-    for (uint64_t base = first + (uint64_t)blockIdx.x * kBlockStep + (uint64_t)warp * 32 * kRoundU;
-         base < last; base += stride) {
-        uint32_t e[kRoundU], c[kRoundU], v[kRoundU][4];
+    const uint64_t first = blockIdx.x < active ? lb + (uint64_t)blockIdx.x * kBlockStep +
+                                                     (uint64_t)warp * 32 * kRoundU
+                                               : (uint64_t)le;
+    for (uint64_t base = first; base < le; base += stride) {
+        uint32_t e[kRoundU], v[kRoundU][4], hg[kRoundU];
         bool mine[kRoundU];
 #pragma unroll
         for (int u = 0; u < kRoundU; u++) {
             const uint64_t i = base + (uint64_t)u * 32 + lane;
-            mine[u] = false;
-            c[u] = kUnclaimed;
+            mine[u] = i < le;
             e[u] = 0;
-            if (i < last) {
-                if (dense) {
-                    e[u] = (uint32_t)i;
-                    c[u] = load_record_stream<R>(rec, i, v[u]);
-                    mine[u] = c[u] != kUnclaimed && (c[u] >> 2) == t;
-                } else {
-                    e[u] = Llist[i];
-                    mine[u] = true;
-                }
+            hg[u] = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[u][k] = 0;
+            if (mine[u]) {
+                e[u] = load_entry<R>(Lw, i, v[u]);
+                hg[u] = part_of<R>(v[u][0], P);
             }
         }
-        if (!dense) {
-#pragma unroll
-            for (int u = 0; u < kRoundU; u++)
-                if (mine[u]) c[u] = load_record<R>(rec, e[u], v[u]);
-        }
-        // DeleteEdge on the non-hinge vertices of every edge (issued together)
+        // DeleteEdge on every vertex but the entry's first (issued together)
         unsigned long long old[kRoundU][R - 1];
 #pragma unroll
         for (int u = 0; u < kRoundU; u++) {
-            const uint32_t h = c[u] & 3u;
             const unsigned long long sub = 0ull - (((unsigned long long)e[u] << 32) | one);
 #pragma unroll
-            for (int k = 0; k < R - 1; k++) {
-                old[u][k] = 0;
-                if (mine[u]) {
-                    // k-th non-hinge position is k or k + 1 (static indices keep v in registers)
-                    const uint32_t x = (uint32_t)k >= h ? v[u][k + 1] : v[u][k];
-                    old[u][k] = atomicAdd(st + x, sub);
-                }
-            }
+            for (int k = 0; k < R - 1; k++)
+                old[u][k] = mine[u] ? atomicAdd(st + v[u][k + 1], sub) : 0ull;
         }
-        // vertices that fell to degree 1 claim their last edge for round t+1
-        bool take[kRoundU][R - 1];
-        uint32_t f[kRoundU][R - 1];
+        // hinge: smallest position among the first vertex and the marked ones
 #pragma unroll
         for (int u = 0; u < kRoundU; u++) {
-            const uint32_t h = c[u] & 3u;
+            uint32_t h = hg[u];
+#pragma unroll
+            for (int k = R - 2; k >= 0; k--) {
+                const uint32_t pos = (uint32_t)k + ((uint32_t)k >= hg[u] ? 1u : 0u);
+                if (((uint32_t)old[u][k] & kMark) && pos < h) h = pos;
+            }
+            if (mine[u] && h != hg[u]) {
+                uint32_t p[4], q[4];
+                unrotate<R>(v[u], hg[u], p);
+                rotate_to<R>(p, h, q);
+                store_entry<R>(Lw, base + (uint64_t)u * 32 + lane, make_entry<R>(q, e[u]));
+                moves++;
+            }
+        }
+        // vertices that fell to degree 1 mark themselves and claim their last
+        // edge for round t+1; the vertex words of that edge come along
+        bool take[kRoundU][R - 1];
+        uint32_t f[kRoundU][R - 1], pf[kRoundU][R - 1][4];
+#pragma unroll
+        for (int u = 0; u < kRoundU; u++) {
 #pragma unroll
             for (int k = 0; k < R - 1; k++) {
                 take[u][k] = false;
                 f[u][k] = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) pf[u][k][q] = 0;
                 if (mine[u] && (uint32_t)old[u][k] == 2u) {
                     cross++;
-                    const uint32_t j = (uint32_t)k + ((uint32_t)k >= h ? 1u : 0u);
+                    const uint32_t j = (uint32_t)k + ((uint32_t)k >= hg[u] ? 1u : 0u);
                     const uint32_t g = (uint32_t)(old[u][k] >> 32) - e[u];  // the edge left
                     if (g < n) {
-                        take[u][k] = atomicMin(claim_ptr<R>(rec, g), ((t + 1) << 2) | j) ==
-                                     kUnclaimed;
+                        const uint32_t tag = ((t + 1) << 2) | j;
+                        const uint32_t c = claim_and_read<R>(rec, g, tag, pf[u][k]);
+                        take[u][k] = c == kUnclaimed;
                         f[u][k] = g;
+                        // a later claimer that lowered the claim marks its
+                        // vertex (never one whose last edge is in L_t: its
+                        // claim holds round t and stays lower)
+                        if (!take[u][k] && tag < c)
+                            atomicOr(reinterpret_cast<unsigned int *>(st + v[u][k + 1]), kMark);
                     } else {
                         raise_err(ctl, kDevBadEdge);
                     }
                 }
             }
-            if (WITH_S && !dense && mine[u]) S[base + (uint64_t)u * 32 + lane] = solve_record(c[u], v[u]);
         }
 #pragma unroll
         for (int u = 0; u < kRoundU; u++)
 #pragma unroll
-            for (int k = 0; k < R - 1; k++) stage.push(take[u][k], f[u][k], &ctl->lcur, Llist);
+            for (int k = 0; k < R - 1; k++) {
+                const uint32_t j = (uint32_t)k + ((uint32_t)k >= hg[u] ? 1u : 0u);
+                uint32_t q[4];
+                rotate_to<R>(pf[u][k], j, q);
+                stage.push(take[u][k], make_entry<R>(q, f[u][k]), &ctl->lcur, Lst);
+            }
     }
-    stage.flush(&ctl->lcur, Llist);
-    close_round(ctl, loff, t, cross, dense, le - lb, max_rounds, active, cond);
+    stage.flush(&ctl->lcur, Lst);
+    close_round(ctl, loff, t, cross, moves, max_rounds, cond);
 }
 
-template <int R, bool WS>
-void *round_fn() { return (void *)k_round<R, WS>; }
+template <int R>
+void *round_fn() { return (void *)k_round<R>; }
 
-RoundLaunch round_launch(const Launch &L, bool with_s, uint32_t r) {
-    RoundLaunch k{};
-    k.grid = grid_fixed(L, 8);
-    k.block = kThreads;
-    if (with_s)
-        k.fn = round_fn<3, true>();  // solve records exist for the r = 3 MPHF only
-    else
-        k.fn = r == 2 ? round_fn<2, false>() : (r == 3 ? round_fn<3, false>() : round_fn<4, false>());
-    return k;
+RoundLaunch round_launch(const Launch &L, uint32_t r) {
+    return staged_launch(L, r == 2 ? round_fn<2>() : (r == 3 ? round_fn<3>() : round_fn<4>()),
+                         HPEEL_ROUND_STAGE_BYTES);
 }
 
-void launch_round(const Launch &L, bool with_s, uint32_t r, const RoundParams *prm) {
-    const unsigned grid = grid_fixed(L, 8);
+void launch_round(const Launch &L, uint32_t r, const RoundParams *prm) {
+    const RoundLaunch k = round_launch(L, r);
     const cudaGraphConditionalHandle c0 = 0;
     count_launch();
-    if (with_s) {
-        k_round<3, true><<<grid, kThreads, 0, L.stream>>>(prm, c0);
-        return;
-    }
     switch (r) {
-    case 2: k_round<2, false><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
-    case 3: k_round<3, false><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
-    case 4: k_round<4, false><<<grid, kThreads, 0, L.stream>>>(prm, c0); break;
+    case 2: k_round<2><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
+    case 3: k_round<3><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
+    case 4: k_round<4><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
     }
 }
 
