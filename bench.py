@@ -93,8 +93,8 @@ def byte_model(step, n, m, st):
 NCU_TRAFFIC = {
     # step: (source file, sha256 prefix, bytes per unit)
     # rounds: k_round0 + k_round of one build at n = 3e7 (host round loop),
-    # 12.62 GB of DRAM traffic for 3e7 peeled edges; profiles/rounds_n3e7_dram.md
-    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "3c03faf2e871eceb", 420.82),
+    # 10.70 GB of DRAM traffic for 3e7 peeled edges; profiles/rounds_n3e7_dram.md
+    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "c48562a64aac5f8e", 356.51),
 }
 
 
