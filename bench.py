@@ -61,6 +61,10 @@ def byte_model(step, n, m, st):
         return {"units": n, "word": w, "sector": w}
     if step == "hash_edges":
         return {"units": n, "word": 24 * n, "sector": 24 * n}
+    if step == "records_bucket":
+        # edge rows read, edge record write, r incidences written to the buckets
+        w = (4 * R + 16 + R * 8) * n
+        return {"units": n, "word": w, "sector": w}
     if step == "fill":
         return {"units": m, "word": 8 * m, "sector": 8 * m}
     if step == "build_incidence":
@@ -224,6 +228,65 @@ def lookup_leg(keys, G, D, m, seed):
             "bits_per_key": hp.mphf_bits_per_key(n, GAMMA_MILLI)}
 
 
+PEEL_N = 10**9
+
+
+def peel_leg(n, steps, warmup):
+    """Plain peel at scale (hpeel_peel, the peel of configs C2): n = 1e9 edges,
+    r = 3, gamma = 1.23, edges device-resident (hashed from SplitMix64 keys,
+    seed 1, hash seed 1), canonical order + claim words + layer offsets out.
+    Reported as peeled edges/s and as the sector-model bytes of its steps
+    against the measured HBM peak."""
+    import numpy as np
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    m = hp.num_vertices(n, GAMMA_MILLI, R)
+    keys = torch.from_numpy(inputs.keys(n, KEY_SEED).view(np.int64)).cuda()
+    edges = hp.hash_edges(keys, m, R, HASH_SEED)
+    del keys
+    torch.cuda.empty_cache()
+    ws = torch.empty(hp.peel_workspace_size(n, m, R), dtype=torch.uint8, device="cuda")
+    res = None
+    for _ in range(max(warmup, 1)):
+        res = hp.peel(edges, m, workspace=ws)
+    torch.cuda.synchronize()
+    hp.profile_reset()
+    hp.profile_enable(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        res = hp.peel(edges, m, workspace=ws)
+    b.record()
+    torch.cuda.synchronize()
+    hp.profile_enable(False)
+    prof = hp.profile_read()
+    ms = a.elapsed_time(b) / steps
+    st = dict(res.stats)
+    sector = word = 0
+    for name, (_, tot) in prof.items():
+        bm = byte_model(name, n, m, st)
+        if bm:
+            sector += bm["sector"]
+            word += bm["word"]
+    peak, peak_kind = measured_peaks()
+    out = {"value": n / ms / 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "n": n, "m": m, "rounds": res.rounds, "n_peeled": res.n_peeled,
+           "steps_ms": {k: v[1] / steps for k, v in sorted(prof.items())},
+           "roofline": {"bound": "hbm", "model": "sector", "achieved": sector / ms / 1e6,
+                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": sector / ms / 1e6 / peak,
+                        "algorithmic_bytes_per_step": sector,
+                        "word_model_gbs": word / ms / 1e6},
+           "config": {"workload": f"plain peel n={n:.0e} r=3 gamma=1.23, edges on the device, "
+                                  "canonical order + claims + layer offsets out"}}
+    del edges, ws, res
+    torch.cuda.empty_cache()
+    return out
+
+
 BATCH_B = 65536
 
 
@@ -384,6 +447,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-serving", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-peel-1e9", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--round-loop", default="graph", choices=["graph", "host"],
                     help="graph: rounds in a CUDA graph (default); host: one launch per round "
                          "(same kernels; for profilers that cannot see inside the graph)")
@@ -552,6 +616,11 @@ def main():
     if world == 1 and not args.no_serving:
         serving = serving_leg()
     lookup = lookup_leg(keys, G, D, m, res.stats["seed_used"])
+    peel_1e9 = None
+    if world == 1 and not args.no_peel_1e9:
+        del keys, ws, order
+        torch.cuda.empty_cache()
+        peel_1e9 = peel_leg(PEEL_N, steps=3, warmup=1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -569,7 +638,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": aggregate_medges(n, world, e2e_ms), "unit": UNIT,
-                "h2d_bytes_per_step": keys.numel() * 8,
+                "h2d_bytes_per_step": n * 8,
                 "d2h_bytes_per_step": (G.numel() + D.numel()) * 8, "ms_per_step": e2e_ms,
                 "copies": "pinned host buffers, second stream, next step's keys copied "
                           "during the current step"},
@@ -577,6 +646,7 @@ def main():
         "batched": batched,
         "serving": serving,
         "lookup": lookup,
+        "peel_1e9": peel_1e9,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -49,8 +49,11 @@ __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
         atomicCAS(&ctl->err, 0u, (uint32_t)kDevBuildOverflow);
 }
 
+#ifndef HPEEL_RB_MIN_BLOCKS
+#define HPEEL_RB_MIN_BLOCKS 3
+#endif
 template <int R, bool FROM_KEYS>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, HPEEL_RB_MIN_BLOCKS)
 k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ rows,
                    uint32_t n, FastMod fm, uint64_t seed, BucketGeom g, uint4 *__restrict__ rec,
                    uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov,
@@ -68,7 +71,36 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 
     for (uint32_t c = threadIdx.x; c < C; c += kThreads) cur[c] = 0;
     const uint64_t tiles = ((uint64_t)n + kTileEdges - 1) / kTileEdges;
+    // the next tile's input (keys, or rows) is loaded while this one is
+    // hashed, sorted and written
+    constexpr int kWords = FROM_KEYS ? 2 : R;  // 32-bit words of input per edge
+    auto load_input = [&](uint64_t tile, uint32_t (&in)[4][kWords]) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint64_t e = tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x;
+#pragma unroll
+            for (int w = 0; w < kWords; w++) in[q][w] = 0;
+            if (e < n) {
+                if (FROM_KEYS) {
+                    const uint64_t k = __ldcs(keys + e);
+                    in[q][0] = (uint32_t)k;
+                    in[q][kWords - 1] = (uint32_t)(k >> 32);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < kWords; j++) in[q][j] = __ldcs(rows + e * R + j);
+                }
+            }
+        }
+    };
+    uint32_t next_in[4][kWords];
+    if ((uint64_t)blockIdx.x < tiles) load_input(blockIdx.x, next_in);
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        uint32_t in[4][kWords];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int w = 0; w < kWords; w++) in[q][w] = next_in[q][w];
+        if (tile + gridDim.x < tiles) load_input(tile + gridDim.x, next_in);
         for (uint32_t c = threadIdx.x; c < C; c += kThreads) hist[c] = 0;
         __syncthreads();
         uint32_t vv[4][R], rank[4][R];
@@ -80,7 +112,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             bool ok = e < n;
             if (ok) {
                 if (FROM_KEYS) {
-                    const uint64_t k = __ldcs(keys + e);
+                    const uint64_t k = ((uint64_t)in[q][kWords - 1] << 32) | in[q][0];
 #pragma unroll
                     for (int j = 0; j < R; j++)
                         v[j] = (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) +
@@ -88,7 +120,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                 } else {
 #pragma unroll
                     for (int j = 0; j < R; j++) {
-                        v[j] = __ldcs(rows + e * R + j);
+                        v[j] = in[q][j];
                         ok &= (v[j] - (uint32_t)j * g.P) < g.P;
                     }
                     if (!ok) raise_err(ctl, kDevBadVertex);
@@ -155,14 +187,18 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 // Refine: the pairs of each chunk (all its regions) are counting-sorted in
 // shared memory, a tile of kRefineTile slots at a time, into 2^(shift -
 // sub_shift) sub-buckets of 2^sub_shift vertices; each tile's run of a
-// sub-bucket is appended to it with one atomicAdd on its cursor.
+// sub-bucket is appended to it with one atomicAdd on its cursor.  One
+// resident wave of blocks strides over all (chunk, tile) items; the next
+// item's pairs are loaded into registers while the current one is sorted
+// and written, so the load latency overlaps the work.
 constexpr int kRefineItems = 16;
 constexpr uint32_t kRefineTile = kThreads * kRefineItems;  // 4096 slots
 
 __global__ void __launch_bounds__(kThreads)
 k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ fill, BucketGeom g,
-                 uint32_t regions, uint32_t sub_shift, uint2 *__restrict__ pairs2,
-                 uint32_t *__restrict__ fill2, uint32_t cap2, Overflow ov, Ctl *ctl) {
+                 uint32_t chunks, uint32_t regions, uint32_t sub_shift,
+                 uint2 *__restrict__ pairs2, uint32_t *__restrict__ fill2, uint32_t cap2,
+                 Overflow ov, Ctl *ctl) {
     extern __shared__ uint32_t smem[];
     const uint32_t S = 1u << (g.shift - sub_shift);
     uint32_t *hist = smem;          // S
@@ -172,35 +208,57 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
     uint2 *stage = reinterpret_cast<uint2 *>(sb + kRefineTile);
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t span = (uint64_t)regions * g.cap;
-    const uint32_t c = blockIdx.y;  // one grid row per chunk
-    const uint32_t part = c / g.chunks_per_part;
-    const uint32_t base_v = part * g.P + (c % g.chunks_per_part) * (1u << g.shift);
-    const uint2 *src = pairs + (uint64_t)c * span;
-    const uint32_t *f = fill + (size_t)c * regions;
     // tiles never straddle regions: region reg has ceil(cap / kRefineTile)
     // tiles, of which those below its fill hold pairs
     const uint32_t tpr = (g.cap + kRefineTile - 1) / kRefineTile;
     const uint32_t tiles = regions * tpr;
-    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint64_t items = (uint64_t)chunks * tiles;
+    // pairs in item `it` (0 past the fill of its region); block-uniform
+    auto item_len = [&](uint64_t it) -> uint32_t {
+        const uint32_t c = (uint32_t)(it / tiles), tile = (uint32_t)(it - (uint64_t)c * tiles);
         const uint32_t reg = tile / tpr, t0 = (tile - reg * tpr) * kRefineTile;
-        const uint32_t cnt = min(__ldg(f + reg), g.cap);
-        if (t0 >= cnt) continue;  // block-uniform: nothing in this tile
-        const uint2 *tsrc = src + (uint64_t)reg * g.cap + t0;
-        const uint32_t tn = min(cnt - t0, kRefineTile);
+        const uint32_t cnt = min(__ldg(fill + (size_t)c * regions + reg), g.cap);
+        return t0 < cnt ? min(cnt - t0, kRefineTile) : 0u;
+    };
+    auto next_item = [&](uint64_t it) -> uint64_t {
+        do it += gridDim.x;
+        while (it < items && item_len(it) == 0);
+        return it;
+    };
+    auto load_item = [&](uint64_t it, uint2 (&p)[kRefineItems]) {
+        const uint32_t c = (uint32_t)(it / tiles), tile = (uint32_t)(it - (uint64_t)c * tiles);
+        const uint32_t reg = tile / tpr, t0 = (tile - reg * tpr) * kRefineTile;
+        const uint32_t tn = item_len(it);
+        const uint2 *tsrc = pairs + (uint64_t)c * span + (uint64_t)reg * g.cap + t0;
+#pragma unroll
+        for (int q = 0; q < kRefineItems; q++) {
+            const uint32_t i = (uint32_t)q * kThreads + threadIdx.x;
+            p[q] = i < tn ? __ldcs(tsrc + i) : make_uint2(0u, 0u);
+        }
+    };
+    uint64_t it = blockIdx.x;
+    if (it < items && item_len(it) == 0) it = next_item(it);
+    uint2 pn[kRefineItems];
+    if (it < items) load_item(it, pn);
+    while (it < items) {
+        const uint32_t c = (uint32_t)(it / tiles);
+        const uint32_t part = c / g.chunks_per_part;
+        const uint32_t base_v = part * g.P + (c % g.chunks_per_part) * (1u << g.shift);
+        const uint32_t tn = item_len(it);
+        uint2 p[kRefineItems];
+#pragma unroll
+        for (int q = 0; q < kRefineItems; q++) p[q] = pn[q];
+        const uint64_t nxt = next_item(it);
+        if (nxt < items) load_item(nxt, pn);
         for (uint32_t b = threadIdx.x; b < S; b += kThreads) hist[b] = 0;
         __syncthreads();
-        uint2 p[kRefineItems];
         uint32_t rk[kRefineItems];
         bool ok[kRefineItems];
 #pragma unroll
         for (int q = 0; q < kRefineItems; q++) {
             const uint32_t i = (uint32_t)q * kThreads + threadIdx.x;
             ok[q] = i < tn;
-            rk[q] = 0;
-            if (ok[q]) {
-                p[q] = __ldcs(tsrc + i);
-                rk[q] = atomicAdd(&hist[(p[q].x - base_v) >> sub_shift], 1u);
-            }
+            rk[q] = ok[q] ? atomicAdd(&hist[(p[q].x - base_v) >> sub_shift], 1u) : 0u;
         }
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < S; b += kThreads)
@@ -240,6 +298,7 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
                 overflow_push(stage[k], ov, ctl);
         }
         __syncthreads();
+        it = nxt;
     }
 }
 
@@ -296,7 +355,9 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift, uint3
     b.chunks_per_part = (uint32_t)((P + (1ull << shift) - 1) >> shift);
     b.chunks = r * b.chunks_per_part;
     const uint64_t tiles = (n + kTileEdges - 1) / kTileEdges;
-    b.regions = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)sms * 2));
+    // one region per block of the record pass, which runs one resident wave
+    b.regions = (uint32_t)std::max<uint64_t>(
+        1, std::min<uint64_t>(tiles, (uint64_t)sms * HPEEL_RB_MIN_BLOCKS));
     // a region gets the incidences of one chunk from about n / regions edges
     const double expect = P ? (double)n * (double)(1ull << shift) / (double)P / b.regions : 0.0;
     uint64_t cap = (uint64_t)(expect + 8.0 * std::sqrt(expect + 1.0) + 64.0);
@@ -356,11 +417,13 @@ void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, cons
     const uint32_t S = 1u << (b.shift - b.sub_shift);
     const size_t smem1 = (3 * (size_t)S + kRefineTile) * 4 + (size_t)kRefineTile * 8;
     cudaFuncSetAttribute(k_refine_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
-    const uint64_t tiles = (uint64_t)b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);
-    const unsigned gx = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)L.sms * 2));
+    const uint64_t items =
+        (uint64_t)b.chunks * b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);
+    const unsigned grid = (unsigned)std::min<uint64_t>(
+        std::max<uint64_t>(items, 1), grid_resident(L, (const void *)k_refine_buckets, 8, smem1));
     count_launch();
-    k_refine_buckets<<<dim3(gx, b.chunks), kThreads, smem1, L.stream>>>(
-        pairs, fill, g, b.regions, b.sub_shift, pairs2, fill2, b.cap2, ov, ctl);
+    k_refine_buckets<<<grid, kThreads, smem1, L.stream>>>(
+        pairs, fill, g, b.chunks, b.regions, b.sub_shift, pairs2, fill2, b.cap2, ov, ctl);
     const size_t smem2 = (size_t)8 << b.sub_shift;
     cudaFuncSetAttribute(k_apply_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     count_launch();

@@ -12,7 +12,9 @@
 //              tile), where that tile's edges of that bin start;
 //   scatter -- each warp ranks its 512 inputs in input order (match_any
 //              peers + per-warp running counts), so equal keys keep the
-//              input order: the sort is stable.
+//              input order: the sort is stable.  The tile's ids are staged
+//              in shared memory in (bin, input) order, so each bin's run of
+//              the tile leaves as one contiguous, coalesced stretch.
 #include "kernels.cuh"
 
 namespace hp {
@@ -57,14 +59,18 @@ __global__ void __launch_bounds__(kThreads)
 k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
                const uint32_t *__restrict__ claim, uint32_t base, uint32_t core_key,
                uint32_t nbins, const uint32_t *__restrict__ offs, uint32_t *__restrict__ out) {
-    __shared__ uint32_t wc[kEmitWarps][kEmitBins];
+    __shared__ uint32_t wc[kEmitWarps][kEmitBins];  // per warp and bin: count, then slot
+    __shared__ uint32_t obase[kEmitBins];            // output index of tile slot 0 of the bin
+    __shared__ uint32_t stage[kEmitTile];            // the tile's edge ids, ordered by bin
+    __shared__ uint8_t sbin[kEmitTile];              // bin of each staged id
     const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     for (uint32_t b = lane; b < kEmitBins; b += 32) wc[warp][b] = 0;
     __syncwarp();
     // this warp's contiguous run of the tile, kEmitItems groups of 32
-    const uint64_t w0 = (uint64_t)blockIdx.x * kEmitTile + (uint64_t)warp * 32 * kEmitItems;
+    const uint64_t t0 = (uint64_t)blockIdx.x * kEmitTile;
+    const uint64_t w0 = t0 + (uint64_t)warp * 32 * kEmitItems;
     uint32_t bin[kEmitItems], eid[kEmitItems];
 #pragma unroll
     for (int g = 0; g < kEmitItems; g++) {
@@ -77,28 +83,53 @@ k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
         __syncwarp();
     }
     __syncthreads();
-    // per bin: warps' starts = tile start of the bin + counts of earlier warps
-    for (uint32_t b = threadIdx.x; b < nbins; b += kThreads) {
-        uint32_t run = offs[(uint64_t)b * tiles + blockIdx.x];
+    // bin totals of the tile -> first stage slot of each bin (warp 0 scans),
+    // then each warp's first slot in each bin (earlier warps first: stable)
+    if (warp == 0) {
+        uint32_t run = 0;
+        for (uint32_t b0 = 0; b0 < kEmitBins; b0 += 32) {
+            const uint32_t b = b0 + lane;
+            uint32_t tot = 0;
 #pragma unroll
-        for (int w = 0; w < kEmitWarps; w++) {
-            const uint32_t c = wc[w][b];
-            wc[w][b] = run;
-            run += c;
+            for (int w = 0; w < kEmitWarps; w++) {
+                const uint32_t c = wc[w][b];
+                wc[w][b] = tot;  // exclusive over warps, relative to the bin start
+                tot += c;
+            }
+            uint32_t x = tot;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+                if (lane >= (uint32_t)d) x += y;
+            }
+            const uint32_t start = run + x - tot;
+#pragma unroll
+            for (int w = 0; w < kEmitWarps; w++) wc[w][b] += start;
+            obase[b] = b < nbins ? offs[(uint64_t)b * tiles + blockIdx.x] - start : 0u;
+            run += __shfl_sync(0xFFFFFFFFu, x, 31);
         }
     }
     __syncthreads();
+    // stage the ids in bin order, input order inside a bin
 #pragma unroll
     for (int g = 0; g < kEmitItems; g++) {
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin[g]);
         if (bin[g] != 0xFFFFFFFFu) {
-            out[wc[warp][bin[g]] + __popc(peers & lt)] = eid[g];
+            const uint32_t slot = wc[warp][bin[g]] + __popc(peers & lt);
+            stage[slot] = eid[g];
+            sbin[slot] = (uint8_t)bin[g];
         }
         __syncwarp();
         if (bin[g] != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
             wc[warp][bin[g]] += __popc(peers);
         __syncwarp();
     }
+    __syncthreads();
+    // each bin's run of the tile is one contiguous stretch of the output:
+    // consecutive threads write consecutive addresses
+    const uint64_t left = (uint64_t)count - t0;
+    const uint32_t tn = left < kEmitTile ? (uint32_t)left : kEmitTile;
+    for (uint32_t k = threadIdx.x; k < tn; k += kThreads) out[obase[sbin[k]] + k] = stage[k];
 }
 
 void launch_emit_scatter(const Launch &L, const uint32_t *src, uint32_t count,
