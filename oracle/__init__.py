@@ -74,6 +74,17 @@ def _load():
         lib.orc_mphf_build.restype = ctypes.c_int
         lib.orc_mphf_build.argtypes = [p, u64, u64, u32, u32, p, p,
                                        ctypes.POINTER(u64), ctypes.POINTER(u32)]
+        lib.orc_sf_bits.restype = u32
+        lib.orc_sf_bits.argtypes = [u64]
+        lib.orc_sf_words.restype = u64
+        lib.orc_sf_words.argtypes = [u64, u32]
+        lib.orc_sf_assign.restype = ctypes.c_int
+        lib.orc_sf_assign.argtypes = [p, u64, u64, p, p, p, u32, p, u64, p]
+        lib.orc_sf_lookup.restype = u64
+        lib.orc_sf_lookup.argtypes = [u64, u64, u64, u64, p]
+        lib.orc_sf_build.restype = ctypes.c_int
+        lib.orc_sf_build.argtypes = [p, p, u64, u64, u64, u32, u32, p,
+                                     ctypes.POINTER(u64), ctypes.POINTER(u32)]
         _lib = lib
         return lib
 
@@ -224,3 +235,62 @@ def mphf_build(keys: np.ndarray, seed: int, gamma_milli: int = 1230,
                                 _ptr(d), ctypes.byref(su), ctypes.byref(rounds))
     _check(rc, "mphf_build")
     return MphfResult(G[:(m + 31) // 32], d, su.value, rounds.value, m)
+
+
+# ------------------------------------------------------ static functions --
+
+def sf_bits(sigma: int) -> int:
+    """ceil(log2 sigma): bits per stored value of a static function."""
+    return int(_load().orc_sf_bits(sigma))
+
+
+def sf_words(m: int, sigma: int) -> int:
+    return int(_load().orc_sf_words(m, sf_bits(sigma)))
+
+
+def sf_assign(edges: np.ndarray, m: int, res: PeelResult, values: np.ndarray,
+              sigma: int) -> np.ndarray:
+    """u with u[h0] + u[h1] + u[h2] = f(x) (mod sigma), reverse layer order,
+    ceil(log2 sigma) bits per vertex (sec. 3)."""
+    edges = np.ascontiguousarray(edges, dtype=np.uint32)
+    values = np.ascontiguousarray(values, dtype=np.uint32)
+    n = edges.shape[0]
+    U = np.zeros(max(sf_words(m, sigma), 1), dtype=np.uint64)
+    loff = np.ascontiguousarray(res.layer_off, dtype=np.uint64)
+    _check(_load().orc_sf_assign(_ptr(edges), n, m, _ptr(res.order), _ptr(res.claim),
+                                 _ptr(loff), res.rounds, _ptr(values), sigma, _ptr(U)),
+           "sf_assign")
+    return U[:sf_words(m, sigma)]
+
+
+def sf_lookup(key: int, seed: int, m: int, sigma: int, U: np.ndarray) -> int:
+    """f(key) = (u[h0] + u[h1] + u[h2]) mod sigma (sec. 3)."""
+    U = np.ascontiguousarray(U, dtype=np.uint64)
+    return int(_load().orc_sf_lookup(key, seed, m, sigma, _ptr(U)))
+
+
+@dataclass
+class SfResult:
+    U: np.ndarray
+    seed_used: int
+    rounds: int
+    m: int
+    bits: int
+
+
+def sf_build(keys: np.ndarray, values: np.ndarray, sigma: int, seed: int = 1,
+             gamma_milli: int = 1230, max_tries: int = 8) -> SfResult:
+    """Static function f(keys[i]) = values[i] in [0, sigma), with
+    reseed-and-retry on a non-empty core (sec. 3)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    values = np.ascontiguousarray(values, dtype=np.uint32)
+    n = keys.shape[0]
+    m = num_vertices(n, gamma_milli, 3)
+    U = np.zeros(max(sf_words(m, sigma), 1), dtype=np.uint64)
+    su = ctypes.c_uint64(0)
+    rounds = ctypes.c_uint32(0)
+    rc = _load().orc_sf_build(_ptr(keys), _ptr(values), n, sigma, seed, gamma_milli, max_tries,
+                              _ptr(U), ctypes.byref(su), ctypes.byref(rounds))
+    _check(rc, "sf_build")
+    return SfResult(U[:sf_words(m, sigma)], su.value, rounds.value, m, sf_bits(sigma))
+

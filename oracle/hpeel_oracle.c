@@ -27,7 +27,12 @@
  *    edges last in ascending id;
  *  - g encoding: 2 bits per vertex; an assigned value 0 is stored as 3 so
  *    that "assigned" is "non-zero" for the rank structure; unassigned = 0;
- *  - rank directory: one cumulative 64-bit count per 512 vertices.
+ *  - rank directory: one cumulative 64-bit count per 512 vertices;
+ *  - static functions (sec. 3, f: S -> [sigma]): 2 <= sigma <= 2^32,
+ *    b = ceil(log2 sigma) bits per vertex, u[v] at bits [v b, (v + 1) b) of
+ *    one bit string (bit i = bit i mod 64 of word i / 64), values stored as
+ *    they are (no "0 as 3" code: a static function needs no rank), vertices
+ *    never a hinge hold 0, a value >= sigma is an input error.
  *
  * Parity status: every function here is pinned by tests against closed
  * forms, published test vectors, brute force or independent invariants.
@@ -633,6 +638,153 @@ int orc_mphf_build(const uint64_t *keys, uint64_t n, uint64_t seed,
         if (rounds_out)
             *rounds_out = rounds;
         rc = ORC_OK;
+        break;
+    }
+out:
+    free(edges);
+    free(order);
+    free(claim);
+    free(loff);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Static functions (sec. 3): any f: S -> [sigma] is stored as an array u  */
+/* of gamma n values in [sigma] with f(x) = u[h0(x)] + u[h1(x)] + u[h2(x)] */
+/* mod sigma, ceil(log2 sigma) bits per value.  The MPHF above is the case */
+/* sigma = 3 with f(x) = hinge position (plus its "0 stored as 3" code).   */
+/* ---------------------------------------------------------------------- */
+
+/* ceil(log2 sigma): bits per stored value (sigma >= 2). */
+uint32_t orc_sf_bits(uint64_t sigma)
+{
+    uint32_t b = 0;
+    while (b < 64 && (1ull << b) < sigma)
+        b++;
+    return b;
+}
+
+/* u[v] occupies bits [v b, (v + 1) b) of the bit string U, bit i of the
+ * string being bit (i mod 64) of word i / 64; read and written one bit at a
+ * time. */
+static uint64_t u_get(const uint64_t *U, uint64_t v, uint32_t b)
+{
+    uint64_t x = 0;
+    for (uint32_t i = 0; i < b; i++) {
+        uint64_t bit = v * b + i;
+        x |= ((U[bit >> 6] >> (bit & 63)) & 1u) << i;
+    }
+    return x;
+}
+
+static void u_put(uint64_t *U, uint64_t v, uint32_t b, uint64_t x)
+{
+    for (uint32_t i = 0; i < b; i++) {
+        uint64_t bit = v * b + i;
+        uint64_t mask = 1ull << (bit & 63);
+        if ((x >> i) & 1u)
+            U[bit >> 6] |= mask;
+        else
+            U[bit >> 6] &= ~mask;
+    }
+}
+
+/* Words of the bit string for m values of b bits. */
+uint64_t orc_sf_words(uint64_t m, uint32_t b)
+{
+    return (m * b + 63) / 64;
+}
+
+/* Solve u[h0] + u[h1] + u[h2] = values[e] (mod sigma) for every peeled edge
+ * e (r = 3), layers from the last to the first: the hinge vertex of e is
+ * the only one of e not fixed yet, so it takes (values[e] - the other two)
+ * mod sigma; vertices never a hinge keep 0.  values[e] >= sigma is an
+ * error (ORC_EINVAL). */
+int orc_sf_assign(const uint32_t *edges, uint64_t n, uint64_t m, const uint32_t *order,
+                  const uint32_t *claim, const uint64_t *layer_off, uint32_t rounds,
+                  const uint32_t *values, uint64_t sigma, uint64_t *U)
+{
+    (void)n;
+    if (sigma < 2 || sigma > (1ull << 32))
+        return ORC_EINVAL;
+    uint32_t b = orc_sf_bits(sigma);
+    memset(U, 0, orc_sf_words(m, b) * sizeof(uint64_t));
+    for (int64_t t = (int64_t)rounds - 1; t >= 0; t--) {
+        for (uint64_t q = layer_off[t]; q < layer_off[t + 1]; q++) {
+            uint32_t e = order[q];
+            if (claim[e] == ORC_UNCLAIMED)
+                return ORC_EINTERNAL;
+            uint32_t h = claim[e] & 3u;
+            if (values[e] >= sigma)
+                return ORC_EINVAL;
+            uint64_t other = 0;
+            for (uint32_t j = 0; j < 3; j++)
+                if (j != h)
+                    other += u_get(U, edges[(uint64_t)e * 3 + j], b);
+            uint64_t val = ((uint64_t)values[e] + sigma - other % sigma) % sigma;
+            u_put(U, edges[(uint64_t)e * 3 + h], b, val);
+        }
+    }
+    return ORC_OK;
+}
+
+/* f(key) = (u[h0] + u[h1] + u[h2]) mod sigma. */
+uint64_t orc_sf_lookup(uint64_t key, uint64_t seed, uint64_t m, uint64_t sigma,
+                       const uint64_t *U)
+{
+    uint64_t P = m / 3;
+    uint32_t b = orc_sf_bits(sigma);
+    uint64_t s = 0;
+    for (uint32_t j = 0; j < 3; j++) {
+        uint64_t v = orc_mix64(key ^ (seed + j)) % P + (uint64_t)j * P;
+        s += u_get(U, v, b);
+    }
+    return s % sigma;
+}
+
+/* Whole static-function build (sec. 3): hash with seed, seed + 1, ... until
+ * the graph peels completely (at most max_tries seeds), then assign.
+ * U has orc_sf_words(m, ceil(log2 sigma)) words. */
+int orc_sf_build(const uint64_t *keys, const uint32_t *values, uint64_t n, uint64_t sigma,
+                 uint64_t seed, uint32_t gamma_milli, uint32_t max_tries, uint64_t *U,
+                 uint64_t *seed_used, uint32_t *rounds_out)
+{
+    uint64_t m = orc_num_vertices(n, gamma_milli, 3);
+    if (m >= (1ull << 32) || n >= (1ull << 32) || sigma < 2 || sigma > (1ull << 32))
+        return ORC_EINVAL;
+    int rc = ORC_ERETRIES;
+    uint32_t *edges = malloc((n * 3 + 1) * sizeof(uint32_t));
+    uint32_t *order = malloc((n + 1) * sizeof(uint32_t));
+    uint32_t *claim = malloc((n + 1) * sizeof(uint32_t));
+    uint64_t max_layers = n + 1;
+    uint64_t *loff = malloc((max_layers + 1) * sizeof(uint64_t));
+    if (!edges || !order || !claim || !loff) {
+        rc = ORC_ENOMEM;
+        goto out;
+    }
+    for (uint32_t a = 0; a < max_tries; a++) {
+        uint64_t s = seed + a;
+        int e1 = orc_hash_edges(keys, n, m, 3, s, edges);
+        if (e1) {
+            rc = e1;
+            goto out;
+        }
+        uint32_t rounds = 0;
+        uint64_t peeled = 0;
+        int e2 = orc_peel_rounds(edges, n, m, 3, order, claim, loff, max_layers,
+                                 &rounds, &peeled);
+        if (e2) {
+            rc = e2;
+            goto out;
+        }
+        if (peeled < n)
+            continue;
+        rc = orc_sf_assign(edges, n, m, order, claim, loff, rounds, values, sigma, U);
+        if (rc == ORC_OK) {
+            *seed_used = s;
+            if (rounds_out)
+                *rounds_out = rounds;
+        }
         break;
     }
 out:

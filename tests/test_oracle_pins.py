@@ -426,3 +426,84 @@ def test_rank_dir_blocks():
     for b in range(blocks):
         want[b + 1] = want[b] + int(nz[b * 512:(b + 1) * 512].sum())
     assert np.array_equal(res.dir.astype(np.int64), want)
+
+
+# ------------------------------------------------------- static functions --
+# sec. 3: f: S -> [sigma] stored as u with f(x) = u[h0] + u[h1] + u[h2] mod
+# sigma, ceil(log2 sigma) bits per value.
+
+def _decode_u(U: np.ndarray, m: int, b: int) -> np.ndarray:
+    """u[v] from the bit string: bits [v b, (v + 1) b), bit i = bit i % 64 of
+    word i // 64 (numpy, independent of the oracle's C code)."""
+    bits = np.unpackbits(U.view(np.uint8), bitorder="little")[: m * b]
+    bits = bits.reshape(m, b).astype(np.uint64)
+    return (bits << np.arange(b, dtype=np.uint64)).sum(axis=1)
+
+
+@pytest.mark.parametrize("sigma", [2, 3, 4, 5, 31, 32, 33, 255, 256, 257, 2**16 + 1,
+                                   2**31, 2**31 + 1, 2**32 - 1, 2**32])
+def test_sf_bits_closed_form(sigma):
+    assert oracle.sf_bits(sigma) == (sigma - 1).bit_length() == math.ceil(math.log2(sigma))
+
+
+def _values(n, sigma, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, sigma, n, dtype=np.uint64).astype(np.uint32)
+
+
+@pytest.mark.parametrize("n,sigma", [(1, 2), (7, 3), (500, 2), (2000, 5), (2000, 100),
+                                     (3000, 2**13 - 1), (1500, 2**31 + 11), (1200, 2**32)])
+def test_sf_every_key_maps_to_its_value(n, sigma):
+    keys = inputs.keys(n, 40 + n % 7)
+    vals = _values(n, sigma, n)
+    r = oracle.sf_build(keys, vals, sigma, seed=1, max_tries=64)
+    assert r.bits == (sigma - 1).bit_length()
+    assert r.U.shape[0] == (r.m * r.bits + 63) // 64
+    for k, v in zip(keys, vals):
+        assert oracle.sf_lookup(int(k), r.seed_used, r.m, sigma, r.U) == int(v)
+
+
+@pytest.mark.parametrize("sigma", [3, 7, 1000, 2**20 + 3])
+def test_sf_solves_the_linear_system_from_the_edge_rows(sigma):
+    # decode u independently and check every equation of the system on the
+    # edge rows (no hashing in the check); only hinges are non-zero
+    n = 4000
+    keys = inputs.keys(n, 77)
+    vals = _values(n, sigma, 5)
+    r = oracle.sf_build(keys, vals, sigma, seed=1, max_tries=64)
+    edges = oracle.hash_edges(keys, r.m, 3, r.seed_used).astype(np.int64)
+    u = _decode_u(r.U, r.m, r.bits)
+    assert (u < sigma).all()
+    lhs = (u[edges[:, 0]] + u[edges[:, 1]] + u[edges[:, 2]]) % np.uint64(sigma)
+    assert np.array_equal(lhs, vals.astype(np.uint64))
+    res = oracle.peel_rounds(edges.astype(np.uint32), r.m)
+    hinge_v = edges[np.arange(n), (res.claim & 3).astype(np.int64)]
+    nonhinge = np.ones(r.m, dtype=bool)
+    nonhinge[hinge_v] = False
+    assert (u[nonhinge] == 0).all()
+    assert len(np.unique(hinge_v)) == n  # each edge its own hinge
+
+
+def test_sf_sigma3_with_hinge_values_is_the_mphf_g():
+    # sec. 3: the MPHF is the static function x -> hinge position with
+    # sigma = 3; its g differs only in storing an assigned 0 as 3
+    n = 20000
+    keys = inputs.keys(n, 9)
+    mp = oracle.mphf_build(keys, seed=1, max_tries=32)
+    edges = oracle.hash_edges(keys, mp.m, 3, mp.seed_used)
+    res = oracle.peel_rounds(edges, mp.m)
+    hinges = (res.claim & 3).astype(np.uint32)
+    u = _decode_u(oracle.sf_assign(edges, mp.m, res, hinges, 3), mp.m, 2)
+    g = _decode_u(mp.G, mp.m, 2)
+    assert np.array_equal(u, g % 3)
+    assert np.array_equal(u != 0, (g != 0) & (g != 3))
+
+
+def test_sf_rejects_a_value_outside_sigma():
+    keys = inputs.keys(300, 2)
+    vals = _values(300, 10, 1)
+    vals[123] = 10
+    with pytest.raises(RuntimeError, match="code 1"):
+        oracle.sf_build(keys, vals, 10, seed=1, max_tries=64)
+    with pytest.raises(RuntimeError, match="code 1"):
+        oracle.sf_build(keys, vals, 1, seed=1)
