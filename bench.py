@@ -229,6 +229,46 @@ def lookup_leg(keys, G, D, m, seed):
 
 
 PEEL_N = 10**9
+SF_SIGMA = 256
+
+
+def sf_leg(n, steps, warmup):
+    """Static function (sec. 3, f: S -> [sigma]) of the n = 1e8 keys with
+    sigma = 256 (8-bit values, uniform from SplitMix64 stream seed 5):
+    hpeel_sf_build per step, keys and values device-resident; every key is
+    looked up afterwards and must return its value."""
+    import numpy as np
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    keys = torch.from_numpy(inputs.keys(n, KEY_SEED).view(np.int64)).cuda()
+    vals = torch.from_numpy((inputs.keys(n, 5) % np.uint64(SF_SIGMA)).astype(np.uint32)
+                            .view(np.int32)).cuda()
+    ws = torch.empty(hp.sf_workspace_size(n, GAMMA_MILLI), dtype=torch.uint8, device="cuda")
+    res = None
+    for _ in range(max(warmup, 1)):
+        res = hp.sf_build(keys, vals, SF_SIGMA, HASH_SEED, GAMMA_MILLI, workspace=ws)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        res = hp.sf_build(keys, vals, SF_SIGMA, HASH_SEED, GAMMA_MILLI, workspace=ws,
+                          U=res.U)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    out = hp.sf_lookup(keys, res.stats["seed_used"], res.m, SF_SIGMA, res.U)
+    ok = bool(torch.equal(out, vals))
+    r = {"value": n / ms / 1e3, "unit": "Mkeys/s", "ms_per_step": ms, "steps": steps,
+         "sigma": SF_SIGMA, "bits_per_vertex": res.bits,
+         "bits_per_key": res.bits * res.m / n, "every_key_maps_to_its_value": ok,
+         "config": {"workload": f"static function n={n:.0e} sigma={SF_SIGMA} gamma=1.23 "
+                                "(hash, incidence, peel, assignment mod sigma)"}}
+    del keys, vals, ws, res, out
+    torch.cuda.empty_cache()
+    return r
 
 
 def peel_leg(n, steps, warmup):
@@ -448,6 +488,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-serving", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-peel-1e9", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-sf", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--round-loop", default="graph", choices=["graph", "host"],
                     help="graph: rounds in a CUDA graph (default); host: one launch per round "
                          "(same kernels; for profilers that cannot see inside the graph)")
@@ -617,9 +658,12 @@ def main():
         serving = serving_leg()
     lookup = lookup_leg(keys, G, D, m, res.stats["seed_used"])
     peel_1e9 = None
+    sf = None
+    del keys, ws, order
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_sf:
+        sf = sf_leg(n, steps=3, warmup=1)
     if world == 1 and not args.no_peel_1e9:
-        del keys, ws, order
-        torch.cuda.empty_cache()
         peel_1e9 = peel_leg(PEEL_N, steps=3, warmup=1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -647,6 +691,7 @@ def main():
         "serving": serving,
         "lookup": lookup,
         "peel_1e9": peel_1e9,
+        "static_function": sf,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -248,6 +248,50 @@ hpeel_status hpeel_mphf_lookup(const uint64_t *d_keys, uint64_t nq, uint64_t see
                                uint32_t *d_out, void *stream);
 
 /*
+ * Static function (sec. 3): the paper's MWHC construction stores any
+ * f: S -> [sigma], not only the MPHF.  It finds u[0..m) with values in
+ * [0, sigma) such that f(x) = (u[h_0(x)] + u[h_1(x)] + u[h_2(x)]) mod sigma
+ * for every key x (the same r = 3 hashing as hpeel_mphf_build), by peeling
+ * and back-substitution in reverse layer order: the hinge of each peeled
+ * edge takes the value that satisfies that edge's equation.  The MPHF is
+ * the case sigma = 3, f(x) = hinge position.
+ *   b = hpeel_sf_bits(sigma) = ceil(log2 sigma) bits per vertex; u[v] sits at
+ *   bits [v b, (v + 1) b) of one bit string, bit i being bit (i mod 64) of
+ *   word i / 64 (a value may straddle two words); vertices never a hinge
+ *   hold 0.  2 <= sigma <= 2^32.
+ */
+uint32_t hpeel_sf_bits(uint64_t sigma);
+/* uint64 words of u for n keys: ceil(m * b / 64), m = hpeel_num_vertices(n, gamma_milli, 3). */
+uint64_t hpeel_sf_words(uint64_t n, uint32_t gamma_milli, uint64_t sigma);
+/* Workspace bytes hpeel_sf_build needs. */
+size_t hpeel_sf_workspace_size(uint64_t n, uint32_t gamma_milli);
+/*
+ *   d_keys    [n] uint64 keys (distinct, else every seed leaves a 2-core).
+ *   d_values  [n] uint32: f(keys[i]) = d_values[i], each below sigma.
+ *   d_U       [hpeel_sf_words(n, gamma_milli, sigma)] uint64 output.
+ *   seed, gamma_milli, max_tries, h_stats, d_ws, ws_bytes: as for
+ *             hpeel_mphf_build (retries with seed + 1, ... on a 2-core;
+ *             h_stats->seed_used is the seed lookups must use).
+ * Synchronises stream.  Errors: HPEEL_ERR_INVALID_ARG (sigma out of range,
+ * n or m >= 2^32, NULL pointer), HPEEL_ERR_WORKSPACE_TOO_SMALL,
+ * HPEEL_ERR_DEVICE_CHECK (a value >= sigma), HPEEL_ERR_RETRIES_EXHAUSTED,
+ * HPEEL_ERR_CUDA.
+ */
+hpeel_status hpeel_sf_build(const uint64_t *d_keys, const uint32_t *d_values, uint64_t n,
+                            uint64_t sigma, uint64_t seed, uint32_t gamma_milli,
+                            uint32_t max_tries, uint64_t *d_U, hpeel_stats *h_stats,
+                            void *d_ws, size_t ws_bytes, void *stream);
+/*
+ * d_out[q] = f(d_keys[q]) = (u[h_0] + u[h_1] + u[h_2]) mod sigma for the u
+ * built with this seed (h_stats->seed_used), m and sigma.  For a key outside
+ * the built set the result is some value in [0, sigma).  Asynchronous on
+ * stream.  Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_CUDA.
+ */
+hpeel_status hpeel_sf_lookup(const uint64_t *d_keys, uint64_t nq, uint64_t seed, uint64_t m,
+                             uint64_t sigma, const uint64_t *d_U, uint32_t *d_out,
+                             void *stream);
+
+/*
  * Batched peel of many independent bucket hypergraphs (the bucketed layout of
  * sec. 3 "Practical workarounds (HEM)": one small MWHC hypergraph per bucket),
  * r = 3.  Bucket b holds keys d_keys[off[b] .. off[b+1]) (n_b of them, at most

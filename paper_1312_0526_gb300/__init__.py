@@ -120,6 +120,17 @@ def lib():
                                          ctypes.POINTER(BatchTuning), p, sz, p]
         L.hpeel_mphf_lookup.restype = st
         L.hpeel_mphf_lookup.argtypes = [p, u64, u64, u64, p, p, p, p]
+        L.hpeel_sf_bits.restype = u32
+        L.hpeel_sf_bits.argtypes = [u64]
+        L.hpeel_sf_words.restype = u64
+        L.hpeel_sf_words.argtypes = [u64, u32, u64]
+        L.hpeel_sf_workspace_size.restype = sz
+        L.hpeel_sf_workspace_size.argtypes = [u64, u32]
+        L.hpeel_sf_build.restype = st
+        L.hpeel_sf_build.argtypes = [p, p, u64, u64, u64, u32, u32, p, ctypes.POINTER(Stats),
+                                     p, sz, p]
+        L.hpeel_sf_lookup.restype = st
+        L.hpeel_sf_lookup.argtypes = [p, u64, u64, u64, u64, p, p, p]
         L.hpeel_kernel_launches.restype = u64
         L.hpeel_kernel_launches.argtypes = []
         L.hpeel_profile_enable.restype = None
@@ -232,6 +243,60 @@ def mphf_lookup(keys, seed: int, m: int, G, rank_dir, out=None):
     _check(lib().hpeel_mphf_lookup(kp, keys.shape[0], seed, m, _dev_ptr(G, "G", torch.int64),
                                    _dev_ptr(rank_dir, "rank_dir", torch.int64),
                                    _dev_ptr(out, "out", torch.int32), _stream()))
+    return out
+
+
+@dataclass
+class SfResult:
+    U: object     # torch.int64 [hpeel_sf_words]: the b-bit values u, one bit string
+    m: int
+    sigma: int
+    bits: int
+    stats: dict
+
+
+def sf_bits(sigma: int) -> int:
+    """ceil(log2 sigma): bits per vertex of a static function."""
+    return int(lib().hpeel_sf_bits(sigma))
+
+
+def sf_workspace_size(n: int, gamma_milli: int = 1230) -> int:
+    return int(lib().hpeel_sf_workspace_size(n, gamma_milli))
+
+
+def sf_build(keys, values, sigma: int, seed: int = 1, gamma_milli: int = 1230,
+             max_tries: int = 8, workspace=None, U=None) -> SfResult:
+    """Static function f(keys[i]) = values[i] in [0, sigma) (sec. 3); see
+    hpeel_sf_build."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    vp = _dev_ptr(values, "values", torch.int32, 1)
+    n = keys.shape[0]
+    if values.shape[0] != n:
+        raise ValueError("values must hold n entries")
+    dev = keys.device
+    m = num_vertices(n, gamma_milli, 3)
+    words = int(lib().hpeel_sf_words(n, gamma_milli, sigma))
+    if U is None:
+        U = torch.empty(max(words, 1), dtype=torch.int64, device=dev)
+    elif U.numel() < words:
+        raise ValueError("U must hold hpeel_sf_words entries")
+    ws = workspace if workspace is not None else _workspace(sf_workspace_size(n, gamma_milli), dev)
+    st = Stats()
+    _check(lib().hpeel_sf_build(kp, vp, n, sigma, seed, gamma_milli, max_tries,
+                                _dev_ptr(U, "U", torch.int64), ctypes.byref(st),
+                                _dev_ptr(ws, "workspace", torch.uint8), ws.numel(), _stream()))
+    return SfResult(U[:words], m, sigma, sf_bits(sigma), st.as_dict())
+
+
+def sf_lookup(keys, seed: int, m: int, sigma: int, U, out=None):
+    """f of the query keys (hpeel_sf_lookup): int32 [nq] holding uint32 values."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    if out is None:
+        out = torch.empty(keys.shape[0], dtype=torch.int32, device=keys.device)
+    _check(lib().hpeel_sf_lookup(kp, keys.shape[0], seed, m, sigma, _dev_ptr(U, "U", torch.int64),
+                                 _dev_ptr(out, "out", torch.int32), _stream()))
     return out
 
 

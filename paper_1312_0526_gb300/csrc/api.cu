@@ -629,6 +629,114 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
                 (unsigned long long)seed, (unsigned long long)(seed + max_tries - 1));
 }
 
+uint32_t hpeel_sf_bits(uint64_t sigma) {
+    uint32_t b = 0;
+    while (b < 64 && (1ull << b) < sigma) b++;
+    return b;
+}
+
+uint64_t hpeel_sf_words(uint64_t n, uint32_t gamma_milli, uint64_t sigma) {
+    const uint64_t m = hpeel_num_vertices(n, gamma_milli, 3);
+    return (m * hpeel_sf_bits(sigma) + 63) / 64;
+}
+
+size_t hpeel_sf_workspace_size(uint64_t n, uint32_t gamma_milli) {
+    return peel_layout(n, hpeel_num_vertices(n, gamma_milli, 3), 3).total;
+}
+
+hpeel_status hpeel_sf_build(const uint64_t *d_keys, const uint32_t *d_values, uint64_t n,
+                            uint64_t sigma, uint64_t seed, uint32_t gamma_milli,
+                            uint32_t max_tries, uint64_t *d_U, hpeel_stats *h_stats, void *d_ws,
+                            size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (h_stats) memset(h_stats, 0, sizeof *h_stats);
+    if (gamma_milli == 0) return fail(HPEEL_ERR_INVALID_ARG, "gamma_milli must be positive");
+    if (sigma < 2 || sigma > (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "sigma = %llu, need 2 <= sigma <= 2^32",
+                    (unsigned long long)sigma);
+    const uint64_t m = hpeel_num_vertices(n, gamma_milli, 3);
+    if (n >= (1ull << 32) || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    if (max_tries == 0) return fail(HPEEL_ERR_INVALID_ARG, "max_tries must be positive");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    if (n == 0) {
+        if (h_stats) h_stats->seed_used = seed;
+        return HPEEL_OK;
+    }
+    if (!d_keys || !d_values || !d_U || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_ws & 255u) != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const PeelLayout lay = peel_layout(n, m, 3);
+    if (ws_bytes < lay.total)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
+                    lay.total);
+    char *ws = (char *)d_ws;
+    Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
+    const uint32_t b = hpeel_sf_bits(sigma);
+    const uint64_t words = (m * b + 63) / 64;
+    const FastMod fm = make_fastmod(m / 3);
+    for (uint32_t a = 0; a < max_tries; a++) {
+        const uint64_t s = seed + a;
+        PeelOut po{};
+        PeelIO io;
+        io.keys = d_keys;
+        io.seed = s;
+        io.fm = fm;
+        HP_TRY(peel_core(L, io, (uint32_t)n, (uint32_t)m, 3, ws, &po));
+        if (h_stats) {
+            h_stats->attempts = a + 1;
+            h_stats->rounds = po.rounds;
+            h_stats->n_peeled = po.n_peeled;
+            h_stats->core_nonempty = po.n_peeled < n;
+            h_stats->first_layer = po.first_layer;
+            h_stats->frontier = po.frontier;
+            h_stats->hinge_moves = po.moves;
+        }
+        if (po.n_peeled < n) continue;
+        // reverse layer order (sec. 3, sec. 4.3 "Avoiding backward scans")
+        HP_CUDA(cudaMemsetAsync(d_U, 0, 8 * words, L.stream));
+        for (int64_t t = (int64_t)po.rounds - 1; t >= 0; t--) {
+            ProfScope ps(L, "sf_assign");
+            launch_sf_assign_layer(L, po.list, po.loff, (uint32_t)t, d_values, sigma, b, d_U, ctl);
+        }
+        HP_TRY(check_launch("sf_assign"));
+        uint32_t err = 0;
+        HP_CUDA(cudaMemcpyAsync(&err, &ctl->err, sizeof err, cudaMemcpyDeviceToHost, L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        prof_flush();
+        if (err) {
+            if (h_stats) h_stats->device_err = err;
+            return fail(HPEEL_ERR_DEVICE_CHECK, "a value is not below sigma (device code %u)",
+                        err);
+        }
+        if (h_stats) h_stats->seed_used = s;
+        return HPEEL_OK;
+    }
+    return fail(HPEEL_ERR_RETRIES_EXHAUSTED, "2-core non-empty for seeds %llu..%llu",
+                (unsigned long long)seed, (unsigned long long)(seed + max_tries - 1));
+}
+
+hpeel_status hpeel_sf_lookup(const uint64_t *d_keys, uint64_t nq, uint64_t seed, uint64_t m,
+                             uint64_t sigma, const uint64_t *d_U, uint32_t *d_out,
+                             void *stream) {
+    g_last_error.clear();
+    if (nq == 0) return HPEEL_OK;
+    if (m < 3 || m % 3 != 0 || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of 3 below 2^32",
+                    (unsigned long long)m);
+    if (sigma < 2 || sigma > (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "sigma = %llu, need 2 <= sigma <= 2^32",
+                    (unsigned long long)sigma);
+    if (!d_keys || !d_U || !d_out) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    ProfScope ps(L, "sf_lookup");
+    launch_sf_lookup(L, d_keys, nq, make_fastmod(m / 3), seed, sigma, hpeel_sf_bits(sigma), d_U,
+                     d_out);
+    return check_launch("sf_lookup");
+}
+
 hpeel_status hpeel_mphf_lookup(const uint64_t *d_keys, uint64_t nq, uint64_t seed,
                                uint64_t m, const uint64_t *d_G, const uint64_t *d_rank_dir,
                                uint32_t *d_out, void *stream) {

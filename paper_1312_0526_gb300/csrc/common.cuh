@@ -18,6 +18,7 @@ enum : uint32_t {
     kDevTimeout = 4,     // a bounded wait gave up
     kDevBuildOverflow = 5,  // the bucketed build's overflow list was full
     kDevDegree = 6,      // a vertex degree of 2^31 or more (no room for the mark bit)
+    kDevBadValue = 7,    // a static-function value outside [0, sigma)
 };
 
 // Device-side control block of one peel (lives in the workspace).

@@ -152,6 +152,14 @@ void launch_scan_u32(const Launch &L, const uint32_t *in, uint32_t *out, uint64_
 // t = R-1 .. 0).
 void launch_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
                          uint32_t P, uint64_t *G);
+// Static function (sec. 3): assignment of layer t mod sigma, b-bit values;
+// lookup of nq keys.
+void launch_sf_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
+                            const uint32_t *values, uint64_t sigma, uint32_t b, uint64_t *U,
+                            Ctl *ctl);
+void launch_sf_lookup(const Launch &L, const uint64_t *keys, uint64_t nq, FastMod fm,
+                      uint64_t seed, uint64_t sigma, uint32_t b, const uint64_t *U,
+                      uint32_t *out);
 // a9: per-512-vertex counts of non-zero 2-bit values, then the directory.
 void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt);
 void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,

@@ -94,6 +94,88 @@ void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *
                                                                           dir);
 }
 
+// ------------------------------------------------------ static functions --
+// sec. 3: any f: S -> [sigma] is stored as u with f(x) = u[h0] + u[h1] +
+// u[h2] mod sigma, b = ceil(log2 sigma) bits per vertex in one bit string
+// (vertex v at bits [v b, (v + 1) b), bit i in word i / 64): a value may
+// straddle two words, so it is read from one or two words and set with one
+// or two atomicOr.  The MPHF above is the case sigma = 3, f = hinge.
+__device__ __forceinline__ uint64_t u_get(const uint64_t *U, uint32_t v, uint32_t b) {
+    const uint64_t bit = (uint64_t)v * b;
+    const uint64_t w = bit >> 6;
+    const uint32_t sh = (uint32_t)(bit & 63u);
+    uint64_t x = __ldcg(U + w) >> sh;
+    if (sh + b > 64) x |= __ldcg(U + w + 1) << (64 - sh);
+    return x & ((1ull << b) - 1ull);  // b <= 32
+}
+
+__device__ __forceinline__ void u_or(uint64_t *U, uint32_t v, uint32_t b, uint64_t x) {
+    const uint64_t bit = (uint64_t)v * b;
+    const uint64_t w = bit >> 6;
+    const uint32_t sh = (uint32_t)(bit & 63u);
+    atomicOr((unsigned long long *)(U + w), (unsigned long long)(x << sh));
+    if (sh + b > 64) atomicOr((unsigned long long *)(U + w + 1), (unsigned long long)(x >> (64 - sh)));
+}
+
+// Layer t: for each entry {v_hinge, v_a, v_b, e}, u[v_hinge] = (values[e] -
+// u[v_a] - u[v_b]) mod sigma.  Inside one layer no entry reads a value
+// another entry of the layer writes (as for the MPHF), so the layer is one
+// parallel launch.  A value >= sigma raises kDevBadValue.
+__global__ void __launch_bounds__(kThreads)
+k_sf_assign(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, uint32_t t,
+            const uint32_t *__restrict__ values, FastMod fs, uint32_t b, uint64_t *U, Ctl *ctl) {
+    const uint32_t lb = __ldcg(loff + t), le = __ldcg(loff + t + 1);
+    const uint64_t sigma = fs.P;
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t i = lb + (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < le; i += stride) {
+        const uint4 s = __ldcg(Lst + i);
+        const uint32_t f = __ldg(values + s.w);
+        if (f >= sigma) {
+            raise_err(ctl, kDevBadValue);
+            continue;
+        }
+        const uint64_t other = fastmod(u_get(U, s.y, b) + u_get(U, s.z, b), fs);
+        const uint64_t val = fastmod((uint64_t)f + sigma - other, fs);
+        if (val) u_or(U, s.x, b, val);
+    }
+}
+
+void launch_sf_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
+                            const uint32_t *values, uint64_t sigma, uint32_t b, uint64_t *U,
+                            Ctl *ctl) {
+    count_launch();
+    k_sf_assign<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(Lst, loff, t, values,
+                                                            make_fastmod(sigma), b, U, ctl);
+}
+
+// f(key) = (u[h0] + u[h1] + u[h2]) mod sigma.
+__global__ void __launch_bounds__(kThreads)
+k_sf_lookup(const uint64_t *__restrict__ keys, uint64_t nq, FastMod fm, uint64_t seed,
+            FastMod fs, uint32_t b, const uint64_t *__restrict__ U, uint32_t *__restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    const uint32_t P = (uint32_t)fm.P;
+    for (uint64_t q = (uint64_t)blockIdx.x * kThreads + threadIdx.x; q < nq; q += stride) {
+        const uint64_t k = __ldcs(keys + q);
+        uint64_t s = 0;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const uint32_t v =
+                (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) + (uint32_t)j * P;
+            s += u_get(U, v, b);
+        }
+        out[q] = (uint32_t)fastmod(s, fs);
+    }
+}
+
+void launch_sf_lookup(const Launch &L, const uint64_t *keys, uint64_t nq, FastMod fm,
+                      uint64_t seed, uint64_t sigma, uint32_t b, const uint64_t *U,
+                      uint32_t *out) {
+    if (nq == 0) return;
+    count_launch();
+    k_sf_lookup<<<grid_for(L, nq, 1, 8), kThreads, 0, L.stream>>>(keys, nq, fm, seed,
+                                                                  make_fastmod(sigma), b, U, out);
+}
+
 // ---------------------------------------------------------------- lookup --
 // MPHF value of a key (sec. 3 and sec. 5): hash to h_0..h_2, i = (g[h_0] +
 // g[h_1] + g[h_2]) mod 3 (a stored 3 counts as 0), v = h_i, and the value is
