@@ -74,6 +74,11 @@ def _load():
         lib.orc_mphf_build.restype = ctypes.c_int
         lib.orc_mphf_build.argtypes = [p, u64, u64, u32, u32, p, p,
                                        ctypes.POINTER(u64), ctypes.POINTER(u32)]
+        lib.orc_peel_rounds_general.restype = ctypes.c_int
+        lib.orc_peel_rounds_general.argtypes = [p, u64, u64, u32, p, p, p, u64,
+                                                ctypes.POINTER(u32), ctypes.POINTER(u64)]
+        lib.orc_hash_edges_general.restype = ctypes.c_int
+        lib.orc_hash_edges_general.argtypes = [p, u64, u64, u32, u64, p]
         lib.orc_sf_bits.restype = u32
         lib.orc_sf_bits.argtypes = [u64]
         lib.orc_sf_words.restype = u64
@@ -159,6 +164,34 @@ def peel_rounds(edges: np.ndarray, m: int) -> PeelResult:
                                    ctypes.byref(peeled)), "peel_rounds")
     R = rounds.value
     return PeelResult(order[:n], claim[:n], loff[:R + 1].copy(), R, peeled.value)
+
+
+def peel_rounds_general(edges: np.ndarray, m: int) -> PeelResult:
+    """Round-synchronous peel of a general (not r-partite) hypergraph on [0, m):
+    positions are read off the edge rows (sec. 2, sec. 4.2)."""
+    edges = np.ascontiguousarray(edges, dtype=np.uint32)
+    n, r = edges.shape
+    order = np.zeros(max(n, 1), dtype=np.uint32)
+    claim = np.zeros(max(n, 1), dtype=np.uint32)
+    max_layers = min(n + 1, 1 << 24)
+    loff = np.zeros(max_layers + 1, dtype=np.uint64)
+    rounds = ctypes.c_uint32(0)
+    peeled = ctypes.c_uint64(0)
+    _check(_load().orc_peel_rounds_general(_ptr(edges), n, m, r, _ptr(order), _ptr(claim),
+                                           _ptr(loff), max_layers, ctypes.byref(rounds),
+                                           ctypes.byref(peeled)), "peel_rounds_general")
+    R = rounds.value
+    return PeelResult(order[:n], claim[:n], loff[:R + 1].copy(), R, peeled.value)
+
+
+def hash_edges_general(keys: np.ndarray, m: int, r: int, seed: int) -> np.ndarray:
+    """Edges uint32[n, r] of a general hypergraph: vertex j = mix64(k ^ (seed + j)) mod m."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    n = keys.shape[0]
+    edges = np.zeros((n, r), dtype=np.uint32)
+    _check(_load().orc_hash_edges_general(_ptr(keys), n, m, r, seed, _ptr(edges)),
+           "hash_edges_general")
+    return edges
 
 
 def peel_greedy(edges: np.ndarray, m: int):

@@ -28,6 +28,11 @@
  *  - g encoding: 2 bits per vertex; an assigned value 0 is stored as 3 so
  *    that "assigned" is "non-zero" for the rank structure; unassigned = 0;
  *  - rank directory: one cumulative 64-bit count per 512 vertices;
+ *  - general (not r-partite) hypergraphs: vertices in [0, m) in any
+ *    position, a row may repeat a vertex and degrees count occurrences (a
+ *    vertex of degree 1 then occurs once in its only edge); the position of
+ *    a degree-1 vertex in its edge is read off the edge's row, and the hinge
+ *    is again the smallest such position;
  *  - static functions (sec. 3, f: S -> [sigma]): 2 <= sigma <= 2^32,
  *    b = ceil(log2 sigma) bits per vertex, u[v] at bits [v b, (v + 1) b) of
  *    one bit string (bit i = bit i mod 64 of word i / 64), values stored as
@@ -153,11 +158,27 @@ static int cmp_u32(const void *a, const void *b)
  *  *rounds          R, the number of non-empty layers;
  *  *n_peeled        |L_0| + ... + |L_{R-1}|.
  */
-int orc_peel_rounds(const uint32_t *edges, uint64_t n, uint64_t m, uint32_t r,
-                    uint32_t *order, uint32_t *claim, uint64_t *layer_off,
-                    uint64_t max_layers, uint32_t *rounds, uint64_t *n_peeled)
+/* Position of vertex v in the row of edge e: the first j with row[j] == v
+ * (a vertex of degree 1 occurs once in its only edge). */
+static uint32_t row_position(const uint32_t *edges, uint64_t e, uint32_t r, uint32_t v)
 {
-    if (r < 2 || r > ORC_MAX_R || (m % r) != 0 || n >= (1ull << 32))
+    for (uint32_t j = 0; j < r; j++)
+        if (edges[e * r + j] == v)
+            return j;
+    return r;
+}
+
+/* general = 0: r-partite graph, the position of v is its part v / P
+ * (sec. 4.3); general = 1: any r-hypergraph on [0, m) (sec. 2: edges are
+ * r-subsets; rows may repeat a vertex, degrees count occurrences), the
+ * position of v in an edge is read off the edge's row. */
+static int peel_rounds_impl(const uint32_t *edges, uint64_t n, uint64_t m, uint32_t r,
+                            uint32_t *order, uint32_t *claim, uint64_t *layer_off,
+                            uint64_t max_layers, uint32_t *rounds, uint64_t *n_peeled,
+                            int general)
+{
+    if (r < 2 || r > ORC_MAX_R || n >= (1ull << 32) || m == 0 ||
+        (!general && (m % r) != 0))
         return ORC_EINVAL;
     *rounds = 0;
     *n_peeled = 0;
@@ -204,7 +225,11 @@ int orc_peel_rounds(const uint32_t *edges, uint64_t n, uint64_t m, uint32_t r,
                 goto out;
             }
             uint32_t e = x[v];
-            uint32_t j = (uint32_t)(v / P);
+            uint32_t j = general ? row_position(edges, e, r, v) : (uint32_t)(v / P);
+            if (j >= r) { /* cannot happen: v is a vertex of its only edge */
+                rc = ORC_EINTERNAL;
+                goto out;
+            }
             uint32_t tag = (t << 2) | j;
             if (claim[e] == ORC_UNCLAIMED) {
                 claim[e] = tag;
@@ -272,6 +297,38 @@ out:
     free(T);
     free(L);
     return rc;
+}
+
+int orc_peel_rounds(const uint32_t *edges, uint64_t n, uint64_t m, uint32_t r,
+                    uint32_t *order, uint32_t *claim, uint64_t *layer_off,
+                    uint64_t max_layers, uint32_t *rounds, uint64_t *n_peeled)
+{
+    return peel_rounds_impl(edges, n, m, r, order, claim, layer_off, max_layers, rounds,
+                            n_peeled, 0);
+}
+
+/* The same round-synchronous peel for a general (not r-partite) hypergraph
+ * on [0, m): the hinge is the smallest position j of the edge's row whose
+ * vertex has degree 1 in the edge's round. */
+int orc_peel_rounds_general(const uint32_t *edges, uint64_t n, uint64_t m, uint32_t r,
+                            uint32_t *order, uint32_t *claim, uint64_t *layer_off,
+                            uint64_t max_layers, uint32_t *rounds, uint64_t *n_peeled)
+{
+    return peel_rounds_impl(edges, n, m, r, order, claim, layer_off, max_layers, rounds,
+                            n_peeled, 1);
+}
+
+/* Edges of a general r-hypergraph: vertex j of key k is mix64(k ^ (seed +
+ * j)) mod m, any vertex in any position (sec. 3's h_j: S -> [gamma n]). */
+int orc_hash_edges_general(const uint64_t *keys, uint64_t n, uint64_t m, uint32_t r,
+                           uint64_t seed, uint32_t *edges)
+{
+    if (r < 2 || r > ORC_MAX_R || m == 0 || m >= (1ull << 32))
+        return ORC_EINVAL;
+    for (uint64_t i = 0; i < n; i++)
+        for (uint32_t j = 0; j < r; j++)
+            edges[i * r + j] = (uint32_t)(orc_mix64(keys[i] ^ (seed + j)) % m);
+    return ORC_OK;
 }
 
 /* Standard linear-time greedy peel (sec. 1, sec. 3), with the packed

@@ -507,3 +507,76 @@ def test_sf_rejects_a_value_outside_sigma():
         oracle.sf_build(keys, vals, 10, seed=1, max_tries=64)
     with pytest.raises(RuntimeError, match="code 1"):
         oracle.sf_build(keys, vals, 1, seed=1)
+
+
+# ------------------------------------------- general (non-partite) graphs --
+# sec. 2: edges are r-subsets of V with no part structure; a row may repeat a
+# vertex (degrees count occurrences), positions are read off the rows.
+
+def _random_general_graph(rng, n, r, m):
+    return np.array([[rng.randrange(m) for _ in range(r)] for _ in range(n)],
+                    dtype=np.uint32).reshape(n, r)
+
+
+@pytest.mark.parametrize("r", [2, 3, 4])
+def test_general_core_matches_bruteforce_and_greedy(r):
+    rng = random.Random(99 + r)
+    nonempty = 0
+    for trial in range(150):
+        n = rng.randint(1, 11)
+        m = rng.randint(1, 9)
+        edges = _random_general_graph(rng, n, r, m)
+        want_core = _core_bruteforce(edges.tolist(), m)
+        res = oracle.peel_rounds_general(edges, m)
+        assert {int(e) for e in res.order[res.n_peeled:]} == want_core
+        assert {int(e) for e in np.nonzero(res.claim == U)[0]} == want_core
+        _, peeled = oracle.peel_greedy(edges, m)
+        assert {i for i in range(n) if not peeled[i]} == want_core
+        assert oracle.validate(edges, m, res.order, res.n_peeled, res.claim) == 0
+        nonempty += bool(want_core)
+    assert 10 < nonempty < 140
+
+
+def test_general_peel_hand_examples():
+    # (0,0,1), (1,2,3): in round 0 vertices 2 and 3 have degree 1 in edge 1,
+    # smallest position 1; vertex 0 occurs twice (degree 2) and vertex 1 is
+    # in both edges.  Deleting edge 1 leaves vertex 1 of degree 1 at position
+    # 2 of edge 0: round 1, hinge 2.
+    e = np.array([[0, 0, 1], [1, 2, 3]], dtype=np.uint32)
+    res = oracle.peel_rounds_general(e, 4)
+    assert res.order.tolist() == [1, 0]
+    assert res.claim.tolist() == [(1 << 2) | 2, (0 << 2) | 1]
+    assert res.layer_off.tolist() == [0, 1, 2]
+    # a row repeating one vertex three times is a 2-core by itself
+    e = np.array([[5, 5, 5], [1, 2, 5]], dtype=np.uint32)
+    res = oracle.peel_rounds_general(e, 7)
+    assert res.n_peeled == 1 and res.order.tolist() == [1, 0]
+    assert res.claim.tolist() == [U, (0 << 2) | 0]
+    # m need not be a multiple of r.  (0,1,2), (2,3,4): both edges peel in
+    # round 0; vertex 2 has degree 2, so edge 1's smallest degree-1 position
+    # is 1 (vertex 3) while edge 0's is 0 (vertex 0)
+    e = np.array([[0, 1, 2], [2, 3, 4]], dtype=np.uint32)
+    res = oracle.peel_rounds_general(e, 5)
+    assert res.order.tolist() == [0, 1] and res.claim.tolist() == [0, 1]
+
+
+def test_general_peel_of_a_partite_graph_is_the_partite_peel():
+    # in an r-partite graph the row position of a vertex is its part
+    for n, r, g in ((50_000, 3, 1230), (20_000, 4, 1300), (30_000, 3, 1200)):
+        m = oracle.num_vertices(n, g, r)
+        edges = oracle.hash_edges(inputs.keys(n, 4), m, r, 1)
+        a = oracle.peel_rounds(edges, m)
+        b = oracle.peel_rounds_general(edges, m)
+        assert np.array_equal(a.order, b.order) and np.array_equal(a.claim, b.claim)
+        assert np.array_equal(a.layer_off, b.layer_off)
+
+
+def test_general_peel_is_invariant_under_vertex_relabelling():
+    n, m = 40_000, 49_200
+    edges = oracle.hash_edges_general(inputs.keys(n, 6), m, 3, 1)
+    assert (edges < m).all() and len(np.unique(edges[:, 0])) < n  # no parts: any vertex anywhere
+    a = oracle.peel_rounds_general(edges, m)
+    perm = np.random.default_rng(3).permutation(m).astype(np.uint32)
+    b = oracle.peel_rounds_general(perm[edges], m)
+    assert np.array_equal(a.order, b.order) and np.array_equal(a.claim, b.claim)
+    assert oracle.validate(edges, m, a.order, a.n_peeled, a.claim) == 0
