@@ -177,7 +177,8 @@ static int peel_rounds_impl(const uint32_t *edges, uint64_t n, uint64_t m, uint3
                             uint64_t max_layers, uint32_t *rounds, uint64_t *n_peeled,
                             int general)
 {
-    if (r < 2 || r > ORC_MAX_R || n >= (1ull << 32) || m == 0 ||
+    /* n = 0 is the empty graph, whatever m (an empty bucket has m = 0) */
+    if (r < 2 || r > ORC_MAX_R || n >= (1ull << 32) || (n > 0 && m == 0) ||
         (!general && (m % r) != 0))
         return ORC_EINVAL;
     *rounds = 0;

@@ -580,3 +580,10 @@ def test_general_peel_is_invariant_under_vertex_relabelling():
     b = oracle.peel_rounds_general(perm[edges], m)
     assert np.array_equal(a.order, b.order) and np.array_equal(a.claim, b.claim)
     assert oracle.validate(edges, m, a.order, a.n_peeled, a.claim) == 0
+
+
+def test_empty_graph_with_no_vertices():
+    # an empty bucket: n = 0 edges on m = 0 vertices is the empty graph
+    for peel in (oracle.peel_rounds, oracle.peel_rounds_general):
+        res = peel(np.zeros((0, 3), dtype=np.uint32), 0)
+        assert res.rounds == 0 and res.n_peeled == 0 and res.layer_off.tolist() == [0]
