@@ -165,6 +165,28 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m,
                         void *stream);
 
 /*
+ * Round-synchronous peel of a general r-hypergraph: the same call as
+ * hpeel_peel without the r-partite structure (sec. 2: an edge is any
+ * r-subset of the vertex set; sec. 3's hash functions h_j map into all of
+ * [gamma n]).
+ *   d_edges  [n][r] uint32, every vertex below m, in any position; a row may
+ *            repeat a vertex (its degree counts occurrences, so such a vertex
+ *            can only leave with its edge through another vertex).
+ *   The position of a degree-1 vertex in its edge is read off the edge's
+ *   row; the hinge is again the smallest such position, so d_claim holds
+ *   (round << 2) | position in the row.  m is any positive value below 2^32.
+ *   n < 2^30 (the layer list keeps the hinge position in the top two bits of
+ *   an edge id).  Other arguments, results and errors: as hpeel_peel, with
+ *   HPEEL_ERR_DEVICE_CHECK for a vertex >= m.
+ */
+size_t hpeel_peel_general_workspace_size(uint64_t n, uint64_t m, uint32_t r);
+hpeel_status hpeel_peel_general(const uint32_t *d_edges, uint64_t n, uint64_t m,
+                                uint32_t r, uint32_t *d_order, uint32_t *d_claim,
+                                uint64_t *d_layer_off, uint32_t max_layers,
+                                hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
+                                void *stream);
+
+/*
  * hpeel_peel without any allocation.  The paper has no counterpart: this is
  * a calling convenience of this library.
  *

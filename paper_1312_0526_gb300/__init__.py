@@ -120,6 +120,11 @@ def lib():
                                          ctypes.POINTER(BatchTuning), p, sz, p]
         L.hpeel_mphf_lookup.restype = st
         L.hpeel_mphf_lookup.argtypes = [p, u64, u64, u64, p, p, p, p]
+        L.hpeel_peel_general_workspace_size.restype = sz
+        L.hpeel_peel_general_workspace_size.argtypes = [u64, u64, u32]
+        L.hpeel_peel_general.restype = st
+        L.hpeel_peel_general.argtypes = [p, u64, u64, u32, p, p, p, u32, ctypes.POINTER(Stats),
+                                         p, sz, p]
         L.hpeel_sf_bits.restype = u32
         L.hpeel_sf_bits.argtypes = [u64]
         L.hpeel_sf_words.restype = u64
@@ -208,12 +213,16 @@ class PeelResult:
         return self.n_peeled < self.order.shape[0]
 
 
-def peel_workspace_size(n: int, m: int, r: int = 3) -> int:
+def peel_workspace_size(n: int, m: int, r: int = 3, general: bool = False) -> int:
+    if general:
+        return int(lib().hpeel_peel_general_workspace_size(n, m, r))
     return int(lib().hpeel_peel_workspace_size(n, m, r))
 
 
-def peel(edges, m: int, workspace=None, max_layers: int = 4096) -> PeelResult:
-    """Round-synchronous peel with canonical order (sec. 4.2); see hpeel_peel."""
+def peel(edges, m: int, workspace=None, max_layers: int = 4096,
+         general: bool = False) -> PeelResult:
+    """Round-synchronous peel with canonical order (sec. 4.2); see hpeel_peel,
+    or hpeel_peel_general for a general (not r-partite) hypergraph."""
     torch = _torch()
     ep = _dev_ptr(edges, "edges", torch.int32, 2)
     n, r = edges.shape
@@ -221,13 +230,14 @@ def peel(edges, m: int, workspace=None, max_layers: int = 4096) -> PeelResult:
     order = torch.empty(n, dtype=torch.int32, device=dev)
     claim = torch.empty(n, dtype=torch.int32, device=dev)
     loff = torch.empty(max_layers + 1, dtype=torch.int64, device=dev)
-    need = peel_workspace_size(n, m, r)
+    need = peel_workspace_size(n, m, r, general)
     ws = workspace if workspace is not None else _workspace(need, dev)
     wp = _dev_ptr(ws, "workspace", torch.uint8)
     st = Stats()
-    _check(lib().hpeel_peel(ep, n, m, r, _dev_ptr(order, "order"), _dev_ptr(claim, "claim"),
-                            _dev_ptr(loff, "layer_off"), max_layers, ctypes.byref(st), wp,
-                            ws.numel(), _stream()))
+    fn = lib().hpeel_peel_general if general else lib().hpeel_peel
+    _check(fn(ep, n, m, r, _dev_ptr(order, "order"), _dev_ptr(claim, "claim"),
+              _dev_ptr(loff, "layer_off"), max_layers, ctypes.byref(st), wp, ws.numel(),
+              _stream()))
     R = int(st.rounds)
     res = PeelResult(order, claim, loff[:R + 1], R, int(st.n_peeled))
     res.stats = st.as_dict()

@@ -65,7 +65,7 @@ hpeel_tuning tuning() {
 // list (one entry per edge, the shape of an edge record), incidence buckets
 // of the L2-blocked build (sharing space with the layer list, which is
 // written only after the build), layer table, order-sort scratch.
-PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r) {
+PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false) {
     PeelLayout p{};
     const hpeel_tuning tu = tuning();
     size_t off = 0;
@@ -77,8 +77,10 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r) {
     p.max_rounds = (uint32_t)std::min<uint64_t>(HPEEL_MAX_ROUNDS, n + 1);
     p.bucketed = n > 0 && m >= tu.bucket_min_vertices;
     if (p.bucketed) {
-        p.plan = bucket_plan(n, m, r, tu.bucket_shift, tu.bucket_sub_shift, current_sms());
-        if (p.plan.chunks > 65535) p.bucketed = false;  // one grid row per chunk
+        p.plan = bucket_plan(n, m, r, general ? 1u : r, tu.bucket_shift, tu.bucket_sub_shift,
+                             current_sms());
+        // the bucketing kernel keeps three counters per chunk in shared memory
+        if (p.plan.smem > (200u << 10)) p.bucketed = false;
     }
     p.ctl = take(sizeof(Ctl));
     p.params = take(sizeof(RoundParams));
@@ -145,6 +147,7 @@ struct PeelIO {
     uint32_t *order = nullptr;  // canonical order output (nullptr: not needed)
     uint32_t *claim = nullptr;  // claim-word output (nullptr: workspace)
     bool force_direct = false;  // update the vertex records directly (no buckets)
+    bool general = false;       // a general (not r-partite) hypergraph on [0, m)
 };
 
 // Executable graphs of the round loop, cached by their parameters: round 0,
@@ -222,11 +225,11 @@ hpeel_status build_round_graph(const RoundLaunch &k0, const RoundLaunch &k1,
     return HPEEL_OK;
 }
 
-hpeel_status launch_round_graph(const Launch &L, uint32_t r, const RoundParams *prm) {
+hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool gen, const RoundParams *prm) {
     int dev = 0;
     HP_CUDA(cudaGetDevice(&dev));
-    const RoundLaunch k0 = round0_launch(L, r);
-    const RoundLaunch k1 = round_launch(L, r);
+    const RoundLaunch k0 = round0_launch(L, r, gen);
+    const RoundLaunch k1 = round_launch(L, r, gen);
     char keybuf[160];
     snprintf(keybuf, sizeof keybuf, "%d|%p|%p|%p|%u|%u", dev, k0.fn, k1.fn, (const void *)prm,
              k0.grid, k1.grid);
@@ -261,7 +264,7 @@ hpeel_status launch_round_graph(const Launch &L, uint32_t r, const RoundParams *
 // hctl: host memory the control block is read back into after every round.
 hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_t m, uint32_t r,
                           char *ws, PeelOut *out, Ctl *hctl) {
-    const PeelLayout lay = peel_layout(n, m, r);
+    const PeelLayout lay = peel_layout(n, m, r, io.general);
     const hpeel_tuning tu = tuning();
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
     uint4 *rec = reinterpret_cast<uint4 *>(ws + lay.rec);
@@ -271,7 +274,8 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     uint32_t *loff = reinterpret_cast<uint32_t *>(ws + lay.loff);
     uint32_t *hist = reinterpret_cast<uint32_t *>(ws + lay.hist);
     uint32_t *scantmp = reinterpret_cast<uint32_t *>(ws + lay.scantmp);
-    const uint32_t P = m / r;
+    // part size: one part [0, m) for a general graph
+    const uint32_t P = io.general ? m : m / r;
 
     HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), L.stream));
     if (lay.bucketed && !io.force_direct) {
@@ -286,7 +290,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         {
             ProfScope ps(L, io.keys ? "hash_bucket" : "records_bucket");
             launch_build_bucketed(L, lay.plan, io.keys, io.edges, n, r, io.fm, io.seed, P, rec,
-                                  pairs, fill, ov, ctl);
+                                  pairs, fill, ov, ctl, io.general);
         }
         // every vertex record is written by the shared-memory apply
         ProfScope ps(L, "apply_buckets");
@@ -301,7 +305,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
             launch_hash_records(L, io.keys, n, r, io.fm, io.seed, rec);
         } else {
             ProfScope ps(L, "records");
-            launch_records(L, io.edges, n, r, P, rec, ctl);
+            launch_records(L, io.edges, n, r, P, rec, ctl, io.general);
         }
         ProfScope ps(L, "build_incidence");
         launch_build_incidence(L, rec, n, r, m, st, ctl);
@@ -323,7 +327,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         // one launch per round, the control block read back after each
         {
             ProfScope ps(L, "round0");
-            launch_round0(L, r, prm);
+            launch_round0(L, r, io.general, prm);
         }
         HP_TRY(check_launch("round0"));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
@@ -331,7 +335,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         while (hctl->more && !hctl->err) {
             {
                 ProfScope ps(L, "rounds");
-                launch_round(L, r, prm);
+                launch_round(L, r, io.general, prm);
             }
             HP_TRY(check_launch("round"));
             HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
@@ -341,7 +345,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         // round 0 and a CUDA-graph while node around the round kernel: the
         // rounds run back to back on the device, one read-back at the end
         ProfScope ps(L, "rounds");
-        HP_TRY(launch_round_graph(L, r, prm));
+        HP_TRY(launch_round_graph(L, r, io.general, prm));
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
         count_launch(hctl->round + (hctl->more ? 1 : 0));
@@ -499,8 +503,14 @@ size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r) {
     return peel_layout(n, m, r).total;
 }
 
-hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
-                        uint32_t *d_order, uint32_t *d_claim, uint64_t *d_layer_off,
+}  // extern "C"
+
+namespace {
+
+// hpeel_peel and hpeel_peel_general: the same path, positions from the parts
+// of an r-partite graph or from the rows of a general one.
+hpeel_status peel_entry(bool general, const uint32_t *d_edges, uint64_t n, uint64_t m,
+                        uint32_t r, uint32_t *d_order, uint32_t *d_claim, uint64_t *d_layer_off,
                         uint32_t max_layers, hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
                         void *stream) {
     g_last_error.clear();
@@ -508,6 +518,8 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
     if (r < 2 || r > 4) return fail(HPEEL_ERR_INVALID_ARG, "r = %u, need 2 <= r <= 4", r);
     if (n >= (1ull << 32) || m >= (1ull << 32))
         return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    if (general && n >= (1ull << 30))
+        return fail(HPEEL_ERR_INVALID_ARG, "a general hypergraph needs n < 2^30");
     Launch L;
     HP_TRY(make_launch(stream, &L));
     if (n == 0) {
@@ -515,13 +527,14 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
         HP_CUDA(cudaStreamSynchronize(L.stream));
         return HPEEL_OK;
     }
-    if (m == 0 || m % r != 0)
-        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of r",
+    if (m == 0 || (!general && m % r != 0))
+        return fail(HPEEL_ERR_INVALID_ARG, general ? "m must be positive"
+                                                   : "m = %llu must be a positive multiple of r",
                     (unsigned long long)m);
     if (!d_edges || !d_order || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
     if (((uintptr_t)d_ws & 255u) != 0)
         return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    const size_t need = peel_layout(n, m, r).total;
+    const size_t need = peel_layout(n, m, r, general).total;
     if (ws_bytes < need)
         return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes, need);
     PeelOut po{};
@@ -529,6 +542,7 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
     io.edges = d_edges;
     io.order = d_order;
     io.claim = d_claim;
+    io.general = general;
     HP_TRY(peel_core(L, io, (uint32_t)n, (uint32_t)m, r, (char *)d_ws, &po));
     if (d_layer_off) {
         if (po.rounds > max_layers)
@@ -547,6 +561,30 @@ hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_
         h_stats->hinge_moves = po.moves;
     }
     return HPEEL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hpeel_status hpeel_peel(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
+                        uint32_t *d_order, uint32_t *d_claim, uint64_t *d_layer_off,
+                        uint32_t max_layers, hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
+                        void *stream) {
+    return peel_entry(false, d_edges, n, m, r, d_order, d_claim, d_layer_off, max_layers, h_stats,
+                      d_ws, ws_bytes, stream);
+}
+
+size_t hpeel_peel_general_workspace_size(uint64_t n, uint64_t m, uint32_t r) {
+    return peel_layout(n, m, r, true).total;
+}
+
+hpeel_status hpeel_peel_general(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
+                                uint32_t *d_order, uint32_t *d_claim, uint64_t *d_layer_off,
+                                uint32_t max_layers, hpeel_stats *h_stats, void *d_ws,
+                                size_t ws_bytes, void *stream) {
+    return peel_entry(true, d_edges, n, m, r, d_order, d_claim, d_layer_off, max_layers, h_stats,
+                      d_ws, ws_bytes, stream);
 }
 
 size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli) {

@@ -34,8 +34,12 @@ struct BucketGeom {
     uint32_t cap;              // region capacity (incidences per chunk and block)
 };
 
+// Chunk of vertex v at position j: chunks never straddle the parts of an
+// r-partite graph; a general graph (GEN) is one part [0, P = m).
+template <bool GEN>
 __device__ __forceinline__ uint32_t chunk_of(uint32_t v, uint32_t j, const BucketGeom &g) {
-    return j * g.chunks_per_part + ((v - j * g.P) >> g.shift);
+    const uint32_t part = GEN ? 0u : j;
+    return part * g.chunks_per_part + ((v - part * g.P) >> g.shift);
 }
 
 // An incidence that finds its region full goes to the overflow list, applied
@@ -52,7 +56,7 @@ __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
 #ifndef HPEEL_RB_MIN_BLOCKS
 #define HPEEL_RB_MIN_BLOCKS 3
 #endif
-template <int R, bool FROM_KEYS>
+template <int R, bool FROM_KEYS, bool GEN>
 __global__ void __launch_bounds__(kThreads, HPEEL_RB_MIN_BLOCKS)
 k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ rows,
                    uint32_t n, FastMod fm, uint64_t seed, BucketGeom g, uint4 *__restrict__ rec,
@@ -60,7 +64,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                    Ctl *ctl) {
     constexpr int kInc = kTileEdges * R;
     extern __shared__ uint32_t smem[];
-    const uint32_t C = R * g.chunks_per_part;
+    const uint32_t C = (GEN ? 1u : (uint32_t)R) * g.chunks_per_part;
     const uint32_t Cp = (C + 1) & ~1u;
     uint32_t *hist = smem;            // C: tile count per chunk
     uint32_t *cur = hist + Cp;        // C: fill of this block's region of each chunk
@@ -121,7 +125,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 #pragma unroll
                     for (int j = 0; j < R; j++) {
                         v[j] = in[q][j];
-                        ok &= (v[j] - (uint32_t)j * g.P) < g.P;
+                        ok &= (v[j] - (GEN ? 0u : (uint32_t)j * g.P)) < g.P;
                     }
                     if (!ok) raise_err(ctl, kDevBadVertex);
                 }
@@ -131,7 +135,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 #pragma unroll
             for (int j = 0; j < R; j++) {
                 vv[q][j] = v[j];
-                rank[q][j] = ok ? atomicAdd(&hist[chunk_of(v[j], j, g)], 1u) : 0u;
+                rank[q][j] = ok ? atomicAdd(&hist[chunk_of<GEN>(v[j], j, g)], 1u) : 0u;
             }
         }
         __syncthreads();
@@ -158,7 +162,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             const uint32_t e = (uint32_t)(tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x);
 #pragma unroll
             for (int j = 0; j < R; j++) {
-                const uint32_t c = chunk_of(vv[q][j], j, g);
+                const uint32_t c = chunk_of<GEN>(vv[q][j], j, g);
                 const uint32_t slot = toff[c] + rank[q][j];
                 stage[slot] = make_uint2(vv[q][j], e);
                 sch[slot] = c;
@@ -347,19 +351,23 @@ __global__ void k_apply_overflow(const uint2 *__restrict__ list, const uint32_t 
     }
 }
 
-BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift, uint32_t sub_shift,
-                       int sms) {
+BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint32_t shift,
+                       uint32_t sub_shift, int sms) {
     BucketPlan b{};
-    const uint64_t P = m / r;
+    const uint64_t P = m / parts;
     b.shift = shift;
     b.chunks_per_part = (uint32_t)((P + (1ull << shift) - 1) >> shift);
-    b.chunks = r * b.chunks_per_part;
+    b.chunks = parts * b.chunks_per_part;
+    // incidences per vertex of a part: one position per part when r-partite,
+    // all r positions in the single part of a general graph
+    const double per = (double)r / (double)parts;
     const uint64_t tiles = (n + kTileEdges - 1) / kTileEdges;
     // one region per block of the record pass, which runs one resident wave
     b.regions = (uint32_t)std::max<uint64_t>(
         1, std::min<uint64_t>(tiles, (uint64_t)sms * HPEEL_RB_MIN_BLOCKS));
     // a region gets the incidences of one chunk from about n / regions edges
-    const double expect = P ? (double)n * (double)(1ull << shift) / (double)P / b.regions : 0.0;
+    const double expect =
+        P ? per * (double)n * (double)(1ull << shift) / (double)P / b.regions : 0.0;
     uint64_t cap = (uint64_t)(expect + 8.0 * std::sqrt(expect + 1.0) + 64.0);
     b.cap = (uint32_t)std::min<uint64_t>(cap, n);
     b.pair_bytes = (uint64_t)b.chunks * b.regions * b.cap * 8;
@@ -370,25 +378,26 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift, uint3
     if (!sub_shift && b.sub_shift > 13) b.sub_shift = 13;
     if (b.sub_shift > shift) b.sub_shift = shift;
     b.subs = b.chunks << (shift - b.sub_shift);
-    const double expect2 = P ? (double)n * (double)(1ull << b.sub_shift) / (double)P : 0.0;
+    const double expect2 = P ? per * (double)n * (double)(1ull << b.sub_shift) / (double)P : 0.0;
     uint64_t cap2 = (uint64_t)(expect2 + 8.0 * std::sqrt(expect2 + 1.0) + 256.0);
     b.cap2 = (uint32_t)std::min<uint64_t>(cap2, n);
     b.pair2_bytes = (uint64_t)b.subs * b.cap2 * 8;
     b.ovf_cap = (uint32_t)std::max<uint64_t>(1u << 16, n / 16);
     b.smem = (size_t)(3 * ((b.chunks + 1) & ~1u)) * 4 + (size_t)kTileEdges * r * (8 + 4);
+    b.parts = parts;
     return b;
 }
 
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           Overflow ov, Ctl *ctl) {
+                           Overflow ov, Ctl *ctl, bool gen) {
     if (n == 0) return;
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
     const unsigned grid = b.regions;  // one bucket region per block and chunk
 #define HP_BK(RR, FK)                                                                         \
     do {                                                                                      \
-        auto kern = k_records_bucketed<RR, FK>;                                               \
+        auto kern = gen ? k_records_bucketed<RR, FK, true> : k_records_bucketed<RR, FK, false>; \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem); \
         count_launch();                                                                       \
         kern<<<grid, kThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, g, rec, pairs,    \

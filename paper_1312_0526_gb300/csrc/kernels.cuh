@@ -64,9 +64,10 @@ void launch_hash_records(const Launch &L, const uint64_t *keys, uint64_t n, uint
 // fill count 32-bit words with value.
 void launch_fill_u32(const Launch &L, uint32_t *p, uint64_t count, uint32_t value);
 
-// Row-major edges -> edge records (checks the r-partite ranges).
+// Row-major edges -> edge records (checks the r-partite ranges; gen: every
+// vertex below P = m).
 void launch_records(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t r, uint32_t P,
-                    uint4 *rec, Ctl *ctl);
+                    uint4 *rec, Ctl *ctl, bool gen);
 
 // a2: vertex records {deg, sum of incident edge ids} from the edge records.
 void launch_build_incidence(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
@@ -87,6 +88,7 @@ struct BucketPlan {
     uint32_t cap2;             // incidences per sub-bucket
     uint64_t pair2_bytes;      // sub-bucket storage
     uint32_t ovf_cap;          // overflow list entries
+    uint32_t parts;            // r (r-partite) or 1 (general graph)
 };
 // Incidences that found their bucket full (applied last).
 struct Overflow {
@@ -94,12 +96,14 @@ struct Overflow {
     uint32_t *count;
     uint32_t cap;
 };
-BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t shift, uint32_t sub_shift,
-                       int sms);
+// parts: r for an r-partite graph (chunks never straddle parts), 1 for a
+// general graph (one part [0, m)).
+BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint32_t shift,
+                       uint32_t sub_shift, int sms);
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           Overflow ov, Ctl *ctl);
+                           Overflow ov, Ctl *ctl, bool gen);
 void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
                           const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
                           unsigned long long *st, Ctl *ctl);
@@ -113,13 +117,14 @@ struct RoundLaunch {
 
 // a3 + a4 of round 0: scan all vertices, claim the edge of every degree-1
 // vertex; publishes loff[0..1].
-void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm);
-RoundLaunch round0_launch(const Launch &L, uint32_t r);
+// gen: a general (not r-partite) hypergraph, positions read off the rows.
+void launch_round0(const Launch &L, uint32_t r, bool gen, const RoundParams *prm);
+RoundLaunch round0_launch(const Launch &L, uint32_t r, bool gen);
 
 // a5 + a4 of the next round + a6: delete layer t (t read on the device),
 // claim and list layer t+1, close the round.
-void launch_round(const Launch &L, uint32_t r, const RoundParams *prm);
-RoundLaunch round_launch(const Launch &L, uint32_t r);
+void launch_round(const Launch &L, uint32_t r, bool gen, const RoundParams *prm);
+RoundLaunch round_launch(const Launch &L, uint32_t r, bool gen);
 
 // claim[e] = claim word of record e.
 void launch_extract_claim(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,

@@ -77,7 +77,8 @@ void launch_fill_u32(const Launch &L, uint32_t *p, uint64_t count, uint32_t valu
 
 // ------------------------------------------------------------ records --
 // Row-major [n][R] edges -> records, with the r-partite check of sec. 4.3.
-template <int R>
+// GEN: a general hypergraph (every vertex below P = m, any position).
+template <int R, bool GEN>
 __global__ void __launch_bounds__(kThreads)
 k_records(const uint32_t *__restrict__ edges, uint32_t n, uint32_t P, uint4 *__restrict__ rec,
           Ctl *ctl) {
@@ -88,7 +89,7 @@ k_records(const uint32_t *__restrict__ edges, uint32_t n, uint32_t P, uint4 *__r
 #pragma unroll
         for (int j = 0; j < R; j++) {
             v[j] = edges[e * R + j];
-            ok &= (v[j] - (uint32_t)j * P) < P;
+            ok &= (v[j] - (GEN ? 0u : (uint32_t)j * P)) < P;
         }
         if (!ok) raise_err(ctl, kDevBadVertex);
         store_record<R>(rec, e, v, ok);
@@ -96,14 +97,19 @@ k_records(const uint32_t *__restrict__ edges, uint32_t n, uint32_t P, uint4 *__r
 }
 
 void launch_records(const Launch &L, const uint32_t *edges, uint32_t n, uint32_t r, uint32_t P,
-                    uint4 *rec, Ctl *ctl) {
+                    uint4 *rec, Ctl *ctl, bool gen) {
     if (n == 0) return;
     const unsigned grid = grid_for(L, n, 1, 8);
+    count_launch();
+#define HP_REC(RR)                                                                           \
+    (gen ? k_records<RR, true><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl)       \
+         : k_records<RR, false><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl))
     switch (r) {
-    case 2: count_launch(); k_records<2><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl); break;
-    case 3: count_launch(); k_records<3><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl); break;
-    case 4: count_launch(); k_records<4><<<grid, kThreads, 0, L.stream>>>(edges, n, P, rec, ctl); break;
+    case 2: HP_REC(2); break;
+    case 3: HP_REC(3); break;
+    case 4: HP_REC(4); break;
     }
+#undef HP_REC
 }
 
 // ---------------------------------------------------------------- build --
@@ -241,15 +247,38 @@ inline RoundLaunch staged_launch(const Launch &L, void *fn, unsigned stage_bytes
 // never taken: a vertex id is below m < 2^32 - 1), so the atomic reaches L2
 // after the load has brought the record's sector in.  Issued independently,
 // the two requests often fetched the same sector from DRAM twice.
-template <int R>
-__device__ __forceinline__ uint32_t claim_and_read(uint4 *rec, uint32_t f, uint32_t tag,
-                                                   uint32_t (&p)[4]) {
+//
+// The claimer's position j goes into the tag (tag_hi | j): in an r-partite
+// graph it is the part of the claiming vertex x (sec. 4.3); in a general
+// graph (GEN) it is x's position in f's row, the first slot holding x (a
+// vertex of degree 1 occurs once in its edge).
+template <int R, bool GEN>
+__device__ __forceinline__ uint32_t claim_and_read(uint4 *rec, uint32_t f, uint32_t tag_hi,
+                                                   uint32_t x, uint32_t P, uint32_t (&p)[4],
+                                                   uint32_t &j) {
     const uint4 q = __ldcg(rec + (R == 4 ? 2 * (uint64_t)f : (uint64_t)f));
     p[0] = q.x;
     p[1] = q.y;
     p[2] = R >= 3 ? q.z : 0u;
     p[3] = R == 4 ? q.w : 0u;
-    return atomicMin(claim_ptr<R>(rec, f) + (q.x == 0xFFFFFFFFu ? 1 : 0), tag);
+    if (GEN) {
+        j = 0;
+#pragma unroll
+        for (int k = R - 1; k >= 1; k--) j = p[k] == x ? (uint32_t)k : j;
+        j = p[0] == x ? 0u : j;
+    } else {
+        j = part_of<R>(x, P);
+    }
+    return atomicMin(claim_ptr<R>(rec, f) + (q.x == 0xFFFFFFFFu ? 1 : 0), tag_hi | j);
+}
+
+// The edge id field of a list entry: for a general graph it also keeps the
+// hinge position in its two top bits (edge ids below 2^30).
+constexpr uint32_t kGenPosShift = 30;
+constexpr uint32_t kGenIdMask = (1u << kGenPosShift) - 1u;
+template <bool GEN>
+__device__ __forceinline__ uint32_t entry_id(uint32_t e, uint32_t h) {
+    return GEN ? e | (h << kGenPosShift) : e;
 }
 
 // ---------------------------------------------------------------- round 0 --
@@ -262,7 +291,7 @@ __device__ __forceinline__ uint32_t claim_and_read(uint4 *rec, uint32_t f, uint3
 constexpr int kR0Items = 4;
 constexpr int kR0Queue = 32 * (kR0Items + 1);  // queued vertices per warp
 
-template <int R>
+template <int R, bool GEN>
 __device__ __forceinline__ void round0_claims(int batches, const uint2 *q, uint32_t lane_limit,
                                               unsigned long long *st, uint4 *rec, uint32_t P,
                                               WarpStage<Entry<R>, stage_cap<R, HPEEL_ROUND0_STAGE_BYTES>()> &stage,
@@ -283,8 +312,8 @@ __device__ __forceinline__ void round0_claims(int batches, const uint2 *q, uint3
             have[b] = slot < lane_limit;
             if (have[b]) {
                 const uint2 it = q[slot];  // {vertex, edge}
-                const uint32_t j = part_of<R>(it.x, P);
-                const uint32_t c = claim_and_read<R>(rec, it.y, j, pv[b]);
+                uint32_t j;
+                const uint32_t c = claim_and_read<R, GEN>(rec, it.y, 0u, it.x, P, pv[b], j);
                 first[b] = c == kUnclaimed;
                 // a later claimer that lowered the claim marks its vertex;
                 // this kernel is the record's only writer
@@ -299,12 +328,12 @@ __device__ __forceinline__ void round0_claims(int batches, const uint2 *q, uint3
         if (b < batches) {
             uint32_t x[4];
             rotate_to<R>(pv[b], jv[b], x);
-            stage.push(first[b], make_entry<R>(x, ev[b]), &ctl->lcur, Lst);
+            stage.push(first[b], make_entry<R>(x, entry_id<GEN>(ev[b], jv[b])), &ctl->lcur, Lst);
         }
     }
 }
 
-template <int R>
+template <int R, bool GEN>
 __global__ void __launch_bounds__(kThreads)
 k_round0(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
     unsigned long long *__restrict__ st = prm->st;
@@ -345,7 +374,7 @@ k_round0(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
         __syncwarp();
         const int full = (int)(qn >> 5);  // < kR0Items + 1 batches
         if (full) {
-            round0_claims<R>(full, q, (uint32_t)full * 32u, st, rec, P, stage, ctl, Lst);
+            round0_claims<R, GEN>(full, q, (uint32_t)full * 32u, st, rec, P, stage, ctl, Lst);
             // move the partial batch to the front
             const uint32_t rest = qn - (uint32_t)full * 32u;
             uint2 keep = make_uint2(0u, 0u);
@@ -356,7 +385,7 @@ k_round0(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
             __syncwarp();
         }
     }
-    if (qn) round0_claims<R>(1, q, qn, st, rec, P, stage, ctl, Lst);
+    if (qn) round0_claims<R, GEN>(1, q, qn, st, rec, P, stage, ctl, Lst);
     stage.flush(&ctl->lcur, Lst);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -380,22 +409,20 @@ k_round0(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
 }
 
 template <int R>
-void *round0_fn() { return (void *)k_round0<R>; }
+void *round0_fn(bool gen) { return gen ? (void *)k_round0<R, true> : (void *)k_round0<R, false>; }
 
-RoundLaunch round0_launch(const Launch &L, uint32_t r) {
-    return staged_launch(L, r == 2 ? round0_fn<2>() : (r == 3 ? round0_fn<3>() : round0_fn<4>()),
-                         HPEEL_ROUND0_STAGE_BYTES);
+RoundLaunch round0_launch(const Launch &L, uint32_t r, bool gen) {
+    return staged_launch(
+        L, r == 2 ? round0_fn<2>(gen) : (r == 3 ? round0_fn<3>(gen) : round0_fn<4>(gen)),
+        HPEEL_ROUND0_STAGE_BYTES);
 }
 
-void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm) {
-    const RoundLaunch k = round0_launch(L, r);
-    const cudaGraphConditionalHandle c0 = 0;
+void launch_round0(const Launch &L, uint32_t r, bool gen, const RoundParams *prm) {
+    const RoundLaunch k = round0_launch(L, r, gen);
+    cudaGraphConditionalHandle c0 = 0;
+    void *args[] = {(void *)&prm, &c0};
     count_launch();
-    switch (r) {
-    case 2: k_round0<2><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
-    case 3: k_round0<3><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
-    case 4: k_round0<4><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
-    }
+    cudaLaunchKernel(k.fn, dim3(k.grid), dim3(k.block), args, k.smem, L.stream);
 }
 
 // ---------------------------------------------------------------- rounds --
@@ -410,7 +437,7 @@ void launch_round0(const Launch &L, uint32_t r, const RoundParams *prm) {
 template <int R>
 constexpr int round_u() { return R == 4 ? 2 : HPEEL_ROUND_U; }
 
-template <int R>
+template <int R, bool GEN>
 __global__ void __launch_bounds__(kThreads)
 k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
     constexpr int kRoundU = round_u<R>();
@@ -453,8 +480,9 @@ k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
 #pragma unroll
             for (int k = 0; k < 4; k++) v[u][k] = 0;
             if (mine[u]) {
-                e[u] = load_entry<R>(Lw, i, v[u]);
-                hg[u] = part_of<R>(v[u][0], P);
+                const uint32_t w = load_entry<R>(Lw, i, v[u]);
+                e[u] = GEN ? w & kGenIdMask : w;
+                hg[u] = GEN ? w >> kGenPosShift : part_of<R>(v[u][0], P);
             }
         }
         // DeleteEdge on every vertex but the entry's first (issued together)
@@ -479,29 +507,34 @@ k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
                 uint32_t p[4], q[4];
                 unrotate<R>(v[u], hg[u], p);
                 rotate_to<R>(p, h, q);
-                store_entry<R>(Lw, base + (uint64_t)u * 32 + lane, make_entry<R>(q, e[u]));
+                store_entry<R>(Lw, base + (uint64_t)u * 32 + lane,
+                               make_entry<R>(q, entry_id<GEN>(e[u], h)));
                 moves++;
             }
         }
         // vertices that fell to degree 1 mark themselves and claim their last
         // edge for round t+1; the vertex words of that edge come along
         bool take[kRoundU][R - 1];
-        uint32_t f[kRoundU][R - 1], pf[kRoundU][R - 1][4];
+        uint32_t f[kRoundU][R - 1], pf[kRoundU][R - 1][4], jf[kRoundU][R - 1];
 #pragma unroll
         for (int u = 0; u < kRoundU; u++) {
 #pragma unroll
             for (int k = 0; k < R - 1; k++) {
                 take[u][k] = false;
                 f[u][k] = 0;
+                jf[u][k] = 0;
 #pragma unroll
                 for (int q = 0; q < 4; q++) pf[u][k][q] = 0;
                 if (mine[u] && (uint32_t)old[u][k] == 2u) {
                     cross++;
-                    const uint32_t j = (uint32_t)k + ((uint32_t)k >= hg[u] ? 1u : 0u);
                     const uint32_t g = (uint32_t)(old[u][k] >> 32) - e[u];  // the edge left
                     if (g < n) {
-                        const uint32_t tag = ((t + 1) << 2) | j;
-                        const uint32_t c = claim_and_read<R>(rec, g, tag, pf[u][k]);
+                        const uint32_t tag_hi = (t + 1) << 2;
+                        uint32_t j;
+                        const uint32_t c =
+                            claim_and_read<R, GEN>(rec, g, tag_hi, v[u][k + 1], P, pf[u][k], j);
+                        const uint32_t tag = tag_hi | j;
+                        jf[u][k] = j;
                         take[u][k] = c == kUnclaimed;
                         f[u][k] = g;
                         // a later claimer that lowered the claim marks its
@@ -519,10 +552,10 @@ k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
         for (int u = 0; u < kRoundU; u++)
 #pragma unroll
             for (int k = 0; k < R - 1; k++) {
-                const uint32_t j = (uint32_t)k + ((uint32_t)k >= hg[u] ? 1u : 0u);
                 uint32_t q[4];
-                rotate_to<R>(pf[u][k], j, q);
-                stage.push(take[u][k], make_entry<R>(q, f[u][k]), &ctl->lcur, Lst);
+                rotate_to<R>(pf[u][k], jf[u][k], q);
+                stage.push(take[u][k], make_entry<R>(q, entry_id<GEN>(f[u][k], jf[u][k])),
+                           &ctl->lcur, Lst);
             }
     }
     stage.flush(&ctl->lcur, Lst);
@@ -530,22 +563,20 @@ k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
 }
 
 template <int R>
-void *round_fn() { return (void *)k_round<R>; }
+void *round_fn(bool gen) { return gen ? (void *)k_round<R, true> : (void *)k_round<R, false>; }
 
-RoundLaunch round_launch(const Launch &L, uint32_t r) {
-    return staged_launch(L, r == 2 ? round_fn<2>() : (r == 3 ? round_fn<3>() : round_fn<4>()),
-                         HPEEL_ROUND_STAGE_BYTES);
+RoundLaunch round_launch(const Launch &L, uint32_t r, bool gen) {
+    return staged_launch(
+        L, r == 2 ? round_fn<2>(gen) : (r == 3 ? round_fn<3>(gen) : round_fn<4>(gen)),
+        HPEEL_ROUND_STAGE_BYTES);
 }
 
-void launch_round(const Launch &L, uint32_t r, const RoundParams *prm) {
-    const RoundLaunch k = round_launch(L, r);
-    const cudaGraphConditionalHandle c0 = 0;
+void launch_round(const Launch &L, uint32_t r, bool gen, const RoundParams *prm) {
+    const RoundLaunch k = round_launch(L, r, gen);
+    cudaGraphConditionalHandle c0 = 0;
+    void *args[] = {(void *)&prm, &c0};
     count_launch();
-    switch (r) {
-    case 2: k_round<2><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
-    case 3: k_round<3><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
-    case 4: k_round<4><<<k.grid, k.block, k.smem, L.stream>>>(prm, c0); break;
-    }
+    cudaLaunchKernel(k.fn, dim3(k.grid), dim3(k.block), args, k.smem, L.stream);
 }
 
 // --------------------------------------------------------------- claims --
