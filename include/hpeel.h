@@ -230,7 +230,10 @@ size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli);
  * (sec. 3 ranking structure, sec. 5 broadword counting).  If the hypergraph
  * keeps a 2-core, the build is retried with hash seed seed+1, seed+2, ...
  * (at most max_tries seeds in total).
- *   d_keys    [n] uint64, distinct keys (duplicates can never peel).
+ *   d_keys    [n] uint64, distinct keys (duplicates can never peel), in
+ *             device memory or in pinned host memory (cudaHostAlloc,
+ *             cudaMallocHost or cudaHostRegister), which the hashing kernel
+ *             reads in place over the host link (read again on a retry).
  *   d_G       [ceil(m/32)] uint64 output: 2 bits per vertex, vertex v at bits
  *             2(v mod 32), 2(v mod 32)+1 of word v/32; 0 = unassigned,
  *             1, 2 = g, 3 = g value 0 of an assigned (hinge) vertex.
@@ -290,6 +293,8 @@ size_t hpeel_sf_workspace_size(uint64_t n, uint32_t gamma_milli);
 /*
  *   d_keys    [n] uint64 keys (distinct, else every seed leaves a 2-core).
  *   d_values  [n] uint32: f(keys[i]) = d_values[i], each below sigma.
+ *             Keys and values may be in pinned host memory (read in place,
+ *             as for hpeel_mphf_build).
  *   d_U       [hpeel_sf_words(n, gamma_milli, sigma)] uint64 output.
  *   seed, gamma_milli, max_tries, h_stats, d_ws, ws_bytes: as for
  *             hpeel_mphf_build (retries with seed + 1, ... on a 2-core;

@@ -158,10 +158,13 @@ def _torch():
     return torch
 
 
-def _dev_ptr(t, name, dtype=None, ndim=None):
+def _dev_ptr(t, name, dtype=None, ndim=None, host_ok=False):
+    """Address of a contiguous CUDA tensor (or, with host_ok, of a tensor in
+    pinned host memory, which the kernels read in place over the host link)."""
     torch = _torch()
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise ValueError(f"{name} must be a CUDA tensor" +
+                         (" or a pinned host tensor" if host_ok else ""))
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
@@ -279,12 +282,12 @@ def sf_build(keys, values, sigma: int, seed: int = 1, gamma_milli: int = 1230,
     """Static function f(keys[i]) = values[i] in [0, sigma) (sec. 3); see
     hpeel_sf_build."""
     torch = _torch()
-    kp = _dev_ptr(keys, "keys", torch.int64, 1)
-    vp = _dev_ptr(values, "values", torch.int32, 1)
+    kp = _dev_ptr(keys, "keys", torch.int64, 1, host_ok=True)
+    vp = _dev_ptr(values, "values", torch.int32, 1, host_ok=True)
     n = keys.shape[0]
     if values.shape[0] != n:
         raise ValueError("values must hold n entries")
-    dev = keys.device
+    dev = keys.device if keys.is_cuda else torch.device("cuda", torch.cuda.current_device())
     m = num_vertices(n, gamma_milli, 3)
     words = int(lib().hpeel_sf_words(n, gamma_milli, sigma))
     if U is None:
@@ -357,11 +360,12 @@ def mphf_workspace_size(n: int, gamma_milli: int = 1230) -> int:
 
 def mphf_build(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
                workspace=None, G=None, rank_dir=None, order=None) -> MphfResult:
-    """MWHC MPHF build (sec. 3) with reseed-and-retry; see hpeel_mphf_build."""
+    """MWHC MPHF build (sec. 3) with reseed-and-retry; see hpeel_mphf_build.
+    keys: a CUDA tensor, or a pinned host tensor read in place by the GPU."""
     torch = _torch()
-    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    kp = _dev_ptr(keys, "keys", torch.int64, 1, host_ok=True)
     n = keys.shape[0]
-    dev = keys.device
+    dev = keys.device if keys.is_cuda else torch.device("cuda", torch.cuda.current_device())
     m = num_vertices(n, gamma_milli, 3)
     if G is None:
         G = torch.empty(max((m + 31) // 32, 1), dtype=torch.int64, device=dev)

@@ -322,7 +322,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     hp_prm.P = P;
     hp_prm.max_rounds = lay.max_rounds;
     RoundParams *prm = reinterpret_cast<RoundParams *>(ws + lay.params);
-    HP_CUDA(cudaMemcpyAsync(prm, &hp_prm, sizeof hp_prm, cudaMemcpyHostToDevice, L.stream));
+    launch_set_params(L, prm, hp_prm);
     if (tu.host_round_loop) {
         // one launch per round, the control block read back after each
         {

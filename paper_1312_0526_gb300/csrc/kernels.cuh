@@ -117,6 +117,9 @@ struct RoundLaunch {
 
 // a3 + a4 of round 0: scan all vertices, claim the edge of every degree-1
 // vertex; publishes loff[0..1].
+// *dst = v, in stream order.
+void launch_set_params(const Launch &L, RoundParams *dst, const RoundParams &v);
+
 // gen: a general (not r-partite) hypergraph, positions read off the rows.
 void launch_round0(const Launch &L, uint32_t r, bool gen, const RoundParams *prm);
 RoundLaunch round0_launch(const Launch &L, uint32_t r, bool gen);

@@ -75,6 +75,15 @@ void launch_fill_u32(const Launch &L, uint32_t *p, uint64_t count, uint32_t valu
     k_fill_u32<<<grid_for(L, count, 16, 8), kThreads, 0, L.stream>>>(p, count, value);
 }
 
+// Round parameters written by a one-thread kernel (stream-ordered, no copy
+// engine, no pageable host copy, which would synchronise the host).
+__global__ void k_set_params(RoundParams *dst, RoundParams v) { *dst = v; }
+
+void launch_set_params(const Launch &L, RoundParams *dst, const RoundParams &v) {
+    count_launch();
+    k_set_params<<<1, 1, 0, L.stream>>>(dst, v);
+}
+
 // ------------------------------------------------------------ records --
 // Row-major [n][R] edges -> records, with the r-partite check of sec. 4.3.
 // GEN: a general hypergraph (every vertex below P = m, any position).

@@ -346,3 +346,21 @@ def test_mphf_lookup_is_a_bijection_and_matches_oracle(n):
 
 def test_bits_per_key_matches_table_space():
     assert round(hp.mphf_bits_per_key(10**8), 2) == 2.61
+
+
+def test_mphf_and_sf_from_pinned_host_keys_equal_device_keys():
+    # keys (and values) in pinned host memory are read in place by the GPU;
+    # the results are those of the device-resident build
+    n = 300_000
+    kh = torch.from_numpy(inputs.keys(n, 77).view(np.int64)).pin_memory()
+    a = hp.mphf_build(kh.cuda(), seed=1, max_tries=32)
+    b = hp.mphf_build(kh, seed=1, max_tries=32)
+    assert a.stats["seed_used"] == b.stats["seed_used"]
+    assert torch.equal(a.G, b.G) and torch.equal(a.rank_dir, b.rank_dir)
+    vh = torch.from_numpy((inputs.keys(n, 78) % np.uint64(1000)).astype(np.uint32)
+                          .view(np.int32)).pin_memory()
+    c = hp.sf_build(kh.cuda(), vh.cuda(), 1000, seed=1, max_tries=32)
+    d = hp.sf_build(kh, vh, 1000, seed=1, max_tries=32)
+    assert torch.equal(c.U, d.U)
+    with pytest.raises(ValueError):
+        hp.mphf_build(kh.clone(), seed=1)  # pageable host memory is refused
