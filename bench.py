@@ -97,8 +97,8 @@ def byte_model(step, n, m, st):
 NCU_TRAFFIC = {
     # step: (source file, sha256 prefix, bytes per unit)
     # rounds: k_round0 + k_round of one build at n = 3e7 (host round loop),
-    # 10.70 GB of DRAM traffic for 3e7 peeled edges; profiles/rounds_n3e7_dram.md
-    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "c48562a64aac5f8e", 356.51),
+    # 10.71 GB of DRAM traffic for 3e7 peeled edges; profiles/rounds_n3e7_dram.md
+    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "d3e6f35e961fa5db", 357.09),
 }
 
 
