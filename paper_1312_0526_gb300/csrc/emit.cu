@@ -10,8 +10,9 @@
 //              bin-major: hist[b * tiles + tile];
 //   scan    -- one exclusive prefix sum over hist gives, for every (bin,
 //              tile), where that tile's edges of that bin start;
-//   scatter -- each warp ranks its 512 inputs in input order (match_any
-//              peers + per-warp running counts), so equal keys keep the
+//   scatter -- each warp ranks its 512 inputs in input order (the lanes
+//              holding the same bin, found with one ballot per bit of the
+//              bin, plus per-warp running counts), so equal keys keep the
 //              input order: the sort is stable.  The tile's ids are staged
 //              in shared memory in (bin, input) order, so each bin's run of
 //              the tile leaves as one contiguous, coalesced stretch.
@@ -24,6 +25,22 @@ __device__ __forceinline__ uint32_t emit_bin(uint32_t c, uint32_t base, uint32_t
     const uint32_t k = (c == kUnclaimed) ? core_key : (c >> 2);
     const uint32_t d = k - base;  // k >= base for every input of the pass
     return d < nbins - 1 ? d : nbins - 1;
+}
+
+// Lanes of the warp holding the same bin (valid lanes only): one ballot per
+// bit of the bin index (planes = bits of nbins - 1), instead of a match.
+__device__ __forceinline__ uint32_t bin_peers(uint32_t bin, bool valid, int planes) {
+    uint32_t m = __ballot_sync(0xFFFFFFFFu, valid);
+    for (int b = 0; b < planes; b++) {
+        const bool bit = (bin >> b) & 1u;
+        const uint32_t x = __ballot_sync(0xFFFFFFFFu, bit);
+        m &= bit ? x : ~x;
+    }
+    return valid ? m : 0u;
+}
+
+__device__ __forceinline__ int bin_planes(uint32_t nbins) {
+    return nbins > 1 ? 32 - __clz(nbins - 1) : 0;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -71,15 +88,20 @@ k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
     // this warp's contiguous run of the tile, kEmitItems groups of 32
     const uint64_t t0 = (uint64_t)blockIdx.x * kEmitTile;
     const uint64_t w0 = t0 + (uint64_t)warp * 32 * kEmitItems;
-    uint32_t bin[kEmitItems], eid[kEmitItems];
+    uint32_t bin[kEmitItems], eid[kEmitItems], peers[kEmitItems];
+    const int planes = bin_planes(nbins);
 #pragma unroll
     for (int g = 0; g < kEmitItems; g++) {
         const uint64_t i = w0 + (uint64_t)g * 32 + lane;
         const bool valid = i < count;
         eid[g] = valid ? (src ? src[i] : (uint32_t)i) : 0u;
         bin[g] = valid ? emit_bin(claim[eid[g]], base, core_key, nbins) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin[g]);
-        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) wc[warp][bin[g]] += __popc(peers);
+    }
+#pragma unroll
+    for (int g = 0; g < kEmitItems; g++) {
+        const bool valid = bin[g] != 0xFFFFFFFFu;
+        peers[g] = bin_peers(valid ? bin[g] : 0u, valid, planes);
+        if (valid && lane == (uint32_t)(__ffs(peers[g]) - 1)) wc[warp][bin[g]] += __popc(peers[g]);
         __syncwarp();
     }
     __syncthreads();
@@ -113,15 +135,14 @@ k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
     // stage the ids in bin order, input order inside a bin
 #pragma unroll
     for (int g = 0; g < kEmitItems; g++) {
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin[g]);
         if (bin[g] != 0xFFFFFFFFu) {
-            const uint32_t slot = wc[warp][bin[g]] + __popc(peers & lt);
+            const uint32_t slot = wc[warp][bin[g]] + __popc(peers[g] & lt);
             stage[slot] = eid[g];
             sbin[slot] = (uint8_t)bin[g];
         }
         __syncwarp();
-        if (bin[g] != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
-            wc[warp][bin[g]] += __popc(peers);
+        if (bin[g] != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers[g]) - 1))
+            wc[warp][bin[g]] += __popc(peers[g]);
         __syncwarp();
     }
     __syncthreads();
