@@ -271,6 +271,48 @@ def sf_leg(n, steps, warmup):
     return r
 
 
+def general_leg(n, steps, warmup):
+    """Peel of a general (not r-partite) 3-hypergraph (hpeel_peel_general):
+    n = 1e8 edges on m = ceil(1.23 n) vertices, vertex j of key k = mix64(k ^
+    (1 + j)) mod m (any vertex in any position, repeats possible), edges
+    device-resident, canonical order + claims + layer offsets out."""
+    import numpy as np
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    m = (n * GAMMA_MILLI + 999) // 1000
+    keys = torch.from_numpy(inputs.keys(n, KEY_SEED).view(np.int64)).cuda()
+    edges = hp.hash_edges(keys, m, R, HASH_SEED, general=True)
+    del keys
+    ws = torch.empty(hp.peel_workspace_size(n, m, R, general=True), dtype=torch.uint8,
+                     device="cuda")
+    res = None
+    for _ in range(max(warmup, 1)):
+        res = hp.peel(edges, m, workspace=ws, general=True)
+    torch.cuda.synchronize()
+    hp.profile_reset()
+    hp.profile_enable(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        res = hp.peel(edges, m, workspace=ws, general=True)
+    b.record()
+    torch.cuda.synchronize()
+    hp.profile_enable(False)
+    prof = hp.profile_read()
+    ms = a.elapsed_time(b) / steps
+    out = {"value": n / ms / 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps, "n": n,
+           "m": m, "rounds": res.rounds, "n_peeled": res.n_peeled,
+           "steps_ms": {k: v[1] / steps for k, v in sorted(prof.items())},
+           "config": {"workload": f"general 3-hypergraph peel n={n:.0e} m=ceil(1.23 n), "
+                                  "edges on the device"}}
+    del edges, ws, res
+    torch.cuda.empty_cache()
+    return out
+
+
 def peel_leg(n, steps, warmup):
     """Plain peel at scale (hpeel_peel, the peel of configs C2): n = 1e9 edges,
     r = 3, gamma = 1.23, edges device-resident (hashed from SplitMix64 keys,
@@ -489,6 +531,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-peel-1e9", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-sf", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-general", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--round-loop", default="graph", choices=["graph", "host"],
                     help="graph: rounds in a CUDA graph (default); host: one launch per round "
                          "(same kernels; for profilers that cannot see inside the graph)")
@@ -651,6 +694,9 @@ def main():
     torch.cuda.empty_cache()
     if world == 1 and not args.no_sf:
         sf = sf_leg(n, steps=3, warmup=1)
+    general = None
+    if world == 1 and not args.no_general:
+        general = general_leg(n, steps=3, warmup=1)
     if world == 1 and not args.no_peel_1e9:
         peel_1e9 = peel_leg(PEEL_N, steps=3, warmup=1)
     line = {
@@ -681,6 +727,7 @@ def main():
         "lookup": lookup,
         "peel_1e9": peel_1e9,
         "static_function": sf,
+        "general_peel": general,
     }
     print(json.dumps(line), flush=True)
     if dist:

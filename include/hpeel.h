@@ -131,6 +131,13 @@ hpeel_status hpeel_hash_edges(const uint64_t *d_keys, uint64_t n, uint64_t m,
                               uint32_t r, uint64_t seed, uint32_t *d_edges,
                               void *stream);
 
+/* General (not r-partite) form: d_edges[i*r + j] = mix64(key_i ^ (seed + j))
+ * mod m, any vertex in any position (rows may repeat a vertex); 0 < m < 2^32.
+ * For hpeel_peel_general.  Asynchronous on stream.  Errors as above. */
+hpeel_status hpeel_hash_edges_general(const uint64_t *d_keys, uint64_t n, uint64_t m,
+                                      uint32_t r, uint64_t seed, uint32_t *d_edges,
+                                      void *stream);
+
 /* Workspace bytes hpeel_peel needs for (n, m, r). */
 size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r);
 

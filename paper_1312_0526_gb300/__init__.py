@@ -120,6 +120,8 @@ def lib():
                                          ctypes.POINTER(BatchTuning), p, sz, p]
         L.hpeel_mphf_lookup.restype = st
         L.hpeel_mphf_lookup.argtypes = [p, u64, u64, u64, p, p, p, p]
+        L.hpeel_hash_edges_general.restype = st
+        L.hpeel_hash_edges_general.argtypes = [p, u64, u64, u32, u64, p, p]
         L.hpeel_peel_general_workspace_size.restype = sz
         L.hpeel_peel_general_workspace_size.argtypes = [u64, u64, u32]
         L.hpeel_peel_general.restype = st
@@ -189,8 +191,9 @@ def num_vertices(n: int, gamma_milli: int = 1230, r: int = 3) -> int:
     return int(lib().hpeel_num_vertices(n, gamma_milli, r))
 
 
-def hash_edges(keys, m: int, r: int = 3, seed: int = 1, out=None):
-    """Edges int32[n, r] of the keys (sec. 3 hashing, sec. 4.3 r parts)."""
+def hash_edges(keys, m: int, r: int = 3, seed: int = 1, out=None, general: bool = False):
+    """Edges int32[n, r] of the keys (sec. 3 hashing, sec. 4.3 r parts; with
+    general=True every vertex in [0, m), see hpeel_hash_edges_general)."""
     torch = _torch()
     kp = _dev_ptr(keys, "keys", torch.int64, 1)
     n = keys.shape[0]
@@ -199,7 +202,8 @@ def hash_edges(keys, m: int, r: int = 3, seed: int = 1, out=None):
     ep = _dev_ptr(out, "out", torch.int32)
     if out.numel() != n * r:
         raise ValueError("out must hold n * r entries")
-    _check(lib().hpeel_hash_edges(kp, n, m, r, seed, ep, _stream()))
+    fn = lib().hpeel_hash_edges_general if general else lib().hpeel_hash_edges
+    _check(fn(kp, n, m, r, seed, ep, _stream()))
     return out
 
 

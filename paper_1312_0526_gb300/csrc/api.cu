@@ -499,6 +499,25 @@ hpeel_status hpeel_hash_edges(const uint64_t *d_keys, uint64_t n, uint64_t m, ui
     return check_launch("hash_edges");
 }
 
+hpeel_status hpeel_hash_edges_general(const uint64_t *d_keys, uint64_t n, uint64_t m,
+                                      uint32_t r, uint64_t seed, uint32_t *d_edges,
+                                      void *stream) {
+    g_last_error.clear();
+    if (r < 2 || r > 4) return fail(HPEEL_ERR_INVALID_ARG, "r = %u, need 2 <= r <= 4", r);
+    if (n == 0) return HPEEL_OK;
+    if (m == 0 || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be positive and below 2^32",
+                    (unsigned long long)m);
+    if (!d_keys || !d_edges) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    {
+        ProfScope ps(L, "hash_edges");
+        launch_hash_edges(L, d_keys, n, r, make_fastmod(m), seed, d_edges, true);
+    }
+    return check_launch("hash_edges");
+}
+
 size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r) {
     return peel_layout(n, m, r).total;
 }

@@ -3,6 +3,8 @@
 // sec. 3: each key x becomes the edge {h_0(x), ..., h_{r-1}(x)}; sec. 4.3:
 // h_j has codomain [j m/r, (j+1) m/r), so the r vertices of an edge are
 // distinct.  Here h_j(x) = (mix64(x ^ (seed + j)) mod P) + j P, P = m / r.
+// For a general hypergraph every h_j maps into all of [0, m) (sec. 3's
+// h_j: S -> [gamma n]): the same kernel with P = m and no part offset.
 #include "kernels.cuh"
 
 namespace hp {
@@ -10,13 +12,14 @@ namespace hp {
 // One key per thread: 8-byte coalesced key loads; the r ids of an edge are
 // staged in shared memory so the block writes its whole edge tile with
 // 16-byte coalesced stores.
+// part_stride: P for the r-partite form, 0 for a general hypergraph.
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_hash_edges(const uint64_t *__restrict__ keys, uint64_t n, FastMod fm, uint64_t seed,
-             uint32_t *__restrict__ edges) {
+             uint32_t part_stride, uint32_t *__restrict__ edges) {
     __shared__ __align__(16) uint32_t tile[kThreads * R];
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    const uint32_t P = (uint32_t)fm.P;
+    const uint32_t P = part_stride;
     for (uint64_t base = (uint64_t)blockIdx.x * kThreads; base < n; base += stride) {
         const uint64_t i = base + threadIdx.x;
         const uint32_t cnt = (n - base < (uint64_t)kThreads) ? (uint32_t)(n - base) : (uint32_t)kThreads;
@@ -43,13 +46,15 @@ k_hash_edges(const uint64_t *__restrict__ keys, uint64_t n, FastMod fm, uint64_t
 }
 
 void launch_hash_edges(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
-                       FastMod fm, uint64_t seed, uint32_t *edges) {
+                       FastMod fm, uint64_t seed, uint32_t *edges, bool gen) {
     if (n == 0) return;
     const unsigned grid = grid_for(L, n, 1, 8);
+    const uint32_t ps = gen ? 0u : (uint32_t)fm.P;
+    count_launch();
     switch (r) {
-    case 2: count_launch(); k_hash_edges<2><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
-    case 3: count_launch(); k_hash_edges<3><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
-    case 4: count_launch(); k_hash_edges<4><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, edges); break;
+    case 2: k_hash_edges<2><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, ps, edges); break;
+    case 3: k_hash_edges<3><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, ps, edges); break;
+    case 4: k_hash_edges<4><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, ps, edges); break;
     }
 }
 

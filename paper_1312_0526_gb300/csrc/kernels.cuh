@@ -57,7 +57,8 @@ inline unsigned grid_for(const Launch &L, uint64_t work, int per_thread, int per
 
 // a1: keys -> r-partite edges (row-major rows, or edge records).
 void launch_hash_edges(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
-                       FastMod fm, uint64_t seed, uint32_t *edges);
+                       FastMod fm, uint64_t seed, uint32_t *edges,
+                       bool gen = false);
 void launch_hash_records(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
                          FastMod fm, uint64_t seed, uint4 *rec);
 

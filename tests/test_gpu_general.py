@@ -117,3 +117,11 @@ def test_general_peel_errors():
         hp._check(rc)
     ok = np.array([[0, 1, 2], [2, 3, 4]], dtype=np.uint32)
     _check(ok, 5)
+
+
+@pytest.mark.parametrize("n,m,r", [(1, 1, 3), (1000, 7, 2), (100_000, 123_001, 3),
+                                   (65_537, 2**32 - 5, 4), (100_000, 3, 3)])
+def test_general_hash_matches_oracle(n, m, r):
+    keys = inputs.keys(n, 21)
+    got = hp.hash_edges(torch.from_numpy(keys.view(np.int64)).cuda(), m, r, 9, general=True)
+    assert np.array_equal(_u32(got).reshape(n, r), oracle.hash_edges_general(keys, m, r, 9))
