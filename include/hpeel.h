@@ -64,7 +64,11 @@ typedef struct hpeel_stats {
     uint64_t hinge_moves;   /* peeled edges whose first claim came from a
                                vertex other than the hinge (a vertex of
                                smaller position claimed later in the round) */
-    uint64_t reserved[2];
+    uint32_t async_status;  /* hpeel_mphf_build_async: 1 peeled (G and rank
+                               directory written), 2 no seed peeled, 3 device
+                               check failed (device_err holds the code) */
+    uint32_t reserved32;
+    uint64_t reserved;
 } hpeel_stats;
 
 /* Largest number of rounds a single peel supports (claim words keep the
@@ -261,6 +265,32 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
                               uint64_t *d_G, uint64_t *d_rank_dir, uint32_t *d_order,
                               hpeel_stats *h_stats, void *d_ws, size_t ws_bytes,
                               void *stream);
+
+/*
+ * hpeel_mphf_build with no host round trip: the whole build is enqueued on
+ * stream as one CUDA graph and the call returns at once.  The reseed-and-
+ * retry loop (sec. 3: a hypergraph that keeps a 2-core is hashed again with
+ * the next seed), the rounds and the reverse-layer assignment are loops on
+ * the device (conditional nodes), so the call can be captured into a
+ * caller's CUDA graph or overlapped with other work on other streams.
+ *   Arguments as hpeel_mphf_build, except:
+ *   d_stats   device memory (not host), written at the end of the graph:
+ *             async_status 1 = peeled (G and rank directory written, seed_used
+ *             set), 2 = no seed among max_tries peeled (G untouched), 3 = a
+ *             device check failed (device_err); attempts, rounds, n_peeled
+ *             and the other counts as hpeel_mphf_build gives them.
+ *   No canonical order output.
+ * The graph is built on the first call with a given set of pointers and
+ * sizes and replayed by later calls with the same set (keep the workspace
+ * and the output buffers to reuse it).  Returns HPEEL_OK once enqueued;
+ * errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL, HPEEL_ERR_CUDA.
+ * When stream is being captured (cudaStreamBeginCapture), the build's nodes
+ * join the caller's graph at the capture position instead.
+ */
+hpeel_status hpeel_mphf_build_async(const uint64_t *d_keys, uint64_t n, uint64_t seed,
+                                    uint32_t gamma_milli, uint32_t max_tries, uint64_t *d_G,
+                                    uint64_t *d_rank_dir, hpeel_stats *d_stats, void *d_ws,
+                                    size_t ws_bytes, void *stream);
 
 /*
  * MPHF lookup (sec. 3; sec. 5 broadword rank): for each query key, hash it

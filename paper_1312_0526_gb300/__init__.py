@@ -65,10 +65,12 @@ class Stats(ctypes.Structure):
                 ("core_nonempty", ctypes.c_uint32), ("seed_used", ctypes.c_uint64),
                 ("attempts", ctypes.c_uint32), ("device_err", ctypes.c_uint32),
                 ("first_layer", ctypes.c_uint64), ("frontier", ctypes.c_uint64),
-                ("hinge_moves", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2)]
+                ("hinge_moves", ctypes.c_uint64), ("async_status", ctypes.c_uint32),
+                ("reserved32", ctypes.c_uint32), ("reserved", ctypes.c_uint64)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_
+                if k not in ("reserved", "reserved32")}
 
 
 _lib = None
@@ -127,6 +129,8 @@ def lib():
         L.hpeel_peel_general.restype = st
         L.hpeel_peel_general.argtypes = [p, u64, u64, u32, p, p, p, u32, ctypes.POINTER(Stats),
                                          p, sz, p]
+        L.hpeel_mphf_build_async.restype = st
+        L.hpeel_mphf_build_async.argtypes = [p, u64, u64, u32, u32, p, p, p, p, sz, p]
         L.hpeel_sf_bits.restype = u32
         L.hpeel_sf_bits.argtypes = [u64]
         L.hpeel_sf_words.restype = u64
@@ -390,6 +394,39 @@ def mphf_build(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
     res = MphfResult(G[:(m + 31) // 32], rank_dir, m, st.as_dict())
     res.order = order
     return res
+
+
+def mphf_build_async(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
+                     workspace=None, G=None, rank_dir=None, stats=None):
+    """Device-driven MPHF build (hpeel_mphf_build_async): enqueued as one CUDA
+    graph on the current stream, no host synchronisation.  Returns (G,
+    rank_dir, stats) where stats is a device uint8 tensor holding an
+    hpeel_stats; read it with stats_from_device after the stream is done."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1, host_ok=True)
+    n = keys.shape[0]
+    dev = keys.device if keys.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    m = num_vertices(n, gamma_milli, 3)
+    if G is None:
+        G = torch.empty(max((m + 31) // 32, 1), dtype=torch.int64, device=dev)
+    if rank_dir is None:
+        rank_dir = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device=dev)
+    if stats is None:
+        stats = torch.zeros(ctypes.sizeof(Stats), dtype=torch.uint8, device=dev)
+    ws = workspace if workspace is not None else _workspace(mphf_workspace_size(n, gamma_milli), dev)
+    _check(lib().hpeel_mphf_build_async(kp, n, seed, gamma_milli, max_tries,
+                                        _dev_ptr(G, "G", torch.int64),
+                                        _dev_ptr(rank_dir, "rank_dir", torch.int64),
+                                        _dev_ptr(stats, "stats", torch.uint8),
+                                        _dev_ptr(ws, "workspace", torch.uint8), ws.numel(),
+                                        _stream()))
+    return G, rank_dir, stats
+
+
+def stats_from_device(stats) -> dict:
+    """The hpeel_stats a device-driven call wrote (copies to the host)."""
+    raw = bytes(stats.cpu().numpy().tobytes())
+    return Stats.from_buffer_copy(raw[:ctypes.sizeof(Stats)]).as_dict()
 
 
 def kernel_launches() -> int:

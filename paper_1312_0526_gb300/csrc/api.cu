@@ -106,7 +106,7 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false)
 }
 
 struct MphfLayout {
-    size_t rank_cnt, rank_scan, rank_tmp, peel, total;
+    size_t state, rank_cnt, rank_scan, rank_tmp, peel, total;
     uint64_t m;
 };
 
@@ -120,6 +120,7 @@ MphfLayout mphf_layout(uint64_t n, uint32_t gamma_milli) {
         return o;
     };
     const uint64_t blocks = (p.m + 511) / 512;
+    p.state = take(sizeof(AsyncState));
     p.rank_cnt = take(4 * blocks + 4);
     p.rank_scan = take(4 * blocks + 4);
     p.rank_tmp = take(4 * scan_tmp_words(blocks));
@@ -432,6 +433,231 @@ hpeel_status peel_core(const Launch &L, const PeelIO &io, uint32_t n, uint32_t m
     return peel_core_rb(L, io, n, m, r, ws, out, hctl);
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven MPHF build: one CUDA graph, no host round trip.
+//
+// The graph is captured from the same launchers the host-driven build uses,
+// with conditional nodes added at the capture position: an outer while loop
+// over hash seeds (build, an if-node that redoes an overflowed L2-blocked
+// build with direct updates, round 0, the while loop of rounds, a decision
+// kernel), then an if-node on success holding the reverse-layer assignment
+// (a while loop over layers) and the rank directory, then the stats.
+// ---------------------------------------------------------------------------
+
+// Capture streams of this thread (one per nesting depth of the graph).
+cudaStream_t capture_stream(int depth) {
+    thread_local cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};
+    thread_local int dev_of[4] = {-1, -1, -1, -1};
+    int d = 0;
+    cudaGetDevice(&d);
+    if (!s[depth] || dev_of[depth] != d) {
+        if (cudaStreamCreateWithFlags(&s[depth], cudaStreamNonBlocking) != cudaSuccess)
+            return nullptr;
+        dev_of[depth] = d;
+    }
+    return s[depth];
+}
+
+// A condition handle on the graph stream s is capturing into.
+cudaError_t new_handle(cudaStream_t s, unsigned default_value, unsigned flags,
+                       cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    return cudaGraphConditionalHandleCreate(h, g, default_value, flags);
+}
+
+// Append a conditional node at the capture position of s; *body receives its
+// body graph, into which another stream captures.
+cudaError_t append_conditional(cudaStream_t s, cudaGraphConditionalHandle h,
+                               cudaGraphConditionalNodeType type, cudaGraph_t *body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+    if (e != cudaSuccess) return e;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies);
+}
+
+struct AsyncArgs {
+    const uint64_t *keys;
+    uint32_t n, m, max_tries;
+    uint64_t seed;
+    uint32_t gamma_milli;
+    uint64_t *G, *D;
+    hpeel_stats *stats;
+    char *ws;
+    int sms;
+};
+
+// into: a stream the caller is capturing (the build joins that graph at the
+// capture position), or null to capture a graph of its own into *out.
+hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGraph_t *out) {
+    cudaStream_t s0 = into ? into : capture_stream(0), s1 = capture_stream(1),
+                 s2 = capture_stream(2);
+    if (!s0 || !s1 || !s2) return fail(HPEEL_ERR_CUDA, "capture stream creation failed");
+    const MphfLayout ml = mphf_layout(a.n, a.gamma_milli);
+    char *pw = a.ws + ml.peel;
+    const PeelLayout lay = peel_layout(a.n, a.m, 3);
+    AsyncState *state = reinterpret_cast<AsyncState *>(a.ws + ml.state);
+    Ctl *ctl = reinterpret_cast<Ctl *>(pw + lay.ctl);
+    uint4 *rec = reinterpret_cast<uint4 *>(pw + lay.rec);
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(pw + lay.state);
+    uint4 *Ll = reinterpret_cast<uint4 *>(pw + lay.L);
+    uint32_t *loff = reinterpret_cast<uint32_t *>(pw + lay.loff);
+    RoundParams *prm = reinterpret_cast<RoundParams *>(pw + lay.params);
+    const uint32_t n = a.n, m = a.m, P = m / 3;
+    const FastMod fm = make_fastmod(P);
+    const uint64_t *seed_dev = &state->seed;
+    Launch L0{s0, a.sms}, L1{s1, a.sms}, L2{s2, a.sms};
+    RoundParams rp{};
+    rp.st = st;
+    rp.rec = rec;
+    rp.L = Ll;
+    rp.loff = loff;
+    rp.ctl = ctl;
+    rp.n = n;
+    rp.m = m;
+    rp.P = P;
+    rp.max_rounds = lay.max_rounds;
+    const RoundLaunch k0 = round0_launch(L0, 3, false), k1 = round_launch(L0, 3, false);
+
+    // captures end in this order whatever fails, so no stream of ours stays
+    // capturing (the caller's capture is left to the caller)
+    int open = 0;
+    const int first = into ? 1 : 0;
+    cudaStream_t opened[3] = {s0, s1, s2};
+    auto abort_all = [&](hpeel_status stt) {
+        for (int i = open - 1; i >= first; i--) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(opened[i], &g);
+            if (i == 0 && g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        return stt;
+    };
+#define HP_CAP(call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return abort_all(fail(HPEEL_ERR_CUDA, "graph capture: %s failed: %s", #call,   \
+                                  cudaGetErrorString(e_)));                                \
+    } while (0)
+    auto begin_body = [&](cudaStream_t s, cudaGraph_t body) {
+        return cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed);
+    };
+
+    if (!into) HP_CAP(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
+    open = 1;
+    launch_set_params(L0, prm, rp);
+    launch_async_init(L0, state, a.seed, a.max_tries, n);
+    cudaGraphConditionalHandle h_out = 0, h_ovf = 0, h_in = 0, h_ok = 0, h_asg = 0;
+    cudaGraph_t b_out = nullptr, b_ovf = nullptr, b_in = nullptr, b_ok = nullptr, b_asg = nullptr;
+    HP_CAP(new_handle(s0, 1u, cudaGraphCondAssignDefault, &h_out));
+    HP_CAP(append_conditional(s0, h_out, cudaGraphCondTypeWhile, &b_out));
+    {   // one attempt (body of the loop over seeds)
+        HP_CAP(begin_body(s1, b_out));
+        open = 2;
+        HP_CAP(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s1));
+        if (lay.bucketed) {
+            uint2 *pairs = reinterpret_cast<uint2 *>(pw + lay.pairs);
+            uint32_t *fill = reinterpret_cast<uint32_t *>(pw + lay.fill);
+            uint2 *pairs2 = reinterpret_cast<uint2 *>(pw + lay.pairs2);
+            uint32_t *fill2 = reinterpret_cast<uint32_t *>(pw + lay.fill2);
+            Overflow ov{reinterpret_cast<uint2 *>(pw + lay.ovf),
+                        reinterpret_cast<uint32_t *>(pw + lay.ovf_count), lay.plan.ovf_cap};
+            HP_CAP(cudaMemsetAsync(fill2, 0, 4 * (size_t)lay.plan.subs, s1));
+            HP_CAP(cudaMemsetAsync(ov.count, 0, 4, s1));
+            launch_build_bucketed(L1, lay.plan, a.keys, nullptr, n, 3, fm, a.seed, P, rec, pairs,
+                                  fill, ov, ctl, false, seed_dev);
+            launch_apply_buckets(L1, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl);
+            // an overflowed build is redone with direct updates (same result)
+            HP_CAP(new_handle(s1, 0u, 0u, &h_ovf));
+            launch_async_check_overflow(L1, ctl, h_ovf);
+            HP_CAP(append_conditional(s1, h_ovf, cudaGraphCondTypeIf, &b_ovf));
+            HP_CAP(begin_body(s2, b_ovf));
+            open = 3;
+            HP_CAP(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s2));
+            launch_fill_u32(L2, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
+            launch_hash_records(L2, a.keys, n, 3, fm, a.seed, rec, seed_dev);
+            launch_build_incidence(L2, rec, n, 3, m, st, ctl);
+            cudaGraph_t g = nullptr;
+            HP_CAP(cudaStreamEndCapture(s2, &g));
+            open = 2;
+        } else {
+            launch_fill_u32(L1, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
+            launch_hash_records(L1, a.keys, n, 3, fm, a.seed, rec, seed_dev);
+            launch_build_incidence(L1, rec, n, 3, m, st, ctl);
+        }
+        // round 0, then the while loop of rounds (as launch_round_graph)
+        HP_CAP(new_handle(s1, 0u, 0u, &h_in));
+        {
+            void *args[] = {(void *)&prm, &h_in};
+            count_launch();
+            HP_CAP(cudaLaunchKernel(k0.fn, dim3(k0.grid), dim3(k0.block), args, k0.smem, s1));
+        }
+        HP_CAP(append_conditional(s1, h_in, cudaGraphCondTypeWhile, &b_in));
+        HP_CAP(begin_body(s2, b_in));
+        open = 3;
+        {
+            void *args[] = {(void *)&prm, &h_in};
+            HP_CAP(cudaLaunchKernel(k1.fn, dim3(k1.grid), dim3(k1.block), args, k1.smem, s2));
+        }
+        cudaGraph_t g = nullptr;
+        HP_CAP(cudaStreamEndCapture(s2, &g));
+        open = 2;
+        launch_async_decide(L1, state, ctl, h_out);
+        HP_CAP(cudaStreamEndCapture(s1, &g));
+        open = 1;
+    }
+    HP_CAP(new_handle(s0, 0u, 0u, &h_ok));
+    launch_async_if_peeled(L0, state, h_ok);
+    HP_CAP(append_conditional(s0, h_ok, cudaGraphCondTypeIf, &b_ok));
+    {   // assignment in reverse layer order, then the rank directory
+        HP_CAP(begin_body(s1, b_ok));
+        open = 2;
+        const uint64_t words = ((uint64_t)m + 31) / 32, blocks = ((uint64_t)m + 511) / 512;
+        HP_CAP(cudaMemsetAsync(a.G, 0, 8 * words, s1));
+        HP_CAP(new_handle(s1, 0u, 0u, &h_asg));
+        launch_async_assign_init(L1, state, h_asg);
+        HP_CAP(append_conditional(s1, h_asg, cudaGraphCondTypeWhile, &b_asg));
+        HP_CAP(begin_body(s2, b_asg));
+        open = 3;
+        launch_assign_layer_at(L2, Ll, loff, &state->t, P, a.G);
+        launch_async_assign_step(L2, state, h_asg);
+        cudaGraph_t g = nullptr;
+        HP_CAP(cudaStreamEndCapture(s2, &g));
+        open = 2;
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(a.ws + ml.rank_cnt);
+        uint32_t *scn = reinterpret_cast<uint32_t *>(a.ws + ml.rank_scan);
+        uint32_t *tmp = reinterpret_cast<uint32_t *>(a.ws + ml.rank_tmp);
+        launch_rank_counts(L1, a.G, m, cnt);
+        launch_scan_u32(L1, cnt, scn, blocks, tmp);
+        launch_widen_dir(L1, scn, cnt, blocks, a.D);
+        HP_CAP(cudaStreamEndCapture(s1, &g));
+        open = 1;
+    }
+    launch_async_stats(L0, state, ctl, a.stats);
+    if (!into) HP_CAP(cudaStreamEndCapture(s0, out));
+    open = 0;
+#undef HP_CAP
+    return HPEEL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -684,6 +910,79 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
     }
     return fail(HPEEL_ERR_RETRIES_EXHAUSTED, "2-core non-empty for seeds %llu..%llu",
                 (unsigned long long)seed, (unsigned long long)(seed + max_tries - 1));
+}
+
+hpeel_status hpeel_mphf_build_async(const uint64_t *d_keys, uint64_t n, uint64_t seed,
+                                    uint32_t gamma_milli, uint32_t max_tries, uint64_t *d_G,
+                                    uint64_t *d_rank_dir, hpeel_stats *d_stats, void *d_ws,
+                                    size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (gamma_milli == 0) return fail(HPEEL_ERR_INVALID_ARG, "gamma_milli must be positive");
+    const MphfLayout lay = mphf_layout(n, gamma_milli);
+    const uint64_t m = lay.m;
+    if (n >= (1ull << 32) || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    if (max_tries == 0) return fail(HPEEL_ERR_INVALID_ARG, "max_tries must be positive");
+    if (!d_stats) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    if (n == 0) {
+        launch_async_empty(L, d_stats, seed, d_rank_dir);
+        return check_launch("async_empty");
+    }
+    if (!d_keys || !d_G || !d_rank_dir || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_ws & 255u) != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < lay.total)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
+                    lay.total);
+    AsyncArgs a{d_keys, (uint32_t)n, (uint32_t)m, max_tries, seed, gamma_milli,
+                d_G, d_rank_dir, d_stats, (char *)d_ws, L.sms};
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HP_CUDA(cudaStreamIsCapturing(L.stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {
+        // the caller is capturing: the build's nodes join the caller's graph
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        return capture_async_build(a, L.stream, nullptr);
+    }
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    const hpeel_tuning tu = tuning();
+    char keybuf[320];
+    snprintf(keybuf, sizeof keybuf, "mphf|%d|%p|%llu|%llu|%u|%u|%p|%p|%p|%p|%u|%u|%u|%d", dev,
+             (const void *)d_keys, (unsigned long long)n, (unsigned long long)seed, gamma_milli,
+             max_tries, (void *)d_G, (void *)d_rank_dir, (void *)d_stats, d_ws, tu.bucket_shift,
+             tu.bucket_min_vertices, tu.bucket_sub_shift, L.sms);
+    const std::string key(keybuf);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) {
+        while (g_graph_lru.size() >= kGraphCache) {
+            auto old = g_graphs.find(g_graph_lru.front());
+            if (old != g_graphs.end()) {
+                destroy_graph(old->second);
+                g_graphs.erase(old);
+            }
+            g_graph_lru.erase(g_graph_lru.begin());
+        }
+        RoundGraph rg;
+        HP_TRY(capture_async_build(a, nullptr, &rg.graph));
+        if (cudaGraphInstantiate(&rg.exec, rg.graph, 0) != cudaSuccess ||
+            cudaEventCreateWithFlags(&rg.done, cudaEventDisableTiming) != cudaSuccess) {
+            const cudaError_t e = cudaGetLastError();
+            destroy_graph(rg);
+            return fail(HPEEL_ERR_CUDA, "device-driven build graph: %s", cudaGetErrorString(e));
+        }
+        it = g_graphs.emplace(key, rg).first;
+        g_graph_lru.push_back(key);
+    } else {
+        auto pos = std::find(g_graph_lru.begin(), g_graph_lru.end(), key);
+        if (pos != g_graph_lru.end()) g_graph_lru.erase(pos);
+        g_graph_lru.push_back(key);
+    }
+    HP_CUDA(cudaGraphLaunch(it->second.exec, L.stream));
+    HP_CUDA(cudaEventRecord(it->second.done, L.stream));
+    return HPEEL_OK;
 }
 
 uint32_t hpeel_sf_bits(uint64_t sigma) {

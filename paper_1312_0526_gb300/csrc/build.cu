@@ -59,10 +59,12 @@ __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
 template <int R, bool FROM_KEYS, bool GEN>
 __global__ void __launch_bounds__(kThreads, HPEEL_RB_MIN_BLOCKS)
 k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ rows,
-                   uint32_t n, FastMod fm, uint64_t seed, BucketGeom g, uint4 *__restrict__ rec,
+                   uint32_t n, FastMod fm, uint64_t seed, const uint64_t *seed_dev, BucketGeom g,
+                   uint4 *__restrict__ rec,
                    uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov,
                    Ctl *ctl) {
     constexpr int kInc = kTileEdges * R;
+    if (FROM_KEYS && seed_dev) seed = *seed_dev;  // the seed of a device-driven attempt
     extern __shared__ uint32_t smem[];
     const uint32_t C = (GEN ? 1u : (uint32_t)R) * g.chunks_per_part;
     const uint32_t Cp = (C + 1) & ~1u;
@@ -391,7 +393,7 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           Overflow ov, Ctl *ctl, bool gen) {
+                           Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev) {
     if (n == 0) return;
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
     const unsigned grid = b.regions;  // one bucket region per block and chunk
@@ -400,8 +402,8 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
         auto kern = gen ? k_records_bucketed<RR, FK, true> : k_records_bucketed<RR, FK, false>; \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem); \
         count_launch();                                                                       \
-        kern<<<grid, kThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, g, rec, pairs,    \
-                                                   fill, ov, ctl);                            \
+        kern<<<grid, kThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, seed_dev, g, rec,  \
+                                                   pairs, fill, ov, ctl);                     \
     } while (0)
     if (keys) {
         switch (r) {

@@ -35,6 +35,23 @@ struct Ctl {
     uint32_t pad[7];
 };
 
+// State of a device-driven build (graph-resident reseed-and-retry).
+enum : uint32_t {
+    kAsyncRunning = 0,
+    kAsyncPeeled = 1,
+    kAsyncRetriesExhausted = 2,
+    kAsyncDeviceError = 3,
+};
+struct AsyncState {
+    uint64_t seed0, seed;  // first seed, seed of the current attempt
+    uint32_t attempt;      // attempts made after the first
+    uint32_t max_tries;
+    uint32_t status;       // kAsync*
+    uint32_t rounds;       // layers of the peeled attempt
+    int32_t t;             // layer being assigned
+    uint32_t n;
+};
+
 // Arguments of the round-loop kernels, kept in the workspace so the CUDA
 // graph of a round loop depends only on where the workspace is.
 struct RoundParams {

@@ -63,7 +63,8 @@ void launch_hash_edges(const Launch &L, const uint64_t *keys, uint64_t n, uint32
 template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_hash_records(const uint64_t *__restrict__ keys, uint64_t n, FastMod fm, uint64_t seed,
-               uint4 *__restrict__ rec) {
+               const uint64_t *seed_dev, uint4 *__restrict__ rec) {
+    if (seed_dev) seed = *seed_dev;  // the seed of a device-driven attempt
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     const uint32_t P = (uint32_t)fm.P;
     for (uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
@@ -77,13 +78,14 @@ k_hash_records(const uint64_t *__restrict__ keys, uint64_t n, FastMod fm, uint64
 }
 
 void launch_hash_records(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
-                         FastMod fm, uint64_t seed, uint4 *rec) {
+                         FastMod fm, uint64_t seed, uint4 *rec, const uint64_t *seed_dev) {
     if (n == 0) return;
     const unsigned grid = grid_for(L, n, 1, 8);
+    count_launch();
     switch (r) {
-    case 2: count_launch(); k_hash_records<2><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, rec); break;
-    case 3: count_launch(); k_hash_records<3><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, rec); break;
-    case 4: count_launch(); k_hash_records<4><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, rec); break;
+    case 2: k_hash_records<2><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, seed_dev, rec); break;
+    case 3: k_hash_records<3><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, seed_dev, rec); break;
+    case 4: k_hash_records<4><<<grid, kThreads, 0, L.stream>>>(keys, n, fm, seed, seed_dev, rec); break;
     }
 }
 

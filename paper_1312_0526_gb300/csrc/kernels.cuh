@@ -59,8 +59,11 @@ inline unsigned grid_for(const Launch &L, uint64_t work, int per_thread, int per
 void launch_hash_edges(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
                        FastMod fm, uint64_t seed, uint32_t *edges,
                        bool gen = false);
+// seed_dev (or NULL): the seed is read from device memory when the kernel
+// runs (device-driven retries), else the seed argument.
 void launch_hash_records(const Launch &L, const uint64_t *keys, uint64_t n, uint32_t r,
-                         FastMod fm, uint64_t seed, uint4 *rec);
+                         FastMod fm, uint64_t seed, uint4 *rec,
+                         const uint64_t *seed_dev = nullptr);
 
 // fill count 32-bit words with value.
 void launch_fill_u32(const Launch &L, uint32_t *p, uint64_t count, uint32_t value);
@@ -104,7 +107,7 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           Overflow ov, Ctl *ctl, bool gen);
+                           Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev = nullptr);
 void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
                           const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
                           unsigned long long *st, Ctl *ctl);
@@ -169,6 +172,22 @@ void launch_sf_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *l
 void launch_sf_lookup(const Launch &L, const uint64_t *keys, uint64_t nq, FastMod fm,
                       uint64_t seed, uint64_t sigma, uint32_t b, const uint64_t *U,
                       uint32_t *out);
+// Assignment of the layer whose index the device holds at *t (device-driven
+// build).
+void launch_assign_layer_at(const Launch &L, const uint4 *Lst, const uint32_t *loff,
+                            const int32_t *t, uint32_t P, uint64_t *G);
+// Device-driven build control (async.cu): one-thread kernels that set the
+// conditions of the graph's loops.
+void launch_async_empty(const Launch &L, hpeel_stats *out, uint64_t seed, uint64_t *D);
+void launch_async_init(const Launch &L, AsyncState *s, uint64_t seed, uint32_t max_tries,
+                       uint32_t n);
+void launch_async_check_overflow(const Launch &L, const Ctl *ctl, cudaGraphConditionalHandle h);
+void launch_async_decide(const Launch &L, AsyncState *s, const Ctl *ctl,
+                         cudaGraphConditionalHandle h);
+void launch_async_if_peeled(const Launch &L, const AsyncState *s, cudaGraphConditionalHandle h);
+void launch_async_assign_init(const Launch &L, AsyncState *s, cudaGraphConditionalHandle h);
+void launch_async_assign_step(const Launch &L, AsyncState *s, cudaGraphConditionalHandle h);
+void launch_async_stats(const Launch &L, const AsyncState *s, const Ctl *ctl, hpeel_stats *out);
 // a9: per-512-vertex counts of non-zero 2-bit values, then the directory.
 void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt);
 void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,

@@ -43,6 +43,31 @@ void launch_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff
     k_assign<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(Lst, loff, t, P, G);
 }
 
+// The same, for the layer whose index the device holds (the assignment loop
+// of a device-driven build).
+__global__ void __launch_bounds__(kThreads)
+k_assign_at(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, const int32_t *t,
+            uint32_t P, uint64_t *G) {
+    const uint32_t tt = (uint32_t)*(volatile const int32_t *)t;
+    const uint32_t lb = __ldcg(loff + tt), le = __ldcg(loff + tt + 1);
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    for (uint64_t i = lb + (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < le; i += stride) {
+        const uint4 s = __ldcs(Lst + i);
+        const uint32_t h = part_of<3>(s.x, P);
+        const uint32_t sum = g_get(G, s.y) + g_get(G, s.z);
+        const uint32_t val = (h + 6u - sum) % 3u;
+        const uint64_t code = val ? val : 3u;
+        atomicOr((unsigned long long *)(G + (s.x >> 5)),
+                 (unsigned long long)(code << (2u * (s.x & 31u))));
+    }
+}
+
+void launch_assign_layer_at(const Launch &L, const uint4 *Lst, const uint32_t *loff,
+                            const int32_t *t, uint32_t P, uint64_t *G) {
+    count_launch();
+    k_assign_at<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(Lst, loff, t, P, G);
+}
+
 // Non-zero 2-bit values of a word: a pair is non-zero when either bit is set.
 __device__ __forceinline__ uint32_t nonzero_pairs(uint64_t w) {
     return (uint32_t)__popcll((w | (w >> 1)) & 0x5555555555555555ull);
