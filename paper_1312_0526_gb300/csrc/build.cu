@@ -199,6 +199,8 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 // and written, so the load latency overlaps the work.
 constexpr int kRefineItems = 16;
 constexpr uint32_t kRefineTile = kThreads * kRefineItems;  // 4096 slots
+constexpr uint32_t kWarps = kThreads / 32;
+constexpr uint32_t kScanRegs = 4;  // sub-buckets per thread whose cursor stays in registers
 
 __global__ void __launch_bounds__(kThreads)
 k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ fill, BucketGeom g,
@@ -210,8 +212,11 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
     uint32_t *hist = smem;          // S
     uint32_t *gbase = hist + S;     // S
     uint32_t *toff = gbase + S;     // S
-    uint32_t *sb = toff + S;        // kRefineTile: sub-bucket of each stage slot
+    uint32_t *wsum = toff + S;      // kWarps: scan totals of the warps
+    uint32_t *sb = wsum + kWarps;   // kRefineTile: sub-bucket of each stage slot
     uint2 *stage = reinterpret_cast<uint2 *>(sb + kRefineTile);
+    // the scan gives each thread `per` consecutive sub-buckets
+    const uint32_t per = (S + kThreads - 1) / kThreads, b0 = threadIdx.x * per;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t span = (uint64_t)regions * g.cap;
     // tiles never straddle regions: region reg has ceil(cap / kRefineTile)
@@ -267,21 +272,38 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             rk[q] = ok[q] ? atomicAdd(&hist[(p[q].x - base_v) >> sub_shift], 1u) : 0u;
         }
         __syncthreads();
-        for (uint32_t b = threadIdx.x; b < S; b += kThreads)
-            gbase[b] = hist[b] ? atomicAdd(fill2 + (size_t)c * S + b, hist[b]) : 0u;
-        if (warp == 0) {  // exclusive scan of hist -> toff
-            uint32_t run = 0;
-            for (uint32_t b0 = 0; b0 < S; b0 += 32) {
-                const uint32_t b = b0 + lane;
-                const uint32_t h = b < S ? hist[b] : 0u;
-                uint32_t x = h;
+        // reserve each sub-bucket's run with one atomicAdd on its cursor;
+        // the results are awaited only after the staging below
+        uint32_t gb[kScanRegs];
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-                    if (lane >= (uint32_t)d) x += y;
+        for (uint32_t q = 0; q < kScanRegs; q++) {
+            const uint32_t b = b0 + q, h = q < per && b < S ? hist[b] : 0u;
+            gb[q] = h ? atomicAdd(fill2 + (size_t)c * S + b, h) : 0u;
+        }
+        for (uint32_t q = kScanRegs; q < per; q++) {  // S > kThreads * kScanRegs
+            const uint32_t b = b0 + q, h = b < S ? hist[b] : 0u;
+            if (b < S) gbase[b] = h ? atomicAdd(fill2 + (size_t)c * S + b, h) : 0u;
+        }
+        {   // exclusive scan of hist -> toff over the whole block
+            uint32_t loc = 0;
+            for (uint32_t q = 0; q < per; q++)
+                if (b0 + q < S) loc += hist[b0 + q];
+            uint32_t x = loc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+                if (lane >= (uint32_t)d) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            uint32_t run = x - loc;
+            for (uint32_t w = 0; w < warp; w++) run += wsum[w];
+            for (uint32_t q = 0; q < per; q++) {
+                const uint32_t b = b0 + q;
+                if (b < S) {
+                    toff[b] = run;
+                    run += hist[b];
                 }
-                if (b < S) toff[b] = run + x - h;
-                run += __shfl_sync(0xFFFFFFFFu, x, 31);
             }
         }
         __syncthreads();
@@ -293,6 +315,9 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             stage[slot] = p[q];
             sb[slot] = b;
         }
+#pragma unroll
+        for (uint32_t q = 0; q < kScanRegs; q++)
+            if (q < per && b0 + q < S) gbase[b0 + q] = gb[q];
         __syncthreads();
         const uint32_t total = toff[S - 1] + hist[S - 1];
         for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
@@ -332,11 +357,22 @@ k_apply_smem(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill
     __syncthreads();
     const uint32_t cnt = min(fill2[s], cap2);
     const uint2 *src = pairs2 + (size_t)s * cap2;
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const uint2 p = __ldcs(src + i);
-        const uint32_t k = p.x - base_v;
-        atomicAdd(deg + k, 1u);
-        atomicAdd(sum + k, p.y);
+    constexpr int kU = 4;  // loads in flight per thread
+    for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += kU * blockDim.x) {
+        uint2 p[kU];
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            const uint32_t i = i0 + (uint32_t)u * blockDim.x;
+            p[u] = i < cnt ? __ldcs(src + i) : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; u++) {
+            if (i0 + (uint32_t)u * blockDim.x < cnt) {
+                const uint32_t k = p[u].x - base_v;
+                atomicAdd(deg + k, 1u);
+                atomicAdd(sum + k, p[u].y);
+            }
+        }
     }
     __syncthreads();
     const uint32_t lim = min(nv, part_end - base_v);
@@ -426,7 +462,7 @@ void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, cons
                           unsigned long long *st, Ctl *ctl) {
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
     const uint32_t S = 1u << (b.shift - b.sub_shift);
-    const size_t smem1 = (3 * (size_t)S + kRefineTile) * 4 + (size_t)kRefineTile * 8;
+    const size_t smem1 = (3 * (size_t)S + kWarps + kRefineTile) * 4 + (size_t)kRefineTile * 8;
     cudaFuncSetAttribute(k_refine_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     const uint64_t items =
         (uint64_t)b.chunks * b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);

@@ -15,26 +15,48 @@
 
 namespace hp {
 
-__device__ __forceinline__ uint32_t g_get(const uint64_t *G, uint32_t v) {
-    return (uint32_t)(__ldcg(G + (v >> 5)) >> (2u * (v & 31u))) & 3u;
+// Solve the list entries [lb, le) of one layer: each {v_hinge, v_a, v_b, e}
+// with the hinge position the part of v_hinge, read as a stream.  A thread
+// takes kAssignU entries at a time and issues all their loads first.
+constexpr int kAssignU = 4;
+
+__device__ __forceinline__ void assign_range(const uint4 *__restrict__ Lst, uint32_t lb,
+                                             uint32_t le, uint32_t P, uint64_t *G) {
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads * kAssignU;
+    for (uint64_t i0 = lb + (uint64_t)blockIdx.x * kThreads * kAssignU + threadIdx.x; i0 < le;
+         i0 += stride) {
+        uint4 s[kAssignU];
+#pragma unroll
+        for (int u = 0; u < kAssignU; u++) {
+            const uint64_t i = i0 + (uint64_t)u * kThreads;
+            s[u] = i < le ? __ldcs(Lst + i) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        uint64_t wa[kAssignU], wb[kAssignU];
+#pragma unroll
+        for (int u = 0; u < kAssignU; u++) {
+            const bool ok = i0 + (uint64_t)u * kThreads < le;
+            wa[u] = ok ? __ldcg(G + (s[u].y >> 5)) : 0ull;
+            wb[u] = ok ? __ldcg(G + (s[u].z >> 5)) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kAssignU; u++) {
+            if (i0 + (uint64_t)u * kThreads >= le) continue;
+            const uint32_t h = part_of<3>(s[u].x, P);
+            const uint32_t sum = (uint32_t)(wa[u] >> (2u * (s[u].y & 31u)) & 3u) +
+                                 (uint32_t)(wb[u] >> (2u * (s[u].z & 31u)) & 3u);
+            const uint32_t val = (h + 6u - sum) % 3u;  // sum <= 6
+            const uint64_t code = val ? val : 3u;
+            atomicOr((unsigned long long *)(G + (s[u].x >> 5)),
+                     (unsigned long long)(code << (2u * (s[u].x & 31u))));
+        }
+    }
 }
 
-// Layer t: list entries loff[t] .. loff[t+1], each {v_hinge, v_a, v_b, e}
-// with the hinge position the part of v_hinge, read as a stream.
+// Layer t: list entries loff[t] .. loff[t+1].
 __global__ void __launch_bounds__(kThreads)
 k_assign(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, uint32_t t,
          uint32_t P, uint64_t *G) {
-    const uint32_t lb = loff[t], le = loff[t + 1];
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t i = lb + (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < le; i += stride) {
-        const uint4 s = __ldcs(Lst + i);
-        const uint32_t h = part_of<3>(s.x, P);
-        const uint32_t sum = g_get(G, s.y) + g_get(G, s.z);
-        const uint32_t val = (h + 6u - sum) % 3u;  // sum <= 6
-        const uint64_t code = val ? val : 3u;
-        atomicOr((unsigned long long *)(G + (s.x >> 5)),
-                 (unsigned long long)(code << (2u * (s.x & 31u))));
-    }
+    assign_range(Lst, loff[t], loff[t + 1], P, G);
 }
 
 void launch_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
@@ -49,17 +71,7 @@ __global__ void __launch_bounds__(kThreads)
 k_assign_at(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, const int32_t *t,
             uint32_t P, uint64_t *G) {
     const uint32_t tt = (uint32_t)*(volatile const int32_t *)t;
-    const uint32_t lb = __ldcg(loff + tt), le = __ldcg(loff + tt + 1);
-    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
-    for (uint64_t i = lb + (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < le; i += stride) {
-        const uint4 s = __ldcs(Lst + i);
-        const uint32_t h = part_of<3>(s.x, P);
-        const uint32_t sum = g_get(G, s.y) + g_get(G, s.z);
-        const uint32_t val = (h + 6u - sum) % 3u;
-        const uint64_t code = val ? val : 3u;
-        atomicOr((unsigned long long *)(G + (s.x >> 5)),
-                 (unsigned long long)(code << (2u * (s.x & 31u))));
-    }
+    assign_range(Lst, __ldcg(loff + tt), __ldcg(loff + tt + 1), P, G);
 }
 
 void launch_assign_layer_at(const Launch &L, const uint4 *Lst, const uint32_t *loff,
