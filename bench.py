@@ -228,6 +228,44 @@ def lookup_leg(keys, G, D, m, seed):
             "bits_per_key": hp.mphf_bits_per_key(n, GAMMA_MILLI)}
 
 
+def random_access_leg(n, m, rounds_ms):
+    """The random-access ceiling the rounds run against: random 64-bit atomics,
+    random 8-byte loads and the access pattern of one peeled edge (a record
+    claim and two vertex updates), over arrays the size of the build's edge
+    records (n x 16 B) and vertex records (m x 8 B), timed with CUDA events
+    (hpeel_probe_random_access)."""
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+
+    A = torch.zeros(n * 2, dtype=torch.int64, device="cuda")
+    B = torch.zeros(m, dtype=torch.int64, device="cuda")
+    out = {}
+    # the loads run first, while the vertex words are still zero
+    for kind, name, arg_b in ((1, "load64", None), (0, "rmw64", None), (2, "peeled_edge", B)):
+        target = A if kind == 2 else B
+        hp.probe_random_access(kind, n, target, arg_b, seed=7)  # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        torch.cuda.synchronize()
+        a.record()
+        for r in range(reps):
+            hp.probe_random_access(kind, n, target, arg_b, seed=100 + r)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"g_per_s": n / ms / 1e6, "ms": ms}
+    del A, B
+    torch.cuda.empty_cache()
+    rounds_g = n / rounds_ms / 1e6
+    out["rounds_g_edges_per_s"] = rounds_g
+    out["rounds_vs_peeled_edge_pattern"] = rounds_g / out["peeled_edge"]["g_per_s"]
+    out["arrays"] = (f"rmw64 and load64 over the vertex-record size ({m * 8 / 1e9:.2f} GB); "
+                     f"peeled_edge: records {n * 16 / 1e9:.2f} GB + vertex words "
+                     f"{m * 8 / 1e9:.2f} GB; {n:.0e} operations each")
+    return out
+
+
 PEEL_N = 10**9
 SF_SIGMA = 256
 
@@ -692,6 +730,9 @@ def main():
     sf = None
     del keys, ws, order
     torch.cuda.empty_cache()
+    random_access = None
+    if world == 1:
+        random_access = random_access_leg(n, m, prof["rounds"][1] / args.steps)
     if world == 1 and not args.no_sf:
         sf = sf_leg(n, steps=3, warmup=1)
     general = None
@@ -728,6 +769,7 @@ def main():
         "peel_1e9": peel_1e9,
         "static_function": sf,
         "general_peel": general,
+        "random_access": random_access,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -131,6 +131,8 @@ def lib():
                                          p, sz, p]
         L.hpeel_mphf_build_async.restype = st
         L.hpeel_mphf_build_async.argtypes = [p, u64, u64, u32, u32, p, p, p, p, sz, p]
+        L.hpeel_probe_random_access.restype = st
+        L.hpeel_probe_random_access.argtypes = [u32, u64, p, sz, p, sz, u64, p]
         L.hpeel_sf_bits.restype = u32
         L.hpeel_sf_bits.argtypes = [u64]
         L.hpeel_sf_words.restype = u64
@@ -427,6 +429,18 @@ def stats_from_device(stats) -> dict:
     """The hpeel_stats a device-driven call wrote (copies to the host)."""
     raw = bytes(stats.cpu().numpy().tobytes())
     return Stats.from_buffer_copy(raw[:ctypes.sizeof(Stats)]).as_dict()
+
+
+def probe_random_access(kind: int, n_ops: int, a, b=None, seed: int = 1) -> None:
+    """Random-access ceiling probe (hpeel_probe_random_access), enqueued on
+    the current stream: kind 0 random 64-bit atomicAdd into a, 1 random
+    8-byte load from a, 2 one peeled edge (record claim in a, two vertex
+    updates in b).  a and b are CUDA tensors used as raw memory."""
+    pa = _dev_ptr(a, "a")
+    pb = _dev_ptr(b, "b") if b is not None else None
+    _check(lib().hpeel_probe_random_access(kind, n_ops, pa, a.numel() * a.element_size(), pb,
+                                           0 if b is None else b.numel() * b.element_size(),
+                                           seed, _stream()))
 
 
 def kernel_launches() -> int:
