@@ -55,9 +55,9 @@ def byte_model(step, n, m, st):
         w = (8 + 16 + R * 8) * n
         return {"units": n, "word": w, "sector": w}
     if step == "apply_buckets":
-        # incidences read back; the vertex records are read and written once
-        # (the updates hit L2)
-        w = R * 8 * n + 16 * m
+        # refine: incidences read, written to their sub-buckets; apply: read
+        # again, accumulated in shared memory, each vertex record written once
+        w = 3 * R * 8 * n + 8 * m
         return {"units": n, "word": w, "sector": w}
     if step == "hash_edges":
         return {"units": n, "word": 24 * n, "sector": 24 * n}
@@ -80,6 +80,8 @@ def byte_model(step, n, m, st):
                   + cross * 64 + 16 * moves)
         return {"units": peeled, "word": word, "sector": sector}
     if step == "extract_claim":
+        # edge records read, claims written (the first pass's counts are
+        # taken on the way)
         return {"units": n, "word": 20 * n, "sector": 20 * n}
     if step == "emit_scatter":
         return {"units": n, "word": 12 * n, "sector": 12 * n}

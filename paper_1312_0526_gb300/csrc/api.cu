@@ -374,15 +374,21 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     out->list = Ll;
 
     if (!io.order && !io.claim) return HPEEL_OK;
-    {
+    if (!io.order) {
         ProfScope ps(L, "extract_claim");
         launch_extract_claim(L, rec, n, r, claim);
+        return check_launch("extract_claim");
     }
-    if (!io.order) return check_launch("extract_claim");
 
-    // Canonical order: stable sort by key = round, core edges key R.
+    // Canonical order: stable sort by key = round, core edges key R.  The
+    // first pass's histogram is taken while the claims are extracted.
     uint32_t *order = io.order;
     const uint32_t nkeys = R + 1;
+    {
+        ProfScope ps(L, "extract_claim");
+        launch_extract_claim_hist(L, rec, n, r, claim, R, std::min<uint32_t>(nkeys, kEmitBins),
+                                  hist);
+    }
     uint32_t base = 0, seg = 0;
     const uint32_t *src = nullptr;
     uint32_t *loff_h = nullptr;
@@ -391,7 +397,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         const uint32_t count = n - seg;
         const uint32_t nb = std::min<uint32_t>(nkeys - base, kEmitBins);
         const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
-        {
+        if (base > 0) {
             ProfScope ps(L, "emit_hist");
             launch_emit_hist(L, src, count, claim, base, R, nb, hist);
         }

@@ -64,6 +64,51 @@ k_emit_hist(const uint32_t *__restrict__ src, uint32_t count, const uint32_t *__
         hist[(uint64_t)b * tiles + blockIdx.x] = h[b];
 }
 
+// The first pass's histogram taken while the claims are extracted from the
+// edge records (one block per tile of kEmitTile consecutive edges): the
+// claim array is written once and not read back for the counts.
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_extract_claim_hist(const uint4 *__restrict__ rec, uint32_t n, uint32_t *__restrict__ claim,
+                     uint32_t core_key, uint32_t nbins, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[kEmitBins];
+    const uint32_t tiles = (n + kEmitTile - 1) / kEmitTile;
+    for (uint32_t b = threadIdx.x; b < nbins; b += kThreads) h[b] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * kEmitTile;
+    uint32_t c[kEmitItems];
+#pragma unroll
+    for (uint32_t q = 0; q < kEmitItems; q++) {
+        const uint64_t e = t0 + (uint64_t)q * kThreads + threadIdx.x;
+        uint32_t v[4];
+        c[q] = e < n ? load_record_stream<R>(rec, e, v) : 0u;
+    }
+#pragma unroll
+    for (uint32_t q = 0; q < kEmitItems; q++) {
+        const uint64_t e = t0 + (uint64_t)q * kThreads + threadIdx.x;
+        if (e < n) {
+            claim[e] = c[q];
+            atomicAdd(&h[emit_bin(c[q], 0u, core_key, nbins)], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < nbins; b += kThreads)
+        hist[(uint64_t)b * tiles + blockIdx.x] = h[b];
+}
+
+void launch_extract_claim_hist(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                               uint32_t *claim, uint32_t core_key, uint32_t nbins,
+                               uint32_t *hist) {
+    if (n == 0) return;
+    const uint32_t tiles = (n + kEmitTile - 1) / kEmitTile;
+    count_launch();
+    switch (r) {
+    case 2: k_extract_claim_hist<2><<<tiles, kThreads, 0, L.stream>>>(rec, n, claim, core_key, nbins, hist); break;
+    case 3: k_extract_claim_hist<3><<<tiles, kThreads, 0, L.stream>>>(rec, n, claim, core_key, nbins, hist); break;
+    case 4: k_extract_claim_hist<4><<<tiles, kThreads, 0, L.stream>>>(rec, n, claim, core_key, nbins, hist); break;
+    }
+}
+
 void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, const uint32_t *claim,
                       uint32_t base, uint32_t core_key, uint32_t nbins, uint32_t *hist) {
     if (count == 0) return;
@@ -83,7 +128,10 @@ k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
     const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t b = lane; b < kEmitBins; b += 32) wc[warp][b] = 0;
+    // bins past nbins hold no input: the counts and the scan stop at the
+    // first multiple of 32 at or above nbins
+    const uint32_t nb32 = (nbins + 31u) & ~31u;
+    for (uint32_t b = lane; b < nb32; b += 32) wc[warp][b] = 0;
     __syncwarp();
     // this warp's contiguous run of the tile, kEmitItems groups of 32
     const uint64_t t0 = (uint64_t)blockIdx.x * kEmitTile;
@@ -109,7 +157,7 @@ k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
     // then each warp's first slot in each bin (earlier warps first: stable)
     if (warp == 0) {
         uint32_t run = 0;
-        for (uint32_t b0 = 0; b0 < kEmitBins; b0 += 32) {
+        for (uint32_t b0 = 0; b0 < nb32; b0 += 32) {
             const uint32_t b = b0 + lane;
             uint32_t tot = 0;
 #pragma unroll

@@ -138,6 +138,9 @@ void launch_extract_claim(const Launch &L, const uint4 *rec, uint32_t n, uint32_
                           uint32_t *claim);
 
 // a7: one pass of the stable counting sort of edge ids by round.
+void launch_extract_claim_hist(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                               uint32_t *claim, uint32_t core_key, uint32_t nbins,
+                               uint32_t *hist);
 void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, const uint32_t *claim,
                       uint32_t base, uint32_t core_key, uint32_t nbins, uint32_t *hist);
 void launch_emit_scatter(const Launch &L, const uint32_t *src, uint32_t count,
