@@ -366,7 +366,7 @@ def peel_leg(n, steps, warmup):
     from paper_1312_0526_gb300 import inputs
 
     m = hp.num_vertices(n, GAMMA_MILLI, R)
-    keys = torch.from_numpy(inputs.keys(n, KEY_SEED).view(np.int64)).cuda()
+    keys = inputs.keys_torch(n, KEY_SEED)
     edges = hp.hash_edges(keys, m, R, HASH_SEED)
     del keys
     torch.cuda.empty_cache()
@@ -407,6 +407,69 @@ def peel_leg(n, steps, warmup):
     del edges, ws, res
     torch.cuda.empty_cache()
     return out
+
+
+MAX_N = 3_400_000_000
+
+
+def max_scale_leg(steps=2, warmup=1):
+    """The largest MPHF one GB300 builds: n = 3.4e9 keys (m = 4,182,000,000
+    vertices, just below the 2^32 vertex ids of the ABI), keys on the device,
+    the incidence build one part per pass.  Every key must peel and the
+    lookups of all keys must be a bijection onto [0, n) (checked)."""
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    n = MAX_N
+    m = hp.num_vertices(n, GAMMA_MILLI, R)
+    torch.cuda.empty_cache()
+    keys = inputs.keys_torch(n, KEY_SEED)
+    wsb = hp.mphf_workspace_size(n, GAMMA_MILLI)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    G = torch.empty((m + 31) // 32, dtype=torch.int64, device="cuda")
+    D = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device="cuda")
+    res = None
+    for _ in range(warmup):
+        res = hp.mphf_build(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D)
+    torch.cuda.synchronize()
+    hp.profile_reset()
+    hp.profile_enable(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        res = hp.mphf_build(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D)
+    b.record()
+    torch.cuda.synchronize()
+    hp.profile_enable(False)
+    prof = hp.profile_read()
+    ms = a.elapsed_time(b) / steps
+    del ws
+    torch.cuda.empty_cache()
+    flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    step = 1 << 28
+    out = torch.empty(step, dtype=torch.int32, device="cuda")
+    ok = True
+    for lo in range(0, n, step):
+        hi = min(n, lo + step)
+        hp.mphf_lookup(keys[lo:hi], res.stats["seed_used"], m, G, D, out=out[:hi - lo])
+        idx = out[:hi - lo].to(torch.int64) & 0xFFFFFFFF
+        if not bool((idx < n).all()):
+            ok = False
+            break
+        flags.index_fill_(0, idx, 1)
+    ok = ok and int(flags.sum(dtype=torch.int64)) == n
+    del keys, flags, out, G, D
+    torch.cuda.empty_cache()
+    return {"value": n / ms / 1e3, "unit": "Mkeys/s", "ms_per_step": ms, "steps": steps,
+            "n": n, "m": m, "rounds": res.stats["rounds"], "n_peeled": res.stats["n_peeled"],
+            "workspace_gb": wsb / 1e9, "workspace_bytes_per_key": wsb / n,
+            "lookup_bijection": ok,
+            "steps_ms": {k: v[1] / steps for k, v in sorted(prof.items())},
+            "config": {"workload": f"mphf-build n={n:.2e} r=3 gamma=1.23, keys on the device "
+                                   f"(SplitMix64 seed {KEY_SEED}), incidence build one part "
+                                   f"per pass"}}
 
 
 BATCH_B = 65536
@@ -572,6 +635,7 @@ def main():
     ap.add_argument("--no-peel-1e9", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-sf", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-general", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--max-scale", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--round-loop", default="graph", choices=["graph", "host"],
                     help="graph: rounds in a CUDA graph (default); host: one launch per round "
                          "(same kernels; for profilers that cannot see inside the graph)")
@@ -742,6 +806,9 @@ def main():
         general = general_leg(n, steps=3, warmup=1)
     if world == 1 and not args.no_peel_1e9:
         peel_1e9 = peel_leg(PEEL_N, steps=3, warmup=1)
+    max_scale = None
+    if world == 1 and args.max_scale:
+        max_scale = max_scale_leg()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -772,6 +839,7 @@ def main():
         "static_function": sf,
         "general_peel": general,
         "random_access": random_access,
+        "max_scale": max_scale,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -94,6 +94,13 @@ typedef struct hpeel_stats {
  *   bucket_sub_shift    log2 of the vertices one block accumulates in shared
  *                       memory in the L2-blocked build (0 = automatic:
  *                       min(13, bucket_shift - 9); at most 14).
+ *   bucket_part_passes  0 (default): automatic -- r-partite graphs of more
+ *                       than 2^30 edges run the L2-blocked build once per
+ *                       part (sec. 4.3: one part at a time), so its buckets
+ *                       hold one incidence per edge instead of r and the
+ *                       workspace shrinks by about 2 x 16 (r - 1) bytes per
+ *                       edge; 1: all parts in one pass; 2: one part per pass
+ *                       (general graphs always take one pass).
  * hpeel_set_tuning(NULL) restores the defaults.  Workspace sizes depend on
  * the tuning: query them after setting it.  Errors: HPEEL_ERR_INVALID_ARG.
  */
@@ -102,7 +109,8 @@ typedef struct hpeel_tuning {
     uint32_t bucket_min_vertices;
     uint32_t host_round_loop;
     uint32_t bucket_sub_shift;
-    uint32_t reserved[4];
+    uint32_t bucket_part_passes;
+    uint32_t reserved[3];
 } hpeel_tuning;
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t);
 void hpeel_get_tuning(hpeel_tuning *t);

@@ -52,7 +52,7 @@ class HpeelError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("bucket_shift", ctypes.c_uint32), ("bucket_min_vertices", ctypes.c_uint32),
                 ("host_round_loop", ctypes.c_uint32), ("bucket_sub_shift", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("bucket_part_passes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -474,7 +474,7 @@ def get_tuning() -> dict:
     lib().hpeel_get_tuning(ctypes.byref(t))
     return {"bucket_shift": t.bucket_shift, "bucket_min_vertices": t.bucket_min_vertices,
             "host_round_loop": t.host_round_loop,
-            "bucket_sub_shift": t.bucket_sub_shift}
+            "bucket_sub_shift": t.bucket_sub_shift, "bucket_part_passes": t.bucket_part_passes}
 
 
 def set_tuning(**kw) -> None:
@@ -485,7 +485,7 @@ def set_tuning(**kw) -> None:
     cur = get_tuning()
     cur.update(kw)
     t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["host_round_loop"],
-               cur["bucket_sub_shift"])
+               cur["bucket_sub_shift"], cur["bucket_part_passes"])
     _check(lib().hpeel_set_tuning(ctypes.byref(t)))
 
 

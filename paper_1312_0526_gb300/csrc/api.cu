@@ -53,7 +53,7 @@ int current_sms() {
 }
 
 // Process-wide tuning (hpeel_set_tuning); read by layouts and launches.
-hpeel_tuning g_tuning = {22u, 8u << 20, 0u, 0u, {0, 0, 0, 0}};
+hpeel_tuning g_tuning = {22u, 8u << 20, 0u, 0u, 0u, {0, 0, 0}};
 std::mutex g_tuning_mu;
 
 hpeel_tuning tuning() {
@@ -61,10 +61,11 @@ hpeel_tuning tuning() {
     return g_tuning;
 }
 
-// Workspace of one peel: edge records, vertex records, claim words, layer
-// list (one entry per edge, the shape of an edge record), incidence buckets
-// of the L2-blocked build (sharing space with the layer list, which is
-// written only after the build), layer table, order-sort scratch.
+// Workspace of one peel: edge records, vertex records, layer list (one entry
+// per edge, the shape of an edge record), the incidence buckets of the
+// L2-blocked build (sharing space with the layer list, which is written only
+// after the build), the sub-buckets (sharing space with the claim words and
+// the order-sort scratch, which are used only after the rounds), layer table.
 PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false) {
     PeelLayout p{};
     const hpeel_tuning tu = tuning();
@@ -78,7 +79,7 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false)
     p.bucketed = n > 0 && m >= tu.bucket_min_vertices;
     if (p.bucketed) {
         p.plan = bucket_plan(n, m, r, general ? 1u : r, tu.bucket_shift, tu.bucket_sub_shift,
-                             current_sms());
+                             current_sms(), tu.bucket_part_passes);
         // the bucketing kernel keeps three counters per chunk in shared memory
         if (p.plan.smem > (200u << 10)) p.bucketed = false;
     }
@@ -86,21 +87,30 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false)
     p.params = take(sizeof(RoundParams));
     p.rec = take((r == 4 ? 32 : 16) * n);
     p.state = take(8 * m);
-    p.claim = take(4 * n);
     const size_t ls = (r == 4 ? 32 : 16) * n;
     const size_t shared = std::max<size_t>(ls, p.bucketed ? p.plan.pair_bytes : 0);
     const size_t region = take(shared);
     p.L = region;
     p.pairs = region;
-    p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks * p.plan.regions : 0);
-    p.pairs2 = take(p.bucketed ? p.plan.pair2_bytes : 0);
-    p.fill2 = take(p.bucketed ? 4 * (size_t)p.plan.subs : 0);
+    p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks_pass * p.plan.regions : 0);
+    p.fill2 = take(p.bucketed ? 4 * (size_t)p.plan.subs_pass : 0);
     p.ovf = take(p.bucketed ? 8 * (size_t)p.plan.ovf_cap : 0);
     p.ovf_count = take(p.bucketed ? 4 : 0);
     p.loff = take(4 * ((size_t)p.max_rounds + 3));
+    // sub-buckets (build only) | claim words + order-sort scratch (after the rounds)
     const uint64_t tiles = (n + kEmitTile - 1) / kEmitTile;
-    p.hist = take(4 * kEmitBins * tiles);
-    p.scantmp = take(4 * scan_tmp_words(kEmitBins * tiles));
+    const size_t region2 = off;
+    size_t o2 = 0;
+    auto take2 = [&](size_t bytes) {
+        size_t o = o2;
+        o2 = align256(o2 + bytes);
+        return region2 + o;
+    };
+    p.claim = take2(4 * n);
+    p.hist = take2(4 * kEmitBins * tiles);
+    p.scantmp = take2(4 * scan_tmp_words(kEmitBins * tiles));
+    p.pairs2 = region2;
+    off = region2 + std::max<size_t>(o2, p.bucketed ? align256(p.plan.pair2_bytes) : 0);
     p.total = off;
     return p;
 }
@@ -286,16 +296,19 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
         uint32_t *fill2 = reinterpret_cast<uint32_t *>(ws + lay.fill2);
         Overflow ov{reinterpret_cast<uint2 *>(ws + lay.ovf),
                     reinterpret_cast<uint32_t *>(ws + lay.ovf_count), lay.plan.ovf_cap};
-        HP_CUDA(cudaMemsetAsync(fill2, 0, 4 * (size_t)lay.plan.subs, L.stream));
-        HP_CUDA(cudaMemsetAsync(ov.count, 0, 4, L.stream));
-        {
-            ProfScope ps(L, io.keys ? "hash_bucket" : "records_bucket");
-            launch_build_bucketed(L, lay.plan, io.keys, io.edges, n, r, io.fm, io.seed, P, rec,
-                                  pairs, fill, ov, ctl, io.general);
+        for (uint32_t pass = 0; pass < lay.plan.passes; pass++) {
+            HP_CUDA(cudaMemsetAsync(fill2, 0, 4 * (size_t)lay.plan.subs_pass, L.stream));
+            HP_CUDA(cudaMemsetAsync(ov.count, 0, 4, L.stream));
+            {
+                ProfScope ps(L, io.keys ? "hash_bucket" : "records_bucket");
+                launch_build_bucketed(L, lay.plan, io.keys, io.edges, n, r, io.fm, io.seed, P,
+                                      rec, pairs, fill, ov, ctl, io.general, nullptr, pass);
+            }
+            // every vertex record of the pass's part is written by the
+            // shared-memory apply
+            ProfScope ps(L, "apply_buckets");
+            launch_apply_buckets(L, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl, pass);
         }
-        // every vertex record is written by the shared-memory apply
-        ProfScope ps(L, "apply_buckets");
-        launch_apply_buckets(L, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl);
     } else {
         {
             ProfScope ps(L, "fill");
@@ -586,11 +599,14 @@ hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGrap
             uint32_t *fill2 = reinterpret_cast<uint32_t *>(pw + lay.fill2);
             Overflow ov{reinterpret_cast<uint2 *>(pw + lay.ovf),
                         reinterpret_cast<uint32_t *>(pw + lay.ovf_count), lay.plan.ovf_cap};
-            HP_CAP(cudaMemsetAsync(fill2, 0, 4 * (size_t)lay.plan.subs, s1));
-            HP_CAP(cudaMemsetAsync(ov.count, 0, 4, s1));
-            launch_build_bucketed(L1, lay.plan, a.keys, nullptr, n, 3, fm, a.seed, P, rec, pairs,
-                                  fill, ov, ctl, false, seed_dev);
-            launch_apply_buckets(L1, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl);
+            for (uint32_t pass = 0; pass < lay.plan.passes; pass++) {
+                HP_CAP(cudaMemsetAsync(fill2, 0, 4 * (size_t)lay.plan.subs_pass, s1));
+                HP_CAP(cudaMemsetAsync(ov.count, 0, 4, s1));
+                launch_build_bucketed(L1, lay.plan, a.keys, nullptr, n, 3, fm, a.seed, P, rec,
+                                      pairs, fill, ov, ctl, false, seed_dev, pass);
+                launch_apply_buckets(L1, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl,
+                                     pass);
+            }
             // an overflowed build is redone with direct updates (same result)
             HP_CAP(new_handle(s1, 0u, 0u, &h_ovf));
             launch_async_check_overflow(L1, ctl, h_ovf);
@@ -687,13 +703,16 @@ const char *hpeel_last_error(void) { return g_last_error.c_str(); }
 
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t) {
     g_last_error.clear();
-    hpeel_tuning v = {22u, 8u << 20, 0u, 0u, {0, 0, 0, 0}};
+    hpeel_tuning v = {22u, 8u << 20, 0u, 0u, 0u, {0, 0, 0}};
     if (t) {
         if (t->bucket_shift < 8 || t->bucket_shift > 30)
             return fail(HPEEL_ERR_INVALID_ARG, "bucket_shift %u outside [8, 30]", t->bucket_shift);
         if (t->bucket_sub_shift > 14 || (t->bucket_sub_shift && t->bucket_sub_shift > t->bucket_shift))
             return fail(HPEEL_ERR_INVALID_ARG, "bucket_sub_shift %u: need 0 or at most "
                         "min(14, bucket_shift)", t->bucket_sub_shift);
+        if (t->bucket_part_passes > 2)
+            return fail(HPEEL_ERR_INVALID_ARG, "bucket_part_passes %u: 0, 1 or 2",
+                        t->bucket_part_passes);
         v = *t;
     }
     std::lock_guard<std::mutex> lk(g_tuning_mu);
@@ -955,10 +974,11 @@ hpeel_status hpeel_mphf_build_async(const uint64_t *d_keys, uint64_t n, uint64_t
     HP_CUDA(cudaGetDevice(&dev));
     const hpeel_tuning tu = tuning();
     char keybuf[320];
-    snprintf(keybuf, sizeof keybuf, "mphf|%d|%p|%llu|%llu|%u|%u|%p|%p|%p|%p|%u|%u|%u|%d", dev,
-             (const void *)d_keys, (unsigned long long)n, (unsigned long long)seed, gamma_milli,
-             max_tries, (void *)d_G, (void *)d_rank_dir, (void *)d_stats, d_ws, tu.bucket_shift,
-             tu.bucket_min_vertices, tu.bucket_sub_shift, L.sms);
+    snprintf(keybuf, sizeof keybuf, "mphf|%d|%p|%llu|%llu|%u|%u|%p|%p|%p|%p|%u|%u|%u|%u|%d",
+             dev, (const void *)d_keys, (unsigned long long)n, (unsigned long long)seed,
+             gamma_milli, max_tries, (void *)d_G, (void *)d_rank_dir, (void *)d_stats, d_ws,
+             tu.bucket_shift, tu.bucket_min_vertices, tu.bucket_sub_shift, tu.bucket_part_passes,
+             L.sms);
     const std::string key(keybuf);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = g_graphs.find(key);

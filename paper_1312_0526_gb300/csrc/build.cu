@@ -15,7 +15,10 @@
 //   pass 2: one kernel walks the buckets in chunk order and adds
 //          (e << 32) + 1 to each vertex record (64-bit reductions, L2 hits).
 // A chunk is 2^shift consecutive vertices of one part of the r-partite
-// vertex set.  Region capacity covers the expected load with a wide margin;
+// vertex set.  Large graphs run the three passes once per part (sec. 4.3
+// builds the incidence lists one part at a time): position j's incidences
+// are bucketed and applied in pass j, so the buckets hold one incidence per
+// edge instead of r.  Region capacity covers the expected load with a wide margin;
 // an incidence that finds its region full is applied directly (same result,
 // random access), so any input is handled.
 #include <algorithm>
@@ -62,11 +65,19 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                    uint32_t n, FastMod fm, uint64_t seed, const uint64_t *seed_dev, BucketGeom g,
                    uint4 *__restrict__ rec,
                    uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov,
-                   Ctl *ctl) {
+                   Ctl *ctl, int pass_part) {
     constexpr int kInc = kTileEdges * R;
     if (FROM_KEYS && seed_dev) seed = *seed_dev;  // the seed of a device-driven attempt
     extern __shared__ uint32_t smem[];
-    const uint32_t C = (GEN ? 1u : (uint32_t)R) * g.chunks_per_part;
+    // pass_part < 0: every position's incidences, chunks of all parts; else
+    // only position pass_part's, chunks numbered inside that part
+    const uint32_t C = pass_part >= 0 ? g.chunks_per_part
+                                      : (GEN ? 1u : (uint32_t)R) * g.chunks_per_part;
+    const bool write_rec = pass_part <= 0;  // records are written by the first pass
+    auto in_pass = [&](int j) { return pass_part < 0 || j == pass_part; };
+    auto chunk_here = [&](uint32_t v, int j) {
+        return pass_part >= 0 ? (v - (uint32_t)j * g.P) >> g.shift : chunk_of<GEN>(v, j, g);
+    };
     const uint32_t Cp = (C + 1) & ~1u;
     uint32_t *hist = smem;            // C: tile count per chunk
     uint32_t *cur = hist + Cp;        // C: fill of this block's region of each chunk
@@ -131,13 +142,13 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                     }
                     if (!ok) raise_err(ctl, kDevBadVertex);
                 }
-                store_record<R>(rec, e, v, ok);
+                if (write_rec) store_record<R>(rec, e, v, ok);
             }
             inc[q] = ok;  // an invalid row adds nothing (the call fails)
 #pragma unroll
             for (int j = 0; j < R; j++) {
                 vv[q][j] = v[j];
-                rank[q][j] = ok ? atomicAdd(&hist[chunk_of<GEN>(v[j], j, g)], 1u) : 0u;
+                rank[q][j] = ok && in_pass(j) ? atomicAdd(&hist[chunk_here(v[j], j)], 1u) : 0u;
             }
         }
         __syncthreads();
@@ -164,7 +175,8 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             const uint32_t e = (uint32_t)(tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x);
 #pragma unroll
             for (int j = 0; j < R; j++) {
-                const uint32_t c = chunk_of<GEN>(vv[q][j], j, g);
+                if (!in_pass(j)) continue;
+                const uint32_t c = chunk_here(vv[q][j], j);
                 const uint32_t slot = toff[c] + rank[q][j];
                 stage[slot] = make_uint2(vv[q][j], e);
                 sch[slot] = c;
@@ -204,7 +216,7 @@ constexpr uint32_t kScanRegs = 4;  // sub-buckets per thread whose cursor stays 
 
 __global__ void __launch_bounds__(kThreads)
 k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ fill, BucketGeom g,
-                 uint32_t chunks, uint32_t regions, uint32_t sub_shift,
+                 uint32_t chunks, uint32_t chunk0, uint32_t regions, uint32_t sub_shift,
                  uint2 *__restrict__ pairs2, uint32_t *__restrict__ fill2, uint32_t cap2,
                  Overflow ov, Ctl *ctl) {
     extern __shared__ uint32_t smem[];
@@ -252,9 +264,10 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
     uint2 pn[kRefineItems];
     if (it < items) load_item(it, pn);
     while (it < items) {
-        const uint32_t c = (uint32_t)(it / tiles);
-        const uint32_t part = c / g.chunks_per_part;
-        const uint32_t base_v = part * g.P + (c % g.chunks_per_part) * (1u << g.shift);
+        const uint32_t c = (uint32_t)(it / tiles);  // chunk of this pass
+        const uint32_t cg = chunk0 + c;              // chunk of the whole build
+        const uint32_t part = cg / g.chunks_per_part;
+        const uint32_t base_v = part * g.P + (cg % g.chunks_per_part) * (1u << g.shift);
         const uint32_t tn = item_len(it);
         uint2 p[kRefineItems];
 #pragma unroll
@@ -339,13 +352,14 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
 // then every vertex record of the range is written once.
 __global__ void __launch_bounds__(1024)
 k_apply_smem(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill2, uint32_t cap2,
-             BucketGeom g, uint32_t sub_shift, unsigned long long *__restrict__ st) {
+             BucketGeom g, uint32_t sub_shift, uint32_t chunk0,
+             unsigned long long *__restrict__ st) {
     extern __shared__ uint32_t smem[];
     const uint32_t nv = 1u << sub_shift;
     uint32_t *deg = smem, *sum = smem + nv;
     const uint32_t S = 1u << (g.shift - sub_shift);
     const uint32_t s = blockIdx.x;
-    const uint32_t c = s / S, b = s % S;
+    const uint32_t c = chunk0 + s / S, b = s % S;  // chunk of the whole build
     const uint32_t part = c / g.chunks_per_part;
     const uint32_t base_v = part * g.P + (c % g.chunks_per_part) * (1u << g.shift) + b * nv;
     const uint32_t part_end = (part + 1) * g.P;
@@ -390,12 +404,17 @@ __global__ void k_apply_overflow(const uint2 *__restrict__ list, const uint32_t 
 }
 
 BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint32_t shift,
-                       uint32_t sub_shift, int sms) {
+                       uint32_t sub_shift, int sms, uint32_t part_passes) {
     BucketPlan b{};
+    // one part per pass: asked for (2), or automatic (0) above 2^30 edges;
+    // a general graph has one part and always takes one pass
+    const bool per_part = parts > 1 && (part_passes == 2 || (part_passes == 0 && n > (1ull << 30)));
+    b.passes = per_part ? parts : 1;
     const uint64_t P = m / parts;
     b.shift = shift;
     b.chunks_per_part = (uint32_t)((P + (1ull << shift) - 1) >> shift);
     b.chunks = parts * b.chunks_per_part;
+    b.chunks_pass = b.chunks / b.passes;
     // incidences per vertex of a part: one position per part when r-partite,
     // all r positions in the single part of a general graph
     const double per = (double)r / (double)parts;
@@ -408,7 +427,7 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
         P ? per * (double)n * (double)(1ull << shift) / (double)P / b.regions : 0.0;
     uint64_t cap = (uint64_t)(expect + 8.0 * std::sqrt(expect + 1.0) + 64.0);
     b.cap = (uint32_t)std::min<uint64_t>(cap, n);
-    b.pair_bytes = (uint64_t)b.chunks * b.regions * b.cap * 8;
+    b.pair_bytes = (uint64_t)b.chunks_pass * b.regions * b.cap * 8;
     // sub-buckets: 2^sub_shift vertices (default 2^13: 64 KiB of shared
     // memory for the apply's two 32-bit counters per vertex, 3 blocks per SM)
     b.sub_shift = sub_shift ? sub_shift : (shift > 9 ? shift - 9 : 0);
@@ -416,10 +435,11 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
     if (!sub_shift && b.sub_shift > 13) b.sub_shift = 13;
     if (b.sub_shift > shift) b.sub_shift = shift;
     b.subs = b.chunks << (shift - b.sub_shift);
+    b.subs_pass = b.subs / b.passes;
     const double expect2 = P ? per * (double)n * (double)(1ull << b.sub_shift) / (double)P : 0.0;
     uint64_t cap2 = (uint64_t)(expect2 + 8.0 * std::sqrt(expect2 + 1.0) + 256.0);
     b.cap2 = (uint32_t)std::min<uint64_t>(cap2, n);
-    b.pair2_bytes = (uint64_t)b.subs * b.cap2 * 8;
+    b.pair2_bytes = (uint64_t)b.subs_pass * b.cap2 * 8;
     b.ovf_cap = (uint32_t)std::max<uint64_t>(1u << 16, n / 16);
     b.smem = (size_t)(3 * ((b.chunks + 1) & ~1u)) * 4 + (size_t)kTileEdges * r * (8 + 4);
     b.parts = parts;
@@ -429,17 +449,19 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev) {
+                           Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev,
+                           uint32_t pass) {
     if (n == 0) return;
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
     const unsigned grid = b.regions;  // one bucket region per block and chunk
+    const int pass_part = b.passes > 1 ? (int)pass : -1;
 #define HP_BK(RR, FK)                                                                         \
     do {                                                                                      \
         auto kern = gen ? k_records_bucketed<RR, FK, true> : k_records_bucketed<RR, FK, false>; \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem); \
         count_launch();                                                                       \
         kern<<<grid, kThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, seed_dev, g, rec,  \
-                                                   pairs, fill, ov, ctl);                     \
+                                                   pairs, fill, ov, ctl, pass_part);          \
     } while (0)
     if (keys) {
         switch (r) {
@@ -459,22 +481,25 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
 
 void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
                           const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
-                          unsigned long long *st, Ctl *ctl) {
+                          unsigned long long *st, Ctl *ctl, uint32_t pass) {
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
+    const uint32_t chunk0 = b.passes > 1 ? pass * b.chunks_per_part : 0u;
     const uint32_t S = 1u << (b.shift - b.sub_shift);
     const size_t smem1 = (3 * (size_t)S + kWarps + kRefineTile) * 4 + (size_t)kRefineTile * 8;
     cudaFuncSetAttribute(k_refine_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     const uint64_t items =
-        (uint64_t)b.chunks * b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);
+        (uint64_t)b.chunks_pass * b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);
     const unsigned grid = (unsigned)std::min<uint64_t>(
         std::max<uint64_t>(items, 1), grid_resident(L, (const void *)k_refine_buckets, 8, smem1));
     count_launch();
     k_refine_buckets<<<grid, kThreads, smem1, L.stream>>>(
-        pairs, fill, g, b.chunks, b.regions, b.sub_shift, pairs2, fill2, b.cap2, ov, ctl);
+        pairs, fill, g, b.chunks_pass, chunk0, b.regions, b.sub_shift, pairs2, fill2, b.cap2, ov,
+        ctl);
     const size_t smem2 = (size_t)8 << b.sub_shift;
     cudaFuncSetAttribute(k_apply_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     count_launch();
-    k_apply_smem<<<b.subs, 1024, smem2, L.stream>>>(pairs2, fill2, b.cap2, g, b.sub_shift, st);
+    k_apply_smem<<<b.subs_pass, 1024, smem2, L.stream>>>(pairs2, fill2, b.cap2, g, b.sub_shift,
+                                                         chunk0, st);
     count_launch();
     k_apply_overflow<<<grid_fixed(L, 4), kThreads, 0, L.stream>>>(ov.list, ov.count, ov.cap, st);
 }

@@ -93,6 +93,9 @@ struct BucketPlan {
     uint64_t pair2_bytes;      // sub-bucket storage
     uint32_t ovf_cap;          // overflow list entries
     uint32_t parts;            // r (r-partite) or 1 (general graph)
+    uint32_t passes;           // 1, or parts (one part per pass)
+    uint32_t chunks_pass;      // chunks of one pass
+    uint32_t subs_pass;        // sub-buckets of one pass
 };
 // Incidences that found their bucket full (applied last).
 struct Overflow {
@@ -102,15 +105,21 @@ struct Overflow {
 };
 // parts: r for an r-partite graph (chunks never straddle parts), 1 for a
 // general graph (one part [0, m)).
+// part_passes: the tuning's bucket_part_passes (0 automatic, 1 one pass,
+// 2 one part per pass).  pair_bytes, pair2_bytes: the storage of one pass.
 BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint32_t shift,
-                       uint32_t sub_shift, int sms);
+                       uint32_t sub_shift, int sms, uint32_t part_passes);
+// Pass `pass` (0 .. passes - 1) of the bucketing; records are written by pass 0.
 void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t *keys,
                            const uint32_t *rows, uint32_t n, uint32_t r, FastMod fm,
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
-                           Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev = nullptr);
+                           Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev,
+                           uint32_t pass);
+// Refine and apply of the same pass (fill2 and the overflow count zeroed
+// before the pass's bucketing).
 void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
                           const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
-                          unsigned long long *st, Ctl *ctl);
+                          unsigned long long *st, Ctl *ctl, uint32_t pass);
 
 // A kernel of the round loop and its launch shape, for graph nodes.
 struct RoundLaunch {

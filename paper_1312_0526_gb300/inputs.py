@@ -46,6 +46,35 @@ def keys(n: int, seed: int = 1) -> np.ndarray:
     return splitmix64_stream(seed, n)
 
 
+def _signed(x: int) -> int:
+    x &= 2**64 - 1
+    return x - 2**64 if x >= 2**63 else x
+
+
+def keys_torch(n: int, seed: int = 1, device="cuda", chunk: int = 1 << 27):
+    """keys(n, seed) generated with torch int64 operations on ``device``
+    (two's-complement products wrap modulo 2^64; right shifts are made
+    logical with a mask), in chunks: the same values, without the host
+    array.  Returns a torch.int64 tensor holding the uint64 bit patterns."""
+    import torch
+
+    out = torch.empty(n, dtype=torch.int64, device=device)
+    golden, m1, m2 = _signed(0x9E3779B97F4A7C15), _signed(0xBF58476D1CE4E5B9), \
+        _signed(0x94D049BB133111EB)
+    s = _signed(seed)
+
+    def lsr(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        z = torch.arange(a + 1, b + 1, dtype=torch.int64, device=device) * golden + s
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        out[a:b] = z ^ lsr(z, 31)
+    return out
+
+
 def uniforms53(seed: int, n: int) -> np.ndarray:
     """float64[n] in [0, 1): top 53 bits of a SplitMix64 stream."""
     return (splitmix64_stream(seed, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)

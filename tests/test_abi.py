@@ -63,6 +63,24 @@ def test_workspace_sizes_grow_with_n(lib):
     assert hp.mphf_workspace_size(100_000) > b
 
 
+def test_one_part_per_pass_takes_a_smaller_workspace(lib):
+    # sec. 4.3's one part at a time: the L2-blocked build's buckets hold one
+    # incidence per edge instead of r
+    n = 10**6
+    m = hp.num_vertices(n)
+    try:
+        hp.set_tuning(bucket_shift=14, bucket_min_vertices=0, bucket_part_passes=1)
+        one = hp.peel_workspace_size(n, m)
+        hp.set_tuning(bucket_shift=14, bucket_min_vertices=0, bucket_part_passes=2)
+        per_part = hp.peel_workspace_size(n, m)
+    finally:
+        hp.set_tuning()
+    assert per_part < one - 20 * n
+    # automatic above 2^30 edges: about 51 B per edge at gamma = 1.23
+    n = 3 * 10**9
+    assert hp.peel_workspace_size(n, hp.num_vertices(n)) < 52 * n
+
+
 def test_binding_rejects_host_tensors(lib):
     torch = pytest.importorskip("torch")
     with pytest.raises(ValueError):

@@ -251,11 +251,51 @@ def test_mphf_parity_bucketed(small_buckets, n):
     assert np.array_equal(_u64(got.rank_dir), want.dir)
 
 
+@pytest.fixture
+def part_passes():
+    """The L2-blocked build with small chunks, one part per pass (the mode
+    graphs of more than 2^30 edges take by default)."""
+    hp.set_tuning(bucket_shift=10, bucket_min_vertices=0, bucket_part_passes=2)
+    yield
+    hp.set_tuning()
+
+
+@pytest.mark.parametrize("n,gamma,r", [(100_000, 1230, 3), (100_003, 1200, 3),
+                                       (50_000, 1300, 4), (20_000, 1500, 2), (1, 1230, 3),
+                                       (1025, 1230, 3)])
+def test_peel_parity_one_part_per_pass(part_passes, n, gamma, r):
+    m = oracle.num_vertices(n, gamma, r)
+    edges = oracle.hash_edges(inputs.keys(n, 6), m, r, 1)
+    _check_peel(edges, m)
+
+
+@pytest.mark.parametrize("span", [1024, 30_000])
+def test_peel_bucket_overflow_one_part_per_pass(part_passes, span):
+    n, P = 60_000, 40_000
+    rng = np.random.default_rng(10)
+    edges = np.stack([rng.integers(0, span, n) + j * P for j in range(3)], axis=1).astype(np.uint32)
+    _check_peel(edges, 3 * P)
+
+
+def test_mphf_parity_one_part_per_pass(part_passes):
+    keys = inputs.keys(100_000, 7)
+    want = oracle.mphf_build(keys, seed=1, max_tries=32)
+    got = hp.mphf_build(_dev(keys), seed=1, max_tries=32)
+    assert got.stats["seed_used"] == want.seed_used
+    assert np.array_equal(_u64(got.G), want.G)
+    assert np.array_equal(_u64(got.rank_dir), want.dir)
+    G, D, st = hp.mphf_build_async(_dev(keys), seed=1, max_tries=32)
+    assert hp.stats_from_device(st)["seed_used"] == want.seed_used
+    assert np.array_equal(_u64(G), want.G) and np.array_equal(_u64(D), want.dir)
+
+
 def test_tuning_rejects_bad_values():
     with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
         hp.set_tuning(bucket_shift=3)
     with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
         hp.set_tuning(bucket_sub_shift=15)
+    with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
+        hp.set_tuning(bucket_part_passes=3)
     hp.set_tuning()
     assert hp.get_tuning()["bucket_shift"] == 22
 

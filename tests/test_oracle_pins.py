@@ -43,6 +43,17 @@ def test_key_stream_published_vectors():
     assert len(np.unique(inputs.keys(100000))) == 100000
 
 
+def test_key_stream_torch_generator_is_the_same_stream():
+    torch = pytest.importorskip("torch")
+    t = inputs.keys_torch(3, 1234567, device="cpu").numpy().view(np.uint64)
+    assert [int(v) for v in t] == [6457827717110365317, 3203168211198807973,
+                                   9817491932198370423]
+    for seed in (1, 0, 2**63 + 5, 2**64 - 1):
+        a = inputs.keys(50_001, seed)
+        b = inputs.keys_torch(50_001, seed, device="cpu", chunk=4099).numpy().view(np.uint64)
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("n,g,r,m", [
     (100_000, 1230, 3, 123_000),
     (10**8, 1230, 3, 123_000_000),

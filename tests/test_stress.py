@@ -59,7 +59,7 @@ def test_full_size_parity(name):
     n, g, r, m = c["n"], c["gamma_milli"], c["r"], c["m"]
     assert hp.num_vertices(n, g, r) == m
     torch.cuda.empty_cache()
-    keys = torch.from_numpy(inputs.keys(n, c["key_seed"]).view(np.int64)).cuda()
+    keys = inputs.keys_torch(n, c["key_seed"])
     edges = hp.hash_edges(keys, m, r, c["hash_seed"])
     assert _digest_dev(edges) == c["edges_sha256"]
     res = hp.peel(edges, m, max_layers=1 << 16)
@@ -76,4 +76,68 @@ def test_full_size_parity(name):
         assert _digest_dev(got.G) == c["G_sha256"]
         assert _digest_dev(got.rank_dir) == c["rank_dir_sha256"]
     del keys
+    torch.cuda.empty_cache()
+
+
+def test_full_size_parity_one_part_per_pass():
+    # the same n = 1e9 workload with the incidence build run one part per
+    # pass (the mode graphs of more than 2^30 edges take by default)
+    c = CASES.get("n1e9_g1230_r3")
+    if c is None:
+        pytest.skip("no digests")
+    n, g, r, m = c["n"], c["gamma_milli"], c["r"], c["m"]
+    torch.cuda.empty_cache()
+    hp.set_tuning(bucket_part_passes=2)
+    try:
+        keys = inputs.keys_torch(n, c["key_seed"])
+        edges = hp.hash_edges(keys, m, r, c["hash_seed"])
+        res = hp.peel(edges, m, max_layers=1 << 16)
+        assert res.rounds == c["rounds"] and res.n_peeled == c["n_peeled"]
+        assert _digest_dev(res.order) == c["order_sha256"]
+        assert _digest_dev(res.claim) == c["claim_sha256"]
+        del edges, res
+        torch.cuda.empty_cache()
+        if "G_sha256" in c:
+            got = hp.mphf_build(keys, seed=c["hash_seed"], gamma_milli=g)
+            assert _digest_dev(got.G) == c["G_sha256"]
+            assert _digest_dev(got.rank_dir) == c["rank_dir_sha256"]
+            del got
+        del keys
+    finally:
+        hp.set_tuning()
+        torch.cuda.empty_cache()
+
+
+def test_largest_mphf_on_one_gpu():
+    # n = 3.4e9 keys: m = 4,182,000,000 vertices, just below the 2^32 vertex
+    # ids of the ABI; the build runs one part per pass (automatic above 2^30
+    # edges).  No oracle output exists at this size: the properties checked
+    # are the ones any size must have -- every key peeled, and the lookups of
+    # all keys a bijection onto [0, n).
+    n = 3_400_000_000
+    m = hp.num_vertices(n)
+    assert m < 2**32
+    free, total = torch.cuda.mem_get_info()
+    need = 8 * n + hp.mphf_workspace_size(n) + (m // 4) + (8 << 30)
+    if free < need:
+        pytest.skip(f"needs {need / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free")
+    torch.cuda.empty_cache()
+    keys = inputs.keys_torch(n, 21)
+    ws = torch.empty(hp.mphf_workspace_size(n), dtype=torch.uint8, device="cuda")
+    got = hp.mphf_build(keys, seed=1, max_tries=4, workspace=ws)
+    del ws
+    torch.cuda.empty_cache()
+    assert got.stats["n_peeled"] == n and got.stats["core_nonempty"] == 0
+    flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    step = 1 << 28
+    out = torch.empty(step, dtype=torch.int32, device="cuda")
+    for a in range(0, n, step):
+        b = min(n, a + step)
+        hp.mphf_lookup(keys[a:b], got.stats["seed_used"], m, got.G, got.rank_dir,
+                       out=out[:b - a])
+        idx = out[:b - a].to(torch.int64) & 0xFFFFFFFF
+        assert bool((idx < n).all())  # checked before it indexes anything
+        flags.index_fill_(0, idx, 1)
+    assert int(flags.sum(dtype=torch.int64)) == n
+    del keys, flags, out, got
     torch.cuda.empty_cache()
