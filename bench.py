@@ -744,39 +744,76 @@ def main():
         break
 
     # ---- end to end through the public API with host buffers: every step
-    # takes its keys from pinned host memory -- the hashing kernel reads them
-    # in place over the host link (the C ABI accepts a pinned host pointer) --
-    # and reads its g values and rank directory back.  The read-back runs on
-    # a second stream into double buffers, overlapping the next step.
-    copy_stream = torch.cuda.Stream()
+    # takes its keys from pinned host memory and reads its g values and rank
+    # directory back to pinned host memory.  Two ways, both timed:
+    #   "copy": a copy stream moves each step's keys into one of two device
+    #           buffers while the previous step builds (the build waits for
+    #           its copy; a buffer is refilled only after the build that read
+    #           it) -- how a stream of key sets is fed;
+    #   "in_place": the hashing kernel reads the keys in place over the host
+    #           link (the C ABI accepts a pinned host pointer), no copy.
+    # The read-back runs on a second stream into double buffers.
+    h2d_stream, copy_stream = torch.cuda.Stream(), torch.cuda.Stream()
     Gb, Db = [G, torch.empty_like(G)], [D, torch.empty_like(D)]
     G_h = [torch.empty_like(G, device="cpu").pin_memory() for _ in range(2)]
     D_h = [torch.empty_like(D, device="cpu").pin_memory() for _ in range(2)]
-    read = [None, None]
-    e2e_steps = max(1, min(args.steps, 5))
-    sync_all()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(e2e_steps):
-        b = i & 1
-        if read[b] is not None:
-            stream.wait_event(read[b])  # step i-2's results are on the host
-        hp.mphf_build(keys_h, HASH_SEED, GAMMA_MILLI, workspace=ws, G=Gb[b], rank_dir=Db[b],
-                      order=order)
-        built = torch.cuda.Event()
-        built.record(stream)
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(built)
-            G_h[b].copy_(Gb[b], non_blocking=True)
-            D_h[b].copy_(Db[b], non_blocking=True)
-            read[b] = torch.cuda.Event()
-            read[b].record(copy_stream)
-    stream.wait_stream(copy_stream)
-    e1.record(stream)
-    sync_all()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
-    for b in range(min(2, e2e_steps)):  # the pipelined steps built what the timed ones did
-        assert torch.equal(G_h[b], G.cpu()) and torch.equal(D_h[b], D.cpu())
+    kd = [keys, torch.empty_like(keys)]
+    e2e_steps = max(1, min(args.steps, 10))
+
+    def run_e2e(mode):
+        read, built_ev, copied = [None, None], [None, None], [None, None]
+
+        def enqueue_copy(i):
+            # step i's keys into kd[i % 2], once step i-2's build has read it
+            b = i & 1
+            with torch.cuda.stream(h2d_stream):
+                h2d_stream.wait_event(e0)
+                if built_ev[b] is not None:
+                    h2d_stream.wait_event(built_ev[b])
+                kd[b].copy_(keys_h, non_blocking=True)
+                copied[b] = torch.cuda.Event()
+                copied[b].record(h2d_stream)
+
+        sync_all()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if mode == "copy":
+            enqueue_copy(0)
+        for i in range(e2e_steps):
+            b = i & 1
+            if mode == "copy":
+                # the build call returns when its step is done, so the next
+                # step's copy is queued first and runs while this one builds
+                if i + 1 < e2e_steps:
+                    enqueue_copy(i + 1)
+                stream.wait_event(copied[b])
+                src = kd[b]
+            else:
+                src = keys_h
+            if read[b] is not None:
+                stream.wait_event(read[b])  # step i-2's results are on the host
+            hp.mphf_build(src, HASH_SEED, GAMMA_MILLI, workspace=ws, G=Gb[b], rank_dir=Db[b],
+                          order=order)
+            built = torch.cuda.Event()
+            built.record(stream)
+            built_ev[b] = built
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(built)
+                G_h[b].copy_(Gb[b], non_blocking=True)
+                D_h[b].copy_(Db[b], non_blocking=True)
+                read[b] = torch.cuda.Event()
+                read[b].record(copy_stream)
+        stream.wait_stream(copy_stream)
+        stream.wait_stream(h2d_stream)
+        e1.record(stream)
+        sync_all()
+        for b in range(min(2, e2e_steps)):  # the pipelined steps built what the timed ones did
+            assert torch.equal(G_h[b], G.cpu()) and torch.equal(D_h[b], D.cpu())
+        return max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
+
+    e2e_ms = run_e2e("copy")
+    e2e_in_place_ms = run_e2e("in_place")
+    del kd
 
     if rank != 0:
         if dist:
@@ -799,6 +836,15 @@ def main():
     random_access = None
     if world == 1:
         random_access = random_access_leg(n, m, prof["rounds"][1] / args.steps)
+        if roof is not None and roof["kernel"] == "rounds":
+            # the rounds against the rate the memory system serves their own
+            # access pattern alone (one record claim + two vertex updates per
+            # peeled edge), next to the copy-bandwidth fraction above
+            roof["random_access_ceiling"] = {
+                "g_edges_per_s": random_access["peeled_edge"]["g_per_s"],
+                "achieved_g_edges_per_s": random_access["rounds_g_edges_per_s"],
+                "frac": random_access["rounds_vs_peeled_edge_pattern"],
+                "source": "random_access leg (hpeel_probe_random_access kind 2)"}
     if world == 1 and not args.no_sf:
         sf = sf_leg(n, steps=3, warmup=1)
     general = None
@@ -828,9 +874,15 @@ def main():
         "e2e": {"value": aggregate_medges(n, world, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": n * 8,
                 "d2h_bytes_per_step": (G.numel() + D.numel()) * 8, "ms_per_step": e2e_ms,
-                "copies": "keys read in place from pinned host memory by the hashing "
-                          "kernel (over the host link, every step); g values and rank "
-                          "directory copied back to pinned host buffers on a second stream"},
+                "steps": e2e_steps,
+                "copies": "every step's keys copied from pinned host memory into one of "
+                          "two device buffers on a copy stream while the previous step "
+                          "builds (the first copy is not overlapped); g values and rank "
+                          "directory copied back to pinned host buffers on a second stream",
+                "in_place": {"value": aggregate_medges(n, world, e2e_in_place_ms),
+                             "ms_per_step": e2e_in_place_ms,
+                             "copies": "keys read in place from pinned host memory by the "
+                                       "hashing kernel over the host link, no copy"}},
         "steps_ms": {k: v[1] / args.steps for k, v in sorted(prof.items())},
         "batched": batched,
         "serving": serving,
