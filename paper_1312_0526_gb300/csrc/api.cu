@@ -463,6 +463,29 @@ hpeel_status peel_core(const Launch &L, const PeelIO &io, uint32_t n, uint32_t m
 // (a while loop over layers) and the rank directory, then the stats.
 // ---------------------------------------------------------------------------
 
+// A second stream and an event of this host thread on the current device:
+// work that does not depend on what the caller's stream runs meanwhile goes
+// there (the MWHC assignment beside the order sort).
+struct SideStream {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int dev = -1;
+};
+
+hpeel_status side_stream(SideStream **out) {
+    thread_local SideStream ss[8];
+    int d = 0;
+    HP_CUDA(cudaGetDevice(&d));
+    SideStream &s = ss[d & 7];
+    if (s.dev != d) {
+        HP_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+        HP_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+        s.dev = d;
+    }
+    *out = &s;
+    return HPEEL_OK;
+}
+
 // Capture streams of this thread (one per nesting depth of the graph).
 cudaStream_t capture_stream(int depth) {
     thread_local cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -909,12 +932,20 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
         h_stats->hinge_moves = po.moves;
         }
         if (po.n_peeled < n) continue;
+        // The rounds are complete (the peel read their outcome back), so the
+        // assignment and the rank directory run on a second stream beside the
+        // order sort the peel left queued on the caller's stream: they share
+        // no memory (layer list, layer table, G, rank scratch vs claim words,
+        // sort scratch, order).
+        SideStream *side = nullptr;
+        HP_TRY(side_stream(&side));
+        const Launch L2{side->stream, L.sms};
         // a8: reverse layer order
         const uint64_t words = (m + 31) / 32;
-        HP_CUDA(cudaMemsetAsync(d_G, 0, 8 * words, L.stream));
+        HP_CUDA(cudaMemsetAsync(d_G, 0, 8 * words, L2.stream));
         for (int64_t t = (int64_t)po.rounds - 1; t >= 0; t--) {
-            ProfScope ps(L, "assign");
-            launch_assign_layer(L, po.list, po.loff, (uint32_t)t, (uint32_t)(m / 3), d_G);
+            ProfScope ps(L2, "assign");
+            launch_assign_layer(L2, po.list, po.loff, (uint32_t)t, (uint32_t)(m / 3), d_G);
         }
         HP_TRY(check_launch("assign"));
         // a9: rank directory
@@ -922,12 +953,14 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
         uint32_t *scn = reinterpret_cast<uint32_t *>(ws + lay.rank_scan);
         uint32_t *tmp = reinterpret_cast<uint32_t *>(ws + lay.rank_tmp);
         {
-            ProfScope ps(L, "rank");
-            launch_rank_counts(L, d_G, m, cnt);
-            launch_scan_u32(L, cnt, scn, blocks, tmp);
-            launch_widen_dir(L, scn, cnt, blocks, d_rank_dir);
+            ProfScope ps(L2, "rank");
+            launch_rank_counts(L2, d_G, m, cnt);
+            launch_scan_u32(L2, cnt, scn, blocks, tmp);
+            launch_widen_dir(L2, scn, cnt, blocks, d_rank_dir);
         }
         HP_TRY(check_launch("rank"));
+        HP_CUDA(cudaEventRecord(side->done, L2.stream));
+        HP_CUDA(cudaStreamWaitEvent(L.stream, side->done, 0));
         HP_CUDA(cudaStreamSynchronize(L.stream));
         prof_flush();
         if (h_stats) h_stats->seed_used = s;
