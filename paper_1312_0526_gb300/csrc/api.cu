@@ -473,10 +473,11 @@ struct SideStream {
 };
 
 hpeel_status side_stream(SideStream **out) {
-    thread_local SideStream ss[8];
+    thread_local SideStream ss[64];
     int d = 0;
     HP_CUDA(cudaGetDevice(&d));
-    SideStream &s = ss[d & 7];
+    if (d < 0 || d >= 64) return fail(HPEEL_ERR_INVALID_ARG, "device %d out of range", d);
+    SideStream &s = ss[d];
     if (s.dev != d) {
         HP_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
         HP_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
