@@ -22,7 +22,7 @@ _lock = threading.Lock()
 CANDIDATES = [
     {"threads": t, "ctas_per_sm": c}
     for t in (128, 256, 512)
-    for c in (1, 2, 3, 4)
+    for c in (1, 2, 3, 4, 6, 8)
     if t * c <= 2048
 ]
 

@@ -15,10 +15,13 @@
 // A bucket's state lives in shared memory when it fits: vertex records of 32
 // bits (degree in the low 16, sum of incident local edge ids mod 2^16 in the
 // high 16; a bucket in shared memory has far fewer than 2^16 edges, so the
-// degree never carries into the sum), edges packed as three 17-bit local
-// vertex ids.  Larger buckets use a per-CTA region of the workspace with 64-bit
-// records.  No block waits on another; the only cross-block state is the
-// bucket counter.
+// degree never carries into the sum), claim words, the layers as 16-bit local
+// edge ids, the layer table and the g values -- no edge rows: an edge's
+// vertices are hashed again from its key (read through the cache) when a
+// round or the assignment needs them, which leaves about 11 bytes of shared
+// memory per key.  Larger buckets use a per-CTA region of the workspace with
+// 64-bit records.  No block waits on another; the only cross-block state is
+// the bucket counter.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -28,7 +31,7 @@ namespace hp {
 constexpr uint32_t kBatchMaxEdges = 65536;        // per bucket
 constexpr uint32_t kBatchMaxVertices = (1u << 17) - 1;  // packed 17-bit local ids
 constexpr uint32_t kBucketUnclaimed = 0xFFFFFFFFu;
-constexpr uint32_t kSmemRounds = 1024;            // layer table of a bucket in shared memory
+constexpr uint32_t kSmemRounds = 256;             // layer table of a bucket in shared memory
 
 // Device copy of hpeel_num_vertices for r = 3.
 __device__ __forceinline__ uint32_t bucket_vertices(uint32_t n, uint32_t gamma_milli) {
@@ -36,13 +39,13 @@ __device__ __forceinline__ uint32_t bucket_vertices(uint32_t n, uint32_t gamma_m
     return (uint32_t)((gn + 2) / 3 * 3);
 }
 
-__device__ __forceinline__ uint64_t pack3(uint32_t a, uint32_t b, uint32_t c) {
-    return (uint64_t)a | ((uint64_t)b << 17) | ((uint64_t)c << 34);
-}
-__device__ __forceinline__ void unpack3(uint64_t w, uint32_t (&v)[3]) {
-    v[0] = (uint32_t)(w & 0x1FFFFu);
-    v[1] = (uint32_t)((w >> 17) & 0x1FFFFu);
-    v[2] = (uint32_t)((w >> 34) & 0x1FFFFu);
+// The three vertices of a bucket's edge: its key hashed with the bucket's
+// seed into the three parts (the same hash as the single-graph path).
+__device__ __forceinline__ void bucket_edge(uint64_t k, uint64_t seed, const FastMod &fm,
+                                            uint32_t P, uint32_t (&v)[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+        v[j] = (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) + (uint32_t)j * P;
 }
 
 // Vertex record arithmetic: degree in the low W bits, id sum in the rest.
@@ -71,10 +74,10 @@ struct VRec<unsigned long long> {
 template <typename T>
 struct BucketState {
     T *rec;          // [m]
-    uint64_t *edge;  // [n] packed local vertex ids
     uint32_t *claim; // [n] (round << 2) | hinge
-    uint32_t *L;     // [n] layers appended
+    uint16_t *L;     // [n] layers appended (local edge ids < 2^16)
     uint32_t *loff;  // [rcap + 2] layer starts
+    uint32_t *cnt;   // [rcap + 2] running starts of the order pass
     uint32_t *G;     // [ceil(m / 16)] 2-bit g values (MPHF)
     uint32_t rcap;   // rounds the loff table holds
 };
@@ -102,8 +105,8 @@ __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15;
 // rcap + 2 entries.
 __host__ __device__ inline size_t bucket_bytes(uint32_t n, uint32_t m, uint32_t rec_bytes,
                                                uint32_t rcap) {
-    return a16((size_t)m * rec_bytes) + a16((size_t)n * 8) + a16((size_t)n * 4) +
-           a16((size_t)n * 4) + a16(((size_t)rcap + 2) * 4) + a16(((size_t)m + 15) / 16 * 4);
+    return a16((size_t)m * rec_bytes) + a16((size_t)n * 4) + a16((size_t)n * 2) +
+           2 * a16(((size_t)rcap + 2) * 4) + a16(((size_t)m + 15) / 16 * 4);
 }
 
 template <typename T>
@@ -112,13 +115,13 @@ __device__ BucketState<T> carve(char *base, uint32_t n, uint32_t m, uint32_t rca
     size_t o = 0;
     s.rec = reinterpret_cast<T *>(base + o);
     o += a16((size_t)m * sizeof(T));
-    s.edge = reinterpret_cast<uint64_t *>(base + o);
-    o += a16((size_t)n * 8);
     s.claim = reinterpret_cast<uint32_t *>(base + o);
     o += a16((size_t)n * 4);
-    s.L = reinterpret_cast<uint32_t *>(base + o);
-    o += a16((size_t)n * 4);
+    s.L = reinterpret_cast<uint16_t *>(base + o);
+    o += a16((size_t)n * 2);
     s.loff = reinterpret_cast<uint32_t *>(base + o);
+    o += a16(((size_t)rcap + 2) * 4);
+    s.cnt = reinterpret_cast<uint32_t *>(base + o);
     o += a16(((size_t)rcap + 2) * 4);
     s.G = reinterpret_cast<uint32_t *>(base + o);
     s.rcap = rcap;
@@ -126,7 +129,7 @@ __device__ BucketState<T> carve(char *base, uint32_t n, uint32_t m, uint32_t rca
 }
 
 // Warp-aggregated append to a block-local list (shared cursor).
-__device__ __forceinline__ void cta_append(uint32_t *cursor, uint32_t *list, bool pred,
+__device__ __forceinline__ void cta_append(uint32_t *cursor, uint16_t *list, bool pred,
                                            uint32_t v) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, pred);
@@ -135,7 +138,7 @@ __device__ __forceinline__ void cta_append(uint32_t *cursor, uint32_t *list, boo
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(cursor, (uint32_t)__popc(ballot));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = v;
+    if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = (uint16_t)v;
 }
 
 // The whole path for one bucket.  Every thread of the block calls it.
@@ -160,14 +163,13 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
     __syncthreads();
     const FastMod fm{P, magic};
     const uint64_t seed = b;
+    // the bucket's keys, read through the cache: hashed here and again
+    // whenever an edge's vertices are needed
+    const uint64_t *keys = a.keys + key0;
     // hash + AddEdge
     for (uint32_t e = tid; e < n; e += T_) {
-        const uint64_t k = __ldcs(a.keys + key0 + e);
         uint32_t v[3];
-#pragma unroll
-        for (int j = 0; j < 3; j++)
-            v[j] = (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) + (uint32_t)j * P;
-        s.edge[e] = pack3(v[0], v[1], v[2]);
+        bucket_edge(__ldg(keys + e), seed, fm, P, v);
 #pragma unroll
         for (int j = 0; j < 3; j++) atomicAdd(s.rec + v[j], V::unit(e));
     }
@@ -209,7 +211,7 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
                 const uint32_t e = s.L[i];
                 const uint32_t h = s.claim[e] & 3u;
                 uint32_t v[3];
-                unpack3(s.edge[e], v);
+                bucket_edge(__ldg(keys + e), seed, fm, P, v);
 #pragma unroll
                 for (int k = 0; k < 2; k++) {
                     const int j = k + ((uint32_t)k >= h ? 1 : 0);
@@ -238,11 +240,11 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
     uint32_t *out = a.order + key0;
     if (too_many) return false;  // block-uniform
     // canonical order: one warp walks the edges in id order (stable), the
-    // running start of every layer in loff[0..R], the core after them
+    // running start of every layer in cnt[0..R], the core after them
     if (tid < 32) {
         const uint32_t lane = tid;
-        uint32_t *cnt = s.loff;  // reused as running starts
-        if (lane == 0) cnt[R] = peeled;
+        uint32_t *cnt = s.cnt;
+        for (uint32_t r = lane; r <= R; r += 32) cnt[r] = r < R ? s.loff[r] : peeled;
         __syncwarp();
         for (uint32_t e0 = 0; e0 < n; e0 += 32) {
             const uint32_t e = e0 + lane;
@@ -264,30 +266,19 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
         if (a.rounds) a.rounds[b] = R;
     }
     __syncthreads();
-    // MWHC g values (sec. 3), last layer first.  The order pass used loff as
-    // its counters; L holds the layers in round order, so each layer's start
-    // is found again by binary search on the rounds of L's entries.
+    // MWHC g values (sec. 3), last layer first: layer r is L[loff[r],
+    // loff[r + 1]).
     if (a.G && peeled == n) {
         const uint32_t words = (m + 15) / 16;
         for (uint32_t w = tid; w < words; w += T_) s.G[w] = 0;
         __syncthreads();
-        uint32_t hi = n;  // L[lo, hi) is layer r
         for (int32_t r = (int32_t)R - 1; r >= 0; r--) {
-            // the layer's start: binary search for the first entry of round r
-            uint32_t lo_ = 0, hi_ = hi;
-            while (lo_ < hi_) {
-                const uint32_t mid = (lo_ + hi_) / 2;
-                if ((s.claim[s.L[mid]] >> 2) < (uint32_t)r)
-                    lo_ = mid + 1;
-                else
-                    hi_ = mid;
-            }
-            const uint32_t lo = lo_;
+            const uint32_t lo = s.loff[r], hi = s.loff[r + 1];
             for (uint32_t i = lo + tid; i < hi; i += T_) {
                 const uint32_t e = s.L[i];
                 const uint32_t h = s.claim[e] & 3u;
                 uint32_t v[3];
-                unpack3(s.edge[e], v);
+                bucket_edge(__ldg(keys + e), seed, fm, P, v);
                 uint32_t sum = 0;
 #pragma unroll
                 for (int j = 0; j < 3; j++)
@@ -298,7 +289,6 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
                 atomicOr(s.G + (vh >> 4), (val ? val : 3u) << (2 * (vh & 15)));
             }
             __syncthreads();
-            hi = lo;
         }
         uint64_t *dst = a.G + a.G_off[b];
         const uint32_t words64 = (m + 31) / 32;
