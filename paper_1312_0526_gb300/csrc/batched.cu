@@ -19,9 +19,9 @@
 // edge ids, the layer table and the g values -- no edge rows: an edge's
 // vertices are hashed again from its key (read through the cache) when a
 // round or the assignment needs them, which leaves about 11 bytes of shared
-// memory per key.  Larger buckets use a per-CTA region of the workspace with
-// 64-bit records.  No block waits on another; the only cross-block state is
-// the bucket counter.
+// memory per key.  Larger buckets use a per-CTA region of the workspace,
+// with 32-bit records too unless the bucket has 2^16 - 1 edges or more.  No
+// block waits on another; the only cross-block state is the bucket counter.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -128,9 +128,10 @@ __device__ BucketState<T> carve(char *base, uint32_t n, uint32_t m, uint32_t rca
     return s;
 }
 
-// Warp-aggregated append to a block-local list (shared cursor).
-__device__ __forceinline__ void cta_append(uint32_t *cursor, uint16_t *list, bool pred,
-                                           uint32_t v) {
+// Warp-aggregated append to a block-local list: slot list_base + the value
+// of a shared counter.
+__device__ __forceinline__ void cta_append(uint32_t *cursor, uint16_t *list, uint32_t list_base,
+                                           bool pred, uint32_t v) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, pred);
     if (!ballot) return;
@@ -138,7 +139,7 @@ __device__ __forceinline__ void cta_append(uint32_t *cursor, uint16_t *list, boo
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(cursor, (uint32_t)__popc(ballot));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = (uint16_t)v;
+    if (pred) list[list_base + base + __popc(ballot & ((1u << lane) - 1u))] = (uint16_t)v;
 }
 
 // The whole path for one bucket.  Every thread of the block calls it.
@@ -187,22 +188,29 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
                 take = atomicMin(s.claim + e, j) == kBucketUnclaimed;
             }
         }
-        cta_append(&lcur, s.L, take, e);
+        cta_append(&lcur, s.L, 0u, take, e);
     }
+    // Rounds, one block barrier each: round t appends layer t + 1 from its
+    // start le through counter t mod 3.  Every thread reads that counter just
+    // after the round's barrier; the counter round t + 1 will use was last
+    // read before the previous barrier, so thread 0 clears it during round t.
+    uint32_t *cnt3 = sh + 4;  // sh[4..6]
     __syncthreads();
     if (tid == 0) {
         s.loff[0] = 0;
         s.loff[1] = lcur;
+        cnt3[0] = cnt3[1] = cnt3[2] = 0;
     }
     __syncthreads();
-    uint32_t t = 0;
+    uint32_t t = 0, lb = 0, le = s.loff[1];
     bool too_many = false;
-    while (s.loff[t + 1] > s.loff[t]) {
+    while (le > lb) {
         if (t + 2 > s.rcap) {  // more rounds than the table holds (block-uniform)
             too_many = true;
             break;
         }
-        const uint32_t lb = s.loff[t], le = s.loff[t + 1];
+        uint32_t *cur = cnt3 + t % 3;
+        if (tid == 0) cnt3[(t + 1) % 3] = 0;
         for (uint32_t i0 = lb; i0 < le; i0 += T_) {
             const uint32_t i = i0 + tid;
             bool take[2] = {false, false};
@@ -226,16 +234,18 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
                     }
                 }
             }
-            cta_append(&lcur, s.L, take[0], f[0]);
-            cta_append(&lcur, s.L, take[1], f[1]);
+            cta_append(cur, s.L, le, take[0], f[0]);
+            cta_append(cur, s.L, le, take[1], f[1]);
         }
         __syncthreads();
-        if (tid == 0) s.loff[t + 2] = lcur;
-        __syncthreads();
+        const uint32_t next = le + *(volatile uint32_t *)cur;
+        if (tid == 0) s.loff[t + 2] = next;
+        lb = le;
+        le = next;
         t++;
     }
     const uint32_t R = t;
-    const uint32_t peeled = s.loff[R];
+    const uint32_t peeled = lb;  // loff[R]: the empty layer R starts where L ends
     __syncthreads();
     uint32_t *out = a.order + key0;
     if (too_many) return false;  // block-uniform
@@ -337,7 +347,12 @@ __global__ void k_batched(BatchArgs a) {
         bool done = false;
         if (n < 0xFFFFu && bucket_bytes(n, m, 4, rcap_s) <= a.smem_bytes)
             done = run_bucket<uint32_t>(a, b, carve<uint32_t>(smem, n, m, rcap_s), n, m, sh);
-        if (!done)  // rounds never exceed n + 1 layer starts: always fits
+        // rounds never exceed n + 1 layer starts: the global region always
+        // fits; its records are 32 bits when the 16-bit fields hold the
+        // bucket (fewer than 2^16 - 1 edges), as in shared memory
+        if (!done && n < 0xFFFFu)
+            done = run_bucket<uint32_t>(a, b, carve<uint32_t>(region, n, m, n + 1), n, m, sh);
+        if (!done)
             run_bucket<unsigned long long>(
                 a, b, carve<unsigned long long>(region, n, m, n + 1), n, m, sh);
     }

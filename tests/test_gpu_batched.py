@@ -77,9 +77,11 @@ def _check_all(keys, off, res, with_g=False, gamma=1230):
 
 def test_batched_parity_lognormal_buckets():
     # lognormal sizes plus edge cases: empty, 1..3 keys (tiny m, 2-cores),
-    # buckets beyond shared memory (global path), the 65,536-key maximum and
-    # one bucket over the limit
-    sizes, keys, off = _workload(extra_sizes=[0, 1, 2, 3, 64, 4097, 20000, 65536, 70000])
+    # buckets beyond shared memory (global path, 32-bit records below 65,535
+    # keys, 64-bit from there), the 65,536-key maximum and one bucket over
+    # the limit
+    sizes, keys, off = _workload(extra_sizes=[0, 1, 2, 3, 64, 4097, 20000, 65534, 65535, 65536,
+                                              70000])
     res = _run(keys, off)
     _check_all(keys, off, res)
 
