@@ -104,7 +104,8 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                     in[q][kWords - 1] = (uint32_t)(k >> 32);
                 } else {
 #pragma unroll
-                    for (int j = 0; j < kWords; j++) in[q][j] = __ldcs(rows + e * R + j);
+                    for (int j = 0; j < kWords; j++)
+                        if (write_rec || j == pass_part) in[q][j] = __ldcs(rows + e * R + j);
                 }
             }
         }
@@ -130,13 +131,16 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             if (ok) {
                 if (FROM_KEYS) {
                     const uint64_t k = ((uint64_t)in[q][kWords - 1] << 32) | in[q][0];
+                    // a pass that writes no records needs only its own position
 #pragma unroll
                     for (int j = 0; j < R; j++)
-                        v[j] = (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) +
-                               (uint32_t)j * g.P;
+                        if (write_rec || j == pass_part)
+                            v[j] = (uint32_t)fastmod(mix64(k ^ (seed + (uint64_t)j)), fm) +
+                                   (uint32_t)j * g.P;
                 } else {
 #pragma unroll
                     for (int j = 0; j < R; j++) {
+                        if (!write_rec && j != pass_part) continue;  // checked by pass 0
                         v[j] = in[q][j];
                         ok &= (v[j] - (GEN ? 0u : (uint32_t)j * g.P)) < g.P;
                     }
