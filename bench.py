@@ -585,6 +585,36 @@ def batched_leg(steps, warmup):
 SERVE_REQUESTS = 200
 
 
+def batched_probe(tuning: str):
+    """One warm-up and one timed call of the batched form on the batched
+    leg's workload with a fixed launch shape ("THREADSxCTAS", no autotuning,
+    no g values): a short, fixed launch sequence for a profiler."""
+    import numpy as np
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    t, c = (int(x) for x in tuning.split("x"))
+    tun = {"threads": t, "ctas_per_sm": c}
+    sizes = inputs.lognormal_bucket_sizes(BATCH_B, median=2000, sigma=0.92, lo=64, hi=65536,
+                                          seed=3)
+    keys, off = inputs.bucketed_keys(sizes, seed=2)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    do = torch.from_numpy(off.view(np.int64)).cuda()
+    ws = torch.empty(hp.batched_workspace_size(BATCH_B, GAMMA_MILLI, tun), dtype=torch.uint8,
+                     device="cuda")
+    res = hp.peel_batched(dk, do, GAMMA_MILLI, tuning=tun, workspace=ws)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    hp.peel_batched(dk, do, GAMMA_MILLI, tuning=tun, workspace=ws, out=res)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"batched_probe_ms": a.elapsed_time(b), "tuning": tun,
+                      "edges": int(off[-1])}), flush=True)
+
+
 def serving_leg():
     """Serving: MPHF build requests with Poisson arrivals, key-set sizes
     log-uniform 1e3..1e7 (SplitMix64 keys, seed 1000 + request), gamma 1.23;
@@ -670,6 +700,7 @@ def main():
     ap.add_argument("--no-sf", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-general", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--max-scale", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--batched-probe", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--round-loop", default="graph", choices=["graph", "host"],
                     help="graph: rounds in a CUDA graph (default); host: one launch per round "
                          "(same kernels; for profilers that cannot see inside the graph)")
@@ -696,6 +727,9 @@ def main():
     if dist:
         dist.barrier()
     hp.lib()
+    if args.batched_probe:
+        batched_probe(args.batched_probe)
+        return 0
 
     if args.round_loop == "host":
         hp.set_tuning(host_round_loop=1)
