@@ -226,11 +226,11 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
     extern __shared__ uint32_t smem[];
     const uint32_t S = 1u << (g.shift - sub_shift);
     uint32_t *hist = smem;          // S
-    uint32_t *gbase = hist + S;     // S
+    uint32_t *gbase = hist + S;     // S: sub-bucket cursor minus the run's first stage slot
     uint32_t *toff = gbase + S;     // S
     uint32_t *wsum = toff + S;      // kWarps: scan totals of the warps
-    uint32_t *sb = wsum + kWarps;   // kRefineTile: sub-bucket of each stage slot
-    uint2 *stage = reinterpret_cast<uint2 *>(sb + kRefineTile);
+    // kRefineTile pairs, 8-byte aligned whatever S is
+    uint2 *stage = reinterpret_cast<uint2 *>(smem + ((3 * S + kWarps + 1) & ~1u));
     // the scan gives each thread `per` consecutive sub-buckets
     const uint32_t per = (S + kThreads - 1) / kThreads, b0 = threadIdx.x * per;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -330,20 +330,24 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             const uint32_t b = (p[q].x - base_v) >> sub_shift;
             const uint32_t slot = toff[b] + rk[q];
             stage[slot] = p[q];
-            sb[slot] = b;
         }
+        // gbase[b] = cursor - first stage slot of the run: a staged pair at
+        // slot k goes to position gbase[b] + k of its sub-bucket
 #pragma unroll
         for (uint32_t q = 0; q < kScanRegs; q++)
-            if (q < per && b0 + q < S) gbase[b0 + q] = gb[q];
+            if (q < per && b0 + q < S) gbase[b0 + q] = gb[q] - toff[b0 + q];
+        for (uint32_t q = kScanRegs; q < per; q++)
+            if (b0 + q < S) gbase[b0 + q] -= toff[b0 + q];
         __syncthreads();
         const uint32_t total = toff[S - 1] + hist[S - 1];
         for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
-            const uint32_t b = sb[k];
-            const uint32_t pos = gbase[b] + (k - toff[b]);
+            const uint2 q = stage[k];
+            const uint32_t b = (q.x - base_v) >> sub_shift;  // its sub-bucket, again
+            const uint32_t pos = gbase[b] + k;
             if (pos < cap2)
-                pairs2[((size_t)c * S + b) * cap2 + pos] = stage[k];
+                pairs2[((size_t)c * S + b) * cap2 + pos] = q;
             else
-                overflow_push(stage[k], ov, ctl);
+                overflow_push(q, ov, ctl);
         }
         __syncthreads();
         it = nxt;
@@ -489,7 +493,7 @@ void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, cons
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
     const uint32_t chunk0 = b.passes > 1 ? pass * b.chunks_per_part : 0u;
     const uint32_t S = 1u << (b.shift - b.sub_shift);
-    const size_t smem1 = (3 * (size_t)S + kWarps + kRefineTile) * 4 + (size_t)kRefineTile * 8;
+    const size_t smem1 = ((3 * (size_t)S + kWarps + 1) & ~(size_t)1) * 4 + (size_t)kRefineTile * 8;
     cudaFuncSetAttribute(k_refine_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     const uint64_t items =
         (uint64_t)b.chunks_pass * b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);

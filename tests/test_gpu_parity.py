@@ -230,6 +230,19 @@ def test_peel_parity_bucketed(small_buckets, n, gamma, r):
     _check_peel(edges, m)
 
 
+@pytest.mark.parametrize("shift,sub", [(10, 10), (14, 2), (12, 3), (16, 4)])
+def test_peel_parity_extreme_sub_buckets(shift, sub):
+    # one sub-bucket per chunk (S = 1) up to 4,096 of them (the refine's scan
+    # then keeps most cursors in shared memory instead of registers)
+    hp.set_tuning(bucket_shift=shift, bucket_sub_shift=sub, bucket_min_vertices=0)
+    try:
+        n = 50_000
+        m = oracle.num_vertices(n, 1230, 3)
+        _check_peel(oracle.hash_edges(inputs.keys(n, 12), m, 3, 1), m)
+    finally:
+        hp.set_tuning()
+
+
 @pytest.mark.parametrize("span", [1024, 4096, 30_000])
 def test_peel_bucket_overflow_falls_back(small_buckets, span):
     # every vertex in the first `span` of its part: buckets sized for a
