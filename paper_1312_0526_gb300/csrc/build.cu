@@ -2,25 +2,27 @@
 //
 // AddEdge hits the vertex records in random order: with the records far
 // larger than L2, every update is a DRAM sector read and write.  Here the
-// updates are first bucketed by vertex chunk -- the paper's own remedy for
+// updates are first bucketed by vertex range -- the paper's own remedy for
 // random access (sec. 4.2 builds E_0 by sorting the orientations by vertex,
-// sec. 4.3 part by part), with the GPU's L2 as the fast memory -- and then
-// applied chunk after chunk, so the records being updated stay in L2:
+// sec. 4.3 part by part) -- and then applied range by range in shared
+// memory, so every vertex record is written once:
 //   pass 1 (fused with hashing, or with the row -> record conversion): each
 //          block takes tiles of edges, writes their records, counting-sorts
-//          a tile's (vertex, edge) incidences by chunk in shared memory and
-//          appends each chunk's run to its own region of that chunk's bucket
-//          (one region per (chunk, block), cursors in shared memory: no
-//          global atomics);
-//   pass 2: one kernel walks the buckets in chunk order and adds
-//          (e << 32) + 1 to each vertex record (64-bit reductions, L2 hits).
-// A chunk is 2^shift consecutive vertices of one part of the r-partite
-// vertex set.  Large graphs run the three passes once per part (sec. 4.3
-// builds the incidence lists one part at a time): position j's incidences
-// are bucketed and applied in pass j, so the buckets hold one incidence per
-// edge instead of r.  Region capacity covers the expected load with a wide margin;
-// an incidence that finds its region full is applied directly (same result,
-// random access), so any input is handled.
+//          a tile's (vertex, edge) incidences by chunk (2^shift vertices of
+//          one part) in shared memory and appends each chunk's run to its
+//          own region of that chunk's bucket (one region per (chunk, block),
+//          cursors in shared memory: no global atomics);
+//   pass 2 (refine): a persistent kernel counting-sorts each chunk's pairs,
+//          a tile at a time, into sub-buckets of 2^sub_shift vertices;
+//   pass 3 (apply): one block per sub-bucket accumulates its vertices'
+//          degrees and id sums in shared memory and writes the records.
+// Large graphs run the three passes once per part (sec. 4.3 builds the
+// incidence lists one part at a time): position j's incidences are bucketed
+// and applied in pass j, so the buckets hold one incidence per edge instead
+// of r.  Capacities cover the expected load with a wide margin; an incidence
+// that finds its region full goes to an overflow list applied with direct
+// updates, and when that list is full as well the build reports it and is
+// redone with direct updates (same result), so any input is handled.
 #include <algorithm>
 #include <cmath>
 
