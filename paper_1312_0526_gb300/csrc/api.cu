@@ -1,7 +1,8 @@
 // api.cu -- the C ABI (include/hpeel.h): argument checks, workspace layout,
-// the round loop and the MPHF retry loop.  Every step of the path runs in the
-// kernels of hash.cu, peel.cu, emit.cu and mphf.cu; this file only orders
-// them and reads back the few scalars the host has to decide on.
+// the round loop, the MPHF retry loop and its device-driven form (one CUDA
+// graph with conditional nodes).  Every step of the path runs in the kernels
+// of hash.cu, build.cu, peel.cu, emit.cu, mphf.cu and async.cu; this file
+// only orders them and reads back the few scalars the host has to decide on.
 #include <cuda_runtime.h>
 
 #include <algorithm>

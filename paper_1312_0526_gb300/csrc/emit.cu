@@ -7,7 +7,8 @@
 // core_key for an unclaimed edge) goes to bin min(k - base, nbins - 1).  The
 // host runs further passes on the last bin when there are more rounds.
 //   hist    -- per tile of kEmitTile consecutive inputs, bin counts, stored
-//              bin-major: hist[b * tiles + tile];
+//              bin-major: hist[b * tiles + tile] (the first pass's counts
+//              are taken while the claims are extracted from the records);
 //   scan    -- one exclusive prefix sum over hist gives, for every (bin,
 //              tile), where that tile's edges of that bin start;
 //   scatter -- each warp ranks its 512 inputs in input order (the lanes
