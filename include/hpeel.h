@@ -397,7 +397,10 @@ typedef struct hpeel_batch_tuning {
     uint32_t smem_bytes;   /* shared memory per block for bucket state (0: the SM's
                               shared memory split between the blocks); buckets
                               that do not fit use the workspace instead */
-    uint32_t reserved[5];
+    uint32_t smem_rounds;  /* layer-table entries of a bucket in shared memory
+                              (0: 256; at least 2); a bucket that needs more
+                              rounds is peeled again in the workspace */
+    uint32_t reserved[4];
 } hpeel_batch_tuning;
 
 size_t hpeel_batched_workspace_size(uint32_t B, uint32_t gamma_milli,

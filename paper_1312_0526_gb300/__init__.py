@@ -57,7 +57,8 @@ class Tuning(ctypes.Structure):
 
 class BatchTuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("smem_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 5)]
+                ("smem_bytes", ctypes.c_uint32), ("smem_rounds", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -493,7 +494,7 @@ def _batch_tuning(tuning):
     if tuning is None:
         return None
     t = BatchTuning(int(tuning.get("threads", 0)), int(tuning.get("ctas_per_sm", 0)),
-                    int(tuning.get("smem_bytes", 0)))
+                    int(tuning.get("smem_bytes", 0)), int(tuning.get("smem_rounds", 0)))
     return ctypes.byref(t)
 
 

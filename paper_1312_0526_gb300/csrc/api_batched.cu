@@ -15,7 +15,7 @@ using namespace hp;
 namespace {
 
 struct BatchPlan {
-    uint32_t threads, ctas_per_sm, smem_bytes, grid;
+    uint32_t threads, ctas_per_sm, smem_bytes, smem_rounds, grid;
     size_t sched, next, words, scanned, tmp, scratch, total;
 };
 
@@ -35,6 +35,8 @@ hpeel_status batch_plan(uint32_t B, uint32_t gamma_milli, const hpeel_batch_tuni
         return fail(HPEEL_ERR_INVALID_ARG, "threads = %u: need a multiple of 32 in [64, 1024]",
                     p->threads);
     if (p->ctas_per_sm > 32) return fail(HPEEL_ERR_INVALID_ARG, "ctas_per_sm > 32");
+    p->smem_rounds = tu && tu->smem_rounds ? tu->smem_rounds : 256u;
+    if (p->smem_rounds < 2) return fail(HPEEL_ERR_INVALID_ARG, "smem_rounds < 2");
     // default shared memory: fill the SM (1 KB per block is reserved by CUDA,
     // 64 B of static shared memory per block)
     const int per = d.smem_per_sm / (int)p->ctas_per_sm - 1024 - 64;
@@ -122,6 +124,7 @@ hpeel_status hpeel_peel_batched(const uint64_t *d_keys, const uint64_t *d_bucket
     ProfScope ps(L, "batched");
     launch_batched(L, d_keys, d_bucket_off, B, gamma_milli, d_order, d_bucket_rounds,
                    d_bucket_status, d_G, d_G_off, p.threads, p.grid, p.smem_bytes,
+                   p.smem_rounds,
                    reinterpret_cast<uint32_t *>(ws + p.sched),
                    reinterpret_cast<uint32_t *>(ws + p.next), ws + p.scratch);
     return check_launch("batched");

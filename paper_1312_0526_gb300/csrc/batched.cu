@@ -31,7 +31,6 @@ namespace hp {
 constexpr uint32_t kBatchMaxEdges = 65536;        // per bucket
 constexpr uint32_t kBatchMaxVertices = (1u << 17) - 1;  // packed 17-bit local ids
 constexpr uint32_t kBucketUnclaimed = 0xFFFFFFFFu;
-constexpr uint32_t kSmemRounds = 256;             // layer table of a bucket in shared memory
 
 // Device copy of hpeel_num_vertices for r = 3.
 __device__ __forceinline__ uint32_t bucket_vertices(uint32_t n, uint32_t gamma_milli) {
@@ -97,6 +96,7 @@ struct BatchArgs {
     char *scratch;            // per-CTA global regions
     size_t scratch_bytes;     // bytes per CTA region
     uint32_t smem_bytes;      // dynamic shared memory per CTA
+    uint32_t smem_rounds;     // layer-table entries of a bucket in shared memory
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -343,7 +343,7 @@ __global__ void k_batched(BatchArgs a) {
         }
         const uint32_t n = (uint32_t)n64;
         const uint32_t m = bucket_vertices(n, a.gamma_milli);
-        const uint32_t rcap_s = min(n + 1, kSmemRounds);
+        const uint32_t rcap_s = min(n + 1, a.smem_rounds);
         bool done = false;
         if (n < 0xFFFFu && bucket_bytes(n, m, 4, rcap_s) <= a.smem_bytes)
             done = run_bucket<uint32_t>(a, b, carve<uint32_t>(smem, n, m, rcap_s), n, m, sh);
@@ -433,11 +433,12 @@ uint32_t batched_max_gamma_milli() {
 void launch_batched(const Launch &L, const uint64_t *keys, const uint64_t *off, uint32_t B,
                     uint32_t gamma_milli, uint32_t *order, uint32_t *rounds, uint32_t *status,
                     uint64_t *G, const uint64_t *G_off, uint32_t threads, uint32_t ctas,
-                    uint32_t smem_bytes, uint32_t *sched, uint32_t *next, char *scratch) {
+                    uint32_t smem_bytes, uint32_t smem_rounds, uint32_t *sched,
+                    uint32_t *next, char *scratch) {
     count_launch();
     k_batch_schedule<<<1, 1024, 0, L.stream>>>(off, B, sched, next);
     BatchArgs a{keys, off, B, gamma_milli, sched, next, order, rounds, status, G, G_off,
-                scratch, batched_scratch_bytes(gamma_milli), smem_bytes};
+                scratch, batched_scratch_bytes(gamma_milli), smem_bytes, smem_rounds};
     static uint32_t attr_set[64] = {0};  // largest dynamic shared size set, per device
     int dev = 0;
     cudaGetDevice(&dev);

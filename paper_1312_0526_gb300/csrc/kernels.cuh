@@ -163,7 +163,8 @@ uint32_t batched_max_gamma_milli();
 void launch_batched(const Launch &L, const uint64_t *keys, const uint64_t *off, uint32_t B,
                     uint32_t gamma_milli, uint32_t *order, uint32_t *rounds, uint32_t *status,
                     uint64_t *G, const uint64_t *G_off, uint32_t threads, uint32_t ctas,
-                    uint32_t smem_bytes, uint32_t *sched, uint32_t *next, char *scratch);
+                    uint32_t smem_bytes, uint32_t smem_rounds, uint32_t *sched,
+                    uint32_t *next, char *scratch);
 void launch_batch_g_offsets(const Launch &L, const uint64_t *off, uint32_t B, uint32_t gamma_milli,
                             uint32_t *words, uint32_t *scanned, uint32_t *tmp, uint64_t *G_off);
 

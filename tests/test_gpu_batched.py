@@ -98,6 +98,9 @@ def test_batched_parity_with_g():
     {"threads": 512, "ctas_per_sm": 4},
     {"threads": 256, "ctas_per_sm": 2, "smem_bytes": 4096},   # nearly all on the global path
     {"threads": 64, "ctas_per_sm": 8},
+    # a layer table of 3 entries in shared memory: every bucket of more than
+    # one round is peeled again in the workspace
+    {"threads": 256, "ctas_per_sm": 8, "smem_rounds": 3},
 ])
 def test_batched_results_do_not_depend_on_tuning(tuning):
     sizes, keys, off = _workload(B=120, median=700, seed=11, key_seed=13, extra_sizes=[25000])
