@@ -215,7 +215,10 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 // resident wave of blocks strides over all (chunk, tile) items; the next
 // item's pairs are loaded into registers while the current one is sorted
 // and written, so the load latency overlaps the work.
-constexpr int kRefineItems = 16;
+#ifndef HPEEL_REFINE_ITEMS
+#define HPEEL_REFINE_ITEMS 16
+#endif
+constexpr int kRefineItems = HPEEL_REFINE_ITEMS;
 constexpr uint32_t kRefineTile = kThreads * kRefineItems;  // 4096 slots
 constexpr uint32_t kWarps = kThreads / 32;
 constexpr uint32_t kScanRegs = 4;  // sub-buckets per thread whose cursor stays in registers
@@ -381,7 +384,10 @@ k_apply_smem(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill
     __syncthreads();
     const uint32_t cnt = min(fill2[s], cap2);
     const uint2 *src = pairs2 + (size_t)s * cap2;
-    constexpr int kU = 4;  // loads in flight per thread
+#ifndef HPEEL_APPLY_U
+#define HPEEL_APPLY_U 4
+#endif
+    constexpr int kU = HPEEL_APPLY_U;  // loads in flight per thread
     for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += kU * blockDim.x) {
         uint2 p[kU];
 #pragma unroll

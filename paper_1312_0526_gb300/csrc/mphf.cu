@@ -18,7 +18,10 @@ namespace hp {
 // Solve the list entries [lb, le) of one layer: each {v_hinge, v_a, v_b, e}
 // with the hinge position the part of v_hinge, read as a stream.  A thread
 // takes kAssignU entries at a time and issues all their loads first.
-constexpr int kAssignU = 4;
+#ifndef HPEEL_ASSIGN_U
+#define HPEEL_ASSIGN_U 4
+#endif
+constexpr int kAssignU = HPEEL_ASSIGN_U;
 
 __device__ __forceinline__ void assign_range(const uint4 *__restrict__ Lst, uint32_t lb,
                                              uint32_t le, uint32_t P, uint64_t *G) {
