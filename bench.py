@@ -200,10 +200,18 @@ def cpu_baseline():
     t0 = time.perf_counter()
     res = oracle.mphf_build(keys, HASH_SEED, GAMMA_MILLI)
     dt = time.perf_counter() - t0
+    # the paper's in-memory baseline form beside it: the greedy (LIFO) peel
+    # with the XOR trick ("Standard+XOR"), hashing included
+    m = oracle.num_vertices(CPU_SAMPLE_KEYS, GAMMA_MILLI, R)
+    t1 = time.perf_counter()
+    oracle.peel_greedy(oracle.hash_edges(keys, m, R, HASH_SEED), m)
+    dg = time.perf_counter() - t1
     return {"value": CPU_SAMPLE_KEYS / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"one single-threaded oracle MPHF build (hash+peel+assign+rank) of the "
                       f"first {CPU_SAMPLE_KEYS:.0e} keys of the same stream, {dt:.2f} s, "
-                      f"{res.rounds} rounds"}
+                      f"{res.rounds} rounds",
+            "greedy_peel": {"value": CPU_SAMPLE_KEYS / dg / 1e6, "unit": UNIT,
+                            "sample": f"hash + greedy LIFO peel of the same keys, {dg:.2f} s"}}
 
 
 def lookup_leg(keys, G, D, m, seed):
