@@ -118,7 +118,10 @@ void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, cons
     k_emit_hist<<<tiles, kThreads, 0, L.stream>>>(src, count, claim, base, core_key, nbins, hist);
 }
 
-__global__ void __launch_bounds__(kThreads)
+#ifndef HPEEL_SCATTER_MIN_BLOCKS
+#define HPEEL_SCATTER_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(kThreads, HPEEL_SCATTER_MIN_BLOCKS)
 k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
                const uint32_t *__restrict__ claim, uint32_t base, uint32_t core_key,
                uint32_t nbins, const uint32_t *__restrict__ offs, uint32_t *__restrict__ out) {
