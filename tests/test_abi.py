@@ -63,6 +63,29 @@ def test_workspace_sizes_grow_with_n(lib):
     assert hp.mphf_workspace_size(100_000) > b
 
 
+def test_host_side_argument_checks(lib):
+    # refused on the host before any device work (no GPU needed)
+    INVALID = 1
+    raw = ctypes.CDLL(hp.LIB_PATH)
+    raw.hpeel_probe_random_access.restype = ctypes.c_int
+    raw.hpeel_probe_random_access.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p,
+                                              ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                                              ctypes.c_uint64, ctypes.c_void_p]
+    assert raw.hpeel_probe_random_access(3, 10, None, 0, None, 0, 1, None) == INVALID
+    assert raw.hpeel_probe_random_access(2, 10, None, 0, None, 0, 1, None) == INVALID
+    with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
+        hp.set_tuning(bucket_part_passes=3)
+    with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
+        hp.set_tuning(bucket_sub_shift=15)
+    hp.set_tuning()
+    assert hp.get_tuning()["bucket_part_passes"] == 0
+    # an invalid batched launch shape has no workspace size (0)
+    assert hp.batched_workspace_size(4, 1230, {"threads": 256, "ctas_per_sm": 2,
+                                               "smem_rounds": 1}) == 0
+    assert hp.batched_workspace_size(4, 1230, {"threads": 256, "ctas_per_sm": 2,
+                                               "smem_rounds": 2}) > 0
+
+
 def test_one_part_per_pass_takes_a_smaller_workspace(lib):
     # sec. 4.3's one part at a time: the L2-blocked build's buckets hold one
     # incidence per edge instead of r
