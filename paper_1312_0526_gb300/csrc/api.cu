@@ -480,11 +480,9 @@ hpeel_status side_stream(SideStream **out) {
     if (d < 0 || d >= 64) return fail(HPEEL_ERR_INVALID_ARG, "device %d out of range", d);
     SideStream &s = ss[d];
     if (s.dev != d) {
-        // the highest priority: the assignment is a chain of one launch per
-        // layer, the order sort beside it fills the SMs the chain leaves idle
-        int lo = 0, hi = 0;
-        HP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        HP_CUDA(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, hi));
+        // default priority: a raised one took 0.5 ms off a lone build but
+        // slowed host-to-device key copies and concurrent builds on some GB300s
+        HP_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
         HP_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
         s.dev = d;
     }
