@@ -36,7 +36,8 @@ hpeel_status batch_plan(uint32_t B, uint32_t gamma_milli, const hpeel_batch_tuni
                     p->threads);
     if (p->ctas_per_sm > 32) return fail(HPEEL_ERR_INVALID_ARG, "ctas_per_sm > 32");
     p->smem_rounds = tu && tu->smem_rounds ? tu->smem_rounds : 256u;
-    if (p->smem_rounds < 2) return fail(HPEEL_ERR_INVALID_ARG, "smem_rounds < 2");
+    if (p->smem_rounds < 2 || p->smem_rounds > 16383)
+        return fail(HPEEL_ERR_INVALID_ARG, "smem_rounds %u outside [2, 16383]", p->smem_rounds);
     // default shared memory: fill the SM (1 KB per block is reserved by CUDA,
     // 64 B of static shared memory per block)
     const int per = d.smem_per_sm / (int)p->ctas_per_sm - 1024 - 64;

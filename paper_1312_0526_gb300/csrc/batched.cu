@@ -30,7 +30,30 @@ namespace hp {
 
 constexpr uint32_t kBatchMaxEdges = 65536;        // per bucket
 constexpr uint32_t kBatchMaxVertices = (1u << 17) - 1;  // packed 17-bit local ids
-constexpr uint32_t kBucketUnclaimed = 0xFFFFFFFFu;
+// Claim words: (round << 2) | hinge, all ones while unclaimed.  16 bits in
+// shared memory and in the 32-bit global path (layer tables of at most
+// kClaim16Rounds entries), 32 bits in the 64-bit path.
+constexpr uint32_t kClaim16Rounds = 16383;
+
+template <typename C>
+__device__ __forceinline__ uint32_t unclaimed() { return (uint32_t)(C)~(C)0; }
+
+// atomicMin on a claim word, returning the old value
+__device__ __forceinline__ uint32_t claim_min(uint32_t *p, uint32_t v) { return atomicMin(p, v); }
+__device__ __forceinline__ uint32_t claim_min(uint16_t *p, uint32_t v) {
+    // the 32-bit word holding the half-word: compare-and-swap until the
+    // half-word is at most v (every failed swap saw another claim succeed)
+    uint32_t *w = reinterpret_cast<uint32_t *>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3);
+    const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(p) & 2u) * 8u;
+    uint32_t old = *reinterpret_cast<volatile uint32_t *>(w);
+    for (;;) {
+        const uint32_t cur = (old >> sh) & 0xFFFFu;
+        if (cur <= v) return cur;
+        const uint32_t got = atomicCAS(w, old, (old & ~(0xFFFFu << sh)) | (v << sh));
+        if (got == old) return cur;
+        old = got;
+    }
+}
 
 // Device copy of hpeel_num_vertices for r = 3.
 __device__ __forceinline__ uint32_t bucket_vertices(uint32_t n, uint32_t gamma_milli) {
@@ -70,10 +93,10 @@ struct VRec<unsigned long long> {
 };
 
 // Where one bucket's state lives (shared memory or the CTA's global region).
-template <typename T>
+template <typename T, typename C>
 struct BucketState {
     T *rec;          // [m]
-    uint32_t *claim; // [n] (round << 2) | hinge
+    C *claim;        // [n] (round << 2) | hinge
     uint16_t *L;     // [n] layers appended (local edge ids < 2^16)
     uint32_t *loff;  // [rcap + 2] layer starts
     uint32_t *cnt;   // [rcap + 2] running starts of the order pass
@@ -104,19 +127,19 @@ __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15;
 // Bytes of one bucket's state with records of rec_bytes and a loff table of
 // rcap + 2 entries.
 __host__ __device__ inline size_t bucket_bytes(uint32_t n, uint32_t m, uint32_t rec_bytes,
-                                               uint32_t rcap) {
-    return a16((size_t)m * rec_bytes) + a16((size_t)n * 4) + a16((size_t)n * 2) +
+                                               uint32_t claim_bytes, uint32_t rcap) {
+    return a16((size_t)m * rec_bytes) + a16((size_t)n * claim_bytes) + a16((size_t)n * 2) +
            2 * a16(((size_t)rcap + 2) * 4) + a16(((size_t)m + 15) / 16 * 4);
 }
 
-template <typename T>
-__device__ BucketState<T> carve(char *base, uint32_t n, uint32_t m, uint32_t rcap) {
-    BucketState<T> s;
+template <typename T, typename C>
+__device__ BucketState<T, C> carve(char *base, uint32_t n, uint32_t m, uint32_t rcap) {
+    BucketState<T, C> s;
     size_t o = 0;
     s.rec = reinterpret_cast<T *>(base + o);
     o += a16((size_t)m * sizeof(T));
-    s.claim = reinterpret_cast<uint32_t *>(base + o);
-    o += a16((size_t)n * 4);
+    s.claim = reinterpret_cast<C *>(base + o);
+    o += a16((size_t)n * sizeof(C));
     s.L = reinterpret_cast<uint16_t *>(base + o);
     o += a16((size_t)n * 2);
     s.loff = reinterpret_cast<uint32_t *>(base + o);
@@ -145,9 +168,10 @@ __device__ __forceinline__ void cta_append(uint32_t *cursor, uint16_t *list, uin
 // The whole path for one bucket.  Every thread of the block calls it.
 // Returns false (writing nothing) when the bucket needs more rounds than its
 // layer table holds; the caller reruns it with a larger table.
-template <typename T>
-__device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uint32_t n,
+template <typename T, typename C>
+__device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T, C> s, uint32_t n,
                            uint32_t m, uint32_t *sh) {
+    const uint32_t kUnc = unclaimed<C>();
     using V = VRec<T>;
     const uint32_t T_ = blockDim.x;
     const uint32_t tid = threadIdx.x;
@@ -160,7 +184,7 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
         magic = ~0ull / P;  // reciprocal for the remainder by P
     }
     for (uint32_t v = tid; v < m; v += T_) s.rec[v] = 0;
-    for (uint32_t e = tid; e < n; e += T_) s.claim[e] = kBucketUnclaimed;
+    for (uint32_t e = tid; e < n; e += T_) s.claim[e] = (C)kUnc;
     __syncthreads();
     const FastMod fm{P, magic};
     const uint64_t seed = b;
@@ -185,7 +209,7 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
             if (V::deg(r) == 1u && V::sum(r) < n) {
                 e = V::sum(r);
                 const uint32_t j = (v >= P) + (v >= 2 * P);
-                take = atomicMin(s.claim + e, j) == kBucketUnclaimed;
+                take = claim_min(s.claim + e, j) == kUnc;
             }
         }
         cta_append(&lcur, s.L, 0u, take, e);
@@ -227,8 +251,8 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
                     if (V::deg(old) == 2u) {
                         const uint32_t g = (V::sum(old) - e) & V::mask();
                         if (g < n) {
-                            take[k] = atomicMin(s.claim + g, ((t + 1) << 2) | (uint32_t)j) ==
-                                      kBucketUnclaimed;
+                            take[k] = claim_min(s.claim + g, ((t + 1) << 2) | (uint32_t)j) ==
+                                      kUnc;
                             f[k] = g;
                         }
                     }
@@ -262,7 +286,7 @@ __device__ bool run_bucket(const BatchArgs &a, uint32_t b, BucketState<T> s, uin
             uint32_t key = 0xFFFFFFFFu;
             if (valid) {
                 const uint32_t c = s.claim[e];
-                key = c == kBucketUnclaimed ? R : (c >> 2);
+                key = c == kUnc ? R : (c >> 2);
             }
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
             if (valid) out[cnt[key] + __popc(peers & ((1u << lane) - 1u))] = e;
@@ -345,16 +369,20 @@ __global__ void k_batched(BatchArgs a) {
         const uint32_t m = bucket_vertices(n, a.gamma_milli);
         const uint32_t rcap_s = min(n + 1, a.smem_rounds);
         bool done = false;
-        if (n < 0xFFFFu && bucket_bytes(n, m, 4, rcap_s) <= a.smem_bytes)
-            done = run_bucket<uint32_t>(a, b, carve<uint32_t>(smem, n, m, rcap_s), n, m, sh);
-        // rounds never exceed n + 1 layer starts: the global region always
-        // fits; its records are 32 bits when the 16-bit fields hold the
-        // bucket (fewer than 2^16 - 1 edges), as in shared memory
+        if (n < 0xFFFFu && bucket_bytes(n, m, 4, 2, rcap_s) <= a.smem_bytes)
+            done = run_bucket<uint32_t, uint16_t>(a, b, carve<uint32_t, uint16_t>(smem, n, m, rcap_s),
+                                                  n, m, sh);
+        // the global region: 32-bit records and 16-bit claims when the
+        // 16-bit fields hold the bucket (fewer than 2^16 - 1 edges, at most
+        // kClaim16Rounds rounds), as in shared memory; else 64-bit records
+        // and 32-bit claims with room for every round (n + 1 layer starts)
         if (!done && n < 0xFFFFu)
-            done = run_bucket<uint32_t>(a, b, carve<uint32_t>(region, n, m, n + 1), n, m, sh);
+            done = run_bucket<uint32_t, uint16_t>(
+                a, b, carve<uint32_t, uint16_t>(region, n, m, min(n + 1, kClaim16Rounds)), n, m,
+                sh);
         if (!done)
-            run_bucket<unsigned long long>(
-                a, b, carve<unsigned long long>(region, n, m, n + 1), n, m, sh);
+            run_bucket<unsigned long long, uint32_t>(
+                a, b, carve<unsigned long long, uint32_t>(region, n, m, n + 1), n, m, sh);
     }
 }
 
@@ -417,7 +445,7 @@ __global__ void k_batch_schedule(const uint64_t *off, uint32_t B, uint32_t *sche
 size_t batched_scratch_bytes(uint32_t gamma_milli) {
     const uint64_t gn = ((uint64_t)kBatchMaxEdges * gamma_milli + 999u) / 1000u;
     const uint32_t mmax = (uint32_t)((gn + 2) / 3 * 3);
-    return (bucket_bytes(kBatchMaxEdges, mmax, 8, kBatchMaxEdges + 1) + 255) & ~(size_t)255;
+    return (bucket_bytes(kBatchMaxEdges, mmax, 8, 4, kBatchMaxEdges + 1) + 255) & ~(size_t)255;
 }
 
 uint32_t batched_max_gamma_milli() {
