@@ -21,7 +21,13 @@
  *     before returning; each call says whether it does.
  *   - Scratch memory is a caller-provided workspace d_ws of at least the
  *     size the matching *_workspace_size() function returns, 256-byte
- *     aligned.  The library allocates no device memory.
+ *     aligned.  The library never calls cudaMalloc: every array of a call
+ *     lives in the caller's buffers.  Two things still take device memory
+ *     from the driver: loading the library's device code (on the first call
+ *     on a device), and the CUDA graphs the library instantiates and caches
+ *     for its device-side loops (the round loop of the default tuning, the
+ *     device-driven calls), which the driver backs with memory of its own.
+ *     hpeel_peel_noalloc uses neither kind of graph.
  *   - Every call returns an hpeel_status; no C++ exception crosses the ABI.
  *     On failure hpeel_last_error() (per host thread) holds a message.
  *   - Edge ids and vertex ids are uint32: n < 2^32 and m < 2^32.
@@ -214,22 +220,29 @@ hpeel_status hpeel_peel_general(const uint32_t *d_edges, uint64_t n, uint64_t m,
  * under a fixed memory budget, plugins where calling the allocator is not
  * allowed.  Same arguments, results and errors as hpeel_peel, without the
  * workspace: the scratch is an array of HPEEL_NOALLOC_SCRATCH_BYTES compiled
- * into this library's device image.  Every GPU on which the library's kernels
- * are loaded holds that array until the process exits.  The call makes no
- * cudaMalloc, cudaFree or other device allocation.
+ * into this library's device image.  Every GPU on which the library's device
+ * code is loaded holds that array until the process exits.
+ *   - No allocation: the call makes no cudaMalloc, cudaFree or other
+ *     allocating call, and it launches its rounds one by one from the host
+ *     (whatever the tuning says), so no CUDA graph is instantiated either.
+ *     What the driver does on its own is outside the call's control: the
+ *     first call on a device loads the library's device code (and with it
+ *     the scratch array) unless an earlier call of this library did, and the
+ *     first launch of a kernel may reserve its local memory.  Make one call
+ *     on each device at start-up to get both done before the budget counts.
  *   - Size limit: the call fails with HPEEL_ERR_WORKSPACE_TOO_SMALL (and
  *     launches nothing) when hpeel_peel_workspace_size(n, m, r) exceeds
  *     HPEEL_NOALLOC_SCRATCH_BYTES -- about 500,000 edges at gamma = 1.23,
  *     r = 3.  Larger graphs need hpeel_peel and a caller workspace.
- *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before
- *     any stream capture.
+ *   - Every call looks up the array's device address with the current device
+ *     (host code cannot use the array's name as an address).
  *   - All calls in the process share the one array, which keeps the last
  *     call's contents.  Each call clears what it needs before use, so leftover
  *     contents never change a result, but two calls whose work overlaps on
  *     the GPU (different streams or host threads on the same device) race on
  *     the array: callers must order such calls.
- * Synchronises stream.
+ * Synchronises stream after every round (the host decides whether another
+ * round follows), so the call cannot be captured into a CUDA graph.
  */
 #define HPEEL_NOALLOC_SCRATCH_BYTES (24u << 20)
 hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, uint64_t m,
@@ -400,7 +413,14 @@ typedef struct hpeel_batch_tuning {
     uint32_t smem_rounds;  /* layer-table entries of a bucket in shared memory
                               (0: 256; at least 2); a bucket that needs more
                               rounds is peeled again in the workspace */
-    uint32_t reserved[4];
+    uint32_t global16_rounds;  /* layer-table entries of a bucket peeled in the
+                              workspace with 32-bit vertex records and 16-bit
+                              claim words (0: 16,383, the most a 16-bit claim
+                              word holds; 2..16,383); a bucket that needs more
+                              rounds is peeled again with 64-bit records and
+                              32-bit claim words, which have room for every
+                              round */
+    uint32_t reserved[3];
 } hpeel_batch_tuning;
 
 size_t hpeel_batched_workspace_size(uint32_t B, uint32_t gamma_milli,

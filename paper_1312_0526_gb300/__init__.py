@@ -58,7 +58,7 @@ class Tuning(ctypes.Structure):
 class BatchTuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("smem_bytes", ctypes.c_uint32), ("smem_rounds", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 4)]
+                ("global16_rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -334,19 +334,25 @@ def mphf_bits_per_key(n: int, gamma_milli: int = 1230) -> float:
 NOALLOC_SCRATCH_BYTES = 24 << 20
 
 
-def peel_noalloc(edges, m: int, max_layers: int = 4096) -> PeelResult:
+def peel_noalloc(edges, m: int, max_layers: int = 4096, out=None) -> PeelResult:
     """hpeel_peel_noalloc: the peel of ``peel`` with no workspace and no device
     allocation inside the call (the library's built-in scratch is used; graphs
-    up to NOALLOC_SCRATCH_BYTES of scratch).  The output tensors are allocated
-    here by torch, before the call; callers that cannot allocate call the C
-    entry point with their own output buffers."""
+    up to NOALLOC_SCRATCH_BYTES of scratch).  out: None (the output tensors
+    are allocated here by torch, before the call), or a tuple (order int32
+    [n], claim int32 [n], layer_off int64 [max_layers + 1]) of the caller's
+    buffers, so that nothing is allocated at call time."""
     torch = _torch()
     ep = _dev_ptr(edges, "edges", torch.int32, 2)
     n, r = edges.shape
     dev = edges.device
-    order = torch.empty(n, dtype=torch.int32, device=dev)
-    claim = torch.empty(n, dtype=torch.int32, device=dev)
-    loff = torch.empty(max_layers + 1, dtype=torch.int64, device=dev)
+    if out is None:
+        order = torch.empty(n, dtype=torch.int32, device=dev)
+        claim = torch.empty(n, dtype=torch.int32, device=dev)
+        loff = torch.empty(max_layers + 1, dtype=torch.int64, device=dev)
+    else:
+        order, claim, loff = out
+        if order.numel() < n or claim.numel() < n or loff.numel() < max_layers + 1:
+            raise ValueError("out buffers too small: need n, n and max_layers + 1 entries")
     st = Stats()
     _check(lib().hpeel_peel_noalloc(ep, n, m, r, _dev_ptr(order, "order"),
                                     _dev_ptr(claim, "claim"), _dev_ptr(loff, "layer_off"),
@@ -494,7 +500,8 @@ def _batch_tuning(tuning):
     if tuning is None:
         return None
     t = BatchTuning(int(tuning.get("threads", 0)), int(tuning.get("ctas_per_sm", 0)),
-                    int(tuning.get("smem_bytes", 0)), int(tuning.get("smem_rounds", 0)))
+                    int(tuning.get("smem_bytes", 0)), int(tuning.get("smem_rounds", 0)),
+                    int(tuning.get("global16_rounds", 0)))
     return ctypes.byref(t)
 
 

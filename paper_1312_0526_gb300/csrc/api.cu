@@ -160,6 +160,7 @@ struct PeelIO {
     uint32_t *claim = nullptr;  // claim-word output (nullptr: workspace)
     bool force_direct = false;  // update the vertex records directly (no buckets)
     bool general = false;       // a general (not r-partite) hypergraph on [0, m)
+    bool host_loop = false;     // launch every round from the host, whatever the tuning
 };
 
 // Executable graphs of the round loop, cached by their parameters: round 0,
@@ -338,7 +339,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     hp_prm.max_rounds = lay.max_rounds;
     RoundParams *prm = reinterpret_cast<RoundParams *>(ws + lay.params);
     launch_set_params(L, prm, hp_prm);
-    if (tu.host_round_loop) {
+    if (tu.host_round_loop || io.host_loop) {
         // one launch per round, the control block read back after each
         {
             ProfScope ps(L, "round0");
@@ -1191,26 +1192,18 @@ namespace {
 // holds these bytes until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[HPEEL_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[64] = {nullptr};  // device address of the scratch, per device
-
 // Device address of the scratch on the current device.  Host code cannot use
 // the symbol itself (on the host it names a stand-in, not device memory), so
-// the address is looked up once per device, with that device current.
+// the address is looked up with the device current.  It is looked up again on
+// every call (a cheap query): a cached address would go stale if the
+// device's context were torn down and the module loaded again.
 hpeel_status noalloc_scratch(void **out) {
-    int dev = 0;
-    HP_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(HPEEL_ERR_INVALID_ARG, "device %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr)
-            return fail(HPEEL_ERR_CUDA, "cudaGetSymbolAddress of the built-in scratch failed: %s",
-                        cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+        return fail(HPEEL_ERR_CUDA, "cudaGetSymbolAddress of the built-in scratch failed: %s",
+                    cudaGetErrorString(e));
+    *out = p;
     return HPEEL_OK;
 }
 
@@ -1250,12 +1243,17 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
     // vertex records are cleared first), so what a previous call left there
     // does not matter.  The control block is read back into ordinary host
     // memory, which needs no pinned allocation.
+    // The rounds are launched from the host one by one (as with the tuning's
+    // host_round_loop), never through the cached round-loop CUDA graph: a
+    // graph is instantiated on first use, and the driver backs an executable
+    // graph with device memory of its own.
     thread_local Ctl readback;
     PeelOut po{};
     PeelIO io;
     io.edges = d_edges;
     io.order = d_order;
     io.claim = d_claim;
+    io.host_loop = true;
     HP_TRY(peel_core_rb(L, io, (uint32_t)n, (uint32_t)m, r, (char *)scratch, &po, &readback));
     if (d_layer_off) {
         if (po.rounds > max_layers)

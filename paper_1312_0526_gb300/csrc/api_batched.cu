@@ -15,7 +15,7 @@ using namespace hp;
 namespace {
 
 struct BatchPlan {
-    uint32_t threads, ctas_per_sm, smem_bytes, smem_rounds, grid;
+    uint32_t threads, ctas_per_sm, smem_bytes, smem_rounds, global16_rounds, grid;
     size_t sched, next, words, scanned, tmp, scratch, total;
 };
 
@@ -38,6 +38,10 @@ hpeel_status batch_plan(uint32_t B, uint32_t gamma_milli, const hpeel_batch_tuni
     p->smem_rounds = tu && tu->smem_rounds ? tu->smem_rounds : 256u;
     if (p->smem_rounds < 2 || p->smem_rounds > 16383)
         return fail(HPEEL_ERR_INVALID_ARG, "smem_rounds %u outside [2, 16383]", p->smem_rounds);
+    p->global16_rounds = tu && tu->global16_rounds ? tu->global16_rounds : batched_claim16_rounds();
+    if (p->global16_rounds < 2 || p->global16_rounds > batched_claim16_rounds())
+        return fail(HPEEL_ERR_INVALID_ARG, "global16_rounds %u outside [2, %u]",
+                    p->global16_rounds, batched_claim16_rounds());
     // default shared memory: fill the SM (1 KB per block is reserved by CUDA,
     // 64 B of static shared memory per block)
     const int per = d.smem_per_sm / (int)p->ctas_per_sm - 1024 - 64;
@@ -125,7 +129,7 @@ hpeel_status hpeel_peel_batched(const uint64_t *d_keys, const uint64_t *d_bucket
     ProfScope ps(L, "batched");
     launch_batched(L, d_keys, d_bucket_off, B, gamma_milli, d_order, d_bucket_rounds,
                    d_bucket_status, d_G, d_G_off, p.threads, p.grid, p.smem_bytes,
-                   p.smem_rounds,
+                   p.smem_rounds, p.global16_rounds,
                    reinterpret_cast<uint32_t *>(ws + p.sched),
                    reinterpret_cast<uint32_t *>(ws + p.next), ws + p.scratch);
     return check_launch("batched");

@@ -32,7 +32,8 @@ constexpr uint32_t kBatchMaxEdges = 65536;        // per bucket
 constexpr uint32_t kBatchMaxVertices = (1u << 17) - 1;  // packed 17-bit local ids
 // Claim words: (round << 2) | hinge, all ones while unclaimed.  16 bits in
 // shared memory and in the 32-bit global path (layer tables of at most
-// kClaim16Rounds entries), 32 bits in the 64-bit path.
+// kClaim16Rounds entries, fewer if the tuning says so), 32 bits in the
+// 64-bit path.
 constexpr uint32_t kClaim16Rounds = 16383;
 
 template <typename C>
@@ -120,6 +121,7 @@ struct BatchArgs {
     size_t scratch_bytes;     // bytes per CTA region
     uint32_t smem_bytes;      // dynamic shared memory per CTA
     uint32_t smem_rounds;     // layer-table entries of a bucket in shared memory
+    uint32_t global16_rounds; // layer-table entries on the 32-bit global path
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -374,12 +376,13 @@ __global__ void k_batched(BatchArgs a) {
                                                   n, m, sh);
         // the global region: 32-bit records and 16-bit claims when the
         // 16-bit fields hold the bucket (fewer than 2^16 - 1 edges, at most
-        // kClaim16Rounds rounds), as in shared memory; else 64-bit records
-        // and 32-bit claims with room for every round (n + 1 layer starts)
+        // global16_rounds <= kClaim16Rounds rounds), as in shared memory;
+        // else 64-bit records and 32-bit claims with room for every round
+        // (n + 1 layer starts)
         if (!done && n < 0xFFFFu)
             done = run_bucket<uint32_t, uint16_t>(
-                a, b, carve<uint32_t, uint16_t>(region, n, m, min(n + 1, kClaim16Rounds)), n, m,
-                sh);
+                a, b, carve<uint32_t, uint16_t>(region, n, m, min(n + 1, a.global16_rounds)), n,
+                m, sh);
         if (!done)
             run_bucket<unsigned long long, uint32_t>(
                 a, b, carve<unsigned long long, uint32_t>(region, n, m, n + 1), n, m, sh);
@@ -448,6 +451,8 @@ size_t batched_scratch_bytes(uint32_t gamma_milli) {
     return (bucket_bytes(kBatchMaxEdges, mmax, 8, 4, kBatchMaxEdges + 1) + 255) & ~(size_t)255;
 }
 
+uint32_t batched_claim16_rounds() { return kClaim16Rounds; }
+
 uint32_t batched_max_gamma_milli() {
     // largest gamma whose biggest bucket keeps its vertex ids within 17 bits
     uint32_t g = 1000;
@@ -461,12 +466,13 @@ uint32_t batched_max_gamma_milli() {
 void launch_batched(const Launch &L, const uint64_t *keys, const uint64_t *off, uint32_t B,
                     uint32_t gamma_milli, uint32_t *order, uint32_t *rounds, uint32_t *status,
                     uint64_t *G, const uint64_t *G_off, uint32_t threads, uint32_t ctas,
-                    uint32_t smem_bytes, uint32_t smem_rounds, uint32_t *sched,
-                    uint32_t *next, char *scratch) {
+                    uint32_t smem_bytes, uint32_t smem_rounds, uint32_t global16_rounds,
+                    uint32_t *sched, uint32_t *next, char *scratch) {
     count_launch();
     k_batch_schedule<<<1, 1024, 0, L.stream>>>(off, B, sched, next);
     BatchArgs a{keys, off, B, gamma_milli, sched, next, order, rounds, status, G, G_off,
-                scratch, batched_scratch_bytes(gamma_milli), smem_bytes, smem_rounds};
+                scratch, batched_scratch_bytes(gamma_milli), smem_bytes, smem_rounds,
+                global16_rounds};
     static uint32_t attr_set[64] = {0};  // largest dynamic shared size set, per device
     int dev = 0;
     cudaGetDevice(&dev);

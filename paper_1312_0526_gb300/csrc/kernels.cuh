@@ -160,10 +160,13 @@ void launch_layer_off(const Launch &L, const uint32_t *loff, uint32_t rounds, ui
 // a10: batched bucket peel (batched.cu).
 size_t batched_scratch_bytes(uint32_t gamma_milli);
 uint32_t batched_max_gamma_milli();
+// Most layer-table entries of a bucket with 16-bit claim words.
+uint32_t batched_claim16_rounds();
 void launch_batched(const Launch &L, const uint64_t *keys, const uint64_t *off, uint32_t B,
                     uint32_t gamma_milli, uint32_t *order, uint32_t *rounds, uint32_t *status,
                     uint64_t *G, const uint64_t *G_off, uint32_t threads, uint32_t ctas,
-                    uint32_t smem_bytes, uint32_t smem_rounds, uint32_t *sched,
+                    uint32_t smem_bytes, uint32_t smem_rounds, uint32_t global16_rounds,
+                    uint32_t *sched,
                     uint32_t *next, char *scratch);
 void launch_batch_g_offsets(const Launch &L, const uint64_t *off, uint32_t B, uint32_t gamma_milli,
                             uint32_t *words, uint32_t *scanned, uint32_t *tmp, uint64_t *G_off);

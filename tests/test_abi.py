@@ -84,6 +84,10 @@ def test_host_side_argument_checks(lib):
                                                "smem_rounds": 1}) == 0
     assert hp.batched_workspace_size(4, 1230, {"threads": 256, "ctas_per_sm": 2,
                                                "smem_rounds": 2}) > 0
+    # the 16-bit claim words of the global path hold at most 16,383 rounds
+    assert hp.batched_workspace_size(4, 1230, {"global16_rounds": 1}) == 0
+    assert hp.batched_workspace_size(4, 1230, {"global16_rounds": 16384}) == 0
+    assert hp.batched_workspace_size(4, 1230, {"global16_rounds": 16383}) > 0
 
 
 def test_one_part_per_pass_takes_a_smaller_workspace(lib):

@@ -101,6 +101,9 @@ def test_batched_parity_with_g():
     # a layer table of 3 entries in shared memory: every bucket of more than
     # one round is peeled again in the workspace
     {"threads": 256, "ctas_per_sm": 8, "smem_rounds": 3},
+    # and 3 entries on the 32-bit global path as well: every bucket of more
+    # than one round ends on the 64-bit path (64-bit records, 32-bit claims)
+    {"threads": 256, "ctas_per_sm": 8, "smem_rounds": 3, "global16_rounds": 3},
 ])
 def test_batched_results_do_not_depend_on_tuning(tuning):
     sizes, keys, off = _workload(B=120, median=700, seed=11, key_seed=13, extra_sizes=[25000])

@@ -99,6 +99,39 @@ def test_hash_degree_law_poisson():
         assert abs(got - mean) < 5 * math.sqrt(mean), (d, got, mean)
 
 
+# Published SplitMix64 (state, output) pairs: the generator's state after
+# i steps of 0x9E3779B97F4A7C15 from seed s is s + i * 0x9E3779B97F4A7C15, and
+# its output is mix64 of that state (seed 0, first output; seed 1234567,
+# outputs 1..3).
+_GOLDEN = 0x9E3779B97F4A7C15
+_PUBLISHED = [
+    (_GOLDEN, 0xE220A8397B1DCDAF),
+    ((1234567 + 1 * _GOLDEN) % 2**64, 6457827717110365317),
+    ((1234567 + 2 * _GOLDEN) % 2**64, 3203168211198807973),
+    ((1234567 + 3 * _GOLDEN) % 2**64, 9817491932198370423),
+]
+
+
+@pytest.mark.parametrize("r", [3, 4])
+@pytest.mark.parametrize("seed", [77, 2**64 - 2])
+@pytest.mark.parametrize("P", [1_000_003, 1_431_655_765])
+def test_hash_composition_from_published_vectors(r, seed, P):
+    # Vertex j of key k is (mix64(k XOR (seed + j)) mod P) + j P (sec. 3
+    # hash functions, sec. 4.3 parts).  Key j is chosen so that k XOR (seed +
+    # j) is a published SplitMix64 state: its vertex j must be the published
+    # output mod P, shifted into part j.  A misread composition -- mix64((k
+    # XOR seed) + j), mix64(k) XOR (seed + j), mix64(k XOR seed XOR j), or a
+    # missing part offset -- misses for some j.  The seed 2^64 - 2 makes seed
+    # + j wrap to 0 at j = 2.
+    if r == 4 and P > (2**32 - 1) // 4:
+        P = 1_000_000_007
+    keys = np.array([st ^ ((seed + j) % 2**64) for j, (st, _) in enumerate(_PUBLISHED[:r])],
+                    dtype=np.uint64)
+    e = oracle.hash_edges(keys, r * P, r, seed)
+    for j, (_, out) in enumerate(_PUBLISHED[:r]):
+        assert int(e[j, j]) == out % P + j * P, (j, int(e[j, j]))
+
+
 def test_hash_seed_changes_edges():
     k = inputs.keys(1000, 1)
     m = oracle.num_vertices(1000, 1230, 3)
