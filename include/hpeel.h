@@ -16,9 +16,11 @@
  *     never frees or keeps them after the call returns.  h_* pointers are
  *     host memory owned by the caller.
  *   - Work is issued on the caller's CUDA stream (a cudaStream_t passed as
- *     void*, NULL = the legacy default stream).  Calls that must decide on
- *     the host (how many rounds, whether to retry) synchronise that stream
- *     before returning; each call says whether it does.
+ *     void*, NULL = the legacy default stream).  Calls that decide on the
+ *     host (how many rounds, whether to retry) synchronise that stream
+ *     before returning and write their stats to host memory; each of them
+ *     has an *_async form that decides on the device instead (stats in
+ *     device memory, no synchronisation, capturable into a CUDA graph).
  *   - Scratch memory is a caller-provided workspace d_ws of at least the
  *     size the matching *_workspace_size() function returns, 256-byte
  *     aligned.  The library never calls cudaMalloc: every array of a call
@@ -70,9 +72,10 @@ typedef struct hpeel_stats {
     uint64_t hinge_moves;   /* peeled edges whose first claim came from a
                                vertex other than the hinge (a vertex of
                                smaller position claimed later in the round) */
-    uint32_t async_status;  /* hpeel_mphf_build_async: 1 peeled (G and rank
-                               directory written), 2 no seed peeled, 3 device
-                               check failed (device_err holds the code) */
+    uint32_t async_status;  /* the *_async calls: 1 done (outputs written),
+                               2 no seed peeled (builds), 3 device check
+                               failed (device_err holds the code), 4 more
+                               rounds than max_layers (peels) */
     uint32_t reserved32;
     uint64_t reserved;
 } hpeel_stats;
@@ -178,7 +181,8 @@ size_t hpeel_peel_workspace_size(uint64_t n, uint64_t m, uint32_t r);
  *   h_stats     host output or NULL: n_peeled, rounds, core_nonempty.
  *   2 <= r <= 4.  n = 0 is valid (empty order, no round).
  * Synchronises stream (the number of rounds is decided on the device and
- * read back).  Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL,
+ * read back); hpeel_peel_async is the form without a host round trip.
+ * Errors: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL,
  * HPEEL_ERR_CAPACITY (R > max_layers or R > HPEEL_MAX_ROUNDS, or a vertex
  * of degree 2^31 or more),
  * HPEEL_ERR_DEVICE_CHECK (a vertex id outside its part), HPEEL_ERR_CUDA.
@@ -212,6 +216,47 @@ hpeel_status hpeel_peel_general(const uint32_t *d_edges, uint64_t n, uint64_t m,
                                 void *stream);
 
 /*
+ * hpeel_peel with no host round trip: the whole peel -- records, incidence
+ * build, round 0 and the rounds (sec. 4.2, a while loop on the device),
+ * the canonical order with as many passes of its sort as the rounds need,
+ * the layer offsets -- is enqueued on stream as one CUDA graph, and the call
+ * returns at once.  It can be captured into a caller's CUDA graph or
+ * overlapped with other work on other streams.  hpeel_peel is its
+ * synchronous form (same results, stats on the host).
+ *   Arguments as hpeel_peel, except:
+ *   d_stats   device memory (not host), written at the end of the graph:
+ *             async_status 1 = peeled (d_order, d_claim and d_layer_off
+ *             written; n_peeled, rounds, core_nonempty, first_layer,
+ *             frontier, hinge_moves as hpeel_peel gives them), 3 = a device
+ *             check failed (device_err holds the code: 1 a vertex outside its
+ *             part, 3 more rounds than HPEEL_MAX_ROUNDS, 6 a vertex of degree
+ *             2^31 or more; nothing else written), 4 = more rounds than
+ *             max_layers (d_order and d_claim written, d_layer_off not).
+ * The graph is built on the first call with a given set of pointers and
+ * sizes and replayed by later calls with the same set (keep the workspace and
+ * the output buffers to reuse it; the inputs' contents may change between
+ * calls).  Returns HPEEL_OK once enqueued; errors found on the host:
+ * HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL, HPEEL_ERR_CUDA.  When
+ * stream is being captured (cudaStreamBeginCapture), the peel's nodes join
+ * the caller's graph at the capture position instead.
+ */
+hpeel_status hpeel_peel_async(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
+                              uint32_t *d_order, uint32_t *d_claim, uint64_t *d_layer_off,
+                              uint32_t max_layers, hpeel_stats *d_stats, void *d_ws,
+                              size_t ws_bytes, void *stream);
+
+/* hpeel_peel_general with no host round trip: as hpeel_peel_async, for a
+ * general r-hypergraph (arguments, results and limits of hpeel_peel_general;
+ * device_err 1 for a vertex >= m).  Workspace:
+ * hpeel_peel_general_workspace_size. */
+hpeel_status hpeel_peel_general_async(const uint32_t *d_edges, uint64_t n, uint64_t m,
+                                      uint32_t r, uint32_t *d_order, uint32_t *d_claim,
+                                      uint64_t *d_layer_off, uint32_t max_layers,
+                                      hpeel_stats *d_stats, void *d_ws, size_t ws_bytes,
+                                      void *stream);
+
+/*
+ * hpeel_peel without any allocation./*
  * hpeel_peel without any allocation.  The paper has no counterpart: this is
  * a calling convenience of this library.
  *
@@ -367,6 +412,24 @@ hpeel_status hpeel_sf_build(const uint64_t *d_keys, const uint32_t *d_values, ui
                             uint32_t max_tries, uint64_t *d_U, hpeel_stats *h_stats,
                             void *d_ws, size_t ws_bytes, void *stream);
 /*
+ * hpeel_sf_build with no host round trip: the reseed-and-retry loop, the
+ * rounds and the reverse-layer assignment run as loops on the device in one
+ * CUDA graph (as hpeel_mphf_build_async does for the MPHF), so the call can
+ * be captured into a caller's CUDA graph.  Arguments as hpeel_sf_build,
+ * except d_stats, which is device memory written at the end of the graph:
+ * async_status 1 = built (d_U written, seed_used set), 2 = no seed among
+ * max_tries peeled (d_U untouched), 3 = a device check failed (device_err 7:
+ * a value not below sigma; d_U incomplete).  Graph caching and capture as
+ * hpeel_mphf_build_async.  Returns HPEEL_OK once enqueued; errors found on
+ * the host: HPEEL_ERR_INVALID_ARG, HPEEL_ERR_WORKSPACE_TOO_SMALL,
+ * HPEEL_ERR_CUDA.
+ */
+hpeel_status hpeel_sf_build_async(const uint64_t *d_keys, const uint32_t *d_values, uint64_t n,
+                                  uint64_t sigma, uint64_t seed, uint32_t gamma_milli,
+                                  uint32_t max_tries, uint64_t *d_U, hpeel_stats *d_stats,
+                                  void *d_ws, size_t ws_bytes, void *stream);
+/*
+ * d_out[q] = f(d_keys[q]) = (u[h_0] + u[h_1] + u[h_2]) mod sigma for the u/*
  * d_out[q] = f(d_keys[q]) = (u[h_0] + u[h_1] + u[h_2]) mod sigma for the u
  * built with this seed (h_stats->seed_used), m and sigma.  For a key outside
  * the built set the result is some value in [0, sigma).  Asynchronous on

@@ -130,6 +130,12 @@ def lib():
         L.hpeel_peel_general.restype = st
         L.hpeel_peel_general.argtypes = [p, u64, u64, u32, p, p, p, u32, ctypes.POINTER(Stats),
                                          p, sz, p]
+        L.hpeel_peel_async.restype = st
+        L.hpeel_peel_async.argtypes = [p, u64, u64, u32, p, p, p, u32, p, p, sz, p]
+        L.hpeel_peel_general_async.restype = st
+        L.hpeel_peel_general_async.argtypes = [p, u64, u64, u32, p, p, p, u32, p, p, sz, p]
+        L.hpeel_sf_build_async.restype = st
+        L.hpeel_sf_build_async.argtypes = [p, p, u64, u64, u64, u32, u32, p, p, p, sz, p]
         L.hpeel_mphf_build_async.restype = st
         L.hpeel_mphf_build_async.argtypes = [p, u64, u64, u32, u32, p, p, p, p, sz, p]
         L.hpeel_probe_random_access.restype = st
@@ -258,6 +264,42 @@ def peel(edges, m: int, workspace=None, max_layers: int = 4096,
     return res
 
 
+@dataclass
+class AsyncPeel:
+    order: object      # int32 [n]
+    claim: object      # int32 [n]
+    layer_off: object  # int64 [max_layers + 1]: entries 0..rounds written
+    stats: object      # uint8 [sizeof(hpeel_stats)] device memory
+
+
+def peel_async(edges, m: int, workspace=None, max_layers: int = 4096, general: bool = False,
+               out=None) -> AsyncPeel:
+    """Device-driven peel (hpeel_peel_async, or hpeel_peel_general_async):
+    enqueued as one CUDA graph on the current stream, no host
+    synchronisation.  Read the stats with stats_from_device once the stream
+    is done.  out: an AsyncPeel of buffers to reuse (the graph is cached by
+    the set of pointers)."""
+    torch = _torch()
+    ep = _dev_ptr(edges, "edges", torch.int32, 2)
+    n, r = edges.shape
+    dev = edges.device
+    if out is None:
+        out = AsyncPeel(torch.empty(n, dtype=torch.int32, device=dev),
+                        torch.empty(n, dtype=torch.int32, device=dev),
+                        torch.empty(max_layers + 1, dtype=torch.int64, device=dev),
+                        torch.zeros(ctypes.sizeof(Stats), dtype=torch.uint8, device=dev))
+    elif out.layer_off.numel() < max_layers + 1:
+        raise ValueError("layer_off must hold max_layers + 1 entries")
+    ws = workspace if workspace is not None else _workspace(
+        peel_workspace_size(n, m, r, general), dev)
+    fn = lib().hpeel_peel_general_async if general else lib().hpeel_peel_async
+    _check(fn(ep, n, m, r, _dev_ptr(out.order, "order"), _dev_ptr(out.claim, "claim"),
+              _dev_ptr(out.layer_off, "layer_off"), max_layers,
+              _dev_ptr(out.stats, "stats", torch.uint8), _dev_ptr(ws, "workspace", torch.uint8),
+              ws.numel(), _stream()))
+    return out
+
+
 def mphf_lookup(keys, seed: int, m: int, G, rank_dir, out=None):
     """MPHF values of the query keys (hpeel_mphf_lookup): int32 [nq]."""
     torch = _torch()
@@ -311,6 +353,34 @@ def sf_build(keys, values, sigma: int, seed: int = 1, gamma_milli: int = 1230,
                                 _dev_ptr(U, "U", torch.int64), ctypes.byref(st),
                                 _dev_ptr(ws, "workspace", torch.uint8), ws.numel(), _stream()))
     return SfResult(U[:words], m, sigma, sf_bits(sigma), st.as_dict())
+
+
+def sf_build_async(keys, values, sigma: int, seed: int = 1, gamma_milli: int = 1230,
+                   max_tries: int = 8, workspace=None, U=None, stats=None):
+    """Device-driven static-function build (hpeel_sf_build_async): one CUDA
+    graph on the current stream, no host synchronisation.  Returns (U,
+    stats), stats a device uint8 tensor holding an hpeel_stats."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1, host_ok=True)
+    vp = _dev_ptr(values, "values", torch.int32, 1, host_ok=True)
+    n = keys.shape[0]
+    if values.shape[0] != n:
+        raise ValueError("values must hold n entries")
+    dev = keys.device if keys.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    words = int(lib().hpeel_sf_words(n, gamma_milli, sigma))
+    if U is None:
+        U = torch.empty(max(words, 1), dtype=torch.int64, device=dev)
+    elif U.numel() < words:
+        raise ValueError("U must hold hpeel_sf_words entries")
+    if stats is None:
+        stats = torch.zeros(ctypes.sizeof(Stats), dtype=torch.uint8, device=dev)
+    ws = workspace if workspace is not None else _workspace(sf_workspace_size(n, gamma_milli), dev)
+    _check(lib().hpeel_sf_build_async(kp, vp, n, sigma, seed, gamma_milli, max_tries,
+                                      _dev_ptr(U, "U", torch.int64),
+                                      _dev_ptr(stats, "stats", torch.uint8),
+                                      _dev_ptr(ws, "workspace", torch.uint8), ws.numel(),
+                                      _stream()))
+    return U, stats
 
 
 def sf_lookup(keys, seed: int, m: int, sigma: int, U, out=None):

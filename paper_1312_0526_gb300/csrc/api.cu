@@ -35,7 +35,7 @@ Ctl *pinned_ctl() {
 }
 
 struct PeelLayout {
-    size_t ctl, params, rec, state, claim, L, pairs, fill, pairs2, fill2, ovf, ovf_count, loff,
+    size_t ctl, params, emit, rec, state, claim, L, pairs, fill, pairs2, fill2, ovf, ovf_count, loff,
         hist, scantmp, total;
     uint32_t max_rounds;
     bool bucketed;
@@ -86,6 +86,7 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false)
     }
     p.ctl = take(sizeof(Ctl));
     p.params = take(sizeof(RoundParams));
+    p.emit = take(sizeof(EmitState));
     p.rec = take((r == 4 ? 32 : 16) * n);
     p.state = take(8 * m);
     const size_t ls = (r == 4 ? 32 : 16) * n;
@@ -548,6 +549,12 @@ struct AsyncArgs {
     hpeel_stats *stats;
     char *ws;
     int sms;
+    // static function (sec. 3, f: S -> [sigma]) instead of the MPHF: values
+    // non-null, U written instead of G and the rank directory
+    const uint32_t *values = nullptr;
+    uint64_t sigma = 0;
+    uint32_t bits = 0;
+    uint64_t *U = nullptr;
 };
 
 // into: a stream the caller is capturing (the build joins that graph at the
@@ -677,27 +684,36 @@ hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGrap
     HP_CAP(new_handle(s0, 0u, 0u, &h_ok));
     launch_async_if_peeled(L0, state, h_ok);
     HP_CAP(append_conditional(s0, h_ok, cudaGraphCondTypeIf, &b_ok));
-    {   // assignment in reverse layer order, then the rank directory
+    {   // assignment in reverse layer order, then the rank directory (MPHF)
         HP_CAP(begin_body(s1, b_ok));
         open = 2;
         const uint64_t words = ((uint64_t)m + 31) / 32, blocks = ((uint64_t)m + 511) / 512;
-        HP_CAP(cudaMemsetAsync(a.G, 0, 8 * words, s1));
+        if (a.values)
+            HP_CAP(cudaMemsetAsync(a.U, 0, 8 * (((uint64_t)m * a.bits + 63) / 64), s1));
+        else
+            HP_CAP(cudaMemsetAsync(a.G, 0, 8 * words, s1));
         HP_CAP(new_handle(s1, 0u, 0u, &h_asg));
         launch_async_assign_init(L1, state, h_asg);
         HP_CAP(append_conditional(s1, h_asg, cudaGraphCondTypeWhile, &b_asg));
         HP_CAP(begin_body(s2, b_asg));
         open = 3;
-        launch_assign_layer_at(L2, Ll, loff, &state->t, P, a.G);
+        if (a.values)
+            launch_sf_assign_layer_at(L2, Ll, loff, &state->t, a.values, a.sigma, a.bits, a.U,
+                                      ctl);
+        else
+            launch_assign_layer_at(L2, Ll, loff, &state->t, P, a.G);
         launch_async_assign_step(L2, state, h_asg);
         cudaGraph_t g = nullptr;
         HP_CAP(cudaStreamEndCapture(s2, &g));
         open = 2;
-        uint32_t *cnt = reinterpret_cast<uint32_t *>(a.ws + ml.rank_cnt);
-        uint32_t *scn = reinterpret_cast<uint32_t *>(a.ws + ml.rank_scan);
-        uint32_t *tmp = reinterpret_cast<uint32_t *>(a.ws + ml.rank_tmp);
-        launch_rank_counts(L1, a.G, m, cnt);
-        launch_scan_u32(L1, cnt, scn, blocks, tmp);
-        launch_widen_dir(L1, scn, cnt, blocks, a.D);
+        if (!a.values) {
+            uint32_t *cnt = reinterpret_cast<uint32_t *>(a.ws + ml.rank_cnt);
+            uint32_t *scn = reinterpret_cast<uint32_t *>(a.ws + ml.rank_scan);
+            uint32_t *tmp = reinterpret_cast<uint32_t *>(a.ws + ml.rank_tmp);
+            launch_rank_counts(L1, a.G, m, cnt);
+            launch_scan_u32(L1, cnt, scn, blocks, tmp);
+            launch_widen_dir(L1, scn, cnt, blocks, a.D);
+        }
         HP_CAP(cudaStreamEndCapture(s1, &g));
         open = 1;
     }
@@ -705,6 +721,204 @@ hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGrap
     if (!into) HP_CAP(cudaStreamEndCapture(s0, out));
     open = 0;
 #undef HP_CAP
+    return HPEEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven peel: the whole of hpeel_peel as one CUDA graph -- the build
+// (with the direct rebuild of an overflowed L2-blocked build in an if node),
+// round 0 and the while node of rounds, then, when no device check failed,
+// the canonical order with its passes in a while node, the layer offsets,
+// and the stats in device memory.
+// ---------------------------------------------------------------------------
+struct AsyncPeelArgs {
+    const uint32_t *edges;
+    uint32_t n, m, r;
+    bool general;
+    uint32_t *order, *claim;
+    uint64_t *layer_off;
+    uint32_t max_layers;
+    hpeel_stats *stats;
+    char *ws;
+    int sms;
+};
+
+hpeel_status capture_async_peel(const AsyncPeelArgs &a, cudaStream_t into, cudaGraph_t *out) {
+    cudaStream_t s0 = into ? into : capture_stream(0), s1 = capture_stream(1),
+                 s2 = capture_stream(2);
+    if (!s0 || !s1 || !s2) return fail(HPEEL_ERR_CUDA, "capture stream creation failed");
+    const PeelLayout lay = peel_layout(a.n, a.m, a.r, a.general);
+    char *ws = a.ws;
+    Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
+    uint4 *rec = reinterpret_cast<uint4 *>(ws + lay.rec);
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(ws + lay.state);
+    uint4 *Ll = reinterpret_cast<uint4 *>(ws + lay.L);
+    uint32_t *loff = reinterpret_cast<uint32_t *>(ws + lay.loff);
+    RoundParams *prm = reinterpret_cast<RoundParams *>(ws + lay.params);
+    EmitState *es = reinterpret_cast<EmitState *>(ws + lay.emit);
+    uint32_t *claim = a.claim ? a.claim : reinterpret_cast<uint32_t *>(ws + lay.claim);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + lay.hist);
+    uint32_t *scantmp = reinterpret_cast<uint32_t *>(ws + lay.scantmp);
+    // the edge records are dead once the claims are extracted: a later pass
+    // of the order sort reads its inputs from their space
+    uint32_t *tail = reinterpret_cast<uint32_t *>(rec);
+    const uint32_t n = a.n, m = a.m, r = a.r, P = a.general ? m : m / r;
+    Launch L0{s0, a.sms}, L1{s1, a.sms}, L2{s2, a.sms};
+    RoundParams rp{};
+    rp.st = st;
+    rp.rec = rec;
+    rp.L = Ll;
+    rp.loff = loff;
+    rp.ctl = ctl;
+    rp.n = n;
+    rp.m = m;
+    rp.P = P;
+    rp.max_rounds = lay.max_rounds;
+    const RoundLaunch k0 = round0_launch(L0, r, a.general), k1 = round_launch(L0, r, a.general);
+
+    int open = 0;
+    const int first = into ? 1 : 0;
+    cudaStream_t opened[3] = {s0, s1, s2};
+    auto abort_all = [&](hpeel_status stt) {
+        for (int i = open - 1; i >= first; i--) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(opened[i], &g);
+            if (i == 0 && g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        return stt;
+    };
+#define HP_CAP(call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return abort_all(fail(HPEEL_ERR_CUDA, "graph capture: %s failed: %s", #call,   \
+                                  cudaGetErrorString(e_)));                                \
+    } while (0)
+    auto begin_body = [&](cudaStream_t s, cudaGraph_t body) {
+        return cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed);
+    };
+
+    if (!into) HP_CAP(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
+    open = 1;
+    HP_CAP(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s0));
+    launch_set_params(L0, prm, rp);
+    cudaGraphConditionalHandle h_ovf = 0, h_in = 0, h_ok = 0, h_emit = 0;
+    cudaGraph_t b_ovf = nullptr, b_in = nullptr, b_ok = nullptr, b_emit = nullptr;
+    if (lay.bucketed) {
+        uint2 *pairs = reinterpret_cast<uint2 *>(ws + lay.pairs);
+        uint32_t *fill = reinterpret_cast<uint32_t *>(ws + lay.fill);
+        uint2 *pairs2 = reinterpret_cast<uint2 *>(ws + lay.pairs2);
+        uint32_t *fill2 = reinterpret_cast<uint32_t *>(ws + lay.fill2);
+        Overflow ov{reinterpret_cast<uint2 *>(ws + lay.ovf),
+                    reinterpret_cast<uint32_t *>(ws + lay.ovf_count), lay.plan.ovf_cap};
+        for (uint32_t pass = 0; pass < lay.plan.passes; pass++) {
+            HP_CAP(cudaMemsetAsync(fill2, 0, 4 * (size_t)lay.plan.subs_pass, s0));
+            HP_CAP(cudaMemsetAsync(ov.count, 0, 4, s0));
+            launch_build_bucketed(L0, lay.plan, nullptr, a.edges, n, r, FastMod{0, 0}, 0, P, rec,
+                                  pairs, fill, ov, ctl, a.general, nullptr, pass);
+            launch_apply_buckets(L0, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl, pass);
+        }
+        // an overflowed build is redone with direct updates (same result)
+        HP_CAP(new_handle(s0, 0u, 0u, &h_ovf));
+        launch_async_check_overflow(L0, ctl, h_ovf);
+        HP_CAP(append_conditional(s0, h_ovf, cudaGraphCondTypeIf, &b_ovf));
+        HP_CAP(begin_body(s1, b_ovf));
+        open = 2;
+        HP_CAP(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s1));
+        launch_fill_u32(L1, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
+        launch_records(L1, a.edges, n, r, P, rec, ctl, a.general);
+        launch_build_incidence(L1, rec, n, r, m, st, ctl);
+        cudaGraph_t g = nullptr;
+        HP_CAP(cudaStreamEndCapture(s1, &g));
+        open = 1;
+    } else {
+        launch_fill_u32(L0, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
+        launch_records(L0, a.edges, n, r, P, rec, ctl, a.general);
+        launch_build_incidence(L0, rec, n, r, m, st, ctl);
+    }
+    // round 0, then the while loop of rounds (as launch_round_graph)
+    HP_CAP(new_handle(s0, 0u, 0u, &h_in));
+    {
+        void *args[] = {(void *)&prm, &h_in};
+        count_launch();
+        HP_CAP(cudaLaunchKernel(k0.fn, dim3(k0.grid), dim3(k0.block), args, k0.smem, s0));
+    }
+    HP_CAP(append_conditional(s0, h_in, cudaGraphCondTypeWhile, &b_in));
+    HP_CAP(begin_body(s1, b_in));
+    open = 2;
+    {
+        void *args[] = {(void *)&prm, &h_in};
+        HP_CAP(cudaLaunchKernel(k1.fn, dim3(k1.grid), dim3(k1.block), args, k1.smem, s1));
+    }
+    {
+        cudaGraph_t g = nullptr;
+        HP_CAP(cudaStreamEndCapture(s1, &g));
+        open = 1;
+    }
+    // the canonical order, only when no device check failed
+    HP_CAP(new_handle(s0, 0u, 0u, &h_ok));
+    launch_async_if_ok(L0, ctl, h_ok);
+    HP_CAP(append_conditional(s0, h_ok, cudaGraphCondTypeIf, &b_ok));
+    {
+        HP_CAP(begin_body(s1, b_ok));
+        open = 2;
+        HP_CAP(new_handle(s1, 0u, 0u, &h_emit));
+        launch_emit_init(L1, ctl, n, es, h_emit);
+        launch_extract_claim_hist_dev(L1, rec, n, r, claim, es, hist);
+        HP_CAP(append_conditional(s1, h_emit, cudaGraphCondTypeWhile, &b_emit));
+        HP_CAP(begin_body(s2, b_emit));
+        open = 3;
+        launch_emit_pass_dev(L2, n, tail, claim, es, hist, scantmp, a.order);
+        launch_emit_advance(L2, es, loff, a.order, tail, h_emit);
+        cudaGraph_t g = nullptr;
+        HP_CAP(cudaStreamEndCapture(s2, &g));
+        open = 2;
+        if (a.layer_off) launch_layer_off_dev(L1, loff, ctl, a.max_layers, a.layer_off);
+        HP_CAP(cudaStreamEndCapture(s1, &g));
+        open = 1;
+    }
+    launch_peel_async_stats(L0, ctl, n, a.max_layers, a.layer_off != nullptr, a.stats);
+    if (!into) HP_CAP(cudaStreamEndCapture(s0, out));
+    open = 0;
+#undef HP_CAP
+    return HPEEL_OK;
+}
+
+// Launch the cached executable graph for key on L.stream, capturing and
+// instantiating it with capture() on first use (least recently used graphs
+// are evicted, after their latest launch has finished).
+template <typename F>
+hpeel_status launch_cached_graph(const Launch &L, const std::string &key, F capture) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it == g_graphs.end()) {
+        while (g_graph_lru.size() >= kGraphCache) {
+            auto old = g_graphs.find(g_graph_lru.front());
+            if (old != g_graphs.end()) {
+                destroy_graph(old->second);
+                g_graphs.erase(old);
+            }
+            g_graph_lru.erase(g_graph_lru.begin());
+        }
+        RoundGraph rg;
+        HP_TRY(capture(&rg.graph));
+        if (cudaGraphInstantiate(&rg.exec, rg.graph, 0) != cudaSuccess ||
+            cudaEventCreateWithFlags(&rg.done, cudaEventDisableTiming) != cudaSuccess) {
+            const cudaError_t e = cudaGetLastError();
+            destroy_graph(rg);
+            return fail(HPEEL_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+        }
+        it = g_graphs.emplace(key, rg).first;
+        g_graph_lru.push_back(key);
+    } else {
+        auto pos = std::find(g_graph_lru.begin(), g_graph_lru.end(), key);
+        if (pos != g_graph_lru.end()) g_graph_lru.erase(pos);
+        g_graph_lru.push_back(key);
+    }
+    HP_CUDA(cudaGraphLaunch(it->second.exec, L.stream));
+    HP_CUDA(cudaEventRecord(it->second.done, L.stream));
     return HPEEL_OK;
 }
 
@@ -885,6 +1099,81 @@ hpeel_status hpeel_peel_general(const uint32_t *d_edges, uint64_t n, uint64_t m,
                       d_ws, ws_bytes, stream);
 }
 
+}  // extern "C"
+
+namespace {
+
+hpeel_status peel_async_entry(bool general, const uint32_t *d_edges, uint64_t n, uint64_t m,
+                              uint32_t r, uint32_t *d_order, uint32_t *d_claim,
+                              uint64_t *d_layer_off, uint32_t max_layers, hpeel_stats *d_stats,
+                              void *d_ws, size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (r < 2 || r > 4) return fail(HPEEL_ERR_INVALID_ARG, "r = %u, need 2 <= r <= 4", r);
+    if (n >= (1ull << 32) || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    if (general && n >= (1ull << 30))
+        return fail(HPEEL_ERR_INVALID_ARG, "a general hypergraph needs n < 2^30");
+    if (!d_stats) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    if (n == 0) {
+        launch_peel_async_empty(L, d_stats, d_layer_off);
+        return check_launch("peel_async_empty");
+    }
+    if (m == 0 || (!general && m % r != 0))
+        return fail(HPEEL_ERR_INVALID_ARG, general ? "m must be positive"
+                                                   : "m = %llu must be a positive multiple of r",
+                    (unsigned long long)m);
+    if (!d_edges || !d_order || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_ws & 255u) != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const size_t need = peel_layout(n, m, r, general).total;
+    if (ws_bytes < need)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes, need);
+    AsyncPeelArgs a{d_edges, (uint32_t)n, (uint32_t)m, r, general, d_order, d_claim,
+                    d_layer_off, max_layers, d_stats, (char *)d_ws, L.sms};
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HP_CUDA(cudaStreamIsCapturing(L.stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {
+        // the caller is capturing: the peel's nodes join the caller's graph
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        return capture_async_peel(a, L.stream, nullptr);
+    }
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    const hpeel_tuning tu = tuning();
+    char keybuf[320];
+    snprintf(keybuf, sizeof keybuf, "peel|%d|%d|%p|%llu|%llu|%u|%p|%p|%p|%u|%p|%p|%u|%u|%u|%u|%d",
+             dev, general ? 1 : 0, (const void *)d_edges, (unsigned long long)n,
+             (unsigned long long)m, r, (void *)d_order, (void *)d_claim, (void *)d_layer_off,
+             max_layers, (void *)d_stats, d_ws, tu.bucket_shift, tu.bucket_min_vertices,
+             tu.bucket_sub_shift, tu.bucket_part_passes, L.sms);
+    return launch_cached_graph(L, std::string(keybuf), [&](cudaGraph_t *g) {
+        return capture_async_peel(a, nullptr, g);
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+hpeel_status hpeel_peel_async(const uint32_t *d_edges, uint64_t n, uint64_t m, uint32_t r,
+                              uint32_t *d_order, uint32_t *d_claim, uint64_t *d_layer_off,
+                              uint32_t max_layers, hpeel_stats *d_stats, void *d_ws,
+                              size_t ws_bytes, void *stream) {
+    return peel_async_entry(false, d_edges, n, m, r, d_order, d_claim, d_layer_off, max_layers,
+                            d_stats, d_ws, ws_bytes, stream);
+}
+
+hpeel_status hpeel_peel_general_async(const uint32_t *d_edges, uint64_t n, uint64_t m,
+                                      uint32_t r, uint32_t *d_order, uint32_t *d_claim,
+                                      uint64_t *d_layer_off, uint32_t max_layers,
+                                      hpeel_stats *d_stats, void *d_ws, size_t ws_bytes,
+                                      void *stream) {
+    return peel_async_entry(true, d_edges, n, m, r, d_order, d_claim, d_layer_off, max_layers,
+                            d_stats, d_ws, ws_bytes, stream);
+}
+
 size_t hpeel_mphf_workspace_size(uint64_t n, uint32_t gamma_milli) {
     return mphf_layout(n, gamma_milli).total;
 }
@@ -1017,36 +1306,9 @@ hpeel_status hpeel_mphf_build_async(const uint64_t *d_keys, uint64_t n, uint64_t
              gamma_milli, max_tries, (void *)d_G, (void *)d_rank_dir, (void *)d_stats, d_ws,
              tu.bucket_shift, tu.bucket_min_vertices, tu.bucket_sub_shift, tu.bucket_part_passes,
              L.sms);
-    const std::string key(keybuf);
-    std::lock_guard<std::mutex> lk(g_graph_mu);
-    auto it = g_graphs.find(key);
-    if (it == g_graphs.end()) {
-        while (g_graph_lru.size() >= kGraphCache) {
-            auto old = g_graphs.find(g_graph_lru.front());
-            if (old != g_graphs.end()) {
-                destroy_graph(old->second);
-                g_graphs.erase(old);
-            }
-            g_graph_lru.erase(g_graph_lru.begin());
-        }
-        RoundGraph rg;
-        HP_TRY(capture_async_build(a, nullptr, &rg.graph));
-        if (cudaGraphInstantiate(&rg.exec, rg.graph, 0) != cudaSuccess ||
-            cudaEventCreateWithFlags(&rg.done, cudaEventDisableTiming) != cudaSuccess) {
-            const cudaError_t e = cudaGetLastError();
-            destroy_graph(rg);
-            return fail(HPEEL_ERR_CUDA, "device-driven build graph: %s", cudaGetErrorString(e));
-        }
-        it = g_graphs.emplace(key, rg).first;
-        g_graph_lru.push_back(key);
-    } else {
-        auto pos = std::find(g_graph_lru.begin(), g_graph_lru.end(), key);
-        if (pos != g_graph_lru.end()) g_graph_lru.erase(pos);
-        g_graph_lru.push_back(key);
-    }
-    HP_CUDA(cudaGraphLaunch(it->second.exec, L.stream));
-    HP_CUDA(cudaEventRecord(it->second.done, L.stream));
-    return HPEEL_OK;
+    return launch_cached_graph(L, std::string(keybuf), [&](cudaGraph_t *g) {
+        return capture_async_build(a, nullptr, g);
+    });
 }
 
 uint32_t hpeel_sf_bits(uint64_t sigma) {
@@ -1060,8 +1322,10 @@ uint64_t hpeel_sf_words(uint64_t n, uint32_t gamma_milli, uint64_t sigma) {
     return (m * hpeel_sf_bits(sigma) + 63) / 64;
 }
 
+// The static-function workspace has the MPHF's layout (the device-driven
+// build keeps its loop state at the front); the rank arrays stay unused.
 size_t hpeel_sf_workspace_size(uint64_t n, uint32_t gamma_milli) {
-    return peel_layout(n, hpeel_num_vertices(n, gamma_milli, 3), 3).total;
+    return mphf_layout(n, gamma_milli).total;
 }
 
 hpeel_status hpeel_sf_build(const uint64_t *d_keys, const uint32_t *d_values, uint64_t n,
@@ -1087,11 +1351,12 @@ hpeel_status hpeel_sf_build(const uint64_t *d_keys, const uint32_t *d_values, ui
     if (!d_keys || !d_values || !d_U || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
     if (((uintptr_t)d_ws & 255u) != 0)
         return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    const PeelLayout lay = peel_layout(n, m, 3);
-    if (ws_bytes < lay.total)
+    const MphfLayout ml = mphf_layout(n, gamma_milli);
+    if (ws_bytes < ml.total)
         return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
-                    lay.total);
-    char *ws = (char *)d_ws;
+                    ml.total);
+    char *ws = (char *)d_ws + ml.peel;
+    const PeelLayout lay = peel_layout(n, m, 3);
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
     const uint32_t b = hpeel_sf_bits(sigma);
     const uint64_t words = (m * b + 63) / 64;
@@ -1135,6 +1400,60 @@ hpeel_status hpeel_sf_build(const uint64_t *d_keys, const uint32_t *d_values, ui
     }
     return fail(HPEEL_ERR_RETRIES_EXHAUSTED, "2-core non-empty for seeds %llu..%llu",
                 (unsigned long long)seed, (unsigned long long)(seed + max_tries - 1));
+}
+
+hpeel_status hpeel_sf_build_async(const uint64_t *d_keys, const uint32_t *d_values, uint64_t n,
+                                  uint64_t sigma, uint64_t seed, uint32_t gamma_milli,
+                                  uint32_t max_tries, uint64_t *d_U, hpeel_stats *d_stats,
+                                  void *d_ws, size_t ws_bytes, void *stream) {
+    g_last_error.clear();
+    if (gamma_milli == 0) return fail(HPEEL_ERR_INVALID_ARG, "gamma_milli must be positive");
+    if (sigma < 2 || sigma > (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "sigma = %llu, need 2 <= sigma <= 2^32",
+                    (unsigned long long)sigma);
+    const MphfLayout lay = mphf_layout(n, gamma_milli);
+    const uint64_t m = lay.m;
+    if (n >= (1ull << 32) || m >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "n and m must be below 2^32");
+    if (max_tries == 0) return fail(HPEEL_ERR_INVALID_ARG, "max_tries must be positive");
+    if (!d_stats) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    if (n == 0) {
+        launch_async_empty(L, d_stats, seed, nullptr);
+        return check_launch("async_empty");
+    }
+    if (!d_keys || !d_values || !d_U || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_ws & 255u) != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < lay.total)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
+                    lay.total);
+    AsyncArgs a{d_keys, (uint32_t)n, (uint32_t)m, max_tries, seed, gamma_milli,
+                nullptr, nullptr, d_stats, (char *)d_ws, L.sms};
+    a.values = d_values;
+    a.sigma = sigma;
+    a.bits = hpeel_sf_bits(sigma);
+    a.U = d_U;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HP_CUDA(cudaStreamIsCapturing(L.stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        return capture_async_build(a, L.stream, nullptr);
+    }
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    const hpeel_tuning tu = tuning();
+    char keybuf[360];
+    snprintf(keybuf, sizeof keybuf,
+             "sf|%d|%p|%p|%llu|%llu|%llu|%u|%u|%p|%p|%p|%u|%u|%u|%u|%d", dev,
+             (const void *)d_keys, (const void *)d_values, (unsigned long long)n,
+             (unsigned long long)sigma, (unsigned long long)seed, gamma_milli, max_tries,
+             (void *)d_U, (void *)d_stats, d_ws, tu.bucket_shift, tu.bucket_min_vertices,
+             tu.bucket_sub_shift, tu.bucket_part_passes, L.sms);
+    return launch_cached_graph(L, std::string(keybuf), [&](cudaGraph_t *g) {
+        return capture_async_build(a, nullptr, g);
+    });
 }
 
 hpeel_status hpeel_sf_lookup(const uint64_t *d_keys, uint64_t nq, uint64_t seed, uint64_t m,

@@ -61,17 +61,70 @@ __global__ void k_async_assign_step(AsyncState *s, cudaGraphConditionalHandle h)
 
 __global__ void k_async_stats(const AsyncState *s, const Ctl *ctl, hpeel_stats *out) {
     hpeel_stats st{};
+    // a check that fails after a successful peel (a static-function value
+    // not below sigma) turns the outcome into a device error
+    const uint32_t status =
+        s->status == kAsyncPeeled && ctl->err ? (uint32_t)kAsyncDeviceError : s->status;
     st.n_peeled = ctl->lcur;
     st.rounds = ctl->more ? ctl->round + 1 : ctl->round;
-    st.core_nonempty = s->status == kAsyncRetriesExhausted ? 1u : 0u;
-    st.seed_used = s->status == kAsyncPeeled ? s->seed : 0ull;
+    st.core_nonempty = status == kAsyncRetriesExhausted ? 1u : 0u;
+    st.seed_used = status == kAsyncPeeled ? s->seed : 0ull;
     st.attempts = s->attempt + 1;
-    st.device_err = s->status == kAsyncDeviceError ? ctl->err : 0u;
+    st.device_err = status == kAsyncDeviceError ? ctl->err : 0u;
     st.first_layer = ctl->first_layer;
     st.frontier = ctl->cross;
     st.hinge_moves = ctl->moves;
-    st.async_status = s->status;
+    st.async_status = status;
     *out = st;
+}
+
+// ------------------------------------------------------ device-driven peel --
+// 1 when no kernel raised a device error: the canonical order runs.
+__global__ void k_async_if_ok(const Ctl *ctl, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, ctl->err == 0u ? 1u : 0u);
+}
+
+// Stats of a device-driven peel: async_status 1 = peeled (order and claims
+// written; core_nonempty tells whether a 2-core is left), 3 = a device check
+// failed (device_err holds the code; outputs not written), 4 = more rounds
+// than the caller's layer table holds (order and claims written, layer
+// offsets not).
+__global__ void k_peel_async_stats(const Ctl *ctl, uint32_t n, uint32_t max_layers,
+                                   uint32_t want_layer_off, hpeel_stats *out) {
+    hpeel_stats st{};
+    st.n_peeled = ctl->lcur;
+    st.rounds = ctl->more ? ctl->round + 1 : ctl->round;
+    st.core_nonempty = ctl->lcur < n ? 1u : 0u;
+    st.attempts = 1;
+    st.device_err = ctl->err;
+    st.first_layer = ctl->first_layer;
+    st.frontier = ctl->cross;
+    st.hinge_moves = ctl->moves;
+    st.async_status = ctl->err ? 3u : (want_layer_off && st.rounds > max_layers ? 4u : 1u);
+    *out = st;
+}
+
+// No edges: an empty order, no round.
+__global__ void k_peel_async_empty(hpeel_stats *out, uint64_t *layer_off) {
+    hpeel_stats st{};
+    st.attempts = 1;
+    st.async_status = 1u;
+    *out = st;
+    if (layer_off) layer_off[0] = 0;
+}
+
+void launch_async_if_ok(const Launch &L, const Ctl *ctl, cudaGraphConditionalHandle h) {
+    count_launch();
+    k_async_if_ok<<<1, 1, 0, L.stream>>>(ctl, h);
+}
+void launch_peel_async_stats(const Launch &L, const Ctl *ctl, uint32_t n, uint32_t max_layers,
+                             bool want_layer_off, hpeel_stats *out) {
+    count_launch();
+    k_peel_async_stats<<<1, 1, 0, L.stream>>>(ctl, n, max_layers, want_layer_off ? 1u : 0u, out);
+}
+void launch_peel_async_empty(const Launch &L, hpeel_stats *out, uint64_t *layer_off) {
+    count_launch();
+    k_peel_async_empty<<<1, 1, 0, L.stream>>>(out, layer_off);
 }
 
 // No keys: nothing to peel; the stats of a build that succeeded at once.

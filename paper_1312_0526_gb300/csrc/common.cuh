@@ -52,6 +52,14 @@ struct AsyncState {
     uint32_t n;
 };
 
+// Pass parameters of the canonical-order sort when the device drives it
+// (the number of rounds is never read back to the host): pass k sorts the
+// count inputs from seg on by keys base .. base + nb - 1 (the last bin takes
+// every larger key); more = 1 while another pass follows.
+struct EmitState {
+    uint32_t n, R, nkeys, base, seg, count, nb, more;
+};
+
 // Arguments of the round-loop kernels, kept in the workspace so the CUDA
 // graph of a round loop depends only on where the workspace is.
 struct RoundParams {

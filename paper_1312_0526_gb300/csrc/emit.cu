@@ -4,8 +4,10 @@
 // makes it unique), then the 2-core edges ascending.
 //
 // One pass sorts by up to kEmitBins keys: key k of an edge (round, or
-// core_key for an unclaimed edge) goes to bin min(k - base, nbins - 1).  The
-// host runs further passes on the last bin when there are more rounds.
+// core_key for an unclaimed edge) goes to bin min(k - base, nbins - 1).
+// Further passes sort the last bin again when there are more rounds; the
+// host decides on them, or, for a graph that never returns to the host, the
+// device (the *_dev kernels at the end of this file).
 //   hist    -- per tile of kEmitTile consecutive inputs, bin counts, stored
 //              bin-major: hist[b * tiles + tile] (the first pass's counts
 //              are taken while the claims are extracted from the records);
@@ -44,9 +46,10 @@ __device__ __forceinline__ int bin_planes(uint32_t nbins) {
     return nbins > 1 ? 32 - __clz(nbins - 1) : 0;
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_emit_hist(const uint32_t *__restrict__ src, uint32_t count, const uint32_t *__restrict__ claim,
-            uint32_t base, uint32_t core_key, uint32_t nbins, uint32_t *__restrict__ hist) {
+__device__ __forceinline__ void emit_hist(const uint32_t *__restrict__ src, uint32_t count,
+                                          const uint32_t *__restrict__ claim, uint32_t base,
+                                          uint32_t core_key, uint32_t nbins,
+                                          uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[kEmitBins];
     const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
     for (uint32_t b = threadIdx.x; b < nbins; b += kThreads) h[b] = 0;
@@ -65,13 +68,20 @@ k_emit_hist(const uint32_t *__restrict__ src, uint32_t count, const uint32_t *__
         hist[(uint64_t)b * tiles + blockIdx.x] = h[b];
 }
 
+__global__ void __launch_bounds__(kThreads)
+k_emit_hist(const uint32_t *__restrict__ src, uint32_t count, const uint32_t *__restrict__ claim,
+            uint32_t base, uint32_t core_key, uint32_t nbins, uint32_t *__restrict__ hist) {
+    emit_hist(src, count, claim, base, core_key, nbins, hist);
+}
+
 // The first pass's histogram taken while the claims are extracted from the
 // edge records (one block per tile of kEmitTile consecutive edges): the
 // claim array is written once and not read back for the counts.
 template <int R>
-__global__ void __launch_bounds__(kThreads)
-k_extract_claim_hist(const uint4 *__restrict__ rec, uint32_t n, uint32_t *__restrict__ claim,
-                     uint32_t core_key, uint32_t nbins, uint32_t *__restrict__ hist) {
+__device__ __forceinline__ void extract_claim_hist(const uint4 *__restrict__ rec, uint32_t n,
+                                                   uint32_t *__restrict__ claim,
+                                                   uint32_t core_key, uint32_t nbins,
+                                                   uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[kEmitBins];
     const uint32_t tiles = (n + kEmitTile - 1) / kEmitTile;
     for (uint32_t b = threadIdx.x; b < nbins; b += kThreads) h[b] = 0;
@@ -95,6 +105,13 @@ k_extract_claim_hist(const uint4 *__restrict__ rec, uint32_t n, uint32_t *__rest
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < nbins; b += kThreads)
         hist[(uint64_t)b * tiles + blockIdx.x] = h[b];
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_extract_claim_hist(const uint4 *__restrict__ rec, uint32_t n, uint32_t *__restrict__ claim,
+                     uint32_t core_key, uint32_t nbins, uint32_t *__restrict__ hist) {
+    extract_claim_hist<R>(rec, n, claim, core_key, nbins, hist);
 }
 
 void launch_extract_claim_hist(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
@@ -121,10 +138,11 @@ void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, cons
 #ifndef HPEEL_SCATTER_MIN_BLOCKS
 #define HPEEL_SCATTER_MIN_BLOCKS 4
 #endif
-__global__ void __launch_bounds__(kThreads, HPEEL_SCATTER_MIN_BLOCKS)
-k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
-               const uint32_t *__restrict__ claim, uint32_t base, uint32_t core_key,
-               uint32_t nbins, const uint32_t *__restrict__ offs, uint32_t *__restrict__ out) {
+__device__ __forceinline__ void emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
+                                             const uint32_t *__restrict__ claim, uint32_t base,
+                                             uint32_t core_key, uint32_t nbins,
+                                             const uint32_t *__restrict__ offs,
+                                             uint32_t *__restrict__ out) {
     __shared__ uint32_t wc[kEmitWarps][kEmitBins];  // per warp and bin: count, then slot
     __shared__ uint32_t obase[kEmitBins];            // output index of tile slot 0 of the bin
     __shared__ uint32_t stage[kEmitTile];            // the tile's edge ids, ordered by bin
@@ -205,6 +223,13 @@ k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
     for (uint32_t k = threadIdx.x; k < tn; k += kThreads) out[obase[sbin[k]] + k] = stage[k];
 }
 
+__global__ void __launch_bounds__(kThreads, HPEEL_SCATTER_MIN_BLOCKS)
+k_emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
+               const uint32_t *__restrict__ claim, uint32_t base, uint32_t core_key,
+               uint32_t nbins, const uint32_t *__restrict__ offs, uint32_t *__restrict__ out) {
+    emit_scatter(src, count, claim, base, core_key, nbins, offs, out);
+}
+
 void launch_emit_scatter(const Launch &L, const uint32_t *src, uint32_t count,
                          const uint32_t *claim, uint32_t base, uint32_t core_key, uint32_t nbins,
                          const uint32_t *offs, uint32_t *out) {
@@ -262,8 +287,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
     return before;
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const uint32_t *__restrict__ in, uint64_t count, uint32_t *__restrict__ sums) {
+__device__ __forceinline__ void scan_reduce_block(const uint32_t *__restrict__ in, uint64_t count,
+                                                  uint32_t *__restrict__ sums) {
     const uint64_t b0 = (uint64_t)blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kScanItems;
     uint32_t s = 0;
 #pragma unroll
@@ -275,7 +300,12 @@ k_scan_reduce(const uint32_t *__restrict__ in, uint64_t count, uint32_t *__restr
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_down(const uint32_t *in, uint32_t *out, uint64_t count, const uint32_t *__restrict__ offs) {
+k_scan_reduce(const uint32_t *__restrict__ in, uint64_t count, uint32_t *__restrict__ sums) {
+    scan_reduce_block(in, count, sums);
+}
+
+__device__ __forceinline__ void scan_down_block(const uint32_t *in, uint32_t *out, uint64_t count,
+                                                const uint32_t *__restrict__ offs) {
     const uint64_t b0 = (uint64_t)blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -290,6 +320,11 @@ k_scan_down(const uint32_t *in, uint32_t *out, uint64_t count, const uint32_t *_
         if (b0 + k < count) out[b0 + k] = run;
         run += v[k];
     }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_down(const uint32_t *in, uint32_t *out, uint64_t count, const uint32_t *__restrict__ offs) {
+    scan_down_block(in, out, count, offs);
 }
 
 size_t scan_tmp_words(uint64_t count) {
@@ -316,6 +351,179 @@ void launch_scan_u32(const Launch &L, const uint32_t *in, uint32_t *out, uint64_
     launch_scan_u32(L, sums, sums, blocks, tmp + blocks);
     count_launch();
     k_scan_down<<<(unsigned)blocks, kScanThreads, 0, L.stream>>>(in, out, count, sums);
+}
+
+}  // namespace hp
+
+// ------------------------------------------------- device-driven passes --
+// The same passes with their parameters in an EmitState in device memory,
+// for a CUDA graph that runs them as the body of a while node: the number
+// of rounds (and so of passes) is never read back to the host.  Every kernel
+// is launched with the grid of the largest pass (the first, over all n
+// edges); blocks past the current pass's tiles return at once.
+namespace hp {
+
+__global__ void k_emit_init(const Ctl *__restrict__ ctl, uint32_t n, EmitState *es,
+                            cudaGraphConditionalHandle h) {
+    EmitState e;
+    e.n = n;
+    e.R = ctl->more ? ctl->round + 1 : ctl->round;
+    e.nkeys = e.R + 1;
+    e.base = 0;
+    e.seg = 0;
+    e.count = n;
+    e.nb = e.nkeys < kEmitBins ? e.nkeys : kEmitBins;
+    e.more = 1;
+    *es = e;
+    cudaGraphSetConditional(h, 1u);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kThreads)
+k_extract_claim_hist_dev(const uint4 *__restrict__ rec, uint32_t n, uint32_t *__restrict__ claim,
+                         const EmitState *__restrict__ es, uint32_t *__restrict__ hist) {
+    extract_claim_hist<R>(rec, n, claim, es->R, es->nb, hist);
+}
+
+// the histogram of a later pass (the first pass's comes with the claims)
+__global__ void __launch_bounds__(kThreads)
+k_emit_hist_dev(const uint32_t *__restrict__ tail, const uint32_t *__restrict__ claim,
+                const EmitState *__restrict__ es, uint32_t *__restrict__ hist) {
+    const EmitState e = *es;
+    if (e.base == 0 || blockIdx.x >= (e.count + kEmitTile - 1) / kEmitTile) return;
+    emit_hist(tail + e.seg, e.count, claim, e.base, e.R, e.nb, hist);
+}
+
+__global__ void __launch_bounds__(kThreads, HPEEL_SCATTER_MIN_BLOCKS)
+k_emit_scatter_dev(const uint32_t *__restrict__ tail, const uint32_t *__restrict__ claim,
+                   const EmitState *__restrict__ es, const uint32_t *__restrict__ offs,
+                   uint32_t *__restrict__ order) {
+    const EmitState e = *es;
+    if (blockIdx.x >= (e.count + kEmitTile - 1) / kEmitTile) return;
+    emit_scatter(e.base ? tail + e.seg : nullptr, e.count, claim, e.base, e.R, e.nb, offs,
+                 order + e.seg);
+}
+
+// After a pass: stop, or move to the last bin's keys (they start at the
+// layer offset of their first round).
+__global__ void k_emit_advance(EmitState *es, const uint32_t *__restrict__ loff,
+                               cudaGraphConditionalHandle h) {
+    EmitState e = *es;
+    if (e.nkeys - e.base <= kEmitBins) {
+        es->more = 0;
+        cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    e.base += e.nb - 1;
+    e.seg = loff[e.base];
+    e.count = e.n - e.seg;
+    e.nb = e.nkeys - e.base < kEmitBins ? e.nkeys - e.base : kEmitBins;
+    e.more = 1;
+    *es = e;
+    cudaGraphSetConditional(h, 1u);
+}
+
+// The next pass reads its inputs from a copy of the order's tail.
+__global__ void k_emit_copy_tail(const uint32_t *__restrict__ order, uint32_t *__restrict__ tail,
+                                 const EmitState *__restrict__ es) {
+    const EmitState e = *es;
+    if (!e.more) return;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = e.seg + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < e.n; i += stride)
+        tail[i] = order[i];
+}
+
+// Scan of the pass's histogram: count = nb x tiles, level l of the reduce-
+// then-scan hierarchy holds ceil(count / 4096^l) values.
+__device__ __forceinline__ uint64_t emit_scan_count(const EmitState *es, int level) {
+    uint64_t c = (uint64_t)es->nb * ((es->count + kEmitTile - 1) / kEmitTile);
+    for (int l = 0; l < level; l++) c = (c + kScanBlock - 1) / kScanBlock;
+    return c;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce_dev(const uint32_t *__restrict__ in, const EmitState *__restrict__ es, int level,
+                  uint32_t *__restrict__ sums) {
+    const uint64_t count = emit_scan_count(es, level);
+    if ((uint64_t)blockIdx.x * kScanBlock >= count) return;
+    scan_reduce_block(in, count, sums);
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_down_dev(const uint32_t *in, uint32_t *out, const EmitState *__restrict__ es, int level,
+                const uint32_t *__restrict__ offs) {
+    const uint64_t count = emit_scan_count(es, level);
+    if ((uint64_t)blockIdx.x * kScanBlock >= count) return;
+    scan_down_block(in, out, count, offs);
+}
+
+// Launch structure of the largest count; smaller counts leave blocks idle.
+void launch_scan_dev(const Launch &L, const uint32_t *in, uint32_t *out, uint64_t max_count,
+                     const EmitState *es, int level, uint32_t *tmp) {
+    if (max_count <= kScanBlock) {
+        count_launch();
+        k_scan_down_dev<<<1, kScanThreads, 0, L.stream>>>(in, out, es, level, nullptr);
+        return;
+    }
+    const uint64_t blocks = (max_count + kScanBlock - 1) / kScanBlock;
+    count_launch();
+    k_scan_reduce_dev<<<(unsigned)blocks, kScanThreads, 0, L.stream>>>(in, es, level, tmp);
+    launch_scan_dev(L, tmp, tmp, blocks, es, level + 1, tmp + blocks);
+    count_launch();
+    k_scan_down_dev<<<(unsigned)blocks, kScanThreads, 0, L.stream>>>(in, out, es, level, tmp);
+}
+
+// layer_off[t] = loff[t] for t <= R, when R fits the caller's table.
+__global__ void k_layer_off_dev(const uint32_t *__restrict__ loff, const Ctl *__restrict__ ctl,
+                                uint32_t max_layers, uint64_t *__restrict__ out) {
+    const uint32_t R = ctl->more ? ctl->round + 1 : ctl->round;
+    if (R > max_layers) return;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t <= R; t += gridDim.x * blockDim.x)
+        out[t] = loff[t];
+}
+
+void launch_emit_init(const Launch &L, const Ctl *ctl, uint32_t n, EmitState *es,
+                      cudaGraphConditionalHandle h) {
+    count_launch();
+    k_emit_init<<<1, 1, 0, L.stream>>>(ctl, n, es, h);
+}
+
+void launch_extract_claim_hist_dev(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                                   uint32_t *claim, const EmitState *es, uint32_t *hist) {
+    if (n == 0) return;
+    const uint32_t tiles = (n + kEmitTile - 1) / kEmitTile;
+    count_launch();
+    switch (r) {
+    case 2: k_extract_claim_hist_dev<2><<<tiles, kThreads, 0, L.stream>>>(rec, n, claim, es, hist); break;
+    case 3: k_extract_claim_hist_dev<3><<<tiles, kThreads, 0, L.stream>>>(rec, n, claim, es, hist); break;
+    case 4: k_extract_claim_hist_dev<4><<<tiles, kThreads, 0, L.stream>>>(rec, n, claim, es, hist); break;
+    }
+}
+
+void launch_emit_pass_dev(const Launch &L, uint32_t n, const uint32_t *tail, const uint32_t *claim,
+                          const EmitState *es, uint32_t *hist, uint32_t *scantmp,
+                          uint32_t *order) {
+    const uint32_t tiles = (n + kEmitTile - 1) / kEmitTile;
+    count_launch();
+    k_emit_hist_dev<<<tiles, kThreads, 0, L.stream>>>(tail, claim, es, hist);
+    launch_scan_dev(L, hist, hist, (uint64_t)kEmitBins * tiles, es, 0, scantmp);
+    count_launch();
+    k_emit_scatter_dev<<<tiles, kThreads, 0, L.stream>>>(tail, claim, es, hist, order);
+}
+
+void launch_emit_advance(const Launch &L, EmitState *es, const uint32_t *loff, uint32_t *order,
+                         uint32_t *tail, cudaGraphConditionalHandle h) {
+    count_launch();
+    k_emit_advance<<<1, 1, 0, L.stream>>>(es, loff, h);
+    count_launch();
+    k_emit_copy_tail<<<grid_fixed(L, 4), kThreads, 0, L.stream>>>(order, tail, es);
+}
+
+void launch_layer_off_dev(const Launch &L, const uint32_t *loff, const Ctl *ctl,
+                          uint32_t max_layers, uint64_t *out) {
+    count_launch();
+    k_layer_off_dev<<<grid_for(L, (uint64_t)max_layers + 1, 1, 4), kThreads, 0, L.stream>>>(
+        loff, ctl, max_layers, out);
 }
 
 }  // namespace hp

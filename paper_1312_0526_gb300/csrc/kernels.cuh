@@ -157,6 +157,22 @@ void launch_emit_scatter(const Launch &L, const uint32_t *src, uint32_t count,
                          const uint32_t *offs, uint32_t *out);
 void launch_layer_off(const Launch &L, const uint32_t *loff, uint32_t rounds, uint64_t *out);
 
+// a7 driven by the device (EmitState in device memory): init (sets the
+// pass loop's condition), the claims with the first histogram, one pass
+// (later histogram, scan, scatter), advance to the next pass (sets the
+// condition, copies the order's tail for the next pass), layer offsets.
+void launch_emit_init(const Launch &L, const Ctl *ctl, uint32_t n, EmitState *es,
+                      cudaGraphConditionalHandle h);
+void launch_extract_claim_hist_dev(const Launch &L, const uint4 *rec, uint32_t n, uint32_t r,
+                                   uint32_t *claim, const EmitState *es, uint32_t *hist);
+void launch_emit_pass_dev(const Launch &L, uint32_t n, const uint32_t *tail, const uint32_t *claim,
+                          const EmitState *es, uint32_t *hist, uint32_t *scantmp,
+                          uint32_t *order);
+void launch_emit_advance(const Launch &L, EmitState *es, const uint32_t *loff, uint32_t *order,
+                         uint32_t *tail, cudaGraphConditionalHandle h);
+void launch_layer_off_dev(const Launch &L, const uint32_t *loff, const Ctl *ctl,
+                          uint32_t max_layers, uint64_t *out);
+
 // a10: batched bucket peel (batched.cu).
 size_t batched_scratch_bytes(uint32_t gamma_milli);
 uint32_t batched_max_gamma_milli();
@@ -185,6 +201,9 @@ void launch_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff
 void launch_sf_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
                             const uint32_t *values, uint64_t sigma, uint32_t b, uint64_t *U,
                             Ctl *ctl);
+void launch_sf_assign_layer_at(const Launch &L, const uint4 *Lst, const uint32_t *loff,
+                               const int32_t *t, const uint32_t *values, uint64_t sigma,
+                               uint32_t b, uint64_t *U, Ctl *ctl);
 void launch_sf_lookup(const Launch &L, const uint64_t *keys, uint64_t nq, FastMod fm,
                       uint64_t seed, uint64_t sigma, uint32_t b, const uint64_t *U,
                       uint32_t *out);
@@ -204,6 +223,12 @@ void launch_async_if_peeled(const Launch &L, const AsyncState *s, cudaGraphCondi
 void launch_async_assign_init(const Launch &L, AsyncState *s, cudaGraphConditionalHandle h);
 void launch_async_assign_step(const Launch &L, AsyncState *s, cudaGraphConditionalHandle h);
 void launch_async_stats(const Launch &L, const AsyncState *s, const Ctl *ctl, hpeel_stats *out);
+// Device-driven peel: the order runs only when no kernel raised an error;
+// stats of the peel; the empty graph.
+void launch_async_if_ok(const Launch &L, const Ctl *ctl, cudaGraphConditionalHandle h);
+void launch_peel_async_stats(const Launch &L, const Ctl *ctl, uint32_t n, uint32_t max_layers,
+                             bool want_layer_off, hpeel_stats *out);
+void launch_peel_async_empty(const Launch &L, hpeel_stats *out, uint64_t *layer_off);
 // a9: per-512-vertex counts of non-zero 2-bit values, then the directory.
 void launch_rank_counts(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt);
 void launch_widen_dir(const Launch &L, const uint32_t *scanned, const uint32_t *cnt,

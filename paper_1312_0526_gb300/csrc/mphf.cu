@@ -161,10 +161,9 @@ __device__ __forceinline__ void u_or(uint64_t *U, uint32_t v, uint32_t b, uint64
 // u[v_a] - u[v_b]) mod sigma.  Inside one layer no entry reads a value
 // another entry of the layer writes (as for the MPHF), so the layer is one
 // parallel launch.  A value >= sigma raises kDevBadValue.
-__global__ void __launch_bounds__(kThreads)
-k_sf_assign(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, uint32_t t,
-            const uint32_t *__restrict__ values, FastMod fs, uint32_t b, uint64_t *U, Ctl *ctl) {
-    const uint32_t lb = __ldcg(loff + t), le = __ldcg(loff + t + 1);
+__device__ __forceinline__ void sf_assign_range(const uint4 *__restrict__ Lst, uint32_t lb,
+                                                uint32_t le, const uint32_t *__restrict__ values,
+                                                FastMod fs, uint32_t b, uint64_t *U, Ctl *ctl) {
     const uint64_t sigma = fs.P;
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     for (uint64_t i = lb + (uint64_t)blockIdx.x * kThreads + threadIdx.x; i < le; i += stride) {
@@ -178,6 +177,29 @@ k_sf_assign(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, ui
         const uint64_t val = fastmod((uint64_t)f + sigma - other, fs);
         if (val) u_or(U, s.x, b, val);
     }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_sf_assign(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, uint32_t t,
+            const uint32_t *__restrict__ values, FastMod fs, uint32_t b, uint64_t *U, Ctl *ctl) {
+    sf_assign_range(Lst, __ldcg(loff + t), __ldcg(loff + t + 1), values, fs, b, U, ctl);
+}
+
+// The same, for the layer whose index the device holds (device-driven build).
+__global__ void __launch_bounds__(kThreads)
+k_sf_assign_at(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff, const int32_t *t,
+               const uint32_t *__restrict__ values, FastMod fs, uint32_t b, uint64_t *U,
+               Ctl *ctl) {
+    const uint32_t tt = (uint32_t)*(volatile const int32_t *)t;
+    sf_assign_range(Lst, __ldcg(loff + tt), __ldcg(loff + tt + 1), values, fs, b, U, ctl);
+}
+
+void launch_sf_assign_layer_at(const Launch &L, const uint4 *Lst, const uint32_t *loff,
+                               const int32_t *t, const uint32_t *values, uint64_t sigma,
+                               uint32_t b, uint64_t *U, Ctl *ctl) {
+    count_launch();
+    k_sf_assign_at<<<grid_fixed(L, 8), kThreads, 0, L.stream>>>(Lst, loff, t, values,
+                                                               make_fastmod(sigma), b, U, ctl);
 }
 
 void launch_sf_assign_layer(const Launch &L, const uint4 *Lst, const uint32_t *loff, uint32_t t,
