@@ -1,7 +1,8 @@
 """Writes tests/golden/stress_digests.json: the oracle's results on the large
-workloads (n = 1e9 at gamma 1.23, 1.222, 1.20; r = 4, n = 1e8, gamma 1.30),
-stored as SHA-256 digests of the output arrays plus the layer sizes, so the
-GPU test can compare full outputs without running the oracle for minutes.
+workloads (n = 1e9 at gamma 1.23, 1.222, 1.20; r = 4, n = 1e8, gamma 1.30;
+the batched workload of 65,536 lognormal buckets, about 2e8 keys), stored as
+SHA-256 digests of the output arrays plus the layer sizes, so the GPU test
+can compare full outputs without running the oracle for minutes.
 
 Calls only the oracle (oracle/) and the seeded input generator.  Run once:
     python tests/golden/make_stress_digests.py [name ...]
@@ -40,7 +41,46 @@ def digest(a: np.ndarray) -> str:
     return h.hexdigest()
 
 
+# The batched workload (sec. 3 "Practical workarounds (HEM)": one small MWHC
+# hypergraph per bucket): 65,536 buckets of clip(round(exp(ln 2000 + 0.92 Z)),
+# 64, 65,536) keys (Z from SplitMix64 stream 3), keys from stream 2 cut into
+# consecutive buckets, bucket b hashed with seed b at gamma 1.23.
+BATCHED = {"batched_65536": (65536, 2000, 0.92, 64, 65536, 3, 2, 1230)}
+
+
+def run_batched(name):
+    B, median, sigma, lo, hi, size_seed, key_seed, g = BATCHED[name]
+    t0 = time.time()
+    sizes = inputs.lognormal_bucket_sizes(B, median=median, sigma=sigma, lo=lo, hi=hi,
+                                          seed=size_seed)
+    keys, off = inputs.bucketed_keys(sizes, seed=key_seed)
+    h_order, h_g = hashlib.sha256(), hashlib.sha256()
+    rounds = np.zeros(B, dtype=np.uint32)
+    status = np.zeros(B, dtype=np.uint32)
+    for b in range(B):
+        k = keys[int(off[b]):int(off[b + 1])]
+        m = oracle.num_vertices(len(k), g, 3)
+        e = oracle.hash_edges(k, m, 3, b)
+        res = oracle.peel_rounds(e, m)
+        rounds[b] = res.rounds
+        status[b] = 1 if res.core_nonempty else 0
+        h_order.update(np.ascontiguousarray(res.order, dtype=np.uint32).tobytes())
+        # g values of the bucket (all zero when it keeps a 2-core), in the
+        # layout of the MPHF's G: ceil(m / 32) words per bucket, concatenated
+        G = (oracle.mphf_assign(e, m, res) if not res.core_nonempty
+             else np.zeros((m + 31) // 32, dtype=np.uint64))
+        h_g.update(np.ascontiguousarray(G, dtype=np.uint64).tobytes())
+    return {"B": B, "median": median, "sigma": sigma, "lo": lo, "hi": hi,
+            "size_seed": size_seed, "key_seed": key_seed, "gamma_milli": g,
+            "total_keys": int(off[-1]), "buckets_with_core": int(status.sum()),
+            "order_sha256": h_order.hexdigest(), "rounds_sha256": digest(rounds),
+            "status_sha256": digest(status), "G_sha256": h_g.hexdigest(),
+            "max_rounds": int(rounds.max()), "oracle_seconds": round(time.time() - t0, 1)}
+
+
 def run(name):
+    if name in BATCHED:
+        return run_batched(name)
     n, g, r, mphf = CONFIGS[name]
     t0 = time.time()
     keys = inputs.keys(n, 1)
@@ -66,7 +106,7 @@ def main(names):
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    for name in names or list(CONFIGS):
+    for name in names or list(CONFIGS) + list(BATCHED):
         print("running", name, flush=True)
         data[name] = run(name)
         with open(OUT, "w") as f:

@@ -69,6 +69,68 @@ def test_admission_respects_the_budget():
     assert srv.max_in_use <= budget
 
 
+@pytest.mark.parametrize("keep", [False, True])
+def test_admission_bounds_the_allocated_device_memory(keep):
+    # mixed 1e5..1e7-key requests on 4 slots: the memory torch's allocator
+    # hands out while the server runs (retained slot workspaces, key copies,
+    # outputs, kept results) stays within the budget plus a small slack for
+    # the allocator's rounding
+    arr, sizes, seeds = inputs.request_stream(12, rate_per_s=1e9, seed=13, lo_exp=5.0,
+                                              hi_exp=7.0)
+    keysets = [torch.from_numpy(inputs.keys(int(s), int(k)).view(np.int64)).pin_memory()
+               for s, k in zip(sizes, seeds)]
+    budget = int(1.5 * max(serve.footprint_bytes(len(k)) for k in keysets))
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    srv = serve.MphfServer(slots=4, hbm_budget=budget, keep_results=keep)
+    try:
+        res = serve.run_stream(srv, keysets, [0.0] * len(keysets))
+        assert all(r.error is None for r in res)
+        assert srv.max_in_use <= budget
+        torch.cuda.synchronize()
+        peak = torch.cuda.max_memory_allocated() - base
+        assert peak <= budget + (16 << 20), (peak, budget)
+        for i in range(len(keysets)):
+            srv.release(i)
+        res = None  # the caller's references to the outputs go too
+    finally:
+        srv.close()
+    assert srv.in_use == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
+
+
+def test_large_requests_same_alone_and_in_the_mix():
+    # a mix that reaches 1e6..1e7 keys per request (the top of the serving
+    # workload's log-uniform range): each result equals the same build alone
+    arr, sizes, seeds = inputs.request_stream(8, rate_per_s=1e9, seed=17, lo_exp=6.0,
+                                              hi_exp=7.0)
+    keysets = [inputs.keys(int(s), int(k)) for s, k in zip(sizes, seeds)]
+    assert max(sizes) > 3_000_000
+    mix = serve.MphfServer(slots=4, hbm_budget=32 << 30)
+    try:
+        got = serve.run_stream(mix, keysets, [0.0] * len(keysets))
+        assert mix.max_running > 1
+    finally:
+        mix.close()
+    alone = serve.MphfServer(slots=1, hbm_budget=32 << 30)
+    try:
+        for i, ks in enumerate(keysets):
+            alone.results.clear()
+            alone.submit(serve.Request(0, ks, 1))
+            alone.wait(1)
+            _same(got[i], alone.results[0])
+    finally:
+        alone.close()
+    # the largest request against the oracle
+    i = int(np.argmax(sizes))
+    want = oracle.mphf_build(keysets[i], seed=1, max_tries=8)
+    assert got[i].stats["seed_used"] == want.seed_used
+    assert np.array_equal(got[i].G.cpu().numpy().view(np.uint64), want.G)
+    assert np.array_equal(got[i].rank_dir.cpu().numpy().view(np.uint64), want.dir)
+
+
 def test_oversized_request_is_reported_and_others_finish():
     keysets = _stream(5, seed=11)
     big = inputs.keys(3_000_000, 5)

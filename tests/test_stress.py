@@ -1,5 +1,7 @@
 """Full-size parity: n = 1e9 (gamma 1.23, 1.222, 1.20) and r = 4, n = 1e8,
-gamma 1.30, in the launch configuration bench.py uses.
+gamma 1.30, in the launch configuration bench.py uses; and the batched
+workload (65,536 lognormal buckets, about 2e8 keys) with the autotuned launch
+shape, once called directly and once replayed from a captured CUDA graph.
 
 The oracle's complete outputs for these workloads were computed once by
 tests/golden/make_stress_digests.py (oracle/ only) and stored as SHA-256
@@ -32,7 +34,8 @@ def _load():
         return json.load(f)
 
 
-CASES = _load()
+CASES = {k: v for k, v in _load().items() if "n" in v}
+BATCHED_CASES = {k: v for k, v in _load().items() if "B" in v}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -140,4 +143,48 @@ def test_largest_mphf_on_one_gpu():
         flags.index_fill_(0, idx, 1)
     assert int(flags.sum(dtype=torch.int64)) == n
     del keys, flags, out, got
+    torch.cuda.empty_cache()
+
+
+def _batched_digests(res):
+    return {"order_sha256": _digest_dev(res.order), "rounds_sha256": _digest_dev(res.rounds),
+            "status_sha256": _digest_dev(res.status), "G_sha256": _digest_dev(res.G)}
+
+
+@pytest.mark.parametrize("name", sorted(BATCHED_CASES))
+def test_batched_full_size_parity(name):
+    from paper_1312_0526_gb300 import autotune
+    c = BATCHED_CASES[name]
+    g = c["gamma_milli"]
+    sizes = inputs.lognormal_bucket_sizes(c["B"], median=c["median"], sigma=c["sigma"],
+                                          lo=c["lo"], hi=c["hi"], seed=c["size_seed"])
+    keys, off = inputs.bucketed_keys(sizes, seed=c["key_seed"])
+    assert int(off[-1]) == c["total_keys"]
+    torch.cuda.empty_cache()
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    do = torch.from_numpy(off.view(np.int64)).cuda()
+    tun = autotune.tune(dk, do, g, with_g=True)
+    ws = torch.empty(hp.batched_workspace_size(c["B"], g, tun), dtype=torch.uint8,
+                     device="cuda")
+    res = hp.peel_batched(dk, do, g, with_g=True, tuning=tun, workspace=ws)
+    torch.cuda.synchronize()
+    want = {k: c[k] for k in ("order_sha256", "rounds_sha256", "status_sha256", "G_sha256")}
+    assert _batched_digests(res) == want
+    assert int((res.status == 1).sum()) == c["buckets_with_core"]
+    # the same launch captured into a CUDA graph and replayed into cleared
+    # outputs
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            hp.peel_batched(dk, do, g, tuning=tun, workspace=ws, out=res)
+    torch.cuda.synchronize()
+    for t in (res.order, res.rounds, res.status):
+        t.fill_(-1)
+    res.G.fill_(-1)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert _batched_digests(res) == want
+    del dk, do, ws, res, graph
     torch.cuda.empty_cache()
