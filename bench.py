@@ -1,17 +1,27 @@
 #!/usr/bin/env python3
-"""Benchmark of the GB300 MWHC MPHF build hot path.
+"""Benchmark of the GB300 hypergraph peeling hot path.
 
-One step = one whole pass of the hot path over one key set: key -> edge
-hashing, packed-incidence build, round-synchronous peel with canonical order,
-reverse-layer g assignment and rank directory (hpeel_mphf_build), on the
-n = 1e8, r = 3, gamma = 1.23 workload (SplitMix64 keys, seed 1).
+One step = one whole pass of the hot path over one hypergraph: the plain
+peel (hpeel_peel) of the n = 1e9, r = 3, gamma = 1.23 workload -- edge
+records and packed incidence build, round-synchronous peel, canonical order,
+claim words and layer offsets out -- with the edges (hashed from SplitMix64
+keys, seed 1, hash seed 1) resident in device memory.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--legs LIST] [--n N]
 
-N > 1 runs under torch.distributed.run, one rank per GPU: every rank builds
-its own independent key set (seed 1 + rank) -- weak scaling, no collective on
-the data path; a barrier and a max-reduction of the timings only.
-Rank 0 prints one JSON line.
+The line also carries the end-to-end figure (edges from pinned host memory,
+order and claims back to it, every step), the CPU oracle on a sample, and the
+other workloads as sub-legs (--legs picks them; "none" times the step alone,
+e.g. under a profiler): the n = 1e8 MPHF build, lookups, the device-driven
+forms, the stress configurations (n = 1e9 at gamma 1.222 and 1.20, r = 4),
+the batched form, serving, static functions, general hypergraphs and the
+random-access ceiling of the rounds.
+
+N > 1 runs under torch.distributed.run, one rank per GPU: every rank peels
+its own independent hypergraph (key seed 1 + rank) -- weak scaling, no
+collective on the data path; a barrier and a max-reduction of the timings
+only.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -20,6 +30,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -28,15 +39,18 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_KEYS = 10**8
+PEEL_N = 10**9                 # the headline: plain peel of 1e9 edges
+MPHF_N = 10**8                 # the MPHF build leg
 GAMMA_MILLI = 1230
 R = 3
 KEY_SEED = 1
 HASH_SEED = 1
 METRIC = "peeled edges/sec (Medges/s)"
 UNIT = "Medges/s"
-CPU_SAMPLE_KEYS = 10**7        # cpu_baseline: one oracle build of this many keys
-REF_STEP_KEYS = 10**6          # --impl reference: keys per oracle step
+CPU_SAMPLE_EDGES = 10**7       # cpu_baseline: one oracle peel of this many edges
+REF_STEP_EDGES = 2 * 10**6     # --impl reference: edges per oracle step
+ALL_LEGS = ("e2e", "cpu", "mphf", "lookup", "async", "peel_async", "stress", "batched",
+            "serving", "sf", "general", "random_access")
 
 # Algorithmic bytes per unit of work, per step of the path (r = 3).  "sector"
 # charges one 32-byte sector per random access (64 bytes for a read-modify-
@@ -97,10 +111,10 @@ def byte_model(step, n, m, st):
 # for a kernel version, keyed by the sha256 of the source file the kernel
 # lives in; stale entries are ignored.  Filled from the summaries in profiles/.
 NCU_TRAFFIC = {
-    # step: (source file, sha256 prefix, bytes per unit)
-    # rounds: k_round0 + k_round of one build at n = 3e7 (host round loop),
-    # 10.71 GB of DRAM traffic for 3e7 peeled edges; profiles/rounds_n3e7_dram.md
-    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "d3e6f35e961fa5db", 357.09),
+    # step: (source file, sha256 prefix, bytes per unit, where measured)
+    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "d3e6f35e961fa5db", 357.09,
+               "k_round0 + k_round of one peel at n = 3e7 (host round loop), scaled by "
+               "peeled edges"),
 }
 
 
@@ -191,27 +205,324 @@ def dist_setup():
     return world, rank, local
 
 
+def host_cpu():
+    """Core count and CPU model of the host the CPU legs run on."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if model and not model.isdigit():
+                    break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
 def cpu_baseline():
-    """The oracle, as it stands, on a bounded sample of the workload."""
+    """The oracle, as it stands, on a bounded sample of the workload: the
+    first 1e7 keys of the same stream hashed (r = 3, gamma = 1.23, hash seed
+    1) and peeled round by round with the canonical order, single-threaded.
+    Beside it the paper's in-memory baseline form: the greedy LIFO peel with
+    the XOR trick ("Standard+XOR"), hashing included."""
     import oracle
     from paper_1312_0526_gb300 import inputs
-    keys = inputs.keys(CPU_SAMPLE_KEYS, KEY_SEED)
     oracle.build()
+    n = CPU_SAMPLE_EDGES
+    keys = inputs.keys(n, KEY_SEED)
+    m = oracle.num_vertices(n, GAMMA_MILLI, R)
     t0 = time.perf_counter()
-    res = oracle.mphf_build(keys, HASH_SEED, GAMMA_MILLI)
+    res = oracle.peel_rounds(oracle.hash_edges(keys, m, R, HASH_SEED), m)
     dt = time.perf_counter() - t0
-    # the paper's in-memory baseline form beside it: the greedy (LIFO) peel
-    # with the XOR trick ("Standard+XOR"), hashing included
-    m = oracle.num_vertices(CPU_SAMPLE_KEYS, GAMMA_MILLI, R)
     t1 = time.perf_counter()
     oracle.peel_greedy(oracle.hash_edges(keys, m, R, HASH_SEED), m)
     dg = time.perf_counter() - t1
-    return {"value": CPU_SAMPLE_KEYS / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one single-threaded oracle MPHF build (hash+peel+assign+rank) of the "
-                      f"first {CPU_SAMPLE_KEYS:.0e} keys of the same stream, {dt:.2f} s, "
-                      f"{res.rounds} rounds",
-            "greedy_peel": {"value": CPU_SAMPLE_KEYS / dg / 1e6, "unit": UNIT,
-                            "sample": f"hash + greedy LIFO peel of the same keys, {dg:.2f} s"}}
+    hc = host_cpu()
+    return {"value": n / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one single-threaded oracle peel (hash + round-synchronous peel + "
+                      f"canonical order) of the first {n:.0e} edges of the same workload, "
+                      f"{dt:.2f} s, {res.rounds} rounds; host {hc['nproc']} cores, "
+                      f"{hc['model']}",
+            "host": hc,
+            "greedy_peel": {"value": n / dg / 1e6, "unit": UNIT,
+                            "sample": f"hash + greedy LIFO peel of the same edges, {dg:.2f} s"}}
+
+
+def roofline_of(prof, steps, n, m, st, round_loop):
+    """Roofline of the step with the largest live CUDA-event total."""
+    peak, peak_kind = measured_peaks()
+    ranked = sorted(((v[1], k) for k, v in prof.items()), reverse=True)
+    for tot_ms, name in ranked:
+        model = byte_model(name, n, m, st)
+        if model is None:
+            continue
+        per_step_ms = tot_ms / steps
+        launches_per_step = prof[name][0] / steps
+        if name == "rounds" and round_loop == "graph":
+            launches_per_step = 1 + st["rounds"]  # round 0 + the graph's iterations
+        achieved = model["sector"] / (per_step_ms / 1e3) / 1e9
+        traffic = traffic_step = source = None
+        if name in NCU_TRAFFIC:
+            src, h, per_unit, where = NCU_TRAFFIC[name]
+            if src_hash(src) == h:
+                traffic_step = per_unit * model["units"]
+                traffic = traffic_step / max(launches_per_step, 1)
+                source = f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {where}"
+        return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "model": "sector", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_step": model["sector"],
+                "units_per_step": model["units"],
+                "word_model_gbs": model["word"] / (per_step_ms / 1e3) / 1e9,
+                "launches_per_step": launches_per_step,
+                "traffic_per_step": traffic_step,
+                "traffic_gbs": traffic_step / (per_step_ms / 1e3) / 1e9 if traffic_step else None,
+                "traffic_source": source,
+                "ms_per_step": per_step_ms,
+                "share": tot_ms / sum(v[1] for v in prof.values())}
+    return None
+
+
+def peel_e2e(edges, m, ws, ref, steps, sync_all, max_over_ranks):
+    """The headline through the public API with host buffers: every step's
+    edges (12 B per edge) come from pinned host memory and its order and
+    claim words (8 B per edge) go back to pinned host memory.  A copy stream
+    moves step i+1's edges into one of two device buffers while step i
+    peels (a buffer is refilled only after the peel that read it); the
+    results go back on another stream into double host buffers."""
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+
+    n = edges.shape[0]
+    stream = torch.cuda.current_stream()
+    edges_h = torch.empty(edges.shape, dtype=edges.dtype, pin_memory=True)
+    edges_h.copy_(edges)
+    ed = [edges, torch.empty_like(edges)]
+    outs = [(torch.empty(n, dtype=torch.int32, device="cuda"),
+             torch.empty(n, dtype=torch.int32, device="cuda"),
+             torch.empty(4097, dtype=torch.int64, device="cuda")) for _ in range(2)]
+    host = [(torch.empty(n, dtype=torch.int32, pin_memory=True),
+             torch.empty(n, dtype=torch.int32, pin_memory=True)) for _ in range(2)]
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    read, built_ev, copied = [None, None], [None, None], [None, None]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def enqueue_copy(i):
+        b = i & 1
+        with torch.cuda.stream(h2d):
+            h2d.wait_event(e0)
+            if built_ev[b] is not None:
+                h2d.wait_event(built_ev[b])
+            ed[b].copy_(edges_h, non_blocking=True)
+            copied[b] = torch.cuda.Event()
+            copied[b].record(h2d)
+
+    sync_all()
+    e0.record(stream)
+    enqueue_copy(0)
+    for i in range(steps):
+        b = i & 1
+        # the peel call returns when its step is done, so the next step's
+        # copy is queued first and runs while this one peels
+        if i + 1 < steps:
+            enqueue_copy(i + 1)
+        stream.wait_event(copied[b])
+        if read[b] is not None:
+            stream.wait_event(read[b])  # step i-2's results are on the host
+        hp.peel(ed[b], m, workspace=ws, out=outs[b])
+        built = torch.cuda.Event()
+        built.record(stream)
+        built_ev[b] = built
+        with torch.cuda.stream(d2h):
+            d2h.wait_event(built)
+            host[b][0].copy_(outs[b][0], non_blocking=True)
+            host[b][1].copy_(outs[b][1], non_blocking=True)
+            read[b] = torch.cuda.Event()
+            read[b].record(d2h)
+    stream.wait_stream(d2h)
+    stream.wait_stream(h2d)
+    e1.record(stream)
+    sync_all()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps)
+    ro, rc = ref[0].cpu(), ref[1].cpu()
+    same = all(torch.equal(host[b][0], ro) and torch.equal(host[b][1], rc)
+               for b in range(min(2, steps)))
+    del ed[1], outs, host, edges_h
+    torch.cuda.empty_cache()
+    return ms, same
+
+
+def mphf_leg(n, steps, warmup, rank):
+    """The MWHC MPHF build (hpeel_mphf_build: hash, incidence, peel,
+    canonical order, g assignment, rank directory) of n = 1e8 keys (BASELINE
+    configs[1]), keys device-resident; and end to end with each step's keys
+    copied from pinned host memory (double-buffered on a copy stream) and
+    the g values and rank directory read back."""
+    import numpy as np
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    m = hp.num_vertices(n, GAMMA_MILLI, R)
+    keys_h = torch.from_numpy(inputs.keys(n, KEY_SEED + rank).view(np.int64)).pin_memory()
+    keys = keys_h.to("cuda", non_blocking=False)
+    ws = torch.empty(hp.mphf_workspace_size(n, GAMMA_MILLI), dtype=torch.uint8, device="cuda")
+    G = torch.empty((m + 31) // 32, dtype=torch.int64, device="cuda")
+    D = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device="cuda")
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(src, g, d):
+        return hp.mphf_build(src, HASH_SEED, GAMMA_MILLI, workspace=ws, G=g, rank_dir=d,
+                             order=order)
+
+    for _ in range(max(warmup, 1)):
+        res = step(keys, G, D)
+    torch.cuda.synchronize()
+    hp.profile_reset()
+    hp.profile_enable(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        res = step(keys, G, D)
+    b.record(stream)
+    torch.cuda.synchronize()
+    hp.profile_enable(False)
+    prof = hp.profile_read()
+    ms = a.elapsed_time(b) / steps
+    # end to end: keys from pinned host memory, results back to it
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    Gb, Db = [G, torch.empty_like(G)], [D, torch.empty_like(D)]
+    G_h = [torch.empty_like(G, device="cpu").pin_memory() for _ in range(2)]
+    D_h = [torch.empty_like(D, device="cpu").pin_memory() for _ in range(2)]
+    kd = [keys, torch.empty_like(keys)]
+    read, built_ev, copied = [None, None], [None, None], [None, None]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def enqueue_copy(i):
+        bb = i & 1
+        with torch.cuda.stream(h2d):
+            h2d.wait_event(e0)
+            if built_ev[bb] is not None:
+                h2d.wait_event(built_ev[bb])
+            kd[bb].copy_(keys_h, non_blocking=True)
+            copied[bb] = torch.cuda.Event()
+            copied[bb].record(h2d)
+
+    torch.cuda.synchronize()
+    e0.record(stream)
+    enqueue_copy(0)
+    for i in range(steps):
+        bb = i & 1
+        if i + 1 < steps:
+            enqueue_copy(i + 1)
+        stream.wait_event(copied[bb])
+        if read[bb] is not None:
+            stream.wait_event(read[bb])
+        step(kd[bb], Gb[bb], Db[bb])
+        built = torch.cuda.Event()
+        built.record(stream)
+        built_ev[bb] = built
+        with torch.cuda.stream(d2h):
+            d2h.wait_event(built)
+            G_h[bb].copy_(Gb[bb], non_blocking=True)
+            D_h[bb].copy_(Db[bb], non_blocking=True)
+            read[bb] = torch.cuda.Event()
+            read[bb].record(d2h)
+    stream.wait_stream(d2h)
+    stream.wait_stream(h2d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / steps
+    same = all(torch.equal(G_h[x], G.cpu()) and torch.equal(D_h[x], D.cpu())
+               for x in range(min(2, steps)))
+    del kd, ws, order, Gb, Db
+    torch.cuda.empty_cache()
+    st = res.stats
+    out = {"value": n / ms / 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "rounds": st["rounds"], "seed_used": st["seed_used"],
+           "steps_ms": {k: v[1] / steps for k, v in sorted(prof.items())},
+           "roofline": roofline_of(prof, steps, n, m, st, "graph"),
+           "e2e": {"value": n / e2e_ms / 1e3, "unit": UNIT, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * (G.numel() + D.numel()),
+                   "same_as_device_resident": same},
+           "config": {"workload": f"mphf-build n={n:.0e} r=3 gamma=1.23, SplitMix64 keys seed "
+                                  "1+rank, hash seed 1 (hash, incidence, peel, canonical "
+                                  "order, g assignment, rank)"}}
+    return out, keys, G, D, m, st["seed_used"]
+
+
+def stress_leg(steps=2, warmup=1):
+    """The other plain-peel stress configurations (BASELINE configs[2]): n =
+    1e9 at gamma 1.222 (near the threshold, many rounds) and 1.20 (below it:
+    a 2-core is left), and r = 4 at n = 1e8, gamma 1.30; hpeel_peel from
+    device-resident edges."""
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    out = {}
+    for name, n, g, r in (("n1e9_g1222", 10**9, 1222, 3), ("n1e9_g1200", 10**9, 1200, 3),
+                          ("n1e8_g1300_r4", 10**8, 1300, 4)):
+        m = hp.num_vertices(n, g, r)
+        keys = inputs.keys_torch(n, KEY_SEED)
+        edges = hp.hash_edges(keys, m, r, HASH_SEED)
+        del keys
+        torch.cuda.empty_cache()
+        ws = torch.empty(hp.peel_workspace_size(n, m, r), dtype=torch.uint8, device="cuda")
+        po = (torch.empty(n, dtype=torch.int32, device="cuda"),
+              torch.empty(n, dtype=torch.int32, device="cuda"),
+              torch.empty(1 << 16 | 1, dtype=torch.int64, device="cuda"))
+        for _ in range(warmup):
+            res = hp.peel(edges, m, workspace=ws, max_layers=1 << 16, out=po)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            res = hp.peel(edges, m, workspace=ws, max_layers=1 << 16, out=po)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[name] = {"value": n / ms / 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+                     "n": n, "gamma": g / 1000, "r": r, "rounds": res.rounds,
+                     "n_peeled": res.n_peeled, "core_nonempty": res.core_nonempty}
+        del edges, ws, po, res
+        torch.cuda.empty_cache()
+    return out
+
+
+def peel_async_leg(edges, m, ws, ref, steps=5, warmup=2):
+    """The headline peel through hpeel_peel_async (one cached CUDA graph, the
+    rounds and the order sort's passes driven by the device, no host
+    synchronisation), on the same edges and workspace; outputs checked equal
+    to hpeel_peel's."""
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+
+    out = hp.peel_async(edges, m, workspace=ws)
+    for _ in range(warmup - 1):
+        hp.peel_async(edges, m, workspace=ws, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        hp.peel_async(edges, m, workspace=ws, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    st = hp.stats_from_device(out.stats)
+    same = bool(torch.equal(out.order, ref[0]) and torch.equal(out.claim, ref[1]))
+    n = edges.shape[0]
+    del out
+    torch.cuda.empty_cache()
+    return {"value": n / ms / 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "async_status": st["async_status"], "rounds": st["rounds"],
+            "same_as_hpeel_peel": same}
 
 
 def lookup_leg(keys, G, D, m, seed):
@@ -243,10 +554,10 @@ def random_access_leg(n, m, rounds_ms):
     random 8-byte loads and the access pattern of one peeled edge (a record
     claim and two vertex updates), over arrays the size of the build's edge
     records (n x 16 B) and vertex records (m x 8 B), timed with CUDA events
-    (hpeel_probe_random_access)."""
+    (the measurement library's probe, measure/probe.cu)."""
     import torch
 
-    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import measure
 
     A = torch.zeros(n * 2, dtype=torch.int64, device="cuda")
     B = torch.zeros(m, dtype=torch.int64, device="cuda")
@@ -254,13 +565,13 @@ def random_access_leg(n, m, rounds_ms):
     # the loads run first, while the vertex words are still zero
     for kind, name, arg_b in ((1, "load64", None), (0, "rmw64", None), (2, "peeled_edge", B)):
         target = A if kind == 2 else B
-        hp.probe_random_access(kind, n, target, arg_b, seed=7)  # warm-up
+        measure.random_access(kind, n, target, arg_b, seed=7)  # warm-up
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 3
         torch.cuda.synchronize()
         a.record()
         for r in range(reps):
-            hp.probe_random_access(kind, n, target, arg_b, seed=100 + r)
+            measure.random_access(kind, n, target, arg_b, seed=100 + r)
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
@@ -276,7 +587,6 @@ def random_access_leg(n, m, rounds_ms):
     return out
 
 
-PEEL_N = 10**9
 SF_SIGMA = 256
 
 
@@ -356,62 +666,6 @@ def general_leg(n, steps, warmup):
            "steps_ms": {k: v[1] / steps for k, v in sorted(prof.items())},
            "config": {"workload": f"general 3-hypergraph peel n={n:.0e} m=ceil(1.23 n), "
                                   "edges on the device"}}
-    del edges, ws, res
-    torch.cuda.empty_cache()
-    return out
-
-
-def peel_leg(n, steps, warmup):
-    """Plain peel at scale (hpeel_peel, the peel of configs C2): n = 1e9 edges,
-    r = 3, gamma = 1.23, edges device-resident (hashed from SplitMix64 keys,
-    seed 1, hash seed 1), canonical order + claim words + layer offsets out.
-    Reported as peeled edges/s and as the sector-model bytes of its steps
-    against the measured HBM peak."""
-    import numpy as np
-    import torch
-
-    import paper_1312_0526_gb300 as hp
-    from paper_1312_0526_gb300 import inputs
-
-    m = hp.num_vertices(n, GAMMA_MILLI, R)
-    keys = inputs.keys_torch(n, KEY_SEED)
-    edges = hp.hash_edges(keys, m, R, HASH_SEED)
-    del keys
-    torch.cuda.empty_cache()
-    ws = torch.empty(hp.peel_workspace_size(n, m, R), dtype=torch.uint8, device="cuda")
-    res = None
-    for _ in range(max(warmup, 1)):
-        res = hp.peel(edges, m, workspace=ws)
-    torch.cuda.synchronize()
-    hp.profile_reset()
-    hp.profile_enable(True)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(steps):
-        res = hp.peel(edges, m, workspace=ws)
-    b.record()
-    torch.cuda.synchronize()
-    hp.profile_enable(False)
-    prof = hp.profile_read()
-    ms = a.elapsed_time(b) / steps
-    st = dict(res.stats)
-    sector = word = 0
-    for name, (_, tot) in prof.items():
-        bm = byte_model(name, n, m, st)
-        if bm:
-            sector += bm["sector"]
-            word += bm["word"]
-    peak, peak_kind = measured_peaks()
-    out = {"value": n / ms / 1e3, "unit": UNIT, "ms_per_step": ms, "steps": steps,
-           "n": n, "m": m, "rounds": res.rounds, "n_peeled": res.n_peeled,
-           "steps_ms": {k: v[1] / steps for k, v in sorted(prof.items())},
-           "roofline": {"bound": "hbm", "model": "sector", "achieved": sector / ms / 1e6,
-                        "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                        "frac": sector / ms / 1e6 / peak,
-                        "algorithmic_bytes_per_step": sector,
-                        "word_model_gbs": word / ms / 1e6},
-           "config": {"workload": f"plain peel n={n:.0e} r=3 gamma=1.23, edges on the device, "
-                                  "canonical order + claims + layer offsets out"}}
     del edges, ws, res
     torch.cuda.empty_cache()
     return out
@@ -552,8 +806,8 @@ BATCH_B = 65536
 def batched_leg(steps, warmup):
     """Batched form (65,536 lognormal buckets, median 2,000 keys, 64..65,536,
     hash seed = bucket id): one persistent launch per step, autotuned launch
-    shape, replayed from a captured CUDA graph; beside it the plain path run
-    bucket by bucket (hash + peel per bucket) on a sample of the buckets."""
+    shape, replayed from a captured CUDA graph; beside it the plain path over
+    the same keys taken as one hypergraph."""
     import numpy as np
     import torch
 
@@ -596,25 +850,35 @@ def batched_leg(steps, warmup):
             "value": total / ms / 1e3, "unit": UNIT, "ms_per_step": ms, "tuning": tun,
             "buckets_peeled": int((st == 0).sum()), "buckets_with_core": int((st == 1).sum()),
             "graph_replays": steps, "hbm_gbs_context": total * (8 + 4) / ms / 1e6}
-    # plain path, one bucket at a time, on every 512th bucket
-    sample = list(range(0, BATCH_B, 512))
-    t_tot, e_tot = 0.0, 0
-    for b in sample:
-        k = dk[int(off[b]):int(off[b + 1])]
-        m = hp.num_vertices(k.shape[0], GAMMA_MILLI, 3)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        e = hp.hash_edges(k, m, 3, b)
-        hp.peel(e, m)
-        ev1.record()
-        torch.cuda.synchronize()
-        t_tot += ev0.elapsed_time(ev1)
-        e_tot += k.shape[0]
-    plain = e_tot / t_tot / 1e3
-    out["plain_per_bucket"] = {"value": plain, "unit": UNIT,
-                               "sample": f"{len(sample)} buckets (every 512th), hpeel_hash_edges "
-                                         f"+ hpeel_peel per bucket, {e_tot} edges"}
-    out["speedup_vs_plain"] = out["peel"]["value"] / plain
+    # the plain path on the same keys as one hypergraph of all 2.01e8 edges
+    # (hash seed 1, gamma 1.23): hpeel_hash_edges + hpeel_peel per step
+    m = hp.num_vertices(total, GAMMA_MILLI, 3)
+    del ws
+    torch.cuda.empty_cache()
+    pws = torch.empty(hp.peel_workspace_size(total, m, 3), dtype=torch.uint8, device="cuda")
+    edges = torch.empty((total, 3), dtype=torch.int32, device="cuda")
+    pout = (torch.empty(total, dtype=torch.int32, device="cuda"),
+            torch.empty(total, dtype=torch.int32, device="cuda"),
+            torch.empty(4097, dtype=torch.int64, device="cuda"))
+    for _ in range(max(warmup, 1)):
+        hp.hash_edges(dk, m, 3, HASH_SEED, out=edges)
+        hp.peel(edges, m, workspace=pws, out=pout)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        hp.hash_edges(dk, m, 3, HASH_SEED, out=edges)
+        hp.peel(edges, m, workspace=pws, out=pout)
+    b.record()
+    torch.cuda.synchronize()
+    pms = a.elapsed_time(b) / steps
+    out["plain_one_graph"] = {"value": total / pms / 1e3, "unit": UNIT, "ms_per_step": pms,
+                              "steps": steps,
+                              "workload": f"the same {total} keys as one 3-hypergraph (hash "
+                                          "seed 1, gamma 1.23): hpeel_hash_edges + hpeel_peel"}
+    out["speedup_vs_plain"] = out["peel"]["value"] / out["plain_one_graph"]["value"]
+    del pws, edges, pout
+    torch.cuda.empty_cache()
     out["config"] = {"workload": "65,536 bucket 3-hypergraphs, lognormal sizes (median 2,000, "
                                  "sigma 0.92, clipped 64..65,536), gamma 1.23, hash seed = "
                                  "bucket id, SplitMix64 keys seed 2",
@@ -623,36 +887,6 @@ def batched_leg(steps, warmup):
 
 
 SERVE_REQUESTS = 200
-
-
-def batched_probe(tuning: str):
-    """One warm-up and one timed call of the batched form on the batched
-    leg's workload with a fixed launch shape ("THREADSxCTAS", no autotuning,
-    no g values): a short, fixed launch sequence for a profiler."""
-    import numpy as np
-    import torch
-
-    import paper_1312_0526_gb300 as hp
-    from paper_1312_0526_gb300 import inputs
-
-    t, c = (int(x) for x in tuning.split("x"))
-    tun = {"threads": t, "ctas_per_sm": c}
-    sizes = inputs.lognormal_bucket_sizes(BATCH_B, median=2000, sigma=0.92, lo=64, hi=65536,
-                                          seed=3)
-    keys, off = inputs.bucketed_keys(sizes, seed=2)
-    dk = torch.from_numpy(keys.view(np.int64)).cuda()
-    do = torch.from_numpy(off.view(np.int64)).cuda()
-    ws = torch.empty(hp.batched_workspace_size(BATCH_B, GAMMA_MILLI, tun), dtype=torch.uint8,
-                     device="cuda")
-    res = hp.peel_batched(dk, do, GAMMA_MILLI, tuning=tun, workspace=ws)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    hp.peel_batched(dk, do, GAMMA_MILLI, tuning=tun, workspace=ws, out=res)
-    b.record()
-    torch.cuda.synchronize()
-    print(json.dumps({"batched_probe_ms": a.elapsed_time(b), "tuning": tun,
-                      "edges": int(off[-1])}), flush=True)
 
 
 def serving_leg():
@@ -696,34 +930,112 @@ def serving_leg():
 
 
 def run_reference(args, world, rank):
+    """The oracle (there is no reference code to install: the paper ships
+    none), timed as it stands on the host cores: each step hashes and peels
+    (round-synchronous, canonical order) the first 2e6 edges of the same
+    workload."""
     if rank != 0:
         return 0
     import oracle
     from paper_1312_0526_gb300 import inputs
     oracle.build()
-    keys = inputs.keys(REF_STEP_KEYS, KEY_SEED)
+    n = REF_STEP_EDGES
+    keys = inputs.keys(n, KEY_SEED)
+    m = oracle.num_vertices(n, GAMMA_MILLI, R)
+
+    def step():
+        oracle.peel_rounds(oracle.hash_edges(keys, m, R, HASH_SEED), m)
+
     for _ in range(args.warmup):
-        oracle.mphf_build(keys, HASH_SEED, GAMMA_MILLI)
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.mphf_build(keys, HASH_SEED, GAMMA_MILLI)
+        step()
     dt = (time.perf_counter() - t0) / args.steps
-    value = REF_STEP_KEYS / dt / 1e6
+    value = n / dt / 1e6
+    hc = host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "mphf-build r=3 gamma=1.23, SplitMix64 keys seed 1; "
-                               f"oracle steps on the first {REF_STEP_KEYS:.0e} keys",
-                   "n": N_KEYS, "gamma": GAMMA_MILLI / 1000, "r": R},
+        "config": {"workload": f"plain peel r=3 gamma=1.23, SplitMix64 keys seed 1, hash "
+                               f"seed 1; oracle steps on the first {n:.0e} edges",
+                   "n": PEEL_N, "gamma": GAMMA_MILLI / 1000, "r": R},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step one single-threaded oracle MPHF build of "
-                                   f"{REF_STEP_KEYS:.0e} keys"},
+                         "sample": f"each step one single-threaded oracle hash + round-"
+                                   f"synchronous peel with canonical order of {n:.0e} edges; "
+                                   f"host {hc['nproc']} cores, {hc['model']}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_shape_call(shape: str):
+    """The batched workload with one fixed launch shape ("THREADSxCTAS", no
+    autotuning, no g values): one warm-up and one timed call -- a short,
+    fixed launch sequence for a profiler.  Prints its own small JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    t, c = (int(x) for x in shape.split("x"))
+    tun = {"threads": t, "ctas_per_sm": c}
+    sizes = inputs.lognormal_bucket_sizes(BATCH_B, median=2000, sigma=0.92, lo=64, hi=65536,
+                                          seed=3)
+    keys, off = inputs.bucketed_keys(sizes, seed=2)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    do = torch.from_numpy(off.view(np.int64)).cuda()
+    ws = torch.empty(hp.batched_workspace_size(BATCH_B, GAMMA_MILLI, tun), dtype=torch.uint8,
+                     device="cuda")
+    res = hp.peel_batched(dk, do, GAMMA_MILLI, tuning=tun, workspace=ws)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    hp.peel_batched(dk, do, GAMMA_MILLI, tuning=tun, workspace=ws, out=res)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"batched_ms": a.elapsed_time(b), "tuning": tun, "edges": int(off[-1])}),
+          flush=True)
+
+
+def summary_of(line):
+    """The headline figures of every leg in one small object, placed last in
+    the line so that a truncated copy of the line still shows them."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or d.get(k) is None:
+                return None
+            d = d[k]
+        return round(d, 3) if isinstance(d, float) else d
+    s = {"peel_1e9_ms": g(line, "ms_per_step"), "peel_1e9_medges_s": g(line, "value"),
+         "peel_1e9_e2e_ms": g(line, "e2e", "ms_per_step"),
+         "rounds_ms": g(line, "roofline", "ms_per_step"),
+         "rounds_frac_sector_model": g(line, "roofline", "frac"),
+         "rounds_vs_random_access_ceiling": g(line, "roofline", "random_access_ceiling", "frac"),
+         "peel_async_ms": g(line, "peel_async", "ms_per_step"),
+         "mphf_1e8_ms": g(line, "mphf_1e8", "ms_per_step"),
+         "mphf_1e8_e2e_ms": g(line, "mphf_1e8", "e2e", "ms_per_step"),
+         "mphf_1e8_device_driven_ms": g(line, "device_driven", "ms_per_step"),
+         "lookup_mlookups_s": g(line, "lookup", "value"),
+         "batched_ms": g(line, "batched", "peel", "ms_per_step"),
+         "batched_medges_s": g(line, "batched", "peel", "value"),
+         "batched_with_g_ms": g(line, "batched", "with_g", "ms_per_step"),
+         "batched_plain_one_graph_ms": g(line, "batched", "plain_one_graph", "ms_per_step"),
+         "batched_vs_plain": g(line, "batched", "speedup_vs_plain"),
+         "serving_capacity_req_s": g(line, "serving", "capacity_req_per_s"),
+         "sf_1e8_ms": g(line, "static_function", "ms_per_step"),
+         "general_1e8_ms": g(line, "general_peel", "ms_per_step"),
+         "cpu_oracle_medges_s": g(line, "cpu_baseline", "value")}
+    for name in ("n1e9_g1222", "n1e9_g1200", "n1e8_g1300_r4"):
+        s[f"stress_{name}_ms"] = g(line, "stress", name, "ms_per_step")
+    rates = g(line, "serving", "rates") or []
+    s["serving_p50_p99_ms_by_load"] = [[r.get("load"), round(r.get("p50_ms") or 0, 2),
+                                        round(r.get("p99_ms") or 0, 2)] for r in rates]
+    return s
 
 
 def main():
@@ -732,24 +1044,29 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_KEYS, help=argparse.SUPPRESS)
-    ap.add_argument("--no-cpu-baseline", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--no-batched", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--no-serving", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--no-peel-1e9", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--no-sf", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--no-general", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--max-scale", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--batched-probe", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--n", type=int, default=PEEL_N,
+                    help="edges of the headline peel (smaller cases for profilers)")
+    ap.add_argument("--legs", default="all",
+                    help="comma-separated sub-legs to run besides the timed step: "
+                         + ",".join(ALL_LEGS) + "; 'all' (default) or 'none'")
+    ap.add_argument("--max-scale", action="store_true",
+                    help="also build the largest MPHF one GB300 holds (n = 3.4e9)")
     ap.add_argument("--round-loop", default="graph", choices=["graph", "host"],
                     help="graph: rounds in a CUDA graph (default); host: one launch per round "
                          "(same kernels; for profilers that cannot see inside the graph)")
+    ap.add_argument("--batched-shape", default=None,
+                    help="THREADSxCTAS: only one call of the batched form with this launch "
+                         "shape (a fixed launch sequence for a profiler)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    legs = (set(ALL_LEGS) if args.legs == "all"
+            else {x for x in args.legs.split(",") if x and x != "none"})
+    unknown = legs - set(ALL_LEGS)
+    if unknown:
+        raise SystemExit(f"unknown legs: {sorted(unknown)}")
 
-    import numpy as np
     import torch
     import paper_1312_0526_gb300 as hp
     from paper_1312_0526_gb300 import build as hpbuild
@@ -767,25 +1084,11 @@ def main():
     if dist:
         dist.barrier()
     hp.lib()
-    if args.batched_probe:
-        batched_probe(args.batched_probe)
+    if args.batched_shape:
+        batched_shape_call(args.batched_shape)
         return 0
-
     if args.round_loop == "host":
         hp.set_tuning(host_round_loop=1)
-    n = args.n
-    m = hp.num_vertices(n, GAMMA_MILLI, R)
-    keys_h = torch.from_numpy(inputs.keys(n, KEY_SEED + rank).view(np.int64)).pin_memory()
-    keys = keys_h.to("cuda", non_blocking=False)
-    ws = torch.empty(hp.mphf_workspace_size(n, GAMMA_MILLI), dtype=torch.uint8, device="cuda")
-    G = torch.empty((m + 31) // 32, dtype=torch.int64, device="cuda")
-    D = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device="cuda")
-    order = torch.empty(n, dtype=torch.int32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def step():
-        return hp.mphf_build(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D,
-                             order=order)
 
     def sync_all():
         torch.cuda.synchronize()
@@ -795,11 +1098,25 @@ def main():
     def max_over_ranks(x):
         return reduce_max(x, dist, "cuda" if dist and dist.get_backend() == "nccl" else "cpu")
 
+    # ---- the headline: plain peel of n edges, edges device-resident
+    n = args.n
+    m = hp.num_vertices(n, GAMMA_MILLI, R)
+    keys = inputs.keys_torch(n, KEY_SEED + rank)
+    edges = hp.hash_edges(keys, m, R, HASH_SEED)
+    del keys
+    torch.cuda.empty_cache()
+    ws = torch.empty(hp.peel_workspace_size(n, m, R), dtype=torch.uint8, device="cuda")
+    out = (torch.empty(n, dtype=torch.int32, device="cuda"),
+           torch.empty(n, dtype=torch.int32, device="cuda"),
+           torch.empty(4097, dtype=torch.int64, device="cuda"))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return hp.peel(edges, m, workspace=ws, out=out)
+
     for _ in range(max(args.warmup, 0)):
         res = step()
     sync_all()
-
-    # ---- timed region: device-resident keys, K full steps
     hp.profile_reset()
     hp.profile_enable(True)
     l0 = hp.kernel_launches()
@@ -814,195 +1131,95 @@ def main():
     launches = hp.kernel_launches() - l0
     hp.profile_enable(False)
     prof = hp.profile_read()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms = max_over_ranks(ms)
-    st = res.stats
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    st = dict(res.stats)
     value = aggregate_medges(n, world, ms)
+    roof = roofline_of(prof, args.steps, n, m, st, args.round_loop)
+    ref = (out[0].clone(), out[1].clone())
 
-    # ---- roofline of the dominant step
-    peak, peak_kind = measured_peaks()
-    ranked = sorted(((v[1], k) for k, v in prof.items()), reverse=True)
-    roof = None
-    for tot_ms, name in ranked:
-        model = byte_model(name, n, m, st)
-        if model is None:
-            continue
-        per_step_ms = tot_ms / args.steps
-        launches_per_step = prof[name][0] / args.steps
-        if name == "rounds" and args.round_loop == "graph":
-            launches_per_step = 1 + st["rounds"]  # round 0 + the graph's iterations
-        achieved = model["sector"] / (per_step_ms / 1e3) / 1e9
-        traffic = traffic_step = None
-        if name in NCU_TRAFFIC:
-            src, h, per_unit = NCU_TRAFFIC[name]
-            if src_hash(src) == h:
-                traffic_step = per_unit * model["units"]
-                traffic = traffic_step / max(launches_per_step, 1)
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "model": "sector", "peak_kind": peak_kind,
-                "algorithmic_bytes_per_step": model["sector"],
-                "word_model_gbs": model["word"] / (per_step_ms / 1e3) / 1e9,
-                "launches_per_step": launches_per_step,
-                "traffic_per_step": traffic_step,
-                "traffic_gbs": traffic_step / (per_step_ms / 1e3) / 1e9 if traffic_step else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at n = 3e7, "
-                                  "scaled by peeled edges" if traffic_step else None,
-                "ms_per_step": per_step_ms, "share": tot_ms / sum(v[1] for v in prof.values())}
-        break
-
-    # ---- end to end through the public API with host buffers: every step
-    # takes its keys from pinned host memory and reads its g values and rank
-    # directory back to pinned host memory.  Two ways, both timed:
-    #   "copy": a copy stream moves each step's keys into one of two device
-    #           buffers while the previous step builds (the build waits for
-    #           its copy; a buffer is refilled only after the build that read
-    #           it) -- how a stream of key sets is fed;
-    #   "in_place": the hashing kernel reads the keys in place over the host
-    #           link (the C ABI accepts a pinned host pointer), no copy.
-    # The read-back runs on a second stream into double buffers.
-    h2d_stream, copy_stream = torch.cuda.Stream(), torch.cuda.Stream()
-    Gb, Db = [G, torch.empty_like(G)], [D, torch.empty_like(D)]
-    G_h = [torch.empty_like(G, device="cpu").pin_memory() for _ in range(2)]
-    D_h = [torch.empty_like(D, device="cpu").pin_memory() for _ in range(2)]
-    kd = [keys, torch.empty_like(keys)]
-    e2e_steps = max(1, min(args.steps, 10))
-
-    def run_e2e(mode):
-        read, built_ev, copied = [None, None], [None, None], [None, None]
-
-        def enqueue_copy(i):
-            # step i's keys into kd[i % 2], once step i-2's build has read it
-            b = i & 1
-            with torch.cuda.stream(h2d_stream):
-                h2d_stream.wait_event(e0)
-                if built_ev[b] is not None:
-                    h2d_stream.wait_event(built_ev[b])
-                kd[b].copy_(keys_h, non_blocking=True)
-                copied[b] = torch.cuda.Event()
-                copied[b].record(h2d_stream)
-
-        sync_all()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        if mode == "copy":
-            enqueue_copy(0)
-        for i in range(e2e_steps):
-            b = i & 1
-            if mode == "copy":
-                # the build call returns when its step is done, so the next
-                # step's copy is queued first and runs while this one builds
-                if i + 1 < e2e_steps:
-                    enqueue_copy(i + 1)
-                stream.wait_event(copied[b])
-                src = kd[b]
-            else:
-                src = keys_h
-            if read[b] is not None:
-                stream.wait_event(read[b])  # step i-2's results are on the host
-            hp.mphf_build(src, HASH_SEED, GAMMA_MILLI, workspace=ws, G=Gb[b], rank_dir=Db[b],
-                          order=order)
-            built = torch.cuda.Event()
-            built.record(stream)
-            built_ev[b] = built
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(built)
-                G_h[b].copy_(Gb[b], non_blocking=True)
-                D_h[b].copy_(Db[b], non_blocking=True)
-                read[b] = torch.cuda.Event()
-                read[b].record(copy_stream)
-        stream.wait_stream(copy_stream)
-        stream.wait_stream(h2d_stream)
-        e1.record(stream)
-        sync_all()
-        for b in range(min(2, e2e_steps)):  # the pipelined steps built what the timed ones did
-            assert torch.equal(G_h[b], G.cpu()) and torch.equal(D_h[b], D.cpu())
-        return max_over_ranks(e0.elapsed_time(e1) / e2e_steps)
-
-    e2e_ms = run_e2e("copy")
-    e2e_in_place_ms = run_e2e("in_place")
-    del kd
+    e2e = None
+    if "e2e" in legs:
+        e2e_steps = max(1, min(args.steps, 10))
+        e2e_ms, same = peel_e2e(edges, m, ws, ref, e2e_steps, sync_all, max_over_ranks)
+        e2e = {"value": aggregate_medges(n, world, e2e_ms), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * R * n, "d2h_bytes_per_step": 8 * n,
+               "ms_per_step": e2e_ms, "steps": e2e_steps, "same_as_device_resident": same,
+               "copies": "every step's edges (12 B each) copied from pinned host memory into "
+                         "one of two device buffers on a copy stream while the previous step "
+                         "peels (the first copy is not overlapped); order and claim words "
+                         "(8 B per edge) copied back to pinned host buffers on a second stream"}
+    peel_async = None
+    if "peel_async" in legs and world == 1:
+        peel_async = peel_async_leg(edges, m, ws, ref)
+    del edges, ws, out, ref
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
-    batched = None
-    if world == 1 and not args.no_batched:
-        batched = batched_leg(args.steps, args.warmup)
-    serving = None
-    if world == 1 and not args.no_serving:
-        serving = serving_leg()
-    lookup = lookup_leg(keys, G, D, m, res.stats["seed_used"])
-    device_driven = async_leg(keys, G, D) if world == 1 else None
-    peel_1e9 = None
-    sf = None
-    del keys, ws, order
-    torch.cuda.empty_cache()
+    cpu = cpu_baseline() if world == 1 and "cpu" in legs else None
+    mphf = lookup = device_driven = None
+    if world == 1 and "mphf" in legs:
+        mphf, mkeys, G, D, mm, seed_used = mphf_leg(MPHF_N, args.steps, args.warmup, rank)
+        if "lookup" in legs:
+            lookup = lookup_leg(mkeys, G, D, mm, seed_used)
+        if "async" in legs:
+            device_driven = async_leg(mkeys, G, D)
+        del mkeys, G, D
+        torch.cuda.empty_cache()
+    stress = stress_leg() if world == 1 and "stress" in legs else None
+    batched = batched_leg(args.steps, args.warmup) if world == 1 and "batched" in legs else None
+    serving = serving_leg() if world == 1 and "serving" in legs else None
+    sf = sf_leg(MPHF_N, steps=3, warmup=1) if world == 1 and "sf" in legs else None
+    general = general_leg(MPHF_N, steps=3, warmup=1) if world == 1 and "general" in legs else None
     random_access = None
-    if world == 1:
+    if world == 1 and "random_access" in legs and "rounds" in prof:
         random_access = random_access_leg(n, m, prof["rounds"][1] / args.steps)
         if roof is not None and roof["kernel"] == "rounds":
             # the rounds against the rate the memory system serves their own
             # access pattern alone (one record claim + two vertex updates per
-            # peeled edge), next to the copy-bandwidth fraction above
+            # peeled edge), next to the copy-bandwidth fraction
             roof["random_access_ceiling"] = {
                 "g_edges_per_s": random_access["peeled_edge"]["g_per_s"],
                 "achieved_g_edges_per_s": random_access["rounds_g_edges_per_s"],
                 "frac": random_access["rounds_vs_peeled_edge_pattern"],
-                "source": "random_access leg (hpeel_probe_random_access kind 2)"}
-    if world == 1 and not args.no_sf:
-        sf = sf_leg(n, steps=3, warmup=1)
-    general = None
-    if world == 1 and not args.no_general:
-        general = general_leg(n, steps=3, warmup=1)
-    if world == 1 and not args.no_peel_1e9:
-        peel_1e9 = peel_leg(PEEL_N, steps=3, warmup=1)
-    max_scale = None
-    if world == 1 and args.max_scale:
-        max_scale = max_scale_leg()
+                "source": "random_access leg (measurement library probe, kind 2)"}
+    max_scale = max_scale_leg() if world == 1 and args.max_scale else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"mphf-build n={n:.0e} r=3 gamma=1.23, SplitMix64 keys seed "
-                               f"1+rank, hash seed 1 (hash, incidence, peel, canonical "
-                               f"order, g assignment, rank)",
+        "config": {"workload": f"plain peel n={n:.0e} r=3 gamma=1.23, edges hashed from "
+                               f"SplitMix64 keys seed 1+rank with hash seed 1, device-resident; "
+                               f"records + incidence build, round-synchronous peel, canonical "
+                               f"order + claim words + layer offsets out (hpeel_peel)",
                    "n": n, "m": m, "gamma": GAMMA_MILLI / 1000, "r": R,
-                   "parallelism": f"{world} independent key sets (one per GPU)",
-                   "l2": "inputs larger than L2: 0.8 GB keys, 1.0 GB vertex state, "
-                         "1.2 GB edges per step"},
-        "rounds": st["rounds"], "seed_used": st["seed_used"],
+                   "parallelism": f"{world} independent hypergraphs (one per GPU)",
+                   "l2": f"inputs larger than L2: {12 * n / 1e9:.1f} GB edges, "
+                         f"{8 * m / 1e9:.1f} GB vertex records, {16 * n / 1e9:.1f} GB edge "
+                         f"records per step"},
+        "stats": {k: st[k] for k in ("rounds", "n_peeled", "core_nonempty", "first_layer",
+                                     "frontier", "hinge_moves")},
         "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "clocks": clk.summary(),
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": aggregate_medges(n, world, e2e_ms), "unit": UNIT,
-                "h2d_bytes_per_step": n * 8,
-                "d2h_bytes_per_step": (G.numel() + D.numel()) * 8, "ms_per_step": e2e_ms,
-                "steps": e2e_steps,
-                "copies": "every step's keys copied from pinned host memory into one of "
-                          "two device buffers on a copy stream while the previous step "
-                          "builds (the first copy is not overlapped); g values and rank "
-                          "directory copied back to pinned host buffers on a second stream",
-                "in_place": {"value": aggregate_medges(n, world, e2e_in_place_ms),
-                             "ms_per_step": e2e_in_place_ms,
-                             "copies": "keys read in place from pinned host memory by the "
-                                       "hashing kernel over the host link, no copy"}},
+        "e2e": e2e,
         "steps_ms": {k: v[1] / args.steps for k, v in sorted(prof.items())},
+        "peel_async": peel_async,
+        "mphf_1e8": mphf,
+        "lookup": lookup,
+        "device_driven": device_driven,
+        "stress": stress,
         "batched": batched,
         "serving": serving,
-        "lookup": lookup,
-        "peel_1e9": peel_1e9,
         "static_function": sf,
         "general_peel": general,
         "random_access": random_access,
-        "device_driven": device_driven,
         "max_scale": max_scale,
     }
+    line["summary"] = summary_of(line)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

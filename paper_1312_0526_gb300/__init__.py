@@ -138,8 +138,6 @@ def lib():
         L.hpeel_sf_build_async.argtypes = [p, p, u64, u64, u64, u32, u32, p, p, p, sz, p]
         L.hpeel_mphf_build_async.restype = st
         L.hpeel_mphf_build_async.argtypes = [p, u64, u64, u32, u32, p, p, p, p, sz, p]
-        L.hpeel_probe_random_access.restype = st
-        L.hpeel_probe_random_access.argtypes = [u32, u64, p, sz, p, sz, u64, p]
         L.hpeel_sf_bits.restype = u32
         L.hpeel_sf_bits.argtypes = [u64]
         L.hpeel_sf_words.restype = u64
@@ -240,16 +238,23 @@ def peel_workspace_size(n: int, m: int, r: int = 3, general: bool = False) -> in
 
 
 def peel(edges, m: int, workspace=None, max_layers: int = 4096,
-         general: bool = False) -> PeelResult:
+         general: bool = False, out=None) -> PeelResult:
     """Round-synchronous peel with canonical order (sec. 4.2); see hpeel_peel,
-    or hpeel_peel_general for a general (not r-partite) hypergraph."""
+    or hpeel_peel_general for a general (not r-partite) hypergraph.  out:
+    None, or a tuple (order int32 [n], claim int32 [n], layer_off int64
+    [max_layers + 1]) of buffers to write."""
     torch = _torch()
     ep = _dev_ptr(edges, "edges", torch.int32, 2)
     n, r = edges.shape
     dev = edges.device
-    order = torch.empty(n, dtype=torch.int32, device=dev)
-    claim = torch.empty(n, dtype=torch.int32, device=dev)
-    loff = torch.empty(max_layers + 1, dtype=torch.int64, device=dev)
+    if out is None:
+        order = torch.empty(n, dtype=torch.int32, device=dev)
+        claim = torch.empty(n, dtype=torch.int32, device=dev)
+        loff = torch.empty(max_layers + 1, dtype=torch.int64, device=dev)
+    else:
+        order, claim, loff = out
+        if order.numel() < n or claim.numel() < n or loff.numel() < max_layers + 1:
+            raise ValueError("out buffers too small: need n, n and max_layers + 1 entries")
     need = peel_workspace_size(n, m, r, general)
     ws = workspace if workspace is not None else _workspace(need, dev)
     wp = _dev_ptr(ws, "workspace", torch.uint8)
@@ -506,18 +511,6 @@ def stats_from_device(stats) -> dict:
     """The hpeel_stats a device-driven call wrote (copies to the host)."""
     raw = bytes(stats.cpu().numpy().tobytes())
     return Stats.from_buffer_copy(raw[:ctypes.sizeof(Stats)]).as_dict()
-
-
-def probe_random_access(kind: int, n_ops: int, a, b=None, seed: int = 1) -> None:
-    """Random-access ceiling probe (hpeel_probe_random_access), enqueued on
-    the current stream: kind 0 random 64-bit atomicAdd into a, 1 random
-    8-byte load from a, 2 one peeled edge (record claim in a, two vertex
-    updates in b).  a and b are CUDA tensors used as raw memory."""
-    pa = _dev_ptr(a, "a")
-    pb = _dev_ptr(b, "b") if b is not None else None
-    _check(lib().hpeel_probe_random_access(kind, n_ops, pa, a.numel() * a.element_size(), pb,
-                                           0 if b is None else b.numel() * b.element_size(),
-                                           seed, _stream()))
 
 
 def kernel_launches() -> int:

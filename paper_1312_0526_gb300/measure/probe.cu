@@ -1,4 +1,6 @@
-// probe.cu -- random-access ceiling of the memory system (measurement only).
+// probe.cu -- random-access ceiling of the memory system (measurement only;
+// built into its own library, libhpeel_measure.so, which only the benchmark
+// and its test load: nothing of it is part of the peeling library).
 //
 // The peeling rounds (sec. 4.2) touch one vertex record per DeleteEdge and
 // one edge record per claim, each at an address no other access predicts:
@@ -6,7 +8,10 @@
 // sector requests, not the copy bandwidth.  These kernels replay that access
 // pattern on synthetic indices (SplitMix64 of the operation number) so that
 // the rounds can be compared with the rate the same pattern reaches alone.
-#include "host.h"
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "probe.h"
 
 namespace hp {
 
@@ -48,32 +53,30 @@ __global__ void k_probe_edge(uint64_t n_ops, uint4 *A, FastMod fa, unsigned long
 
 using namespace hp;
 
-extern "C" hpeel_status hpeel_probe_random_access(uint32_t kind, uint64_t n_ops, void *d_a,
-                                                  size_t a_bytes, void *d_b, size_t b_bytes,
-                                                  uint64_t seed, void *stream) {
-    g_last_error.clear();
-    if (kind > 2) return fail(HPEEL_ERR_INVALID_ARG, "kind %u: 0, 1 or 2", kind);
+extern "C" int hpeel_measure_random_access(uint32_t kind, uint64_t n_ops, void *d_a,
+                                           size_t a_bytes, void *d_b, size_t b_bytes,
+                                           uint64_t seed, void *stream) {
+    if (kind > 2) return 1;
     const size_t unit = kind == 2 ? 16 : 8;
-    if (!d_a || a_bytes < unit || ((uintptr_t)d_a & 15u))
-        return fail(HPEEL_ERR_INVALID_ARG, "d_a: NULL, misaligned or below one element");
-    if (kind == 2 && (!d_b || b_bytes < 8 || ((uintptr_t)d_b & 7u)))
-        return fail(HPEEL_ERR_INVALID_ARG, "d_b: NULL, misaligned or below one word");
-    if (n_ops == 0) return HPEEL_OK;
-    Launch L;
-    HP_TRY(make_launch(stream, &L));
-    const unsigned grid = (unsigned)L.sms * 8;
+    if (!d_a || a_bytes < unit || ((uintptr_t)d_a & 15u)) return 1;
+    if (kind == 2 && (!d_b || b_bytes < 8 || ((uintptr_t)d_b & 7u))) return 1;
+    if (n_ops == 0) return 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 2;
+    const unsigned grid = (unsigned)sms * 8;
+    const cudaStream_t s = (cudaStream_t)stream;
     const FastMod fa = make_fastmod(a_bytes / unit);
-    count_launch();
     if (kind == 0) {
-        k_probe_rmw<<<grid, kThreads, 0, L.stream>>>(n_ops, (unsigned long long *)d_a, fa, seed);
+        k_probe_rmw<<<grid, 256, 0, s>>>(n_ops, (unsigned long long *)d_a, fa, seed);
     } else if (kind == 1) {
         // the sink is the first word: written only for an impossible sum
-        k_probe_read<<<grid, kThreads, 0, L.stream>>>(n_ops, (const unsigned long long *)d_a, fa,
-                                                      seed, (unsigned long long *)d_a);
+        k_probe_read<<<grid, 256, 0, s>>>(n_ops, (const unsigned long long *)d_a, fa, seed,
+                                          (unsigned long long *)d_a);
     } else {
-        k_probe_edge<<<grid, kThreads, 0, L.stream>>>(n_ops, (uint4 *)d_a, fa,
-                                                      (unsigned long long *)d_b,
-                                                      make_fastmod(b_bytes / 8), seed);
+        k_probe_edge<<<grid, 256, 0, s>>>(n_ops, (uint4 *)d_a, fa, (unsigned long long *)d_b,
+                                          make_fastmod(b_bytes / 8), seed);
     }
-    return check_launch("probe");
+    return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

@@ -67,12 +67,19 @@ def test_host_side_argument_checks(lib):
     # refused on the host before any device work (no GPU needed)
     INVALID = 1
     raw = ctypes.CDLL(hp.LIB_PATH)
-    raw.hpeel_probe_random_access.restype = ctypes.c_int
-    raw.hpeel_probe_random_access.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p,
-                                              ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
-                                              ctypes.c_uint64, ctypes.c_void_p]
-    assert raw.hpeel_probe_random_access(3, 10, None, 0, None, 0, 1, None) == INVALID
-    assert raw.hpeel_probe_random_access(2, 10, None, 0, None, 0, 1, None) == INVALID
+    u64, u32, vp, sz = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t
+    for fn in (raw.hpeel_peel_async, raw.hpeel_peel_general_async):
+        fn.restype = ctypes.c_int
+        fn.argtypes = [vp, u64, u64, u32, vp, vp, vp, u32, vp, vp, sz, vp]
+        assert fn(None, 10, 30, 5, None, None, None, 0, None, None, 0, None) == INVALID  # r
+        assert fn(None, 10, 30, 3, None, None, None, 0, None, None, 0, None) == INVALID  # stats
+        assert fn(None, 2**32, 30, 3, None, None, None, 0, None, None, 0, None) == INVALID
+    raw.hpeel_sf_build_async.restype = ctypes.c_int
+    raw.hpeel_sf_build_async.argtypes = [vp, vp, u64, u64, u64, u32, u32, vp, vp, vp, sz, vp]
+    assert raw.hpeel_sf_build_async(None, None, 10, 1, 1, 1230, 8, None, None, None, 0,
+                                    None) == INVALID  # sigma < 2
+    assert raw.hpeel_sf_build_async(None, None, 10, 5, 1, 1230, 0, None, None, None, 0,
+                                    None) == INVALID  # max_tries
     with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
         hp.set_tuning(bucket_part_passes=3)
     with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
@@ -123,3 +130,14 @@ def test_oracle_is_not_imported_by_the_product():
         assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
     for f in glob.glob(os.path.join(ROOT, "paper_1312_0526_gb300", "csrc", "*")):
         assert "hpeel_oracle" not in open(f).read(), f
+
+
+def test_measurement_probe_is_a_separate_library(lib):
+    # the benchmark's random-access probe lives in its own library: the
+    # peeling library exports no probe symbol
+    from paper_1312_0526_gb300 import measure
+    raw = ctypes.CDLL(hp.LIB_PATH)
+    assert not hasattr(raw, "hpeel_measure_random_access")
+    ml = measure.lib()
+    assert ml.hpeel_measure_random_access(3, 10, None, 0, None, 0, 1, None) == 1
+    assert ml.hpeel_measure_random_access(2, 10, None, 0, None, 0, 1, None) == 1

@@ -1,12 +1,13 @@
-"""The random-access probe (hpeel_probe_random_access) does the operations it
-states: every atomicAdd lands (the words sum to the operation count) and
-every claim lowers a record's claim word to an operation number."""
+"""The benchmark's random-access probe (measure/probe.cu, a library of its
+own) does the operations it states: every atomicAdd lands (the words sum to
+the operation count) and every claim lowers a record's claim word to an
+operation number."""
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-import paper_1312_0526_gb300 as hp  # noqa: E402
+from paper_1312_0526_gb300 import measure  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -19,9 +20,9 @@ def _built():
 
 def test_probe_rmw_and_load():
     words = torch.zeros(1001, dtype=torch.int64, device="cuda")
-    hp.probe_random_access(1, 50_000, words)
+    measure.random_access(1, 50_000, words)
     assert int(words.sum()) == 0
-    hp.probe_random_access(0, 50_000, words, seed=3)
+    measure.random_access(0, 50_000, words, seed=3)
     assert int(words.sum()) == 50_000
     assert int((words > 0).sum()) > 900  # spread over the words
 
@@ -30,7 +31,7 @@ def test_probe_peeled_edge():
     n_ops, n_rec = 40_000, 3001
     rec = torch.full((n_rec, 4), -1, dtype=torch.int32, device="cuda")
     words = torch.zeros(777, dtype=torch.int64, device="cuda")
-    hp.probe_random_access(2, n_ops, rec, words, seed=5)
+    measure.random_access(2, n_ops, rec, words, seed=5)
     assert int(words.sum()) == 2 * n_ops
     # records read 0xFFFFFFFF in their first word, so the claim hit word 2
     claim = rec[:, 2].cpu().numpy().view("uint32")
@@ -42,5 +43,5 @@ def test_probe_peeled_edge():
 
 def test_probe_rejects_bad_kind():
     words = torch.zeros(16, dtype=torch.int64, device="cuda")
-    with pytest.raises(hp.HpeelError, match="INVALID_ARG"):
-        hp.probe_random_access(3, 10, words)
+    with pytest.raises(ValueError, match="refused"):
+        measure.random_access(3, 10, words)
