@@ -76,7 +76,8 @@ typedef struct hpeel_stats {
                                2 no seed peeled (builds), 3 device check
                                failed (device_err holds the code), 4 more
                                rounds than max_layers (peels) */
-    uint32_t reserved32;
+    uint32_t sorted_rounds; /* rounds whose layer was deleted in sorted form
+                               (see the tuning's sorted_round_min) */
     uint64_t reserved;
 } hpeel_stats;
 
@@ -110,6 +111,15 @@ typedef struct hpeel_stats {
  *                       workspace shrinks by about 2 x 16 (r - 1) bytes per
  *                       edge; 1: all parts in one pass; 2: one part per pass
  *                       (general graphs always take one pass).
+ *   sorted_round_min    rounds whose layer holds at least this many edges
+ *                       run in sorted form (sec. 4.2's sorting of the
+ *                       orientations by edge and of the updates by vertex,
+ *                       with shared memory as the fast tier) instead of with
+ *                       atomics at random addresses -- the first rounds, until
+ *                       one is smaller; 0 (default): automatic, n / 8, for
+ *                       r = 3 r-partite graphs whose incidence build is
+ *                       L2-blocked in one pass; 0xFFFFFFFF: never.  Results
+ *                       are the same either way.
  * hpeel_set_tuning(NULL) restores the defaults.  Workspace sizes depend on
  * the tuning: query them after setting it.  Errors: HPEEL_ERR_INVALID_ARG.
  */
@@ -119,7 +129,8 @@ typedef struct hpeel_tuning {
     uint32_t host_round_loop;
     uint32_t bucket_sub_shift;
     uint32_t bucket_part_passes;
-    uint32_t reserved[3];
+    uint32_t sorted_round_min;
+    uint32_t reserved[2];
 } hpeel_tuning;
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t);
 void hpeel_get_tuning(hpeel_tuning *t);

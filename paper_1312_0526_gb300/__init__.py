@@ -52,7 +52,8 @@ class HpeelError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("bucket_shift", ctypes.c_uint32), ("bucket_min_vertices", ctypes.c_uint32),
                 ("host_round_loop", ctypes.c_uint32), ("bucket_sub_shift", ctypes.c_uint32),
-                ("bucket_part_passes", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("bucket_part_passes", ctypes.c_uint32), ("sorted_round_min", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -67,11 +68,11 @@ class Stats(ctypes.Structure):
                 ("attempts", ctypes.c_uint32), ("device_err", ctypes.c_uint32),
                 ("first_layer", ctypes.c_uint64), ("frontier", ctypes.c_uint64),
                 ("hinge_moves", ctypes.c_uint64), ("async_status", ctypes.c_uint32),
-                ("reserved32", ctypes.c_uint32), ("reserved", ctypes.c_uint64)]
+                ("sorted_rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_
-                if k not in ("reserved", "reserved32")}
+                if k != "reserved"}
 
 
 _lib = None
@@ -544,7 +545,8 @@ def get_tuning() -> dict:
     lib().hpeel_get_tuning(ctypes.byref(t))
     return {"bucket_shift": t.bucket_shift, "bucket_min_vertices": t.bucket_min_vertices,
             "host_round_loop": t.host_round_loop,
-            "bucket_sub_shift": t.bucket_sub_shift, "bucket_part_passes": t.bucket_part_passes}
+            "bucket_sub_shift": t.bucket_sub_shift, "bucket_part_passes": t.bucket_part_passes,
+            "sorted_round_min": t.sorted_round_min}
 
 
 def set_tuning(**kw) -> None:
@@ -555,7 +557,7 @@ def set_tuning(**kw) -> None:
     cur = get_tuning()
     cur.update(kw)
     t = Tuning(cur["bucket_shift"], cur["bucket_min_vertices"], cur["host_round_loop"],
-               cur["bucket_sub_shift"], cur["bucket_part_passes"])
+               cur["bucket_sub_shift"], cur["bucket_part_passes"], cur["sorted_round_min"])
     _check(lib().hpeel_set_tuning(ctypes.byref(t)))
 
 

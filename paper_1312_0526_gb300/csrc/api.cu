@@ -37,9 +37,11 @@ Ctl *pinned_ctl() {
 struct PeelLayout {
     size_t ctl, params, emit, rec, state, claim, L, pairs, fill, pairs2, fill2, ovf, ovf_count, loff,
         hist, scantmp, total;
+    size_t s_pairs, s_fill, s_pairs2, s_fill2, s_claims;  // sorted rounds
     uint32_t max_rounds;
     bool bucketed;
     BucketPlan plan;
+    SortedPlan sp;
 };
 
 // SM count of the current device (152 when there is none: plan for a GB300).
@@ -54,7 +56,7 @@ int current_sms() {
 }
 
 // Process-wide tuning (hpeel_set_tuning); read by layouts and launches.
-hpeel_tuning g_tuning = {22u, 8u << 20, 0u, 0u, 0u, {0, 0, 0}};
+hpeel_tuning g_tuning = {22u, 8u << 20, 0u, 0u, 0u, 0u, {0, 0}};
 std::mutex g_tuning_mu;
 
 hpeel_tuning tuning() {
@@ -84,16 +86,25 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false)
         // the bucketing kernel keeps three counters per chunk in shared memory
         if (p.plan.smem > (200u << 10)) p.bucketed = false;
     }
+    if (p.bucketed && !general)
+        p.sp = sorted_plan(n, m, r, p.plan, tu.sorted_round_min, current_sms());
     p.ctl = take(sizeof(Ctl));
     p.params = take(sizeof(RoundParams));
     p.emit = take(sizeof(EmitState));
     p.rec = take((r == 4 ? 32 : 16) * n);
     p.state = take(8 * m);
+    // the layer list, the build's first-level buckets (dead once refined)
+    // and, after the list's n entries, the claim list of the sorted rounds
+    // (written from the build's apply on, so not where the build's live
+    // sub-buckets are)
     const size_t ls = (r == 4 ? 32 : 16) * n;
-    const size_t shared = std::max<size_t>(ls, p.bucketed ? p.plan.pair_bytes : 0);
+    size_t shared = std::max<size_t>(ls, p.bucketed ? p.plan.pair_bytes : 0);
+    const size_t claims_at = align256(ls);
+    if (p.sp.enabled) shared = std::max<size_t>(shared, claims_at + p.sp.claims_bytes);
     const size_t region = take(shared);
     p.L = region;
     p.pairs = region;
+    if (p.sp.enabled) p.s_claims = region + claims_at;
     p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks_pass * p.plan.regions : 0);
     p.fill2 = take(p.bucketed ? 4 * (size_t)p.plan.subs_pass : 0);
     p.ovf = take(p.bucketed ? 8 * (size_t)p.plan.ovf_cap : 0);
@@ -112,9 +123,32 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false)
     p.hist = take2(4 * kEmitBins * tiles);
     p.scantmp = take2(4 * scan_tmp_words(kEmitBins * tiles));
     p.pairs2 = region2;
-    off = region2 + std::max<size_t>(o2, p.bucketed ? align256(p.plan.pair2_bytes) : 0);
+    // the buckets of the sorted rounds live there too: they are used after
+    // the build and before the order
+    size_t o3 = 0;
+    auto take3 = [&](size_t bytes) {
+        size_t o = o3;
+        o3 = align256(o3 + bytes);
+        return region2 + o;
+    };
+    if (p.sp.enabled) {
+        p.s_pairs = take3(p.sp.pairs_bytes);
+        p.s_fill = take3(p.sp.fill_bytes);
+        p.s_pairs2 = take3(p.sp.pairs2_bytes);
+        p.s_fill2 = take3(p.sp.fill2_bytes);
+    }
+    off = region2 + std::max<size_t>(std::max<size_t>(o2, o3),
+                                     p.bucketed ? align256(p.plan.pair2_bytes) : 0);
     p.total = off;
     return p;
+}
+
+SortedBufs sorted_bufs(const PeelLayout &lay, char *ws) {
+    return SortedBufs{reinterpret_cast<uint2 *>(ws + lay.s_pairs),
+                      reinterpret_cast<uint32_t *>(ws + lay.s_fill),
+                      reinterpret_cast<uint2 *>(ws + lay.s_pairs2),
+                      reinterpret_cast<uint32_t *>(ws + lay.s_fill2),
+                      reinterpret_cast<uint2 *>(ws + lay.s_claims)};
 }
 
 struct MphfLayout {
@@ -147,6 +181,7 @@ struct PeelOut {
     uint64_t first_layer;
     uint64_t frontier;
     uint64_t moves;
+    uint32_t sorted_rounds;
     uint32_t *loff;  // device layer table (uint32[rounds + 2])
     uint4 *list;     // device layer list: entries {v_hinge, others, e}
 };
@@ -162,6 +197,7 @@ struct PeelIO {
     bool force_direct = false;  // update the vertex records directly (no buckets)
     bool general = false;       // a general (not r-partite) hypergraph on [0, m)
     bool host_loop = false;     // launch every round from the host, whatever the tuning
+    bool random_rounds = false; // no round in sorted form
 };
 
 // Executable graphs of the round loop, cached by their parameters: round 0,
@@ -191,76 +227,78 @@ void destroy_graph(RoundGraph &g) {
     g = RoundGraph{};
 }
 
-hpeel_status build_round_graph(const RoundLaunch &k0, const RoundLaunch &k1,
-                               const RoundParams *prm, RoundGraph *out) {
-    RoundGraph rg;
-    auto cleanup = [&](hpeel_status st) {
-        destroy_graph(rg);
-        return st;
-    };
-    if (cudaGraphCreate(&rg.graph, 0) != cudaSuccess ||
-        cudaEventCreateWithFlags(&rg.done, cudaEventDisableTiming) != cudaSuccess)
-        return cleanup(fail(HPEEL_ERR_CUDA, "graph creation failed: %s",
-                            cudaGetErrorString(cudaGetLastError())));
-    cudaGraphConditionalHandle h = 0;
-    void *args[] = {(void *)&prm, &h};
-    cudaKernelNodeParams p0{};
-    p0.func = k0.fn;
-    p0.gridDim = dim3(k0.grid);
-    p0.blockDim = dim3(k0.block);
-    p0.kernelParams = args;
-    p0.sharedMemBytes = k0.smem;
-    cudaGraphNode_t n0, nw, n1;
-    cudaGraphNodeParams cp{};
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h, rg.graph, 0, 0);
-    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n0, rg.graph, nullptr, 0, &p0);
-    if (e == cudaSuccess) {
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        e = cudaGraphAddNode(&nw, rg.graph, &n0, nullptr, 1, &cp);
+// Capture streams of this thread (one per nesting depth of the graph).
+cudaStream_t capture_stream(int depth) {
+    thread_local cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};
+    thread_local int dev_of[4] = {-1, -1, -1, -1};
+    int d = 0;
+    cudaGetDevice(&d);
+    if (!s[depth] || dev_of[depth] != d) {
+        if (cudaStreamCreateWithFlags(&s[depth], cudaStreamNonBlocking) != cudaSuccess)
+            return nullptr;
+        dev_of[depth] = d;
     }
-    if (e == cudaSuccess) {
-        cudaKernelNodeParams p1{};
-        p1.func = k1.fn;
-        p1.gridDim = dim3(k1.grid);
-        p1.blockDim = dim3(k1.block);
-        p1.kernelParams = args;
-        p1.sharedMemBytes = k1.smem;
-        e = cudaGraphAddKernelNode(&n1, cp.conditional.phGraph_out[0], nullptr, 0, &p1);
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&rg.exec, rg.graph, 0);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return cleanup(fail(HPEEL_ERR_CUDA, "round graph: %s", cudaGetErrorString(e)));
-    }
-    *out = rg;
-    return HPEEL_OK;
+    return s[depth];
 }
 
-hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool gen, const RoundParams *prm) {
-    int dev = 0;
-    HP_CUDA(cudaGetDevice(&dev));
-    const RoundLaunch k0 = round0_launch(L, r, gen);
-    const RoundLaunch k1 = round_launch(L, r, gen);
-    char keybuf[160];
-    snprintf(keybuf, sizeof keybuf, "%d|%p|%p|%p|%u|%u", dev, k0.fn, k1.fn, (const void *)prm,
-             k0.grid, k1.grid);
-    const std::string key(keybuf);
+// A condition handle on the graph stream s is capturing into.
+cudaError_t new_handle(cudaStream_t s, unsigned default_value, unsigned flags,
+                       cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    return cudaGraphConditionalHandleCreate(h, g, default_value, flags);
+}
+
+// Append a conditional node at the capture position of s; *body receives its
+// body graph, into which another stream captures.
+cudaError_t append_conditional(cudaStream_t s, cudaGraphConditionalHandle h,
+                               cudaGraphConditionalNodeType type, cudaGraph_t *body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+    if (e != cudaSuccess) return e;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies);
+}
+
+// Launch the cached executable graph for key on L.stream, capturing and
+// instantiating it with capture() on first use (least recently used graphs
+// are evicted, after their latest launch has finished).
+template <typename F>
+hpeel_status launch_cached_graph(const Launch &L, const std::string &key, F capture) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it == g_graphs.end()) {
         while (g_graph_lru.size() >= kGraphCache) {
             auto old = g_graphs.find(g_graph_lru.front());
             if (old != g_graphs.end()) {
-                destroy_graph(old->second);  // waits for its latest launch
+                destroy_graph(old->second);
                 g_graphs.erase(old);
             }
             g_graph_lru.erase(g_graph_lru.begin());
         }
         RoundGraph rg;
-        HP_TRY(build_round_graph(k0, k1, prm, &rg));
+        HP_TRY(capture(&rg.graph));
+        if (cudaGraphInstantiate(&rg.exec, rg.graph, 0) != cudaSuccess ||
+            cudaEventCreateWithFlags(&rg.done, cudaEventDisableTiming) != cudaSuccess) {
+            const cudaError_t e = cudaGetLastError();
+            destroy_graph(rg);
+            return fail(HPEEL_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+        }
         it = g_graphs.emplace(key, rg).first;
         g_graph_lru.push_back(key);
     } else {
@@ -268,10 +306,106 @@ hpeel_status launch_round_graph(const Launch &L, uint32_t r, bool gen, const Rou
         if (pos != g_graph_lru.end()) g_graph_lru.erase(pos);
         g_graph_lru.push_back(key);
     }
-    count_launch(1);  // round 0; the caller counts the round kernel's iterations
     HP_CUDA(cudaGraphLaunch(it->second.exec, L.stream));
     HP_CUDA(cudaEventRecord(it->second.done, L.stream));
     return HPEEL_OK;
+}
+
+// Round 0 and the loops of rounds, added at the capture position of s0; the
+// loop bodies are captured on s1.  With a sorted plan: round 0 and the first
+// rounds in sorted form (a while node over sorted rounds, rounds_bucketed.cu),
+// then a while node over the random round kernel; without one: the random
+// round 0 and its loop.  The round kernels' last blocks (or the sorted
+// rounds' closing kernel) set the loop conditions.
+struct RoundsArgs {
+    uint32_t n, m, r;
+    bool gen;
+    const RoundParams *prm;
+    const SortedPlan *sp;  // null: random rounds only
+    SortedBufs sw;
+    unsigned long long *st;
+    uint4 *rec, *Ll;
+    uint32_t *loff;
+    Ctl *ctl;
+    uint32_t max_rounds;
+};
+
+cudaError_t capture_rounds(cudaStream_t s0, cudaStream_t s1, int sms, const RoundsArgs &a) {
+    Launch L0{s0, sms}, L1{s1, sms};
+    const RoundLaunch k0 = round0_launch(L0, a.r, a.gen), k1 = round_launch(L0, a.r, a.gen);
+    cudaGraphConditionalHandle h_s = 0, h_r = 0;
+    cudaGraph_t body = nullptr, g = nullptr;
+    auto begin_body = [&](cudaGraph_t b) {
+        return cudaStreamBeginCaptureToGraph(s1, b, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed);
+    };
+    cudaError_t e = new_handle(s0, 0u, 0u, &h_r);
+    if (e != cudaSuccess) return e;
+    if (a.sp) {
+        e = new_handle(s0, 0u, 0u, &h_s);
+        if (e != cudaSuccess) return e;
+        launch_sorted_round0(L0, *a.sp, a.sw, a.st, a.n, a.m, a.rec, a.Ll, a.loff, a.ctl,
+                             a.max_rounds, h_s, h_r);
+        e = append_conditional(s0, h_s, cudaGraphCondTypeWhile, &body);
+        if (e == cudaSuccess) e = begin_body(body);
+        if (e != cudaSuccess) return e;
+        launch_sorted_round(L1, *a.sp, a.sw, a.st, a.n, a.rec, a.Ll, a.loff, a.ctl, a.max_rounds,
+                            h_s, h_r);
+        e = cudaStreamEndCapture(s1, &g);
+        if (e != cudaSuccess) return e;
+    } else {
+        void *args[] = {(void *)&a.prm, &h_r};
+        count_launch();
+        e = cudaLaunchKernel(k0.fn, dim3(k0.grid), dim3(k0.block), args, k0.smem, s0);
+        if (e != cudaSuccess) return e;
+    }
+    e = append_conditional(s0, h_r, cudaGraphCondTypeWhile, &body);
+    if (e == cudaSuccess) e = begin_body(body);
+    if (e != cudaSuccess) return e;
+    {
+        void *args[] = {(void *)&a.prm, &h_r};
+        e = cudaLaunchKernel(k1.fn, dim3(k1.grid), dim3(k1.block), args, k1.smem, s1);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(s1, &g);
+    return e != cudaSuccess ? e : e2;
+}
+
+// Kernels one peel's rounds launched, from its control block: round 0 (6 in
+// sorted form), 7 per sorted round, 1 per random round.
+uint64_t round_kernels(const Ctl &c, bool sorted) {
+    const uint64_t rounds = (uint64_t)c.round + (c.more ? 1 : 0);
+    return (sorted ? 6 : 1) + 7ull * c.brounds + (rounds - c.brounds);
+}
+
+// The device-driven round loop of a host-driven peel: round 0 and the loops
+// of rounds as one cached CUDA graph, launched on L.stream.
+hpeel_status launch_round_graph(const Launch &L, const RoundsArgs &a) {
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    const hpeel_tuning tu = tuning();
+    char keybuf[256];
+    snprintf(keybuf, sizeof keybuf, "rounds|%d|%p|%u|%u|%u|%d|%d|%u|%u|%u|%u|%d", dev,
+             (const void *)a.prm, a.n, a.m, a.r, a.gen ? 1 : 0, a.sp ? 1 : 0, tu.bucket_shift,
+             tu.bucket_sub_shift, tu.bucket_part_passes, tu.sorted_round_min, L.sms);
+    return launch_cached_graph(L, std::string(keybuf), [&](cudaGraph_t *g) -> hpeel_status {
+        cudaStream_t s0 = capture_stream(0), s1 = capture_stream(1);
+        if (!s0 || !s1) return fail(HPEEL_ERR_CUDA, "capture stream creation failed");
+        LaunchCountPause pause;
+        cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            e = capture_rounds(s0, s1, L.sms, a);
+            cudaGraph_t got = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(s0, &got);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) {
+                *g = got;
+                return HPEEL_OK;
+            }
+            if (got) cudaGraphDestroy(got);
+        }
+        cudaGetLastError();
+        return fail(HPEEL_ERR_CUDA, "round graph capture: %s", cudaGetErrorString(e));
+    });
 }
 
 // Round-synchronous peel (sec. 4.2) of n edges on m vertices.
@@ -292,6 +426,12 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     const uint32_t P = io.general ? m : m / r;
 
     HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), L.stream));
+    // the first rounds in sorted form when the plan allows it; the
+    // L2-blocked build then also lists round 0's claims
+    const bool sorted = lay.sp.enabled && !io.force_direct && !io.random_rounds && !io.general;
+    const SortedBufs sbufs = sorted ? sorted_bufs(lay, ws) : SortedBufs{};
+    const ClaimSink sink = sorted ? ClaimSink{sbufs.claims, lay.sp.claim_cap, n}
+                                  : ClaimSink{nullptr, 0, 0};
     if (lay.bucketed && !io.force_direct) {
         uint2 *pairs = reinterpret_cast<uint2 *>(ws + lay.pairs);
         uint32_t *fill = reinterpret_cast<uint32_t *>(ws + lay.fill);
@@ -310,7 +450,8 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
             // every vertex record of the pass's part is written by the
             // shared-memory apply
             ProfScope ps(L, "apply_buckets");
-            launch_apply_buckets(L, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl, pass);
+            launch_apply_buckets(L, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl, pass,
+                                 sink);
         }
     } else {
         {
@@ -340,32 +481,63 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     hp_prm.max_rounds = lay.max_rounds;
     RoundParams *prm = reinterpret_cast<RoundParams *>(ws + lay.params);
     launch_set_params(L, prm, hp_prm);
-    if (tu.host_round_loop || io.host_loop) {
-        // one launch per round, the control block read back after each
-        {
-            ProfScope ps(L, "round0");
-            launch_round0(L, r, io.general, prm);
-        }
-        HP_TRY(check_launch("round0"));
+    RoundsArgs ra{n, m, r, io.general, prm, sorted ? &lay.sp : nullptr, sbufs, st, rec, Ll,
+                  loff, ctl, lay.max_rounds};
+    auto read_ctl = [&]() -> hpeel_status {
         HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
         HP_CUDA(cudaStreamSynchronize(L.stream));
+        return HPEEL_OK;
+    };
+    if (tu.host_round_loop || io.host_loop) {
+        // one launch (or, sorted, one short sequence) per round, the control
+        // block read back after each
+        if (sorted) {
+            {
+                ProfScope ps(L, "round0");
+                launch_sorted_round0(L, lay.sp, ra.sw, st, n, m, rec, Ll, loff, ctl,
+                                     lay.max_rounds, 0, 0);
+            }
+            HP_TRY(check_launch("round0"));
+            HP_TRY(read_ctl());
+            while (hctl->more && !hctl->err && hctl->bmode) {
+                {
+                    ProfScope ps(L, "rounds_sorted");
+                    launch_sorted_round(L, lay.sp, ra.sw, st, n, rec, Ll, loff, ctl,
+                                        lay.max_rounds, 0, 0);
+                }
+                HP_TRY(check_launch("sorted round"));
+                HP_TRY(read_ctl());
+            }
+        } else {
+            {
+                ProfScope ps(L, "round0");
+                launch_round0(L, r, io.general, prm);
+            }
+            HP_TRY(check_launch("round0"));
+            HP_TRY(read_ctl());
+        }
         while (hctl->more && !hctl->err) {
             {
                 ProfScope ps(L, "rounds");
                 launch_round(L, r, io.general, prm);
             }
             HP_TRY(check_launch("round"));
-            HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
-            HP_CUDA(cudaStreamSynchronize(L.stream));
+            HP_TRY(read_ctl());
         }
     } else {
-        // round 0 and a CUDA-graph while node around the round kernel: the
-        // rounds run back to back on the device, one read-back at the end
+        // round 0 and the loops of rounds in one CUDA graph: the rounds run
+        // back to back on the device, one read-back at the end
         ProfScope ps(L, "rounds");
-        HP_TRY(launch_round_graph(L, r, io.general, prm));
-        HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, L.stream));
-        HP_CUDA(cudaStreamSynchronize(L.stream));
-        count_launch(hctl->round + (hctl->more ? 1 : 0));
+        HP_TRY(launch_round_graph(L, ra));
+        HP_TRY(read_ctl());
+        count_launch((uint32_t)round_kernels(*hctl, sorted));
+    }
+    if (hctl->err == kDevRoundOverflow && sorted) {
+        // a sorted round's buckets or claim list were full (a skewed input):
+        // redo the peel with every round in random form (same result)
+        PeelIO again = io;
+        again.random_rounds = true;
+        return peel_core_rb(L, again, n, m, r, ws, out, hctl);
     }
     if (hctl->err == kDevBuildOverflow && !io.force_direct) {
         // a skewed input overflowed the incidence buckets: redo the whole
@@ -386,6 +558,7 @@ hpeel_status peel_core_rb(const Launch &L, const PeelIO &io, uint32_t n, uint32_
     out->n_peeled = hctl->lcur;
     out->frontier = hctl->cross;
     out->moves = hctl->moves;
+    out->sorted_rounds = hctl->brounds;
     out->loff = loff;
     out->list = Ll;
 
@@ -492,54 +665,6 @@ hpeel_status side_stream(SideStream **out) {
     return HPEEL_OK;
 }
 
-// Capture streams of this thread (one per nesting depth of the graph).
-cudaStream_t capture_stream(int depth) {
-    thread_local cudaStream_t s[4] = {nullptr, nullptr, nullptr, nullptr};
-    thread_local int dev_of[4] = {-1, -1, -1, -1};
-    int d = 0;
-    cudaGetDevice(&d);
-    if (!s[depth] || dev_of[depth] != d) {
-        if (cudaStreamCreateWithFlags(&s[depth], cudaStreamNonBlocking) != cudaSuccess)
-            return nullptr;
-        dev_of[depth] = d;
-    }
-    return s[depth];
-}
-
-// A condition handle on the graph stream s is capturing into.
-cudaError_t new_handle(cudaStream_t s, unsigned default_value, unsigned flags,
-                       cudaGraphConditionalHandle *h) {
-    cudaStreamCaptureStatus st;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr);
-    if (e != cudaSuccess) return e;
-    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
-    return cudaGraphConditionalHandleCreate(h, g, default_value, flags);
-}
-
-// Append a conditional node at the capture position of s; *body receives its
-// body graph, into which another stream captures.
-cudaError_t append_conditional(cudaStream_t s, cudaGraphConditionalHandle h,
-                               cudaGraphConditionalNodeType type, cudaGraph_t *body) {
-    cudaStreamCaptureStatus st;
-    cudaGraph_t g = nullptr;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t nd = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd);
-    if (e != cudaSuccess) return e;
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = type;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
-    if (e != cudaSuccess) return e;
-    *body = cp.conditional.phGraph_out[0];
-    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
-                                               cudaStreamSetCaptureDependencies);
-}
-
 struct AsyncArgs {
     const uint64_t *keys;
     uint32_t n, m, max_tries;
@@ -561,8 +686,9 @@ struct AsyncArgs {
 // capture position), or null to capture a graph of its own into *out.
 hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGraph_t *out) {
     cudaStream_t s0 = into ? into : capture_stream(0), s1 = capture_stream(1),
-                 s2 = capture_stream(2);
-    if (!s0 || !s1 || !s2) return fail(HPEEL_ERR_CUDA, "capture stream creation failed");
+                 s2 = capture_stream(2), s3 = capture_stream(3);
+    if (!s0 || !s1 || !s2 || !s3) return fail(HPEEL_ERR_CUDA, "capture stream creation failed");
+    LaunchCountPause pause;
     const MphfLayout ml = mphf_layout(a.n, a.gamma_milli);
     char *pw = a.ws + ml.peel;
     const PeelLayout lay = peel_layout(a.n, a.m, 3);
@@ -619,8 +745,8 @@ hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGrap
     open = 1;
     launch_set_params(L0, prm, rp);
     launch_async_init(L0, state, a.seed, a.max_tries, n);
-    cudaGraphConditionalHandle h_out = 0, h_ovf = 0, h_in = 0, h_ok = 0, h_asg = 0;
-    cudaGraph_t b_out = nullptr, b_ovf = nullptr, b_in = nullptr, b_ok = nullptr, b_asg = nullptr;
+    cudaGraphConditionalHandle h_out = 0, h_ovf = 0, h_red = 0, h_ok = 0, h_asg = 0;
+    cudaGraph_t b_out = nullptr, b_ovf = nullptr, b_red = nullptr, b_ok = nullptr, b_asg = nullptr;
     HP_CAP(new_handle(s0, 1u, cudaGraphCondAssignDefault, &h_out));
     HP_CAP(append_conditional(s0, h_out, cudaGraphCondTypeWhile, &b_out));
     {   // one attempt (body of the loop over seeds)
@@ -640,7 +766,11 @@ hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGrap
                 launch_build_bucketed(L1, lay.plan, a.keys, nullptr, n, 3, fm, a.seed, P, rec,
                                       pairs, fill, ov, ctl, false, seed_dev, pass);
                 launch_apply_buckets(L1, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl,
-                                     pass);
+                                     pass,
+                                     lay.sp.enabled
+                                         ? ClaimSink{sorted_bufs(lay, pw).claims,
+                                                     lay.sp.claim_cap, n}
+                                         : ClaimSink{nullptr, 0, 0});
             }
             // an overflowed build is redone with direct updates (same result)
             HP_CAP(new_handle(s1, 0u, 0u, &h_ovf));
@@ -660,23 +790,30 @@ hpeel_status capture_async_build(const AsyncArgs &a, cudaStream_t into, cudaGrap
             launch_hash_records(L1, a.keys, n, 3, fm, a.seed, rec, seed_dev);
             launch_build_incidence(L1, rec, n, 3, m, st, ctl);
         }
-        // round 0, then the while loop of rounds (as launch_round_graph)
-        HP_CAP(new_handle(s1, 0u, 0u, &h_in));
-        {
-            void *args[] = {(void *)&prm, &h_in};
-            count_launch();
-            HP_CAP(cudaLaunchKernel(k0.fn, dim3(k0.grid), dim3(k0.block), args, k0.smem, s1));
-        }
-        HP_CAP(append_conditional(s1, h_in, cudaGraphCondTypeWhile, &b_in));
-        HP_CAP(begin_body(s2, b_in));
-        open = 3;
-        {
-            void *args[] = {(void *)&prm, &h_in};
-            HP_CAP(cudaLaunchKernel(k1.fn, dim3(k1.grid), dim3(k1.block), args, k1.smem, s2));
-        }
+        // round 0, then the loops of rounds (as launch_round_graph)
+        RoundsArgs ra{n, m, 3, false, prm, lay.sp.enabled ? &lay.sp : nullptr,
+                      lay.sp.enabled ? sorted_bufs(lay, pw) : SortedBufs{}, st, rec, Ll, loff,
+                      ctl, lay.max_rounds};
+        HP_CAP(capture_rounds(s1, s2, a.sms, ra));
         cudaGraph_t g = nullptr;
-        HP_CAP(cudaStreamEndCapture(s2, &g));
-        open = 2;
+        if (ra.sp) {
+            // a sorted round whose buckets overflowed (a skewed input): the
+            // attempt's build and rounds are redone in random form
+            HP_CAP(new_handle(s1, 0u, 0u, &h_red));
+            launch_async_check_code(L1, ctl, kDevRoundOverflow, h_red);
+            HP_CAP(append_conditional(s1, h_red, cudaGraphCondTypeIf, &b_red));
+            HP_CAP(begin_body(s2, b_red));
+            open = 3;
+            HP_CAP(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s2));
+            launch_fill_u32(L2, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
+            launch_hash_records(L2, a.keys, n, 3, fm, a.seed, rec, seed_dev);
+            launch_build_incidence(L2, rec, n, 3, m, st, ctl);
+            RoundsArgs rr = ra;
+            rr.sp = nullptr;
+            HP_CAP(capture_rounds(s2, s3, a.sms, rr));
+            HP_CAP(cudaStreamEndCapture(s2, &g));
+            open = 2;
+        }
         launch_async_decide(L1, state, ctl, h_out);
         HP_CAP(cudaStreamEndCapture(s1, &g));
         open = 1;
@@ -747,6 +884,7 @@ hpeel_status capture_async_peel(const AsyncPeelArgs &a, cudaStream_t into, cudaG
     cudaStream_t s0 = into ? into : capture_stream(0), s1 = capture_stream(1),
                  s2 = capture_stream(2);
     if (!s0 || !s1 || !s2) return fail(HPEEL_ERR_CUDA, "capture stream creation failed");
+    LaunchCountPause pause;
     const PeelLayout lay = peel_layout(a.n, a.m, a.r, a.general);
     char *ws = a.ws;
     Ctl *ctl = reinterpret_cast<Ctl *>(ws + lay.ctl);
@@ -804,8 +942,8 @@ hpeel_status capture_async_peel(const AsyncPeelArgs &a, cudaStream_t into, cudaG
     open = 1;
     HP_CAP(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s0));
     launch_set_params(L0, prm, rp);
-    cudaGraphConditionalHandle h_ovf = 0, h_in = 0, h_ok = 0, h_emit = 0;
-    cudaGraph_t b_ovf = nullptr, b_in = nullptr, b_ok = nullptr, b_emit = nullptr;
+    cudaGraphConditionalHandle h_ovf = 0, h_red = 0, h_ok = 0, h_emit = 0;
+    cudaGraph_t b_ovf = nullptr, b_red = nullptr, b_ok = nullptr, b_emit = nullptr;
     if (lay.bucketed) {
         uint2 *pairs = reinterpret_cast<uint2 *>(ws + lay.pairs);
         uint32_t *fill = reinterpret_cast<uint32_t *>(ws + lay.fill);
@@ -818,7 +956,10 @@ hpeel_status capture_async_peel(const AsyncPeelArgs &a, cudaStream_t into, cudaG
             HP_CAP(cudaMemsetAsync(ov.count, 0, 4, s0));
             launch_build_bucketed(L0, lay.plan, nullptr, a.edges, n, r, FastMod{0, 0}, 0, P, rec,
                                   pairs, fill, ov, ctl, a.general, nullptr, pass);
-            launch_apply_buckets(L0, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl, pass);
+            launch_apply_buckets(L0, lay.plan, P, pairs, fill, pairs2, fill2, ov, st, ctl, pass,
+                                 lay.sp.enabled && !a.general
+                                     ? ClaimSink{sorted_bufs(lay, ws).claims, lay.sp.claim_cap, n}
+                                     : ClaimSink{nullptr, 0, 0});
         }
         // an overflowed build is redone with direct updates (same result)
         HP_CAP(new_handle(s0, 0u, 0u, &h_ovf));
@@ -838,21 +979,27 @@ hpeel_status capture_async_peel(const AsyncPeelArgs &a, cudaStream_t into, cudaG
         launch_records(L0, a.edges, n, r, P, rec, ctl, a.general);
         launch_build_incidence(L0, rec, n, r, m, st, ctl);
     }
-    // round 0, then the while loop of rounds (as launch_round_graph)
-    HP_CAP(new_handle(s0, 0u, 0u, &h_in));
-    {
-        void *args[] = {(void *)&prm, &h_in};
-        count_launch();
-        HP_CAP(cudaLaunchKernel(k0.fn, dim3(k0.grid), dim3(k0.block), args, k0.smem, s0));
-    }
-    HP_CAP(append_conditional(s0, h_in, cudaGraphCondTypeWhile, &b_in));
-    HP_CAP(begin_body(s1, b_in));
-    open = 2;
-    {
-        void *args[] = {(void *)&prm, &h_in};
-        HP_CAP(cudaLaunchKernel(k1.fn, dim3(k1.grid), dim3(k1.block), args, k1.smem, s1));
-    }
-    {
+    // round 0, then the loops of rounds (as launch_round_graph)
+    const bool sorted = lay.sp.enabled && !a.general;
+    RoundsArgs ra{n, m, r, a.general, prm, sorted ? &lay.sp : nullptr,
+                  sorted ? sorted_bufs(lay, ws) : SortedBufs{}, st, rec, Ll, loff, ctl,
+                  lay.max_rounds};
+    HP_CAP(capture_rounds(s0, s1, a.sms, ra));
+    if (sorted) {
+        // a sorted round whose buckets overflowed (a skewed input): the build
+        // and the rounds are redone in random form
+        HP_CAP(new_handle(s0, 0u, 0u, &h_red));
+        launch_async_check_code(L0, ctl, kDevRoundOverflow, h_red);
+        HP_CAP(append_conditional(s0, h_red, cudaGraphCondTypeIf, &b_red));
+        HP_CAP(begin_body(s1, b_red));
+        open = 2;
+        HP_CAP(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s1));
+        launch_fill_u32(L1, reinterpret_cast<uint32_t *>(st), 2ull * m, 0u);
+        launch_records(L1, a.edges, n, r, P, rec, ctl, a.general);
+        launch_build_incidence(L1, rec, n, r, m, st, ctl);
+        RoundsArgs rr = ra;
+        rr.sp = nullptr;
+        HP_CAP(capture_rounds(s1, s2, a.sms, rr));
         cudaGraph_t g = nullptr;
         HP_CAP(cudaStreamEndCapture(s1, &g));
         open = 1;
@@ -886,42 +1033,6 @@ hpeel_status capture_async_peel(const AsyncPeelArgs &a, cudaStream_t into, cudaG
     return HPEEL_OK;
 }
 
-// Launch the cached executable graph for key on L.stream, capturing and
-// instantiating it with capture() on first use (least recently used graphs
-// are evicted, after their latest launch has finished).
-template <typename F>
-hpeel_status launch_cached_graph(const Launch &L, const std::string &key, F capture) {
-    std::lock_guard<std::mutex> lk(g_graph_mu);
-    auto it = g_graphs.find(key);
-    if (it == g_graphs.end()) {
-        while (g_graph_lru.size() >= kGraphCache) {
-            auto old = g_graphs.find(g_graph_lru.front());
-            if (old != g_graphs.end()) {
-                destroy_graph(old->second);
-                g_graphs.erase(old);
-            }
-            g_graph_lru.erase(g_graph_lru.begin());
-        }
-        RoundGraph rg;
-        HP_TRY(capture(&rg.graph));
-        if (cudaGraphInstantiate(&rg.exec, rg.graph, 0) != cudaSuccess ||
-            cudaEventCreateWithFlags(&rg.done, cudaEventDisableTiming) != cudaSuccess) {
-            const cudaError_t e = cudaGetLastError();
-            destroy_graph(rg);
-            return fail(HPEEL_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
-        }
-        it = g_graphs.emplace(key, rg).first;
-        g_graph_lru.push_back(key);
-    } else {
-        auto pos = std::find(g_graph_lru.begin(), g_graph_lru.end(), key);
-        if (pos != g_graph_lru.end()) g_graph_lru.erase(pos);
-        g_graph_lru.push_back(key);
-    }
-    HP_CUDA(cudaGraphLaunch(it->second.exec, L.stream));
-    HP_CUDA(cudaEventRecord(it->second.done, L.stream));
-    return HPEEL_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -945,7 +1056,7 @@ const char *hpeel_last_error(void) { return g_last_error.c_str(); }
 
 hpeel_status hpeel_set_tuning(const hpeel_tuning *t) {
     g_last_error.clear();
-    hpeel_tuning v = {22u, 8u << 20, 0u, 0u, 0u, {0, 0, 0}};
+    hpeel_tuning v = {22u, 8u << 20, 0u, 0u, 0u, 0u, {0, 0}};
     if (t) {
         if (t->bucket_shift < 8 || t->bucket_shift > 30)
             return fail(HPEEL_ERR_INVALID_ARG, "bucket_shift %u outside [8, 30]", t->bucket_shift);
@@ -1071,6 +1182,7 @@ hpeel_status peel_entry(bool general, const uint32_t *d_edges, uint64_t n, uint6
         h_stats->first_layer = po.first_layer;
         h_stats->frontier = po.frontier;
         h_stats->hinge_moves = po.moves;
+        h_stats->sorted_rounds = po.sorted_rounds;
     }
     return HPEEL_OK;
 }
@@ -1224,6 +1336,7 @@ hpeel_status hpeel_mphf_build(const uint64_t *d_keys, uint64_t n, uint64_t seed,
             h_stats->first_layer = po.first_layer;
             h_stats->frontier = po.frontier;
         h_stats->hinge_moves = po.moves;
+        h_stats->sorted_rounds = po.sorted_rounds;
         }
         if (po.n_peeled < n) continue;
         // The rounds are complete (the peel read their outcome back), so the
@@ -1377,6 +1490,7 @@ hpeel_status hpeel_sf_build(const uint64_t *d_keys, const uint32_t *d_values, ui
             h_stats->first_layer = po.first_layer;
             h_stats->frontier = po.frontier;
             h_stats->hinge_moves = po.moves;
+        h_stats->sorted_rounds = po.sorted_rounds;
         }
         if (po.n_peeled < n) continue;
         // reverse layer order (sec. 3, sec. 4.3 "Avoiding backward scans")
@@ -1589,6 +1703,7 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
         h_stats->first_layer = po.first_layer;
         h_stats->frontier = po.frontier;
         h_stats->hinge_moves = po.moves;
+        h_stats->sorted_rounds = po.sorted_rounds;
     }
     return HPEEL_OK;
 }

@@ -25,6 +25,12 @@ __global__ void k_async_check_overflow(const Ctl *ctl, cudaGraphConditionalHandl
     cudaGraphSetConditional(h, ctl->err == kDevBuildOverflow ? 1u : 0u);
 }
 
+// 1 when the control block holds error code `code` (an if node redoes what
+// raised it).
+__global__ void k_async_check_code(const Ctl *ctl, uint32_t code, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, ctl->err == code ? 1u : 0u);
+}
+
 // After the round loop: stop on success, on a device error or when the
 // seeds are used up; otherwise take the next seed and loop again.
 __global__ void k_async_decide(AsyncState *s, const Ctl *ctl, cudaGraphConditionalHandle h) {
@@ -74,6 +80,7 @@ __global__ void k_async_stats(const AsyncState *s, const Ctl *ctl, hpeel_stats *
     st.first_layer = ctl->first_layer;
     st.frontier = ctl->cross;
     st.hinge_moves = ctl->moves;
+    st.sorted_rounds = ctl->brounds;
     st.async_status = status;
     *out = st;
 }
@@ -100,6 +107,7 @@ __global__ void k_peel_async_stats(const Ctl *ctl, uint32_t n, uint32_t max_laye
     st.first_layer = ctl->first_layer;
     st.frontier = ctl->cross;
     st.hinge_moves = ctl->moves;
+    st.sorted_rounds = ctl->brounds;
     st.async_status = ctl->err ? 3u : (want_layer_off && st.rounds > max_layers ? 4u : 1u);
     *out = st;
 }
@@ -149,6 +157,11 @@ void launch_async_init(const Launch &L, AsyncState *s, uint64_t seed, uint32_t m
 void launch_async_check_overflow(const Launch &L, const Ctl *ctl, cudaGraphConditionalHandle h) {
     count_launch();
     k_async_check_overflow<<<1, 1, 0, L.stream>>>(ctl, h);
+}
+void launch_async_check_code(const Launch &L, const Ctl *ctl, uint32_t code,
+                             cudaGraphConditionalHandle h) {
+    count_launch();
+    k_async_check_code<<<1, 1, 0, L.stream>>>(ctl, code, h);
 }
 void launch_async_decide(const Launch &L, AsyncState *s, const Ctl *ctl,
                          cudaGraphConditionalHandle h) {

@@ -473,14 +473,7 @@ void launch_batched(const Launch &L, const uint64_t *keys, const uint64_t *off, 
     BatchArgs a{keys, off, B, gamma_milli, sched, next, order, rounds, status, G, G_off,
                 scratch, batched_scratch_bytes(gamma_milli), smem_bytes, smem_rounds,
                 global16_rounds};
-    static uint32_t attr_set[64] = {0};  // largest dynamic shared size set, per device
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && attr_set[dev] < smem_bytes) {
-        cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes);
-        attr_set[dev] = smem_bytes;
-    }
+    smem_optin((const void *)k_batched);
     count_launch();
     k_batched<<<ctas, threads, smem_bytes, L.stream>>>(a);
 }

@@ -32,13 +32,6 @@ namespace hp {
 
 constexpr int kTileEdges = 1024;  // edges per block step (4 per thread)
 
-struct BucketGeom {
-    uint32_t P;                // part size
-    uint32_t shift;            // log2 of the vertices per chunk
-    uint32_t chunks_per_part;
-    uint32_t cap;              // region capacity (incidences per chunk and block)
-};
-
 // Chunk of vertex v at position j: chunks never straddle the parts of an
 // r-partite graph; a general graph (GEN) is one part [0, P = m).
 template <bool GEN>
@@ -51,11 +44,11 @@ __device__ __forceinline__ uint32_t chunk_of(uint32_t v, uint32_t j, const Bucke
 // after everything else; when the list itself is full the build fails with
 // kDevBuildOverflow and the host redoes it with direct updates.
 __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
-    const uint32_t k = atomicAdd(ov.count, 1u);
+    const uint32_t k = ov.count ? atomicAdd(ov.count, 1u) : ov.cap;
     if (k < ov.cap)
         ov.list[k] = p;
     else
-        atomicCAS(&ctl->err, 0u, (uint32_t)kDevBuildOverflow);
+        atomicCAS(&ctl->err, 0u, ov.code);
 }
 
 #ifndef HPEEL_RB_MIN_BLOCKS
@@ -291,6 +284,11 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
         for (int q = 0; q < kRefineItems; q++) {
             const uint32_t i = (uint32_t)q * kThreads + threadIdx.x;
             ok[q] = i < tn;
+            // a pair outside the chunk (inconsistent input) is dropped with an error
+            if (ok[q] && ((p[q].x - base_v) >> sub_shift) >= S) {
+                raise_err(ctl, kDevBadVertex);
+                ok[q] = false;
+            }
             rk[q] = ok[q] ? atomicAdd(&hist[(p[q].x - base_v) >> sub_shift], 1u) : 0u;
         }
         __syncthreads();
@@ -363,11 +361,41 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
 // accumulate in shared memory (two 32-bit atomics per incidence: the record's
 // halves are independent, AddEdge never carries from one into the other),
 // then every vertex record of the range is written once.
+// Exclusive block-wide prefix sum of one value per thread (1024 threads);
+// *total receives the sum.  Every thread calls it.
+__device__ __forceinline__ uint32_t block_scan_1024(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t ws[32];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = ws[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+            if (lane >= (uint32_t)d) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = (warp ? ws[warp - 1] : 0u) + x - v;
+    *total = ws[31];
+    __syncthreads();
+    return before;
+}
+
 __global__ void __launch_bounds__(1024)
 k_apply_smem(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill2, uint32_t cap2,
              BucketGeom g, uint32_t sub_shift, uint32_t chunk0,
-             unsigned long long *__restrict__ st) {
+             unsigned long long *__restrict__ st, ClaimSink sink, Ctl *ctl) {
     extern __shared__ uint32_t smem[];
+    __shared__ uint32_t s_base;
     const uint32_t nv = 1u << sub_shift;
     uint32_t *deg = smem, *sum = smem + nv;
     const uint32_t S = 1u << (g.shift - sub_shift);
@@ -399,8 +427,12 @@ k_apply_smem(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill
         for (int u = 0; u < kU; u++) {
             if (i0 + (uint32_t)u * blockDim.x < cnt) {
                 const uint32_t k = p[u].x - base_v;
-                atomicAdd(deg + k, 1u);
-                atomicAdd(sum + k, p[u].y);
+                if (k < nv) {
+                    atomicAdd(deg + k, 1u);
+                    atomicAdd(sum + k, p[u].y);
+                } else {
+                    raise_err(ctl, kDevBadVertex);
+                }
             }
         }
     }
@@ -408,11 +440,45 @@ k_apply_smem(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill
     const uint32_t lim = min(nv, part_end - base_v);
     for (uint32_t k = threadIdx.x; k < lim; k += blockDim.x)
         st[base_v + k] = (unsigned long long)deg[k] | ((unsigned long long)sum[k] << 32);
+    if (!sink.claims) return;  // block-uniform
+    // round 0's claims (sec. 4.2: F_0), one per vertex of degree 1: each
+    // thread counts its own, one block-wide scan gives every thread its place
+    // in the block's run, and the run is reserved with one atomic
+    uint32_t mine = 0;
+    for (uint32_t k = threadIdx.x; k < lim; k += blockDim.x) {
+        if (deg[k] & kMark) raise_err(ctl, kDevDegree);
+        if (deg[k] == 1u) {
+            if (sum[k] < sink.n)
+                mine++;
+            else
+                raise_err(ctl, kDevBadEdge);
+        }
+    }
+    uint32_t total;
+    uint32_t pos = block_scan_1024(mine, &total);
+    if (threadIdx.x == 0) {
+        const uint32_t q = total ? atomicAdd(&ctl->ccur, total) : 0u;
+        if (total && (q + total > sink.cap || q + total < q)) raise_err(ctl, kDevRoundOverflow);
+        s_base = q;
+    }
+    __syncthreads();
+    pos += s_base;
+    for (uint32_t k = threadIdx.x; k < lim; k += blockDim.x) {
+        if (deg[k] == 1u && sum[k] < sink.n) {
+            if (pos < sink.cap) sink.claims[pos] = make_uint2(sum[k], base_v + k);
+            pos++;
+        }
+    }
 }
 
+// Incidences that found their bucket full, applied last with direct updates;
+// with claims emitted by the apply, the list is complete only when there
+// were none (ctl->cvalid).
 __global__ void k_apply_overflow(const uint2 *__restrict__ list, const uint32_t *__restrict__ count,
-                                 uint32_t cap, unsigned long long *__restrict__ st) {
+                                 uint32_t cap, unsigned long long *__restrict__ st, Ctl *ctl,
+                                 uint32_t emitted) {
     const uint32_t cnt = min(*count, cap);
+    if (emitted && blockIdx.x == 0 && threadIdx.x == 0) ctl->cvalid = *count == 0 ? 1u : 0u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
         const uint2 p = list[i];
         atomicAdd(st + p.x, ((unsigned long long)p.y << 32) | 1ull);
@@ -474,7 +540,7 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
 #define HP_BK(RR, FK)                                                                         \
     do {                                                                                      \
         auto kern = gen ? k_records_bucketed<RR, FK, true> : k_records_bucketed<RR, FK, false>; \
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.smem); \
+        smem_optin((const void *)kern);                                                      \
         count_launch();                                                                       \
         kern<<<grid, kThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, seed_dev, g, rec,  \
                                                    pairs, fill, ov, ctl, pass_part);          \
@@ -495,29 +561,36 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
 #undef HP_BK
 }
 
-void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
-                          const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
-                          unsigned long long *st, Ctl *ctl, uint32_t pass) {
-    BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
-    const uint32_t chunk0 = b.passes > 1 ? pass * b.chunks_per_part : 0u;
-    const uint32_t S = 1u << (b.shift - b.sub_shift);
+void launch_refine(const Launch &L, const BucketGeom &g, uint32_t chunks, uint32_t chunk0,
+                   uint32_t regions, uint32_t sub_shift, const uint2 *pairs, const uint32_t *fill,
+                   uint2 *pairs2, uint32_t *fill2, uint32_t cap2, Overflow ov, Ctl *ctl) {
+    const uint32_t S = 1u << (g.shift - sub_shift);
     const size_t smem1 = ((3 * (size_t)S + kWarps + 1) & ~(size_t)1) * 4 + (size_t)kRefineTile * 8;
-    cudaFuncSetAttribute(k_refine_buckets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
-    const uint64_t items =
-        (uint64_t)b.chunks_pass * b.regions * ((b.cap + kRefineTile - 1) / kRefineTile);
+    smem_optin((const void *)k_refine_buckets);
+    const uint64_t items = (uint64_t)chunks * regions * ((g.cap + kRefineTile - 1) / kRefineTile);
     const unsigned grid = (unsigned)std::min<uint64_t>(
         std::max<uint64_t>(items, 1), grid_resident(L, (const void *)k_refine_buckets, 8, smem1));
     count_launch();
-    k_refine_buckets<<<grid, kThreads, smem1, L.stream>>>(
-        pairs, fill, g, b.chunks_pass, chunk0, b.regions, b.sub_shift, pairs2, fill2, b.cap2, ov,
-        ctl);
+    k_refine_buckets<<<grid, kThreads, smem1, L.stream>>>(pairs, fill, g, chunks, chunk0, regions,
+                                                         sub_shift, pairs2, fill2, cap2, ov, ctl);
+}
+
+void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
+                          const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
+                          unsigned long long *st, Ctl *ctl, uint32_t pass, ClaimSink sink) {
+    if (b.passes > 1) sink.claims = nullptr;  // claims need every part's degrees
+    BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
+    const uint32_t chunk0 = b.passes > 1 ? pass * b.chunks_per_part : 0u;
+    launch_refine(L, g, b.chunks_pass, chunk0, b.regions, b.sub_shift, pairs, fill, pairs2, fill2,
+                  b.cap2, ov, ctl);
     const size_t smem2 = (size_t)8 << b.sub_shift;
-    cudaFuncSetAttribute(k_apply_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    smem_optin((const void *)k_apply_smem);
     count_launch();
     k_apply_smem<<<b.subs_pass, 1024, smem2, L.stream>>>(pairs2, fill2, b.cap2, g, b.sub_shift,
-                                                         chunk0, st);
+                                                         chunk0, st, sink, ctl);
     count_launch();
-    k_apply_overflow<<<grid_fixed(L, 4), kThreads, 0, L.stream>>>(ov.list, ov.count, ov.cap, st);
+    k_apply_overflow<<<grid_fixed(L, 4), kThreads, 0, L.stream>>>(ov.list, ov.count, ov.cap, st,
+                                                                 ctl, sink.claims ? 1u : 0u);
 }
 
 }  // namespace hp

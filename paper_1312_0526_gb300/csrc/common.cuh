@@ -19,6 +19,7 @@ enum : uint32_t {
     kDevBuildOverflow = 5,  // the bucketed build's overflow list was full
     kDevDegree = 6,      // a vertex degree of 2^31 or more (no room for the mark bit)
     kDevBadValue = 7,    // a static-function value outside [0, sigma)
+    kDevRoundOverflow = 8,  // a sorted round's buckets or claim list were full
 };
 
 // Device-side control block of one peel (lives in the workspace).
@@ -32,7 +33,11 @@ struct Ctl {
     uint32_t cross;      // vertices that fell from degree 2 to 1 (all rounds)
     uint32_t first_layer;   // |L_0|
     uint32_t moves;      // list entries whose first claimer was not the hinge
-    uint32_t pad[7];
+    uint32_t ccur;       // append cursor of the claim list of a sorted round
+    uint32_t bmode;      // 1: the next round runs in sorted (bucketed) form
+    uint32_t brounds;    // rounds run in sorted form
+    uint32_t cvalid;     // 1: the incidence build left round 0's claims in the claim list
+    uint32_t pad[3];
 };
 
 // State of a device-driven build (graph-resident reseed-and-retry).

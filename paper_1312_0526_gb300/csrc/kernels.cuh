@@ -23,6 +23,11 @@ struct Launch {
 // Instrumentation (prof.cu): every kernel launch is counted; when profiling
 // is on, a ProfScope brackets a step with CUDA events on its stream.
 void count_launch(uint32_t kernels = 1);
+// While one lives on this thread, launches are not counted (graph capture).
+struct LaunchCountPause {
+    LaunchCountPause();
+    ~LaunchCountPause();
+};
 struct ProfScope {
     ProfScope(const Launch &L, const char *name);
     ~ProfScope();
@@ -31,6 +36,12 @@ struct ProfScope {
     void *a;
 };
 void prof_flush();  // after a stream synchronisation: accumulate timings
+
+// Let fn take up to the device's opt-in maximum of dynamic shared memory.
+// Set once per (device, kernel) under a lock and never lowered: the limit is
+// process-wide state, and a per-launch value that another host thread lowers
+// in between would make that thread's launch fail.
+void smem_optin(const void *fn);
 
 // Persistent grid size for grid-stride kernels over device-sized ranges.
 inline unsigned grid_fixed(const Launch &L, int per_sm) { return (unsigned)(L.sms * per_sm); }
@@ -97,11 +108,22 @@ struct BucketPlan {
     uint32_t chunks_pass;      // chunks of one pass
     uint32_t subs_pass;        // sub-buckets of one pass
 };
-// Incidences that found their bucket full (applied last).
+// Incidences that found their bucket full (applied last).  Without a list
+// (count == nullptr) a full bucket raises code instead.
 struct Overflow {
     uint2 *list;
     uint32_t *count;
     uint32_t cap;
+    uint32_t code = kDevBuildOverflow;
+};
+
+// Geometry of one bucketing: part size, log2 of the keys per chunk, chunks
+// per part, region capacity.
+struct BucketGeom {
+    uint32_t P;                // part size
+    uint32_t shift;            // log2 of the vertices per chunk
+    uint32_t chunks_per_part;
+    uint32_t cap;              // region capacity (incidences per chunk and block)
 };
 // parts: r for an r-partite graph (chunks never straddle parts), 1 for a
 // general graph (one part [0, m)).
@@ -115,11 +137,66 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
                            uint64_t seed, uint32_t P, uint4 *rec, uint2 *pairs, uint32_t *fill,
                            Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev,
                            uint32_t pass);
+// Refine only: the pairs of `chunks` chunks (from chunk0) counting-sorted
+// into sub-buckets of 2^sub_shift keys (pair.x is the key); fill2 zeroed
+// before.
+void launch_refine(const Launch &L, const BucketGeom &g, uint32_t chunks, uint32_t chunk0,
+                   uint32_t regions, uint32_t sub_shift, const uint2 *pairs, const uint32_t *fill,
+                   uint2 *pairs2, uint32_t *fill2, uint32_t cap2, Overflow ov, Ctl *ctl);
+// Round 0's claims emitted by the incidence build itself (the shared-memory
+// apply sees every final degree): claims == nullptr for none.
+struct ClaimSink {
+    uint2 *claims;
+    uint32_t cap;
+    uint32_t n;
+};
 // Refine and apply of the same pass (fill2 and the overflow count zeroed
-// before the pass's bucketing).
+// before the pass's bucketing).  With a sink, every vertex of degree 1 appends
+// its claim {edge, vertex} (ctl->cvalid tells round 0 whether the list is
+// complete: not when overflowed incidences were applied afterwards).
 void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
                           const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
-                          unsigned long long *st, Ctl *ctl, uint32_t pass);
+                          unsigned long long *st, Ctl *ctl, uint32_t pass,
+                          ClaimSink sink = ClaimSink{nullptr, 0, 0});
+
+// Rounds in sorted form (rounds_bucketed.cu): the plan of a peel and the
+// buffers it uses in the workspace.
+struct SortedPlan {
+    bool enabled;
+    uint32_t min_edges, max_edges;  // layers deleted in sorted form
+    uint32_t claim_cap;             // claims one round may make
+    uint32_t regions;               // blocks of the bucketing pass
+    BucketGeom vg;                  // updates by vertex (parts, chunks)
+    uint32_t vchunks, vsub_shift, vsubs, vcap2;
+    BucketGeom eg;                  // claims by edge (one part of n edges)
+    uint32_t eshift, esub, echunks, esubs, ecap2;
+    size_t bucket_smem;
+    uint64_t pairs_bytes, fill_bytes, pairs2_bytes, fill2_bytes, claims_bytes;
+};
+struct SortedBufs {
+    uint2 *pairs;
+    uint32_t *fill;
+    uint2 *pairs2;
+    uint32_t *fill2;
+    uint2 *claims;
+};
+// min_edges: 0 automatic (n / 24), 0xFFFFFFFF never; b: the incidence
+// build's bucket plan (its vertex chunks are reused).
+SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, uint32_t min_edges,
+                       int sms);
+// Round 0 (claims of the degree-1 vertices, L_0 listed) and one sorted round
+// t = ctl->round (layer t deleted, layer t+1 claimed and listed); each ends
+// by closing the round and setting the conditions (h_sorted: the next round
+// is sorted; h_random: a round follows).
+void launch_sorted_round0(const Launch &L, const SortedPlan &p, const SortedBufs &w,
+                          const unsigned long long *st, uint32_t n, uint32_t m, uint4 *rec,
+                          uint4 *Lst, uint32_t *loff, Ctl *ctl, uint32_t max_rounds,
+                          cudaGraphConditionalHandle h_sorted,
+                          cudaGraphConditionalHandle h_random);
+void launch_sorted_round(const Launch &L, const SortedPlan &p, const SortedBufs &w,
+                         unsigned long long *st, uint32_t n, uint4 *rec, uint4 *Lst,
+                         uint32_t *loff, Ctl *ctl, uint32_t max_rounds,
+                         cudaGraphConditionalHandle h_sorted, cudaGraphConditionalHandle h_random);
 
 // A kernel of the round loop and its launch shape, for graph nodes.
 struct RoundLaunch {
@@ -217,6 +294,8 @@ void launch_async_empty(const Launch &L, hpeel_stats *out, uint64_t seed, uint64
 void launch_async_init(const Launch &L, AsyncState *s, uint64_t seed, uint32_t max_tries,
                        uint32_t n);
 void launch_async_check_overflow(const Launch &L, const Ctl *ctl, cudaGraphConditionalHandle h);
+void launch_async_check_code(const Launch &L, const Ctl *ctl, uint32_t code,
+                             cudaGraphConditionalHandle h);
 void launch_async_decide(const Launch &L, AsyncState *s, const Ctl *ctl,
                          cudaGraphConditionalHandle h);
 void launch_async_if_peeled(const Launch &L, const AsyncState *s, cudaGraphConditionalHandle h);

@@ -237,15 +237,7 @@ inline RoundLaunch staged_launch(const Launch &L, void *fn, unsigned stage_bytes
     k.fn = fn;
     k.block = kThreads;
     k.smem = (kThreads / 32) * stage_bytes;
-    if (k.smem > (48u << 10)) {
-        static std::mutex mu;
-        static std::set<std::pair<int, void *>> done;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        std::lock_guard<std::mutex> lk(mu);
-        if (done.insert({dev, fn}).second)
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
-    }
+    if (k.smem > (48u << 10)) smem_optin(fn);
     k.grid = grid_resident(L, fn, 8, k.smem);
     return k;
 }

@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "kernels.cuh"
@@ -47,7 +48,40 @@ cudaEvent_t get_event() {
 }
 }  // namespace
 
-void count_launch(uint32_t kernels) { g_launches.fetch_add(kernels, std::memory_order_relaxed); }
+// Launches recorded into a CUDA graph while it is captured are counted when
+// the graph runs, not at capture time.
+thread_local int t_count_pause = 0;
+LaunchCountPause::LaunchCountPause() { t_count_pause++; }
+LaunchCountPause::~LaunchCountPause() { t_count_pause--; }
+
+void smem_optin(const void *fn) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, bool> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, fn})) return;
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    // the kernel's static shared memory counts against the same limit
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) optin -= (int)fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) ==
+        cudaSuccess)
+        done[{dev, fn}] = true;
+    cudaGetLastError();
+}
+
+void count_launch(uint32_t kernels) {
+    if (t_count_pause == 0) g_launches.fetch_add(kernels, std::memory_order_relaxed);
+}
 
 ProfScope::ProfScope(const Launch &L_, const char *name_) : L(L_), name(name_), a(nullptr) {
     if (!g_enabled.load(std::memory_order_relaxed)) return;
