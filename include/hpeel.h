@@ -370,6 +370,47 @@ hpeel_status hpeel_mphf_build_async(const uint64_t *d_keys, uint64_t n, uint64_t
                                     size_t ws_bytes, void *stream);
 
 /*
+ * MWHC MPHF build for key sets beyond 32-bit ids (sec. 3 and 4.2; sec. 5
+ * builds 7.6e9 keys): the same function as hpeel_mphf_build -- the same
+ * hashing, peel, hinges, g values and rank directory, bit for bit, for any n
+ * both accept -- with 64-bit edge and vertex ids.  n may reach the size at
+ * which a part of m / 3 vertices still has 32-bit local ids (about 1.05e10
+ * keys at gamma = 1.23).  The state is compact: 8 bytes per vertex, 4 per
+ * key of claim words, 8 per key of layer list; no edge is stored (an edge's
+ * vertices are hashed again from its key when needed), so the keys must stay
+ * readable by the device during the call.  No canonical order output.
+ *   d_keys     [n] uint64 distinct keys in device memory (pinned host memory
+ *              works but is read at random addresses over the host link).
+ *   d_G        [ceil(m/32)] uint64 output, layout as hpeel_mphf_build's.
+ *   d_rank_dir [ceil(m/512) + 1] uint64 output, as hpeel_mphf_build's.
+ *   h_list     NULL (the layer list lives in the workspace), or n uint64
+ *              entries of page-locked host memory (cudaHostAlloc,
+ *              cudaMallocHost, cudaHostRegister): the kernels append the
+ *              layers there and read them back as streams over the host
+ *              link, which takes 8 bytes per key out of device memory.
+ *   d_ws       hpeel_mphf_large_workspace_size(n, gamma_milli, h_list != NULL)
+ *              bytes, 256-byte aligned.
+ *   seed, gamma_milli, max_tries, h_stats: as hpeel_mphf_build (retries with
+ *   seed + 1, ...; h_stats->seed_used is the seed lookups must use).
+ * Synchronises stream.  Errors: HPEEL_ERR_INVALID_ARG (m / 3 >= 2^32, h_list
+ * not page-locked), HPEEL_ERR_WORKSPACE_TOO_SMALL, HPEEL_ERR_RETRIES_EXHAUSTED,
+ * HPEEL_ERR_CAPACITY (more than HPEEL_MAX_ROUNDS rounds, or a vertex of degree
+ * 2^24 or more), HPEEL_ERR_DEVICE_CHECK, HPEEL_ERR_CUDA.
+ */
+size_t hpeel_mphf_large_workspace_size(uint64_t n, uint32_t gamma_milli, int list_on_host);
+hpeel_status hpeel_mphf_build_large(const uint64_t *d_keys, uint64_t n, uint64_t seed,
+                                    uint32_t gamma_milli, uint32_t max_tries, uint64_t *d_G,
+                                    uint64_t *d_rank_dir, hpeel_stats *h_stats, void *d_ws,
+                                    size_t ws_bytes, uint64_t *h_list, void *stream);
+/* Lookup of the function hpeel_mphf_build_large built: as hpeel_mphf_lookup
+ * with 64-bit results (the MPHF value of a key of the set, in [0, n)); m =
+ * hpeel_num_vertices(n, gamma_milli, 3).  Asynchronous.  Errors:
+ * HPEEL_ERR_INVALID_ARG, HPEEL_ERR_CUDA. */
+hpeel_status hpeel_mphf_lookup_large(const uint64_t *d_keys, uint64_t nq, uint64_t seed,
+                                     uint64_t m, const uint64_t *d_G, const uint64_t *d_rank_dir,
+                                     uint64_t *d_out, void *stream);
+
+/*
  * MPHF lookup (sec. 3; sec. 5 broadword rank): for each query key, hash it
  * with the build's seed into v_0, v_1, v_2 (as hpeel_hash_edges with r = 3),
  * take i = (g[v_0] + g[v_1] + g[v_2]) mod 3 (a stored 3 is 0) and return the

@@ -131,6 +131,13 @@ def lib():
         L.hpeel_peel_general.restype = st
         L.hpeel_peel_general.argtypes = [p, u64, u64, u32, p, p, p, u32, ctypes.POINTER(Stats),
                                          p, sz, p]
+        L.hpeel_mphf_large_workspace_size.restype = sz
+        L.hpeel_mphf_large_workspace_size.argtypes = [u64, u32, ctypes.c_int]
+        L.hpeel_mphf_build_large.restype = st
+        L.hpeel_mphf_build_large.argtypes = [p, u64, u64, u32, u32, p, p, ctypes.POINTER(Stats),
+                                             p, sz, p, p]
+        L.hpeel_mphf_lookup_large.restype = st
+        L.hpeel_mphf_lookup_large.argtypes = [p, u64, u64, u64, p, p, p, p]
         L.hpeel_peel_async.restype = st
         L.hpeel_peel_async.argtypes = [p, u64, u64, u32, p, p, p, u32, p, p, sz, p]
         L.hpeel_peel_general_async.restype = st
@@ -479,6 +486,55 @@ def mphf_build(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
     res = MphfResult(G[:(m + 31) // 32], rank_dir, m, st.as_dict())
     res.order = order
     return res
+
+
+def mphf_large_workspace_size(n: int, gamma_milli: int = 1230, list_on_host: bool = False) -> int:
+    return int(lib().hpeel_mphf_large_workspace_size(n, gamma_milli, 1 if list_on_host else 0))
+
+
+def mphf_build_large(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,
+                     workspace=None, G=None, rank_dir=None, host_list=None) -> MphfResult:
+    """MPHF build beyond 32-bit ids (hpeel_mphf_build_large): the function of
+    mphf_build, for key sets up to about 1e10 keys.  host_list: None, or a
+    pinned host int64 tensor of n entries that holds the layer list."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1, host_ok=True)
+    n = keys.shape[0]
+    dev = keys.device if keys.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    m = num_vertices(n, gamma_milli, 3)
+    if G is None:
+        G = torch.empty(max((m + 31) // 32, 1), dtype=torch.int64, device=dev)
+    if rank_dir is None:
+        rank_dir = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device=dev)
+    hp_list = None
+    if host_list is not None:
+        if not (isinstance(host_list, torch.Tensor) and host_list.is_pinned()
+                and host_list.dtype == torch.int64 and host_list.numel() >= n):
+            raise ValueError("host_list must be a pinned int64 host tensor of n entries")
+        hp_list = ctypes.c_void_p(host_list.data_ptr())
+    ws = workspace if workspace is not None else _workspace(
+        mphf_large_workspace_size(n, gamma_milli, host_list is not None), dev)
+    st = Stats()
+    _check(lib().hpeel_mphf_build_large(kp, n, seed, gamma_milli, max_tries,
+                                        _dev_ptr(G, "G", torch.int64),
+                                        _dev_ptr(rank_dir, "rank_dir", torch.int64),
+                                        ctypes.byref(st), _dev_ptr(ws, "workspace", torch.uint8),
+                                        ws.numel(), hp_list, _stream()))
+    return MphfResult(G[:(m + 31) // 32], rank_dir, m, st.as_dict())
+
+
+def mphf_lookup_large(keys, seed: int, m: int, G, rank_dir, out=None):
+    """MPHF values of the query keys for a function mphf_build_large built:
+    int64 [nq]."""
+    torch = _torch()
+    kp = _dev_ptr(keys, "keys", torch.int64, 1)
+    if out is None:
+        out = torch.empty(keys.shape[0], dtype=torch.int64, device=keys.device)
+    _check(lib().hpeel_mphf_lookup_large(kp, keys.shape[0], seed, m,
+                                         _dev_ptr(G, "G", torch.int64),
+                                         _dev_ptr(rank_dir, "rank_dir", torch.int64),
+                                         _dev_ptr(out, "out", torch.int64), _stream()))
+    return out
 
 
 def mphf_build_async(keys, seed: int = 1, gamma_milli: int = 1230, max_tries: int = 8,

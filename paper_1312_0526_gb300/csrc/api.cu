@@ -1707,3 +1707,246 @@ extern "C" hpeel_status hpeel_peel_noalloc(const uint32_t *d_edges, uint64_t n, 
     }
     return HPEEL_OK;
 }
+
+// ---------------------------------------------------------------------------
+// MPHF build beyond 32-bit ids (large.cu): the paper's 7.6e9-key instance and
+// larger, with the layer list optionally in pinned host memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t kLargeRankSeg = 4096;  // as large.cu
+
+struct LargeLayout {
+    size_t ctl, params, st, claim, L, loff, cnt, seg, total;
+    uint64_t m, blocks, nseg;
+    uint32_t max_rounds;
+};
+
+LargeLayout large_layout(uint64_t n, uint32_t gamma_milli, bool list_on_host) {
+    LargeLayout p{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    p.m = hpeel_num_vertices(n, gamma_milli, 3);
+    p.max_rounds = (uint32_t)std::min<uint64_t>(HPEEL_MAX_ROUNDS, n + 1);
+    p.blocks = (p.m + 511) / 512;
+    p.nseg = (p.blocks + kLargeRankSeg - 1) / kLargeRankSeg;
+    p.ctl = take(sizeof(LargeCtl));
+    p.params = take(sizeof(LargeParams));
+    p.st = take(8 * p.m);
+    p.claim = take(4 * n);
+    p.L = take(list_on_host ? 0 : 8 * n);
+    p.loff = take(8 * ((size_t)p.max_rounds + 3));
+    p.cnt = take(4 * p.blocks + 4);
+    p.seg = take(8 * (p.nseg + 1));
+    p.total = off;
+    return p;
+}
+
+// Round 0 and the while node over the round kernel (the kernels' last
+// blocks set its condition), captured at the capture position of s0.
+cudaError_t capture_large_rounds(cudaStream_t s0, cudaStream_t s1, int sms,
+                                 const LargeParams *prm) {
+    Launch L0{s0, sms};
+    const RoundLaunch k0 = large_round_launch(L0, true), k1 = large_round_launch(L0, false);
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = new_handle(s0, 0u, 0u, &h);
+    if (e != cudaSuccess) return e;
+    {
+        void *args[] = {(void *)&prm, &h};
+        e = cudaLaunchKernel(k0.fn, dim3(k0.grid), dim3(k0.block), args, 0, s0);
+        if (e != cudaSuccess) return e;
+    }
+    cudaGraph_t body = nullptr, g = nullptr;
+    e = append_conditional(s0, h, cudaGraphCondTypeWhile, &body);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    {
+        void *args[] = {(void *)&prm, &h};
+        e = cudaLaunchKernel(k1.fn, dim3(k1.grid), dim3(k1.block), args, 0, s1);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(s1, &g);
+    return e != cudaSuccess ? e : e2;
+}
+
+LargeCtl *pinned_large_ctl() {
+    thread_local LargeCtl *p = nullptr;
+    if (!p && cudaMallocHost((void **)&p, sizeof(LargeCtl)) != cudaSuccess) p = nullptr;
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t hpeel_mphf_large_workspace_size(uint64_t n, uint32_t gamma_milli, int list_on_host) {
+    return large_layout(n, gamma_milli ? gamma_milli : 1230, list_on_host != 0).total;
+}
+
+hpeel_status hpeel_mphf_build_large(const uint64_t *d_keys, uint64_t n, uint64_t seed,
+                                    uint32_t gamma_milli, uint32_t max_tries, uint64_t *d_G,
+                                    uint64_t *d_rank_dir, hpeel_stats *h_stats, void *d_ws,
+                                    size_t ws_bytes, uint64_t *h_list, void *stream) {
+    g_last_error.clear();
+    if (h_stats) memset(h_stats, 0, sizeof *h_stats);
+    if (gamma_milli == 0) return fail(HPEEL_ERR_INVALID_ARG, "gamma_milli must be positive");
+    if (max_tries == 0) return fail(HPEEL_ERR_INVALID_ARG, "max_tries must be positive");
+    const LargeLayout lay = large_layout(n, gamma_milli, h_list != nullptr);
+    const uint64_t m = lay.m, P = m / 3;
+    if (P >= (1ull << 32) || n >= (1ull << 40))
+        return fail(HPEEL_ERR_INVALID_ARG,
+                    "n = %llu: a part of m / 3 vertices needs ids below 2^32",
+                    (unsigned long long)n);
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    if (n == 0) {
+        if (d_rank_dir) HP_CUDA(cudaMemsetAsync(d_rank_dir, 0, sizeof(uint64_t), L.stream));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        if (h_stats) h_stats->seed_used = seed;
+        return HPEEL_OK;
+    }
+    if (!d_keys || !d_G || !d_rank_dir || !d_ws) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_ws & 255u) != 0)
+        return fail(HPEEL_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < lay.total)
+        return fail(HPEEL_ERR_WORKSPACE_TOO_SMALL, "workspace %zu < %zu bytes", ws_bytes,
+                    lay.total);
+    if (h_list) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, h_list) != cudaSuccess ||
+            pa.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return fail(HPEEL_ERR_INVALID_ARG,
+                        "h_list must be page-locked host memory (cudaHostAlloc, "
+                        "cudaMallocHost or cudaHostRegister)");
+        }
+    }
+    LargeCtl *hctl = pinned_large_ctl();
+    if (!hctl) return fail(HPEEL_ERR_CUDA, "cudaMallocHost of the control read-back failed");
+    char *ws = (char *)d_ws;
+    LargeCtl *ctl = reinterpret_cast<LargeCtl *>(ws + lay.ctl);
+    LargeParams *prm = reinterpret_cast<LargeParams *>(ws + lay.params);
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(ws + lay.st);
+    uint32_t *claim = reinterpret_cast<uint32_t *>(ws + lay.claim);
+    unsigned long long *Ll =
+        h_list ? reinterpret_cast<unsigned long long *>(h_list)
+               : reinterpret_cast<unsigned long long *>(ws + lay.L);
+    unsigned long long *loff = reinterpret_cast<unsigned long long *>(ws + lay.loff);
+    const FastMod fm = make_fastmod(P);
+    const hpeel_tuning tu = tuning();
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    for (uint32_t a = 0; a < max_tries; a++) {
+        const uint64_t s = seed + a;
+        HP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(LargeCtl), L.stream));
+        {
+            ProfScope ps(L, "large_build");
+            launch_fill_u32(L, reinterpret_cast<uint32_t *>(st), 2 * m, 0u);
+            launch_large_build(L, d_keys, n, s, fm, st, claim, ctl);
+        }
+        LargeParams lp{st, claim, Ll, loff, ctl, d_keys, n, m, s, fm, lay.max_rounds};
+        launch_large_set_params(L, prm, lp);
+        HP_TRY(check_launch("large build"));
+        {
+            ProfScope ps(L, "large_rounds");
+            if (tu.host_round_loop) {
+                const RoundLaunch k0 = large_round_launch(L, true), k1 = large_round_launch(L, false);
+                cudaGraphConditionalHandle c0 = 0;
+                void *args[] = {(void *)&prm, &c0};
+                count_launch();
+                HP_CUDA(cudaLaunchKernel(k0.fn, dim3(k0.grid), dim3(k0.block), args, 0, L.stream));
+                HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(LargeCtl), cudaMemcpyDeviceToHost, L.stream));
+                HP_CUDA(cudaStreamSynchronize(L.stream));
+                while (hctl->more && !hctl->err) {
+                    count_launch();
+                    HP_CUDA(cudaLaunchKernel(k1.fn, dim3(k1.grid), dim3(k1.block), args, 0,
+                                             L.stream));
+                    HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(LargeCtl), cudaMemcpyDeviceToHost,
+                                            L.stream));
+                    HP_CUDA(cudaStreamSynchronize(L.stream));
+                }
+            } else {
+                char keybuf[160];
+                snprintf(keybuf, sizeof keybuf, "large|%d|%p|%d", dev, (const void *)prm, L.sms);
+                HP_TRY(launch_cached_graph(L, std::string(keybuf), [&](cudaGraph_t *g) -> hpeel_status {
+                    cudaStream_t s0 = capture_stream(0), s1 = capture_stream(1);
+                    if (!s0 || !s1) return fail(HPEEL_ERR_CUDA, "capture stream creation failed");
+                    LaunchCountPause pause;
+                    cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed);
+                    if (e == cudaSuccess) {
+                        e = capture_large_rounds(s0, s1, L.sms, prm);
+                        cudaGraph_t got = nullptr;
+                        const cudaError_t e2 = cudaStreamEndCapture(s0, &got);
+                        if (e == cudaSuccess) e = e2;
+                        if (e == cudaSuccess) {
+                            *g = got;
+                            return HPEEL_OK;
+                        }
+                        if (got) cudaGraphDestroy(got);
+                    }
+                    cudaGetLastError();
+                    return fail(HPEEL_ERR_CUDA, "large round graph: %s", cudaGetErrorString(e));
+                }));
+                HP_CUDA(cudaMemcpyAsync(hctl, ctl, sizeof(LargeCtl), cudaMemcpyDeviceToHost, L.stream));
+                HP_CUDA(cudaStreamSynchronize(L.stream));
+                count_launch(1 + hctl->round + (hctl->more ? 1 : 0));
+            }
+        }
+        if (hctl->err == kDevCapacity)
+            return fail(HPEEL_ERR_CAPACITY, "more than %u rounds", lay.max_rounds - 1);
+        if (hctl->err == kDevDegree)
+            return fail(HPEEL_ERR_CAPACITY, "a vertex has degree 2^24 or more");
+        if (hctl->err)
+            return fail(HPEEL_ERR_DEVICE_CHECK, "device check failed with code %u", hctl->err);
+        const uint32_t R = hctl->more ? hctl->round + 1 : hctl->round;
+        if (h_stats) {
+            h_stats->attempts = a + 1;
+            h_stats->rounds = R;
+            h_stats->n_peeled = hctl->lcur;
+            h_stats->core_nonempty = hctl->lcur < n;
+            h_stats->first_layer = hctl->first_layer;
+            h_stats->frontier = hctl->cross;
+        }
+        if (hctl->lcur < n) continue;
+        // a8: reverse layer order; a9: rank directory (64-bit counts)
+        {
+            ProfScope ps(L, "large_assign");
+            HP_CUDA(cudaMemsetAsync(d_G, 0, 8 * ((m + 31) / 32), L.stream));
+            for (int64_t t = (int64_t)R - 1; t >= 0; t--) launch_large_assign(L, prm, (uint32_t)t, d_G);
+        }
+        {
+            ProfScope ps(L, "large_rank");
+            launch_large_rank(L, d_G, m, reinterpret_cast<uint32_t *>(ws + lay.cnt),
+                              reinterpret_cast<unsigned long long *>(ws + lay.seg), d_rank_dir);
+        }
+        HP_TRY(check_launch("large assign"));
+        HP_CUDA(cudaStreamSynchronize(L.stream));
+        prof_flush();
+        if (h_stats) h_stats->seed_used = s;
+        return HPEEL_OK;
+    }
+    return fail(HPEEL_ERR_RETRIES_EXHAUSTED, "2-core non-empty for seeds %llu..%llu",
+                (unsigned long long)seed, (unsigned long long)(seed + max_tries - 1));
+}
+
+hpeel_status hpeel_mphf_lookup_large(const uint64_t *d_keys, uint64_t nq, uint64_t seed,
+                                     uint64_t m, const uint64_t *d_G, const uint64_t *d_rank_dir,
+                                     uint64_t *d_out, void *stream) {
+    g_last_error.clear();
+    if (nq == 0) return HPEEL_OK;
+    if (m < 3 || m % 3 != 0 || m / 3 >= (1ull << 32))
+        return fail(HPEEL_ERR_INVALID_ARG, "m = %llu must be a positive multiple of 3 with "
+                    "m / 3 below 2^32", (unsigned long long)m);
+    if (!d_keys || !d_G || !d_rank_dir || !d_out) return fail(HPEEL_ERR_INVALID_ARG, "NULL pointer");
+    Launch L;
+    HP_TRY(make_launch(stream, &L));
+    ProfScope ps(L, "large_lookup");
+    launch_large_lookup(L, d_keys, nq, make_fastmod(m / 3), seed, d_G, d_rank_dir, d_out);
+    return check_launch("large_lookup");
+}
+
+}  // extern "C"

@@ -104,6 +104,27 @@ __device__ __forceinline__ uint64_t fastmod(uint64_t x, const FastMod f) {
     return r;
 }
 
+// Control block and parameters of the large-n MPHF build (large.cu): 64-bit
+// edge and vertex ids, 64-bit list cursors.
+struct LargeCtl {
+    unsigned long long lcur;         // append cursor of the layer list
+    unsigned long long cross;        // vertices that fell from degree 2 to 1
+    unsigned long long first_layer;  // |L_0|
+    uint32_t round, done, err, more;
+    uint32_t pad[8];
+};
+struct LargeParams {
+    unsigned long long *st;    // vertex records [m]
+    uint32_t *claim;           // claim words [n]
+    unsigned long long *L;     // layer list [n] (device or pinned host memory)
+    unsigned long long *loff;  // layer starts
+    LargeCtl *ctl;
+    const uint64_t *keys;
+    uint64_t n, m, seed;
+    FastMod fm;                // part size P = m / 3
+    uint32_t max_rounds;
+};
+
 // Position (part index) of vertex v in an r-partite graph with part size P:
 // the number of part boundaries at or below v.
 template <int R>

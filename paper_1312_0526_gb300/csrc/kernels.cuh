@@ -250,6 +250,17 @@ void launch_emit_advance(const Launch &L, EmitState *es, const uint32_t *loff, u
 void launch_layer_off_dev(const Launch &L, const uint32_t *loff, const Ctl *ctl,
                           uint32_t max_layers, uint64_t *out);
 
+// f4: MPHF build beyond 32-bit ids (large.cu).
+RoundLaunch large_round_launch(const Launch &L, bool first);
+void launch_large_set_params(const Launch &L, LargeParams *dst, const LargeParams &v);
+void launch_large_build(const Launch &L, const uint64_t *keys, uint64_t n, uint64_t seed,
+                        FastMod fm, unsigned long long *st, uint32_t *claim, LargeCtl *ctl);
+void launch_large_assign(const Launch &L, const LargeParams *prm, uint32_t t, uint64_t *G);
+void launch_large_rank(const Launch &L, const uint64_t *G, uint64_t m, uint32_t *cnt,
+                       unsigned long long *seg, uint64_t *dir);
+void launch_large_lookup(const Launch &L, const uint64_t *keys, uint64_t nq, FastMod fm,
+                         uint64_t seed, const uint64_t *G, const uint64_t *dir, uint64_t *out);
+
 // a10: batched bucket peel (batched.cu).
 size_t batched_scratch_bytes(uint32_t gamma_milli);
 uint32_t batched_max_gamma_milli();

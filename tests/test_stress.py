@@ -188,3 +188,56 @@ def test_batched_full_size_parity(name):
     assert _batched_digests(res) == want
     del dk, do, ws, res, graph
     torch.cuda.empty_cache()
+
+
+def test_large_path_matches_the_1e9_digests():
+    # the MPHF build beyond 32-bit ids, on the n = 1e9 workload: g values and
+    # rank directory equal the oracle's (its digests), the layer list once in
+    # device memory and once in pinned host memory
+    c = CASES.get("n1e9_g1230_r3")
+    if c is None or "G_sha256" not in c:
+        pytest.skip("no digests")
+    n, g = c["n"], c["gamma_milli"]
+    torch.cuda.empty_cache()
+    keys = inputs.keys_torch(n, c["key_seed"])
+    for on_host in (False, True):
+        hl = torch.empty(n, dtype=torch.int64, pin_memory=True) if on_host else None
+        got = hp.mphf_build_large(keys, seed=c["hash_seed"], gamma_milli=g, host_list=hl)
+        assert got.stats["seed_used"] == c["hash_seed"] and got.stats["rounds"] == c["rounds"]
+        assert _digest_dev(got.G) == c["G_sha256"]
+        assert _digest_dev(got.rank_dir) == c["rank_dir_sha256"]
+        del got, hl
+        torch.cuda.empty_cache()
+    del keys
+    torch.cuda.empty_cache()
+
+
+def test_large_path_5e9_keys_layer_list_on_host():
+    # beyond the 32-bit ids: n = 5e9 keys (m = 6.15e9 vertices), the layer
+    # list in pinned host memory.  No oracle output exists at this size: every
+    # key must peel and the lookups of all keys must be a bijection onto [0, n)
+    n = 5_000_000_000
+    m = hp.num_vertices(n)
+    free, total = torch.cuda.mem_get_info()
+    need = 8 * n + hp.mphf_large_workspace_size(n, 1230, True) + m // 4 + n + (8 << 30)
+    if free < need:
+        pytest.skip(f"needs {need / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free")
+    torch.cuda.empty_cache()
+    keys = inputs.keys_torch(n, 23)
+    hl = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    got = hp.mphf_build_large(keys, seed=1, max_tries=4, host_list=hl)
+    del hl
+    assert got.stats["n_peeled"] == n and got.stats["core_nonempty"] == 0
+    flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    step = 1 << 28
+    out = torch.empty(step, dtype=torch.int64, device="cuda")
+    for a in range(0, n, step):
+        b = min(n, a + step)
+        hp.mphf_lookup_large(keys[a:b], got.stats["seed_used"], m, got.G, got.rank_dir,
+                             out=out[:b - a])
+        idx = out[:b - a]
+        assert bool(((idx >= 0) & (idx < n)).all())  # checked before it indexes anything
+        flags.index_fill_(0, idx, 1)
+    assert int(flags.sum(dtype=torch.int64)) == n
+    del keys, flags, out, got
+    torch.cuda.empty_cache()
