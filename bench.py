@@ -50,7 +50,8 @@ UNIT = "Medges/s"
 CPU_SAMPLE_EDGES = 10**7       # cpu_baseline: one oracle peel of this many edges
 REF_STEP_EDGES = 2 * 10**6     # --impl reference: edges per oracle step
 ALL_LEGS = ("e2e", "cpu", "mphf", "lookup", "async", "peel_async", "stress", "batched",
-            "serving", "sf", "general", "random_access")
+            "serving", "sf", "general", "random_access", "large")
+LARGE_N = 7_600_000_000        # the paper's largest key set (sec. 5: 7.6e9 n-grams)
 
 # Algorithmic bytes per unit of work, per step of the path (r = 3).  "sector"
 # charges one 32-byte sector per random access (64 bytes for a read-modify-
@@ -800,6 +801,68 @@ def max_scale_leg(steps=2, warmup=1):
                                    f"per pass"}}
 
 
+def large_leg(n=LARGE_N, steps=2, warmup=1):
+    """The MPHF of the paper's largest key set, 7.6e9 keys (sec. 5), on one
+    GB300 through hpeel_mphf_build_large (64-bit ids, edges re-hashed from
+    the keys), the layer list in pinned host memory; every key must peel and
+    the lookups of all keys must be a bijection onto [0, n) (checked)."""
+    import torch
+
+    import paper_1312_0526_gb300 as hp
+    from paper_1312_0526_gb300 import inputs
+
+    m = hp.num_vertices(n, GAMMA_MILLI, R)
+    torch.cuda.empty_cache()
+    keys = inputs.keys_torch(n, KEY_SEED)
+    wsb = hp.mphf_large_workspace_size(n, GAMMA_MILLI, True)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    hl = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    G = torch.empty((m + 31) // 32, dtype=torch.int64, device="cuda")
+    D = torch.empty((m + 511) // 512 + 1, dtype=torch.int64, device="cuda")
+    res = None
+    for _ in range(warmup):
+        res = hp.mphf_build_large(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D,
+                                  host_list=hl)
+    torch.cuda.synchronize()
+    hp.profile_reset()
+    hp.profile_enable(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        res = hp.mphf_build_large(keys, HASH_SEED, GAMMA_MILLI, workspace=ws, G=G, rank_dir=D,
+                                  host_list=hl)
+    b.record()
+    torch.cuda.synchronize()
+    hp.profile_enable(False)
+    prof = hp.profile_read()
+    ms = a.elapsed_time(b) / steps
+    del ws, hl
+    torch.cuda.empty_cache()
+    flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    step = 1 << 28
+    out = torch.empty(step, dtype=torch.int64, device="cuda")
+    ok = True
+    for lo in range(0, n, step):
+        hi = min(n, lo + step)
+        hp.mphf_lookup_large(keys[lo:hi], res.stats["seed_used"], m, G, D, out=out[:hi - lo])
+        idx = out[:hi - lo]
+        if not bool(((idx >= 0) & (idx < n)).all()):
+            ok = False
+            break
+        flags.index_fill_(0, idx, 1)
+    ok = ok and int(flags.sum(dtype=torch.int64)) == n
+    del keys, flags, out, G, D
+    torch.cuda.empty_cache()
+    return {"value": n / ms / 1e3, "unit": "Mkeys/s", "ms_per_step": ms, "steps": steps,
+            "n": n, "m": m, "rounds": res.stats["rounds"], "n_peeled": res.stats["n_peeled"],
+            "seed_used": res.stats["seed_used"], "workspace_gb": wsb / 1e9,
+            "host_list_gb": 8 * n / 1e9, "lookup_bijection": ok,
+            "steps_ms": {k: v[1] / steps for k, v in sorted(prof.items())},
+            "config": {"workload": f"mphf-build n={n:.2e} r=3 gamma=1.23 (the paper's 7.6e9-key "
+                                   f"set, sec. 5), 64-bit ids, keys on the device (SplitMix64 "
+                                   f"seed {KEY_SEED}), layer list in pinned host memory"}}
+
+
 BATCH_B = 65536
 
 
@@ -1029,7 +1092,10 @@ def summary_of(line):
          "serving_capacity_req_s": g(line, "serving", "capacity_req_per_s"),
          "sf_1e8_ms": g(line, "static_function", "ms_per_step"),
          "general_1e8_ms": g(line, "general_peel", "ms_per_step"),
-         "cpu_oracle_medges_s": g(line, "cpu_baseline", "value")}
+         "cpu_oracle_medges_s": g(line, "cpu_baseline", "value"),
+         "large_7_6e9_mphf_s": (round(line["large_7_6e9"]["ms_per_step"] / 1e3, 3)
+                                if line.get("large_7_6e9") else None),
+         "large_7_6e9_bijection": g(line, "large_7_6e9", "lookup_bijection")}
     for name in ("n1e9_g1222", "n1e9_g1200", "n1e8_g1300_r4"):
         s[f"stress_{name}_ms"] = g(line, "stress", name, "ms_per_step")
     rates = g(line, "serving", "rates") or []
@@ -1186,6 +1252,7 @@ def main():
                 "frac": random_access["rounds_vs_peeled_edge_pattern"],
                 "source": "random_access leg (measurement library probe, kind 2)"}
     max_scale = max_scale_leg() if world == 1 and args.max_scale else None
+    large = large_leg() if world == 1 and "large" in legs else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -1218,6 +1285,7 @@ def main():
         "general_peel": general,
         "random_access": random_access,
         "max_scale": max_scale,
+        "large_7_6e9": large,
     }
     line["summary"] = summary_of(line)
     print(json.dumps(line), flush=True)
