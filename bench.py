@@ -109,19 +109,24 @@ def byte_model(step, n, m, st):
 
 
 # DRAM bytes per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# for a kernel version, keyed by the sha256 of the source file the kernel
-# lives in; stale entries are ignored.  Filled from the summaries in profiles/.
+# for a kernel version, keyed by the sha256 of the source files its kernels
+# live in; stale entries are ignored.  Filled from the summaries in profiles/.
 NCU_TRAFFIC = {
-    # step: (source file, sha256 prefix, bytes per unit, where measured)
-    "rounds": ("paper_1312_0526_gb300/csrc/peel.cu", "d3e6f35e961fa5db", 357.09,
-               "k_round0 + k_round of one peel at n = 3e7 (host round loop), scaled by "
-               "peeled edges"),
+    # step: (source files, sha256 prefix, bytes per unit, where measured)
+    "rounds": (("paper_1312_0526_gb300/csrc/peel.cu",
+                "paper_1312_0526_gb300/csrc/rounds_bucketed.cu",
+                "paper_1312_0526_gb300/csrc/build.cu"), "fca7234e879030d5", 325.74,
+               "every round kernel (sorted round 0 and L_0, random k_round) of one peel at "
+               "n = 3e7 (host round loop), scaled by peeled edges"),
 }
 
 
-def src_hash(rel):
-    with open(os.path.join(ROOT, rel), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def src_hash(rels):
+    h = hashlib.sha256()
+    for rel in rels:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -253,6 +258,14 @@ def cpu_baseline():
 def roofline_of(prof, steps, n, m, st, round_loop):
     """Roofline of the step with the largest live CUDA-event total."""
     peak, peak_kind = measured_peaks()
+    prof = dict(prof)
+    if round_loop == "host":
+        # the host loop times round 0, the sorted rounds and the random rounds
+        # apart; the byte model covers all of them, the graph loop's one scope
+        for part in ("round0", "rounds_sorted"):
+            if part in prof and "rounds" in prof:
+                c, t = prof.pop(part)[:2]
+                prof["rounds"] = [prof["rounds"][0] + c, prof["rounds"][1] + t]
     ranked = sorted(((v[1], k) for k, v in prof.items()), reverse=True)
     for tot_ms, name in ranked:
         model = byte_model(name, n, m, st)
@@ -261,7 +274,9 @@ def roofline_of(prof, steps, n, m, st, round_loop):
         per_step_ms = tot_ms / steps
         launches_per_step = prof[name][0] / steps
         if name == "rounds" and round_loop == "graph":
-            launches_per_step = 1 + st["rounds"]  # round 0 + the graph's iterations
+            # one launch of the CUDA graph that holds round 0 and both loops
+            # of rounds (sorted, random); its kernels run back to back
+            launches_per_step = 1
         achieved = model["sector"] / (per_step_ms / 1e3) / 1e9
         traffic = traffic_step = source = None
         if name in NCU_TRAFFIC:
