@@ -105,7 +105,7 @@ PeelLayout peel_layout(uint64_t n, uint64_t m, uint32_t r, bool general = false)
     p.L = region;
     p.pairs = region;
     if (p.sp.enabled) p.s_claims = region + claims_at;
-    p.fill = take(p.bucketed ? 4 * (size_t)p.plan.chunks_pass * p.plan.regions : 0);
+    p.fill = take(p.bucketed ? 4 * (size_t)p.plan.fill_words : 0);
     p.fill2 = take(p.bucketed ? 4 * (size_t)p.plan.subs_pass : 0);
     p.ovf = take(p.bucketed ? 8 * (size_t)p.plan.ovf_cap : 0);
     p.ovf_count = take(p.bucketed ? 4 : 0);

@@ -9,9 +9,9 @@
 //   pass 1 (fused with hashing, or with the row -> record conversion): each
 //          block takes tiles of edges, writes their records, counting-sorts
 //          a tile's (vertex, edge) incidences by chunk (2^shift vertices of
-//          one part) in shared memory and appends each chunk's run to its
-//          own region of that chunk's bucket (one region per (chunk, block),
-//          cursors in shared memory: no global atomics);
+//          one part) in shared memory and appends each chunk's run to the
+//          chunk's array (one atomicAdd per chunk and tile on its cursor),
+//          so the pass writes at one moving front per chunk;
 //   pass 2 (refine): a persistent kernel counting-sorts each chunk's pairs,
 //          a tile at a time, into sub-buckets of 2^sub_shift vertices;
 //   pass 3 (apply): one block per sub-bucket accumulates its vertices'
@@ -54,6 +54,7 @@ __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
 #ifndef HPEEL_RB_MIN_BLOCKS
 #define HPEEL_RB_MIN_BLOCKS 3
 #endif
+constexpr uint32_t kCurRegs = 2;  // chunk cursors per thread held in registers
 template <int R, bool FROM_KEYS, bool GEN>
 __global__ void __launch_bounds__(kThreads, HPEEL_RB_MIN_BLOCKS)
 k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ rows,
@@ -75,13 +76,12 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
     };
     const uint32_t Cp = (C + 1) & ~1u;
     uint32_t *hist = smem;            // C: tile count per chunk
-    uint32_t *cur = hist + Cp;        // C: fill of this block's region of each chunk
+    uint32_t *cur = hist + Cp;        // C: the run's place in its chunk minus its stage slot
     uint32_t *toff = cur + Cp;        // C: start of the chunk's run in stage
     uint32_t *sch = toff + Cp;        // kInc: chunk of each stage slot
     uint2 *stage = reinterpret_cast<uint2 *>(sch + kInc);  // kInc (8-byte aligned: Cp, kInc even)
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 
-    for (uint32_t c = threadIdx.x; c < C; c += kThreads) cur[c] = 0;
     const uint64_t tiles = ((uint64_t)n + kTileEdges - 1) / kTileEdges;
     // the next tile's input (keys, or rows) is loaded while this one is
     // hashed, sorted and written
@@ -151,6 +151,18 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             }
         }
         __syncthreads();
+        // reserve each chunk's run with one atomicAdd on its cursor; the
+        // results are awaited only after the staging below
+        uint32_t gb[kCurRegs];
+#pragma unroll
+        for (uint32_t q = 0; q < kCurRegs; q++) {
+            const uint32_t c = q * kThreads + threadIdx.x, h = c < C ? hist[c] : 0u;
+            gb[q] = h ? atomicAdd(fill + ((size_t)c << g.fill_shift), h) : 0u;
+        }
+        for (uint32_t c = kCurRegs * kThreads + threadIdx.x; c < C; c += kThreads) {
+            const uint32_t h = hist[c];
+            cur[c] = h ? atomicAdd(fill + ((size_t)c << g.fill_shift), h) : 0u;
+        }
         // exclusive scan of hist -> toff (warp 0, 32 chunks per step)
         if (warp == 0) {
             uint32_t run = 0;
@@ -181,24 +193,29 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                 sch[slot] = c;
             }
         }
+        // cur[c] = the run's first place in chunk c - its first stage slot
+        // (mod 2^32): staged pair k of chunk c goes to place cur[c] + k
+#pragma unroll
+        for (uint32_t q = 0; q < kCurRegs; q++) {
+            const uint32_t c = q * kThreads + threadIdx.x;
+            if (c < C) cur[c] = gb[q] - toff[c];
+        }
+        for (uint32_t c = kCurRegs * kThreads + threadIdx.x; c < C; c += kThreads)
+            cur[c] -= toff[c];
         __syncthreads();
         // write the staged runs: consecutive slots -> consecutive addresses
         const uint32_t total = toff[C - 1] + hist[C - 1];
         for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
             const uint32_t c = sch[k];
-            const uint32_t pos = cur[c] + (k - toff[c]);
+            const uint32_t pos = cur[c] + k;
             const uint2 p = stage[k];
             if (pos < g.cap)
-                pairs[((uint64_t)c * gridDim.x + blockIdx.x) * g.cap + pos] = p;
+                pairs[(uint64_t)c * g.cap + pos] = p;
             else
                 overflow_push(p, ov, ctl);
         }
         __syncthreads();
-        for (uint32_t c = threadIdx.x; c < C; c += kThreads) cur[c] += hist[c];
-        __syncthreads();
     }
-    for (uint32_t c = threadIdx.x; c < C; c += kThreads)
-        fill[(size_t)c * gridDim.x + blockIdx.x] = cur[c];
 }
 
 // Refine: the pairs of each chunk (all its regions) are counting-sorted in
@@ -242,7 +259,8 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
     auto item_len = [&](uint64_t it) -> uint32_t {
         const uint32_t c = (uint32_t)(it / tiles), tile = (uint32_t)(it - (uint64_t)c * tiles);
         const uint32_t reg = tile / tpr, t0 = (tile - reg * tpr) * kRefineTile;
-        const uint32_t cnt = min(__ldg(fill + (size_t)c * regions + reg), g.cap);
+        const uint32_t cnt =
+            min(__ldg(fill + (((size_t)c * regions + reg) << g.fill_shift)), g.cap);
         return t0 < cnt ? min(cnt - t0, kRefineTile) : 0u;
     };
     auto next_item = [&](uint64_t it) -> uint64_t {
@@ -501,15 +519,15 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
     // all r positions in the single part of a general graph
     const double per = (double)r / (double)parts;
     const uint64_t tiles = (n + kTileEdges - 1) / kTileEdges;
-    // one region per block of the record pass, which runs one resident wave
-    b.regions = (uint32_t)std::max<uint64_t>(
+    // the record pass runs one resident wave; each chunk is one array
+    b.blocks = (uint32_t)std::max<uint64_t>(
         1, std::min<uint64_t>(tiles, (uint64_t)sms * HPEEL_RB_MIN_BLOCKS));
-    // a region gets the incidences of one chunk from about n / regions edges
-    const double expect =
-        P ? per * (double)n * (double)(1ull << shift) / (double)P / b.regions : 0.0;
+    b.regions = 1;
+    const double expect = P ? per * (double)n * (double)(1ull << shift) / (double)P : 0.0;
     uint64_t cap = (uint64_t)(expect + 8.0 * std::sqrt(expect + 1.0) + 64.0);
-    b.cap = (uint32_t)std::min<uint64_t>(cap, n);
-    b.pair_bytes = (uint64_t)b.chunks_pass * b.regions * b.cap * 8;
+    b.cap = (uint32_t)std::min<uint64_t>(cap, per * (double)n + 64.0);
+    b.pair_bytes = (uint64_t)b.chunks_pass * b.cap * 8;
+    b.fill_words = (uint64_t)b.chunks_pass << kFillShift;
     // sub-buckets: 2^sub_shift vertices (default 2^13: 64 KiB of shared
     // memory for the apply's two 32-bit counters per vertex, 3 blocks per SM)
     b.sub_shift = sub_shift ? sub_shift : (shift > 9 ? shift - 9 : 0);
@@ -534,9 +552,11 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
                            Overflow ov, Ctl *ctl, bool gen, const uint64_t *seed_dev,
                            uint32_t pass) {
     if (n == 0) return;
-    BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
-    const unsigned grid = b.regions;  // one bucket region per block and chunk
+    BucketGeom g{P, b.shift, b.chunks_per_part, b.cap, kFillShift};
+    const unsigned grid = b.blocks;
     const int pass_part = b.passes > 1 ? (int)pass : -1;
+    // the chunk cursors start at 0 every pass
+    cudaMemsetAsync(fill, 0, 4 * b.fill_words, L.stream);
 #define HP_BK(RR, FK)                                                                         \
     do {                                                                                      \
         auto kern = gen ? k_records_bucketed<RR, FK, true> : k_records_bucketed<RR, FK, false>; \
@@ -579,7 +599,7 @@ void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, cons
                           const uint32_t *fill, uint2 *pairs2, uint32_t *fill2, Overflow ov,
                           unsigned long long *st, Ctl *ctl, uint32_t pass, ClaimSink sink) {
     if (b.passes > 1) sink.claims = nullptr;  // claims need every part's degrees
-    BucketGeom g{P, b.shift, b.chunks_per_part, b.cap};
+    BucketGeom g{P, b.shift, b.chunks_per_part, b.cap, kFillShift};
     const uint32_t chunk0 = b.passes > 1 ? pass * b.chunks_per_part : 0u;
     launch_refine(L, g, b.chunks_pass, chunk0, b.regions, b.sub_shift, pairs, fill, pairs2, fill2,
                   b.cap2, ov, ctl);

@@ -94,9 +94,11 @@ struct BucketPlan {
     uint32_t shift;            // log2 vertices per chunk
     uint32_t chunks_per_part;
     uint32_t chunks;
-    uint32_t regions;          // bucket regions per chunk (= blocks of the bucketing kernel)
+    uint32_t regions;          // bucket regions per chunk (1: one array per chunk)
+    uint32_t blocks;           // blocks of the bucketing kernel
     uint32_t cap;              // incidences per region
     uint64_t pair_bytes;       // bucket storage
+    uint64_t fill_words;       // fill counters (one per region, 2^kFillShift words apart)
     size_t smem;               // dynamic shared memory of the bucketing kernel
     uint32_t sub_shift;        // log2 vertices per sub-bucket
     uint32_t subs;             // sub-buckets in all
@@ -123,8 +125,12 @@ struct BucketGeom {
     uint32_t P;                // part size
     uint32_t shift;            // log2 of the vertices per chunk
     uint32_t chunks_per_part;
-    uint32_t cap;              // region capacity (incidences per chunk and block)
+    uint32_t cap;              // region capacity (incidences per region)
+    uint32_t fill_shift;       // region k's fill counter is fill[k << fill_shift]
 };
+// The build's chunk cursors sit one 128-byte line apart: every block of the
+// bucketing pass advances them, and cursors sharing a line would serialise.
+constexpr uint32_t kFillShift = 5;
 // parts: r for an r-partite graph (chunks never straddle parts), 1 for a
 // general graph (one part [0, m)).
 // part_passes: the tuning's bucket_part_passes (0 automatic, 1 one pass,

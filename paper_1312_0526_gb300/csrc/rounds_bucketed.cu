@@ -126,9 +126,9 @@ k_round0_emit(const unsigned long long *__restrict__ st, uint32_t m, uint32_t n,
 
 // -------------------------------------------------------------- bucketing --
 // One counting-sort pass: each block takes tiles of input items, sorts their
-// pairs by chunk in shared memory and appends each chunk's run to its own
-// region of the chunk's bucket (one region per (chunk, block); cursors in
-// shared memory).  Items:
+// pairs by chunk in shared memory and appends each chunk's run to the chunk's
+// array (one atomicAdd per chunk and tile on its cursor; cursors one 128-byte
+// line apart, zeroed before the pass).  Items:
 //   ENTRIES  -- the entries of layer t = ctl->round, each giving the pairs
 //               {w, e} of its R - 1 non-hinge vertices; chunks by vertex
 //               (part j, then 2^shift vertices of the part);
@@ -146,9 +146,9 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
     constexpr int kInc = kBucketItems * kPer;
     extern __shared__ uint32_t smem[];
     const uint32_t Cp = (C + 1) & ~1u;
-    uint32_t *hist = smem;                                 // C
-    uint32_t *cur = hist + Cp;                             // C
-    uint32_t *toff = cur + Cp;                             // C
+    uint32_t *hist = smem;                                 // C: tile count per chunk
+    uint32_t *cur = hist + Cp;                             // C: run's place - its stage slot
+    uint32_t *toff = cur + Cp;                             // C: run's first stage slot
     uint32_t *sch = toff + Cp;                             // kInc
     uint2 *stage = reinterpret_cast<uint2 *>(sch + kInc);  // kInc
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -169,7 +169,6 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
         }
         return x >> g.shift;
     };
-    for (uint32_t c = threadIdx.x; c < C; c += kBucketThreads) cur[c] = 0;
     const uint64_t tiles = ((uint64_t)(i1 - i0) + kBucketItems - 1) / kBucketItems;
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         for (uint32_t c = threadIdx.x; c < C; c += kBucketThreads) hist[c] = 0;
@@ -204,6 +203,13 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
             for (int k = 0; k < kPer; k++) rank[q][k] = ok[q] ? atomicAdd(&hist[ch[q][k]], 1u) : 0u;
         }
         __syncthreads();
+        // reserve each chunk's run; the result is awaited after the staging
+        const uint32_t h0 = threadIdx.x < C ? hist[threadIdx.x] : 0u;
+        const uint32_t gb0 = h0 ? atomicAdd(fill + ((size_t)threadIdx.x << g.fill_shift), h0) : 0u;
+        for (uint32_t c = kBucketThreads + threadIdx.x; c < C; c += kBucketThreads) {
+            const uint32_t h = hist[c];
+            cur[c] = h ? atomicAdd(fill + ((size_t)c << g.fill_shift), h) : 0u;
+        }
         if (warp == 0) {  // exclusive scan of hist -> toff, 32 chunks per step
             uint32_t run = 0;
             for (uint32_t c0 = 0; c0 < C; c0 += 32) {
@@ -230,23 +236,23 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
                 sch[slot] = ch[q][k];
             }
         }
+        // staged pair k of chunk c goes to place cur[c] + k (mod 2^32)
+        if (threadIdx.x < C) cur[threadIdx.x] = gb0 - toff[threadIdx.x];
+        for (uint32_t c = kBucketThreads + threadIdx.x; c < C; c += kBucketThreads)
+            cur[c] -= toff[c];
         __syncthreads();
         const uint32_t total = toff[C - 1] + hist[C - 1];
         for (uint32_t k = threadIdx.x; k < total; k += kBucketThreads) {
             const uint32_t c = sch[k];
-            const uint32_t pos = cur[c] + (k - toff[c]);
+            const uint32_t pos = cur[c] + k;
             const uint2 p = stage[k];
             if (pos < g.cap)
-                pairs[((uint64_t)c * gridDim.x + blockIdx.x) * g.cap + pos] = p;
+                pairs[(uint64_t)c * g.cap + pos] = p;
             else
                 raise_err(ctl, ov.code);
         }
         __syncthreads();
-        for (uint32_t c = threadIdx.x; c < C; c += kBucketThreads) cur[c] += hist[c];
-        __syncthreads();
     }
-    for (uint32_t c = threadIdx.x; c < C; c += kBucketThreads)
-        fill[(size_t)c * gridDim.x + blockIdx.x] = cur[c];
 }
 
 // ------------------------------------------------------------------ updates --
@@ -544,22 +550,19 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     p.claim_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0u, m * 38 / 100 + 4096);
     p.regions = (uint32_t)std::max<int>(1, sms);  // one bucketing block per SM
     // updates, by vertex: the build's chunks and sub-buckets
-    p.vg = BucketGeom{(uint32_t)P, b.shift, b.chunks_per_part, 0};
+    p.vg = BucketGeom{(uint32_t)P, b.shift, b.chunks_per_part, 0, kFillShift};
     p.vchunks = b.chunks;
     p.vsub_shift = b.sub_shift;
     p.vsubs = b.subs;
-    // a region of the bucketing pass receives the pairs of the tiles its
-    // block takes, spread over the chunks (whole tiles: a block of a small
-    // round: a block of a small round may take all of it); share: the part
-    // of the pairs that the largest chunk receives (a part's last chunk is
-    // partial, so a full chunk gets more than an even split)
+    // a chunk's array holds its share of the pairs of the largest layer
+    // (share: the part of the pairs that the largest chunk receives; a
+    // part's last chunk is partial, so a full chunk gets more than an even
+    // split)
     auto region_cap = [&](uint64_t items, uint32_t per_item, double share) {
-        const uint64_t tiles = (items + kBucketItems - 1) / kBucketItems;
-        const uint64_t per_block =
-            (tiles + p.regions - 1) / p.regions * (uint64_t)kBucketItems * per_item;
-        const double e = (double)per_block * std::min(1.0, share);
+        const uint64_t all = items * per_item;
+        const double e = (double)all * std::min(1.0, share);
         return (uint32_t)std::min<uint64_t>((uint64_t)(e + 8.0 * std::sqrt(e + 1.0) + 64.0),
-                                            per_block);
+                                            all);
     };
     // a part holds about a third of the updates (0.4 leaves room for the
     // hinge positions' skew)
@@ -571,7 +574,8 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     p.esub = kEsub;
     p.eshift = 22;
     while (p.eshift > p.esub && ((n - 1) >> p.eshift) == 0 && p.eshift > 14) p.eshift--;
-    p.eg = BucketGeom{(uint32_t)n, p.eshift, (uint32_t)((n + (1ull << p.eshift) - 1) >> p.eshift), 0};
+    p.eg = BucketGeom{(uint32_t)n, p.eshift, (uint32_t)((n + (1ull << p.eshift) - 1) >> p.eshift), 0,
+                      kFillShift};
     p.echunks = p.eg.chunks_per_part;
     p.esubs = p.echunks << (p.eshift - p.esub);
     p.eg.cap = region_cap(p.claim_cap, 1, (double)(1ull << p.eshift) / (double)n);
@@ -582,9 +586,9 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     const uint32_t C = std::max(p.vchunks, p.echunks);
     p.bucket_smem = (size_t)3 * ((C + 1) & ~1u) * 4 + (size_t)kBucketItems * 2 * (4 + 8);
     if (p.bucket_smem > (200u << 10)) return SortedPlan{};
-    p.pairs_bytes = 8 * std::max<uint64_t>((uint64_t)p.vchunks * p.regions * p.vg.cap,
-                                           (uint64_t)p.echunks * p.regions * p.eg.cap);
-    p.fill_bytes = 4 * (uint64_t)std::max(p.vchunks, p.echunks) * p.regions;
+    p.pairs_bytes = 8 * std::max<uint64_t>((uint64_t)p.vchunks * p.vg.cap,
+                                           (uint64_t)p.echunks * p.eg.cap);
+    p.fill_bytes = 4 * ((uint64_t)std::max(p.vchunks, p.echunks) << kFillShift);
     p.pairs2_bytes = 8 * std::max<uint64_t>((uint64_t)p.vsubs * p.vcap2,
                                             (uint64_t)p.esubs * p.ecap2);
     p.fill2_bytes = 4 * (uint64_t)std::max(p.vsubs, p.esubs);
@@ -600,13 +604,14 @@ void set_smem(const void *fn, size_t) { smem_optin(fn); }
 void launch_sorted_claims(const Launch &L, const SortedPlan &p, const SortedBufs &w, uint32_t n,
                           uint4 *rec, uint4 *Lst, Ctl *ctl, uint32_t round_add) {
     Overflow none{nullptr, nullptr, 0, kDevRoundOverflow};
+    cudaMemsetAsync(w.fill, 0, 4 * ((size_t)p.echunks << kFillShift), L.stream);
     cudaMemsetAsync(w.fill2, 0, 4 * (size_t)p.esubs, L.stream);
     BucketGeom eg = p.eg;
     set_smem((const void *)k_pairs_bucket<3, false>, p.bucket_smem);
     count_launch();
     k_pairs_bucket<3, false><<<p.regions, kBucketThreads, p.bucket_smem, L.stream>>>(
         nullptr, nullptr, w.claims, p.claim_cap, eg, p.echunks, w.pairs, w.fill, none, ctl);
-    launch_refine(L, eg, p.echunks, 0, p.regions, p.esub, w.pairs, w.fill, w.pairs2, w.fill2,
+    launch_refine(L, eg, p.echunks, 0, 1, p.esub, w.pairs, w.fill, w.pairs2, w.fill2,
                   p.ecap2, none, ctl);
     const size_t tsmem = ((size_t)1 << p.esub) / 2;
     set_smem((const void *)k_claim_resolve, tsmem);
@@ -635,13 +640,14 @@ void launch_sorted_round(const Launch &L, const SortedPlan &p, const SortedBufs 
                          uint32_t *loff, Ctl *ctl, uint32_t max_rounds,
                          cudaGraphConditionalHandle h_sorted, cudaGraphConditionalHandle h_random) {
     Overflow none{nullptr, nullptr, 0, kDevRoundOverflow};
+    cudaMemsetAsync(w.fill, 0, 4 * ((size_t)p.vchunks << kFillShift), L.stream);
     cudaMemsetAsync(w.fill2, 0, 4 * (size_t)p.vsubs, L.stream);
     BucketGeom vg = p.vg;
     set_smem((const void *)k_pairs_bucket<3, true>, p.bucket_smem);
     count_launch();
     k_pairs_bucket<3, true><<<p.regions, kBucketThreads, p.bucket_smem, L.stream>>>(
         Lst, loff, nullptr, 0, vg, p.vchunks, w.pairs, w.fill, none, ctl);
-    launch_refine(L, vg, p.vchunks, 0, p.regions, p.vsub_shift, w.pairs, w.fill, w.pairs2, w.fill2,
+    launch_refine(L, vg, p.vchunks, 0, 1, p.vsub_shift, w.pairs, w.fill, w.pairs2, w.fill2,
                   p.vcap2, none, ctl);
     const size_t dsmem = (size_t)8 << p.vsub_shift;
     set_smem((const void *)k_delete_apply, dsmem);
