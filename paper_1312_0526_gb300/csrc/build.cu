@@ -30,7 +30,11 @@
 
 namespace hp {
 
-constexpr int kTileEdges = 1024;  // edges per block step (4 per thread)
+#ifndef HPEEL_RB_TILE
+#define HPEEL_RB_TILE 1024
+#endif
+constexpr int kTileEdges = HPEEL_RB_TILE;  // edges per block step
+constexpr int kTileU = kTileEdges / kThreads;  // edges per thread and step
 
 // Chunk of vertex v at position j: chunks never straddle the parts of an
 // r-partite graph; a general graph (GEN) is one part [0, P = m).
@@ -52,7 +56,7 @@ __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
 }
 
 #ifndef HPEEL_RB_MIN_BLOCKS
-#define HPEEL_RB_MIN_BLOCKS 3
+#define HPEEL_RB_MIN_BLOCKS 4
 #endif
 constexpr uint32_t kCurRegs = 2;  // chunk cursors per thread held in registers
 template <int R, bool FROM_KEYS, bool GEN>
@@ -62,7 +66,6 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                    uint4 *__restrict__ rec,
                    uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov,
                    Ctl *ctl, int pass_part) {
-    constexpr int kInc = kTileEdges * R;
     if (FROM_KEYS && seed_dev) seed = *seed_dev;  // the seed of a device-driven attempt
     extern __shared__ uint32_t smem[];
     // pass_part < 0: every position's incidences, chunks of all parts; else
@@ -78,17 +81,16 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
     uint32_t *hist = smem;            // C: tile count per chunk
     uint32_t *cur = hist + Cp;        // C: the run's place in its chunk minus its stage slot
     uint32_t *toff = cur + Cp;        // C: start of the chunk's run in stage
-    uint32_t *sch = toff + Cp;        // kInc: chunk of each stage slot
-    uint2 *stage = reinterpret_cast<uint2 *>(sch + kInc);  // kInc (8-byte aligned: Cp, kInc even)
+    uint2 *stage = reinterpret_cast<uint2 *>(toff + Cp);  // R per edge (8-byte aligned: Cp even)
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 
     const uint64_t tiles = ((uint64_t)n + kTileEdges - 1) / kTileEdges;
     // the next tile's input (keys, or rows) is loaded while this one is
     // hashed, sorted and written
     constexpr int kWords = FROM_KEYS ? 2 : R;  // 32-bit words of input per edge
-    auto load_input = [&](uint64_t tile, uint32_t (&in)[4][kWords]) {
+    auto load_input = [&](uint64_t tile, uint32_t (&in)[kTileU][kWords]) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < kTileU; q++) {
             const uint64_t e = tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x;
 #pragma unroll
             for (int w = 0; w < kWords; w++) in[q][w] = 0;
@@ -105,21 +107,21 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             }
         }
     };
-    uint32_t next_in[4][kWords];
+    uint32_t next_in[kTileU][kWords];
     if ((uint64_t)blockIdx.x < tiles) load_input(blockIdx.x, next_in);
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        uint32_t in[4][kWords];
+        uint32_t in[kTileU][kWords];
 #pragma unroll
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < kTileU; q++)
 #pragma unroll
             for (int w = 0; w < kWords; w++) in[q][w] = next_in[q][w];
         if (tile + gridDim.x < tiles) load_input(tile + gridDim.x, next_in);
         for (uint32_t c = threadIdx.x; c < C; c += kThreads) hist[c] = 0;
         __syncthreads();
-        uint32_t vv[4][R], rank[4][R];
-        bool inc[4];
+        uint32_t vv[kTileU][R], rank[kTileU][R];
+        bool inc[kTileU];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < kTileU; q++) {
             const uint64_t e = tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x;
             uint32_t v[4] = {0, 0, 0, 0};
             bool ok = e < n;
@@ -181,7 +183,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < kTileU; q++) {
             if (!inc[q]) continue;
             const uint32_t e = (uint32_t)(tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x);
 #pragma unroll
@@ -190,7 +192,6 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
                 const uint32_t c = chunk_here(vv[q][j], j);
                 const uint32_t slot = toff[c] + rank[q][j];
                 stage[slot] = make_uint2(vv[q][j], e);
-                sch[slot] = c;
             }
         }
         // cur[c] = the run's first place in chunk c - its first stage slot
@@ -206,9 +207,12 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
         // write the staged runs: consecutive slots -> consecutive addresses
         const uint32_t total = toff[C - 1] + hist[C - 1];
         for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
-            const uint32_t c = sch[k];
-            const uint32_t pos = cur[c] + k;
             const uint2 p = stage[k];
+            // its chunk again, from the vertex (an r-partite graph's part
+            // follows from the vertex id)
+            const uint32_t c = pass_part >= 0 ? chunk_here(p.x, pass_part)
+                                              : chunk_of<GEN>(p.x, GEN ? 0u : part_of<R>(p.x, g.P), g);
+            const uint32_t pos = cur[c] + k;
             if (pos < g.cap)
                 pairs[(uint64_t)c * g.cap + pos] = p;
             else
@@ -225,17 +229,24 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 // resident wave of blocks strides over all (chunk, tile) items; the next
 // item's pairs are loaded into registers while the current one is sorted
 // and written, so the load latency overlaps the work.
-#ifndef HPEEL_REFINE_ITEMS
-#define HPEEL_REFINE_ITEMS 16
+#ifndef HPEEL_REFINE_THREADS
+#define HPEEL_REFINE_THREADS 512
 #endif
+#ifndef HPEEL_REFINE_ITEMS
+#define HPEEL_REFINE_ITEMS 8
+#endif
+#ifndef HPEEL_REFINE_MIN_BLOCKS
+#define HPEEL_REFINE_MIN_BLOCKS 2
+#endif
+constexpr int kRefThreads = HPEEL_REFINE_THREADS;
 constexpr int kRefineItems = HPEEL_REFINE_ITEMS;
-constexpr uint32_t kRefineTile = kThreads * kRefineItems;  // 4096 slots
-constexpr uint32_t kWarps = kThreads / 32;
+constexpr uint32_t kRefineTile = kRefThreads * kRefineItems;  // 4096 slots
+constexpr uint32_t kRefWarps = kRefThreads / 32;
 constexpr uint32_t kScanRegs = 4;  // sub-buckets per thread whose cursor stays in registers
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kRefThreads, HPEEL_REFINE_MIN_BLOCKS)
 k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ fill, BucketGeom g,
-                 uint32_t chunks, uint32_t chunk0, uint32_t regions, uint32_t sub_shift,
+                 uint32_t chunks, uint32_t chunk0, uint32_t sub_shift,
                  uint2 *__restrict__ pairs2, uint32_t *__restrict__ fill2, uint32_t cap2,
                  Overflow ov, Ctl *ctl) {
     extern __shared__ uint32_t smem[];
@@ -243,64 +254,64 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
     uint32_t *hist = smem;          // S
     uint32_t *gbase = hist + S;     // S: sub-bucket cursor minus the run's first stage slot
     uint32_t *toff = gbase + S;     // S
-    uint32_t *wsum = toff + S;      // kWarps: scan totals of the warps
+    uint32_t *wsum = toff + S;      // kRefWarps: scan totals of the warps
     // kRefineTile pairs, 8-byte aligned whatever S is
-    uint2 *stage = reinterpret_cast<uint2 *>(smem + ((3 * S + kWarps + 1) & ~1u));
+    uint2 *stage = reinterpret_cast<uint2 *>(smem + ((3 * S + kRefWarps + 1) & ~1u));
     // the scan gives each thread `per` consecutive sub-buckets
-    const uint32_t per = (S + kThreads - 1) / kThreads, b0 = threadIdx.x * per;
+    const uint32_t per = (S + kRefThreads - 1) / kRefThreads, b0 = threadIdx.x * per;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint64_t span = (uint64_t)regions * g.cap;
-    // tiles never straddle regions: region reg has ceil(cap / kRefineTile)
-    // tiles, of which those below its fill hold pairs
-    const uint32_t tpr = (g.cap + kRefineTile - 1) / kRefineTile;
-    const uint32_t tiles = regions * tpr;
-    const uint64_t items = (uint64_t)chunks * tiles;
-    // pairs in item `it` (0 past the fill of its region); block-uniform
-    auto item_len = [&](uint64_t it) -> uint32_t {
-        const uint32_t c = (uint32_t)(it / tiles), tile = (uint32_t)(it - (uint64_t)c * tiles);
-        const uint32_t reg = tile / tpr, t0 = (tile - reg * tpr) * kRefineTile;
-        const uint32_t cnt =
-            min(__ldg(fill + (((size_t)c * regions + reg) << g.fill_shift)), g.cap);
+    // item = (chunk, tile): chunk c's array has ceil(cap / kRefineTile)
+    // tiles, of which those below its fill hold pairs (fewer than 2^32 items)
+    const uint32_t tpc = (g.cap + kRefineTile - 1) / kRefineTile;
+    const uint32_t items = chunks * tpc;
+    // pairs in item `it` (0 past the fill of its chunk); block-uniform
+    auto item_len = [&](uint32_t it) -> uint32_t {
+        const uint32_t c = it / tpc, t0 = (it - c * tpc) * kRefineTile;
+        const uint32_t cnt = min(__ldg(fill + ((size_t)c << g.fill_shift)), g.cap);
         return t0 < cnt ? min(cnt - t0, kRefineTile) : 0u;
     };
-    auto next_item = [&](uint64_t it) -> uint64_t {
+    auto next_item = [&](uint32_t it) -> uint32_t {
         do it += gridDim.x;
         while (it < items && item_len(it) == 0);
         return it;
     };
-    auto load_item = [&](uint64_t it, uint2 (&p)[kRefineItems]) {
-        const uint32_t c = (uint32_t)(it / tiles), tile = (uint32_t)(it - (uint64_t)c * tiles);
-        const uint32_t reg = tile / tpr, t0 = (tile - reg * tpr) * kRefineTile;
-        const uint32_t tn = item_len(it);
-        const uint2 *tsrc = pairs + (uint64_t)c * span + (uint64_t)reg * g.cap + t0;
+    auto load_item = [&](uint32_t it, uint32_t tn, uint2 (&p)[kRefineItems]) {
+        const uint32_t c = it / tpc, t0 = (it - c * tpc) * kRefineTile;
+        const uint2 *tsrc = pairs + (uint64_t)c * g.cap + t0;
 #pragma unroll
         for (int q = 0; q < kRefineItems; q++) {
-            const uint32_t i = (uint32_t)q * kThreads + threadIdx.x;
+            const uint32_t i = (uint32_t)q * kRefThreads + threadIdx.x;
             p[q] = i < tn ? __ldcs(tsrc + i) : make_uint2(0u, 0u);
         }
     };
-    uint64_t it = blockIdx.x;
-    if (it < items && item_len(it) == 0) it = next_item(it);
+    uint32_t it = blockIdx.x, tn_next = 0;
+    if (it < items && (tn_next = item_len(it)) == 0) {
+        it = next_item(it);
+        if (it < items) tn_next = item_len(it);
+    }
     uint2 pn[kRefineItems];
-    if (it < items) load_item(it, pn);
+    if (it < items) load_item(it, tn_next, pn);
     while (it < items) {
-        const uint32_t c = (uint32_t)(it / tiles);  // chunk of this pass
+        const uint32_t c = it / tpc;  // chunk of this pass
         const uint32_t cg = chunk0 + c;              // chunk of the whole build
         const uint32_t part = cg / g.chunks_per_part;
         const uint32_t base_v = part * g.P + (cg % g.chunks_per_part) * (1u << g.shift);
-        const uint32_t tn = item_len(it);
+        const uint32_t tn = tn_next;
         uint2 p[kRefineItems];
 #pragma unroll
         for (int q = 0; q < kRefineItems; q++) p[q] = pn[q];
-        const uint64_t nxt = next_item(it);
-        if (nxt < items) load_item(nxt, pn);
-        for (uint32_t b = threadIdx.x; b < S; b += kThreads) hist[b] = 0;
+        const uint32_t nxt = next_item(it);
+        if (nxt < items) {
+            tn_next = item_len(nxt);
+            load_item(nxt, tn_next, pn);
+        }
+        for (uint32_t b = threadIdx.x; b < S; b += kRefThreads) hist[b] = 0;
         __syncthreads();
         uint32_t rk[kRefineItems];
         bool ok[kRefineItems];
 #pragma unroll
         for (int q = 0; q < kRefineItems; q++) {
-            const uint32_t i = (uint32_t)q * kThreads + threadIdx.x;
+            const uint32_t i = (uint32_t)q * kRefThreads + threadIdx.x;
             ok[q] = i < tn;
             // a pair outside the chunk (inconsistent input) is dropped with an error
             if (ok[q] && ((p[q].x - base_v) >> sub_shift) >= S) {
@@ -318,7 +329,7 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             const uint32_t b = b0 + q, h = q < per && b < S ? hist[b] : 0u;
             gb[q] = h ? atomicAdd(fill2 + (size_t)c * S + b, h) : 0u;
         }
-        for (uint32_t q = kScanRegs; q < per; q++) {  // S > kThreads * kScanRegs
+        for (uint32_t q = kScanRegs; q < per; q++) {  // S > kRefThreads * kScanRegs
             const uint32_t b = b0 + q, h = b < S ? hist[b] : 0u;
             if (b < S) gbase[b] = h ? atomicAdd(fill2 + (size_t)c * S + b, h) : 0u;
         }
@@ -361,7 +372,7 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             if (b0 + q < S) gbase[b0 + q] -= toff[b0 + q];
         __syncthreads();
         const uint32_t total = toff[S - 1] + hist[S - 1];
-        for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
+        for (uint32_t k = threadIdx.x; k < total; k += kRefThreads) {
             const uint2 q = stage[k];
             const uint32_t b = (q.x - base_v) >> sub_shift;  // its sub-bucket, again
             const uint32_t pos = gbase[b] + k;
@@ -522,7 +533,6 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
     // the record pass runs one resident wave; each chunk is one array
     b.blocks = (uint32_t)std::max<uint64_t>(
         1, std::min<uint64_t>(tiles, (uint64_t)sms * HPEEL_RB_MIN_BLOCKS));
-    b.regions = 1;
     const double expect = P ? per * (double)n * (double)(1ull << shift) / (double)P : 0.0;
     uint64_t cap = (uint64_t)(expect + 8.0 * std::sqrt(expect + 1.0) + 64.0);
     b.cap = (uint32_t)std::min<uint64_t>(cap, per * (double)n + 64.0);
@@ -541,7 +551,7 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
     b.cap2 = (uint32_t)std::min<uint64_t>(cap2, n);
     b.pair2_bytes = (uint64_t)b.subs_pass * b.cap2 * 8;
     b.ovf_cap = (uint32_t)std::max<uint64_t>(1u << 16, n / 16);
-    b.smem = (size_t)(3 * ((b.chunks + 1) & ~1u)) * 4 + (size_t)kTileEdges * r * (8 + 4);
+    b.smem = (size_t)(3 * ((b.chunks + 1) & ~1u)) * 4 + (size_t)kTileEdges * r * 8;
     b.parts = parts;
     return b;
 }
@@ -582,17 +592,22 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
 }
 
 void launch_refine(const Launch &L, const BucketGeom &g, uint32_t chunks, uint32_t chunk0,
-                   uint32_t regions, uint32_t sub_shift, const uint2 *pairs, const uint32_t *fill,
+                   uint32_t sub_shift, const uint2 *pairs, const uint32_t *fill,
                    uint2 *pairs2, uint32_t *fill2, uint32_t cap2, Overflow ov, Ctl *ctl) {
     const uint32_t S = 1u << (g.shift - sub_shift);
-    const size_t smem1 = ((3 * (size_t)S + kWarps + 1) & ~(size_t)1) * 4 + (size_t)kRefineTile * 8;
+    const size_t smem1 =
+        ((3 * (size_t)S + kRefWarps + 1) & ~(size_t)1) * 4 + (size_t)kRefineTile * 8;
     smem_optin((const void *)k_refine_buckets);
-    const uint64_t items = (uint64_t)chunks * regions * ((g.cap + kRefineTile - 1) / kRefineTile);
+    // items < 2^32: each holds up to 4096 of the pass's pairs, and the pair
+    // storage of a pass is far below 2^44 pairs
+    const uint64_t items = (uint64_t)chunks * ((g.cap + kRefineTile - 1) / kRefineTile);
     const unsigned grid = (unsigned)std::min<uint64_t>(
-        std::max<uint64_t>(items, 1), grid_resident(L, (const void *)k_refine_buckets, 8, smem1));
+        std::max<uint64_t>(items, 1),
+        grid_resident(L, (const void *)k_refine_buckets, 8, smem1, kRefThreads));
     count_launch();
-    k_refine_buckets<<<grid, kThreads, smem1, L.stream>>>(pairs, fill, g, chunks, chunk0, regions,
-                                                         sub_shift, pairs2, fill2, cap2, ov, ctl);
+    k_refine_buckets<<<grid, kRefThreads, smem1, L.stream>>>(pairs, fill, g, chunks, chunk0,
+                                                            sub_shift, pairs2, fill2, cap2, ov,
+                                                            ctl);
 }
 
 void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, const uint2 *pairs,
@@ -601,7 +616,7 @@ void launch_apply_buckets(const Launch &L, const BucketPlan &b, uint32_t P, cons
     if (b.passes > 1) sink.claims = nullptr;  // claims need every part's degrees
     BucketGeom g{P, b.shift, b.chunks_per_part, b.cap, kFillShift};
     const uint32_t chunk0 = b.passes > 1 ? pass * b.chunks_per_part : 0u;
-    launch_refine(L, g, b.chunks_pass, chunk0, b.regions, b.sub_shift, pairs, fill, pairs2, fill2,
+    launch_refine(L, g, b.chunks_pass, chunk0, b.sub_shift, pairs, fill, pairs2, fill2,
                   b.cap2, ov, ctl);
     const size_t smem2 = (size_t)8 << b.sub_shift;
     smem_optin((const void *)k_apply_smem);

@@ -48,9 +48,9 @@ inline unsigned grid_fixed(const Launch &L, int per_sm) { return (unsigned)(L.sm
 // One wave: as many blocks of kThreads as fit on the device at once (at most
 // cap_per_sm per SM), for grid-stride kernels.
 inline unsigned grid_resident(const Launch &L, const void *fn, int cap_per_sm,
-                              size_t dyn_smem = 0) {
+                              size_t dyn_smem = 0, int threads = kThreads) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, dyn_smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, dyn_smem) != cudaSuccess ||
         nb <= 0) {
         cudaGetLastError();
         nb = 1;
@@ -94,11 +94,10 @@ struct BucketPlan {
     uint32_t shift;            // log2 vertices per chunk
     uint32_t chunks_per_part;
     uint32_t chunks;
-    uint32_t regions;          // bucket regions per chunk (1: one array per chunk)
     uint32_t blocks;           // blocks of the bucketing kernel
-    uint32_t cap;              // incidences per region
+    uint32_t cap;              // incidences per chunk (one array each)
     uint64_t pair_bytes;       // bucket storage
-    uint64_t fill_words;       // fill counters (one per region, 2^kFillShift words apart)
+    uint64_t fill_words;       // fill counters (one per chunk, 2^kFillShift words apart)
     size_t smem;               // dynamic shared memory of the bucketing kernel
     uint32_t sub_shift;        // log2 vertices per sub-bucket
     uint32_t subs;             // sub-buckets in all
@@ -125,8 +124,8 @@ struct BucketGeom {
     uint32_t P;                // part size
     uint32_t shift;            // log2 of the vertices per chunk
     uint32_t chunks_per_part;
-    uint32_t cap;              // region capacity (incidences per region)
-    uint32_t fill_shift;       // region k's fill counter is fill[k << fill_shift]
+    uint32_t cap;              // chunk capacity (incidences per chunk)
+    uint32_t fill_shift;       // chunk c's fill counter is fill[c << fill_shift]
 };
 // The build's chunk cursors sit one 128-byte line apart: every block of the
 // bucketing pass advances them, and cursors sharing a line would serialise.
@@ -147,7 +146,7 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
 // into sub-buckets of 2^sub_shift keys (pair.x is the key); fill2 zeroed
 // before.
 void launch_refine(const Launch &L, const BucketGeom &g, uint32_t chunks, uint32_t chunk0,
-                   uint32_t regions, uint32_t sub_shift, const uint2 *pairs, const uint32_t *fill,
+                   uint32_t sub_shift, const uint2 *pairs, const uint32_t *fill,
                    uint2 *pairs2, uint32_t *fill2, uint32_t cap2, Overflow ov, Ctl *ctl);
 // Round 0's claims emitted by the incidence build itself (the shared-memory
 // apply sees every final degree): claims == nullptr for none.

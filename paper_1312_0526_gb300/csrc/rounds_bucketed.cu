@@ -143,14 +143,12 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
                const uint2 *__restrict__ claims, uint32_t claim_cap, BucketGeom g, uint32_t C,
                uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov, Ctl *ctl) {
     constexpr int kPer = ENTRIES ? R - 1 : 1;
-    constexpr int kInc = kBucketItems * kPer;
     extern __shared__ uint32_t smem[];
     const uint32_t Cp = (C + 1) & ~1u;
     uint32_t *hist = smem;                                 // C: tile count per chunk
     uint32_t *cur = hist + Cp;                             // C: run's place - its stage slot
     uint32_t *toff = cur + Cp;                             // C: run's first stage slot
-    uint32_t *sch = toff + Cp;                             // kInc
-    uint2 *stage = reinterpret_cast<uint2 *>(sch + kInc);  // kInc
+    uint2 *stage = reinterpret_cast<uint2 *>(toff + Cp);   // kPer per item (8-byte aligned)
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t i0, i1;
     if (ENTRIES) {
@@ -233,7 +231,6 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
             for (int k = 0; k < kPer; k++) {
                 const uint32_t slot = toff[ch[q][k]] + rank[q][k];
                 stage[slot] = pp[q][k];
-                sch[slot] = ch[q][k];
             }
         }
         // staged pair k of chunk c goes to place cur[c] + k (mod 2^32)
@@ -243,9 +240,9 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
         __syncthreads();
         const uint32_t total = toff[C - 1] + hist[C - 1];
         for (uint32_t k = threadIdx.x; k < total; k += kBucketThreads) {
-            const uint32_t c = sch[k];
-            const uint32_t pos = cur[c] + k;
             const uint2 p = stage[k];
+            const uint32_t c = chunk_of_key(p.x);  // its chunk again
+            const uint32_t pos = cur[c] + k;
             if (pos < g.cap)
                 pairs[(uint64_t)c * g.cap + pos] = p;
             else
@@ -584,7 +581,7 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
                                            p.claim_cap);
     // shared memory of the bucketing pass (counters of every chunk + a tile)
     const uint32_t C = std::max(p.vchunks, p.echunks);
-    p.bucket_smem = (size_t)3 * ((C + 1) & ~1u) * 4 + (size_t)kBucketItems * 2 * (4 + 8);
+    p.bucket_smem = (size_t)3 * ((C + 1) & ~1u) * 4 + (size_t)kBucketItems * 2 * 8;
     if (p.bucket_smem > (200u << 10)) return SortedPlan{};
     p.pairs_bytes = 8 * std::max<uint64_t>((uint64_t)p.vchunks * p.vg.cap,
                                            (uint64_t)p.echunks * p.eg.cap);
@@ -611,7 +608,7 @@ void launch_sorted_claims(const Launch &L, const SortedPlan &p, const SortedBufs
     count_launch();
     k_pairs_bucket<3, false><<<p.regions, kBucketThreads, p.bucket_smem, L.stream>>>(
         nullptr, nullptr, w.claims, p.claim_cap, eg, p.echunks, w.pairs, w.fill, none, ctl);
-    launch_refine(L, eg, p.echunks, 0, 1, p.esub, w.pairs, w.fill, w.pairs2, w.fill2,
+    launch_refine(L, eg, p.echunks, 0, p.esub, w.pairs, w.fill, w.pairs2, w.fill2,
                   p.ecap2, none, ctl);
     const size_t tsmem = ((size_t)1 << p.esub) / 2;
     set_smem((const void *)k_claim_resolve, tsmem);
@@ -647,7 +644,7 @@ void launch_sorted_round(const Launch &L, const SortedPlan &p, const SortedBufs 
     count_launch();
     k_pairs_bucket<3, true><<<p.regions, kBucketThreads, p.bucket_smem, L.stream>>>(
         Lst, loff, nullptr, 0, vg, p.vchunks, w.pairs, w.fill, none, ctl);
-    launch_refine(L, vg, p.vchunks, 0, 1, p.vsub_shift, w.pairs, w.fill, w.pairs2, w.fill2,
+    launch_refine(L, vg, p.vchunks, 0, p.vsub_shift, w.pairs, w.fill, w.pairs2, w.fill2,
                   p.vcap2, none, ctl);
     const size_t dsmem = (size_t)8 << p.vsub_shift;
     set_smem((const void *)k_delete_apply, dsmem);
