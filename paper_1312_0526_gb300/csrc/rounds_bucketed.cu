@@ -381,14 +381,23 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
 // ------------------------------------------------------------------- claims --
 // One block per edge sub-chunk of 2^esub edges: the claims of round tr on
 // the sub-chunk (see the file comment).  The shared table keeps 4 bits per
-// edge, bit j set when the vertex at position j claims the edge.
-constexpr int kResThreads = 1024;
-constexpr int kResU = 8;  // edges per thread: one sub-chunk of 2^kEsub edges per block
+// edge, bit j set when the vertex at position j claims the edge.  The block
+// walks its sub-chunk in spans of kResThreads * kResU edges (small blocks,
+// several per SM, so one block's loads overlap another's scans).
+#ifndef HPEEL_RES_THREADS
+#define HPEEL_RES_THREADS 256
+#endif
+constexpr int kResThreads = HPEEL_RES_THREADS;
+constexpr int kResU = 8;  // edges per thread and span
+constexpr uint32_t kResSpan = (uint32_t)kResThreads * kResU;
 constexpr uint32_t kEsub = 13;
-static_assert((1u << kEsub) == (uint32_t)kResU * kResThreads, "a block covers its sub-chunk");
+static_assert((1u << kEsub) % kResSpan == 0, "spans tile the sub-chunk");
 
+// Exclusive block-wide prefix sum of one value per thread; *total gets the
+// sum.  Every thread calls it; it ends with the block synchronised.
 __device__ __forceinline__ uint32_t res_block_scan(uint32_t v, uint32_t *total) {
-    __shared__ uint32_t ws[32];
+    constexpr int kW = kResThreads / 32;
+    __shared__ uint32_t ws[kW];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -399,17 +408,17 @@ __device__ __forceinline__ uint32_t res_block_scan(uint32_t v, uint32_t *total) 
     if (lane == 31) ws[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = ws[lane];
+        uint32_t w = lane < (uint32_t)kW ? ws[lane] : 0u;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
             if (lane >= (uint32_t)d) w += y;
         }
-        ws[lane] = w;
+        if (lane < (uint32_t)kW) ws[lane] = w;
     }
     __syncthreads();
     const uint32_t before = (warp ? ws[warp - 1] : 0u) + x - v;
-    *total = ws[31];
+    *total = ws[kW - 1];
     return before;
 }
 
@@ -451,39 +460,42 @@ k_claim_resolve(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ f
     }
     __syncthreads();
     const uint32_t tr = *(volatile uint32_t *)&ctl->round + round_add;
-    // the sub-chunk in edge order, kResU edges per thread with all their
-    // record loads in flight (a warp covers 32 consecutive records per step,
-    // and only the claimed ones are read); the entries of the block are
-    // placed by one block-wide scan and reserved with one atomic
-    uint32_t mask[kResU];
-    uint4 q[kResU];
-    uint32_t mine = 0;
+    // the sub-chunk in edge order, a span at a time, kResU edges per thread
+    // with all their record loads in flight (a warp covers 32 consecutive
+    // records per step, and only the claimed ones are read); the entries of
+    // a span are placed by one block-wide scan and reserved with one atomic
+    for (uint32_t sp = 0; sp < ne; sp += kResSpan) {
+        uint32_t mask[kResU];
+        uint4 q[kResU];
+        uint32_t mine = 0;
 #pragma unroll
-    for (int u = 0; u < kResU; u++) {
-        const uint32_t el = (uint32_t)u * kResThreads + threadIdx.x;
-        mask[u] = el < ne ? (mtab[el >> 3] >> (4u * (el & 7u))) & 0xFu : 0u;
-        q[u] = mask[u] ? __ldcg(rec + e0 + el) : make_uint4(0u, 0u, 0u, 0u);
-    }
+        for (int u = 0; u < kResU; u++) {
+            const uint32_t el = sp + (uint32_t)u * kResThreads + threadIdx.x;
+            mask[u] = el < ne ? (mtab[el >> 3] >> (4u * (el & 7u))) & 0xFu : 0u;
+            q[u] = mask[u] ? __ldcg(rec + e0 + el) : make_uint4(0u, 0u, 0u, 0u);
+        }
 #pragma unroll
-    for (int u = 0; u < kResU; u++) {
-        if (mask[u] && q[u].w != kUnclaimed) mask[u] = 0;  // claimed in an earlier round
-        mine += mask[u] ? 1u : 0u;
-    }
-    uint32_t total;
-    uint32_t pos = res_block_scan(mine, &total);
-    if (threadIdx.x == 0) s_base = total ? atomicAdd(&ctl->lcur, total) : 0u;
-    __syncthreads();
-    pos += s_base;
+        for (int u = 0; u < kResU; u++) {
+            if (mask[u] && q[u].w != kUnclaimed) mask[u] = 0;  // claimed in an earlier round
+            mine += mask[u] ? 1u : 0u;
+        }
+        uint32_t total;
+        uint32_t pos = res_block_scan(mine, &total);
+        if (threadIdx.x == 0) s_base = total ? atomicAdd(&ctl->lcur, total) : 0u;
+        __syncthreads();
+        pos += s_base;
 #pragma unroll
-    for (int u = 0; u < kResU; u++) {
-        if (!mask[u]) continue;
-        const uint32_t e = (uint32_t)(e0 + (uint32_t)u * kResThreads + threadIdx.x);
-        const uint32_t h = (uint32_t)(__ffs(mask[u]) - 1);
-        rec[e].w = (tr << 2) | h;
-        const uint32_t p[4] = {q[u].x, q[u].y, q[u].z, 0u};
-        uint32_t x[4];
-        rotate_to<3>(p, h, x);
-        Lst[pos++] = make_uint4(x[0], x[1], x[2], e);
+        for (int u = 0; u < kResU; u++) {
+            if (!mask[u]) continue;
+            const uint32_t e = (uint32_t)(e0 + sp + (uint32_t)u * kResThreads + threadIdx.x);
+            const uint32_t h = (uint32_t)(__ffs(mask[u]) - 1);
+            rec[e].w = (tr << 2) | h;
+            const uint32_t p[4] = {q[u].x, q[u].y, q[u].z, 0u};
+            uint32_t x[4];
+            rotate_to<3>(p, h, x);
+            Lst[pos++] = make_uint4(x[0], x[1], x[2], e);
+        }
+        __syncthreads();  // s_base and the scan's table are reused by the next span
     }
 }
 
