@@ -256,8 +256,14 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
 // One block per vertex sub-bucket: the DeleteEdge updates of layer t applied
 // in shared memory (see the file comment).  Every thread of the block runs
 // every loop: the claim staging is warp-synchronous.
+#ifndef HPEEL_DEL_CLAIMS
+#define HPEEL_DEL_CLAIMS 1024
+#endif
 constexpr int kDelThreads = 512;
-constexpr int kDelClaims = 2048;  // claims a block gathers before one reservation
+// claims a block gathers before one reservation: the expected number of
+// vertices of a sub-bucket that fall to degree 1 in the first rounds is a
+// few hundred; 1024 keeps the block at 74 KB of shared memory (3 per SM)
+constexpr int kDelClaims = HPEEL_DEL_CLAIMS;
 constexpr int kDelU = 8;          // loads in flight per thread
 
 __global__ void __launch_bounds__(kDelThreads)
