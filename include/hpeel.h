@@ -116,7 +116,7 @@ typedef struct hpeel_stats {
  *                       orientations by edge and of the updates by vertex,
  *                       with shared memory as the fast tier) instead of with
  *                       atomics at random addresses -- the first rounds, until
- *                       one is smaller; 0 (default): automatic, n / 8, for
+ *                       one is smaller; 0 (default): automatic, n / 20, for
  *                       r = 3 r-partite graphs whose incidence build is
  *                       L2-blocked in one pass; 0xFFFFFFFF: never.  Results
  *                       are the same either way.

@@ -14,10 +14,11 @@
 //              flat list; the claims are bucketed by edge range (two
 //              counting-sort passes, as the incidence build does for
 //              vertices), and one block per 2^esub edges gathers the
-//              positions that claim each edge in a shared table, then walks
-//              the range in edge order: an edge still unclaimed takes the
-//              round with the smallest claiming position as its hinge and
-//              its list entry {v_hinge, others, e} is appended.  The hinge
+//              positions that claim each edge in a shared table, then goes
+//              over its claims again: the claim of an edge's smallest
+//              claiming position, if no earlier round took the edge, makes
+//              that vertex the hinge and appends the list entry
+//              {v_hinge, others, e}.  The hinge
 //              is exact, so no entry of a sorted round is ever rewritten and
 //              no vertex is marked.
 //   updates -- the entries of the layer give their r - 1 DeleteEdge updates
@@ -388,16 +389,15 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
 // One block per edge sub-chunk of 2^esub edges: the claims of round tr on
 // the sub-chunk (see the file comment).  The shared table keeps 4 bits per
 // edge, bit j set when the vertex at position j claims the edge.  The block
-// walks its sub-chunk in spans of kResThreads * kResU edges (small blocks,
+// then takes its claims in spans of kResThreads * kResU (small blocks,
 // several per SM, so one block's loads overlap another's scans).
 #ifndef HPEEL_RES_THREADS
 #define HPEEL_RES_THREADS 256
 #endif
 constexpr int kResThreads = HPEEL_RES_THREADS;
-constexpr int kResU = 8;  // edges per thread and span
+constexpr int kResU = 8;  // claims per thread and span
 constexpr uint32_t kResSpan = (uint32_t)kResThreads * kResU;
 constexpr uint32_t kEsub = 13;
-static_assert((1u << kEsub) % kResSpan == 0, "spans tile the sub-chunk");
 
 // Exclusive block-wide prefix sum of one value per thread; *total gets the
 // sum.  Every thread calls it; it ends with the block synchronised.
@@ -428,7 +428,10 @@ __device__ __forceinline__ uint32_t res_block_scan(uint32_t v, uint32_t *total) 
     return before;
 }
 
-__global__ void __launch_bounds__(kResThreads)
+#ifndef HPEEL_RES_MIN_BLOCKS
+#define HPEEL_RES_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(kResThreads, HPEEL_RES_MIN_BLOCKS)
 k_claim_resolve(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill2,
                 uint32_t cap2, uint32_t esub, uint32_t n, uint32_t P, uint32_t round_add,
                 uint4 *__restrict__ rec, uint4 *__restrict__ Lst, Ctl *ctl) {
@@ -450,7 +453,7 @@ k_claim_resolve(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ f
 #pragma unroll
         for (int u = 0; u < kResU; u++) {
             const uint32_t i = i0 + (uint32_t)u * kResThreads;
-            pv[u] = i < cnt ? __ldcs(src + i) : make_uint2(0u, 0u);  // {g, v}
+            pv[u] = i < cnt ? __ldcg(src + i) : make_uint2(0u, 0u);  // {g, v}
         }
 #pragma unroll
         for (int u = 0; u < kResU; u++) {
@@ -466,24 +469,31 @@ k_claim_resolve(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ f
     }
     __syncthreads();
     const uint32_t tr = *(volatile uint32_t *)&ctl->round + round_add;
-    // the sub-chunk in edge order, a span at a time, kResU edges per thread
-    // with all their record loads in flight (a warp covers 32 consecutive
-    // records per step, and only the claimed ones are read); the entries of
-    // a span are placed by one block-wide scan and reserved with one atomic
-    for (uint32_t sp = 0; sp < ne; sp += kResSpan) {
-        uint32_t mask[kResU];
+    // the claims again, a span at a time: the claim of each edge's smallest
+    // claiming position (read from the table) lists the edge, unless an
+    // earlier round took it; the work follows the claims, not the 2^esub
+    // edges of the sub-chunk.  The entries of a span are placed by one
+    // block-wide scan and reserved with one atomic.
+    for (uint32_t sp = 0; sp < cnt; sp += kResSpan) {
+        uint2 pv[kResU];
+        uint32_t hj[kResU];
         uint4 q[kResU];
+        bool win[kResU];
         uint32_t mine = 0;
 #pragma unroll
         for (int u = 0; u < kResU; u++) {
-            const uint32_t el = sp + (uint32_t)u * kResThreads + threadIdx.x;
-            mask[u] = el < ne ? (mtab[el >> 3] >> (4u * (el & 7u))) & 0xFu : 0u;
-            q[u] = mask[u] ? __ldcg(rec + e0 + el) : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t i = sp + (uint32_t)u * kResThreads + threadIdx.x;
+            pv[u] = i < cnt ? __ldcs(src + i) : make_uint2(0u, 0u);
+            const uint32_t el = (uint32_t)(pv[u].x - e0);
+            hj[u] = part_of<3>(pv[u].y, P);
+            const uint32_t bits = el < ne ? (mtab[el >> 3] >> (4u * (el & 7u))) & 0xFu : 0u;
+            win[u] = i < cnt && el < ne && (bits & ((1u << hj[u]) - 1u)) == 0u;
+            q[u] = win[u] ? __ldcg(rec + pv[u].x) : make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
         for (int u = 0; u < kResU; u++) {
-            if (mask[u] && q[u].w != kUnclaimed) mask[u] = 0;  // claimed in an earlier round
-            mine += mask[u] ? 1u : 0u;
+            if (win[u] && q[u].w != kUnclaimed) win[u] = false;  // claimed in an earlier round
+            mine += win[u] ? 1u : 0u;
         }
         uint32_t total;
         uint32_t pos = res_block_scan(mine, &total);
@@ -492,9 +502,8 @@ k_claim_resolve(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ f
         pos += s_base;
 #pragma unroll
         for (int u = 0; u < kResU; u++) {
-            if (!mask[u]) continue;
-            const uint32_t e = (uint32_t)(e0 + sp + (uint32_t)u * kResThreads + threadIdx.x);
-            const uint32_t h = (uint32_t)(__ffs(mask[u]) - 1);
+            if (!win[u]) continue;
+            const uint32_t e = pv[u].x, h = hj[u];
             rec[e].w = (tr << 2) | h;
             const uint32_t p[4] = {q[u].x, q[u].y, q[u].z, 0u};
             uint32_t x[4];
@@ -556,9 +565,10 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     const uint64_t P = m / 3;
     // the largest layer deleted in sorted form: covers L_0 up to gamma 1.35
     p.max_edges = (uint32_t)std::min<uint64_t>(n, (n * 3) / 10 + 1024);
-    // automatic: a sorted round costs a fixed ~8 ms at n = 1e9 plus about 45
-    // ps per edge, a random one ~110 ps per edge: sorted from 1/8 of the edges
-    p.min_edges = min_edges ? min_edges : (uint32_t)std::max<uint64_t>(1, n / 8);
+    // automatic: a sorted round costs a fixed few ms at n = 1e9 plus about
+    // 40 ps per edge, a random one ~110 ps per edge: sorted from 1/20 of the
+    // edges (L_0, L_1 and L_2 at gamma = 1.23)
+    p.min_edges = min_edges ? min_edges : (uint32_t)std::max<uint64_t>(1, n / 20);
     if (p.min_edges > p.max_edges) return p;
     // claims of one round: at most the degree-1 vertices of round 0 (a
     // fraction lambda e^-lambda <= 1/e of the vertices for random graphs)

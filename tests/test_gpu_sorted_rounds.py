@@ -85,7 +85,7 @@ def test_sorted_rounds_run_where_expected():
     try:
         hp.set_tuning(bucket_shift=10, bucket_min_vertices=0, sorted_round_min=1)
         every = hp.peel(e, m)
-        hp.set_tuning(bucket_shift=10, bucket_min_vertices=0, sorted_round_min=0)  # n / 8
+        hp.set_tuning(bucket_shift=10, bucket_min_vertices=0, sorted_round_min=0)  # n / 20
         auto = hp.peel(e, m)
         hp.set_tuning(bucket_shift=10, bucket_min_vertices=0, sorted_round_min=NEVER)
         never = hp.peel(e, m)
