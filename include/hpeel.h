@@ -32,7 +32,8 @@
  *     hpeel_peel_noalloc uses neither kind of graph.
  *   - Every call returns an hpeel_status; no C++ exception crosses the ABI.
  *     On failure hpeel_last_error() (per host thread) holds a message.
- *   - Edge ids and vertex ids are uint32: n < 2^32 and m < 2^32.
+ *   - Edge ids and vertex ids are uint32: n < 2^32 and m < 2^32, except in
+ *     the *_large calls (64-bit ids, for key sets like the paper's 7.6e9).
  *   - All results are exact and deterministic: the same inputs give the
  *     same bytes on every run and in every launch configuration.
  */
