@@ -255,28 +255,54 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
     uint32_t *gbase = hist + S;     // S: sub-bucket cursor minus the run's first stage slot
     uint32_t *toff = gbase + S;     // S
     uint32_t *wsum = toff + S;      // kRefWarps: scan totals of the warps
+    uint32_t *tstart = wsum + kRefWarps;  // chunks + 1: first item of each chunk
     // kRefineTile pairs, 8-byte aligned whatever S is
-    uint2 *stage = reinterpret_cast<uint2 *>(smem + ((3 * S + kRefWarps + 1) & ~1u));
+    uint2 *stage =
+        reinterpret_cast<uint2 *>(smem + ((3 * S + kRefWarps + chunks + 1 + 1) & ~1u));
     // the scan gives each thread `per` consecutive sub-buckets
     const uint32_t per = (S + kRefThreads - 1) / kRefThreads, b0 = threadIdx.x * per;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    // item = (chunk, tile): chunk c's array has ceil(cap / kRefineTile)
-    // tiles, of which those below its fill hold pairs (fewer than 2^32 items)
-    const uint32_t tpc = (g.cap + kRefineTile - 1) / kRefineTile;
-    const uint32_t items = chunks * tpc;
-    // pairs in item `it` (0 past the fill of its chunk); block-uniform
-    auto item_len = [&](uint32_t it) -> uint32_t {
-        const uint32_t c = it / tpc, t0 = (it - c * tpc) * kRefineTile;
-        const uint32_t cnt = min(__ldg(fill + ((size_t)c << g.fill_shift)), g.cap);
-        return t0 < cnt ? min(cnt - t0, kRefineTile) : 0u;
+    // items = the filled tiles of kRefineTile pairs of every chunk, numbered
+    // chunk after chunk (a chunk's array may be far from full: a sorted
+    // round's layer is a fraction of the largest one): tstart[c] = first
+    // item of chunk c, from one block-wide scan of the tile counts
+    auto chunk_fill = [&](uint32_t c) {
+        return min(__ldg(fill + ((size_t)c << g.fill_shift)), g.cap);
     };
-    auto next_item = [&](uint32_t it) -> uint32_t {
-        do it += gridDim.x;
-        while (it < items && item_len(it) == 0);
-        return it;
+    {
+        const uint32_t cper = (chunks + kRefThreads - 1) / kRefThreads, c0 = threadIdx.x * cper;
+        uint32_t loc = 0;
+        for (uint32_t q = 0; q < cper; q++)
+            if (c0 + q < chunks) loc += (chunk_fill(c0 + q) + kRefineTile - 1) / kRefineTile;
+        uint32_t x = loc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= (uint32_t)d) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        uint32_t run = x - loc;
+        for (uint32_t w = 0; w < warp; w++) run += wsum[w];
+        for (uint32_t q = 0; q < cper; q++) {
+            const uint32_t c = c0 + q;
+            if (c < chunks) {
+                tstart[c] = run;
+                run += (chunk_fill(c) + kRefineTile - 1) / kRefineTile;
+            }
+        }
+        if (threadIdx.x == kRefThreads - 1) tstart[chunks] = run;
+        __syncthreads();
+    }
+    const uint32_t items = tstart[chunks];
+    // the chunk of an item: a block's items only go up, so its chunk cursor
+    // only moves forward (the last c with tstart[c] <= it)
+    auto advance = [&](uint32_t it, uint32_t &c) {
+        while (tstart[c + 1] <= it) c++;
     };
-    auto load_item = [&](uint32_t it, uint32_t tn, uint2 (&p)[kRefineItems]) {
-        const uint32_t c = it / tpc, t0 = (it - c * tpc) * kRefineTile;
+    auto load_item = [&](uint32_t it, uint32_t c, uint32_t &tn, uint2 (&p)[kRefineItems]) {
+        const uint32_t t0 = (it - tstart[c]) * kRefineTile;
+        tn = min(chunk_fill(c) - t0, kRefineTile);
         const uint2 *tsrc = pairs + (uint64_t)c * g.cap + t0;
 #pragma unroll
         for (int q = 0; q < kRefineItems; q++) {
@@ -284,15 +310,14 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             p[q] = i < tn ? __ldcs(tsrc + i) : make_uint2(0u, 0u);
         }
     };
-    uint32_t it = blockIdx.x, tn_next = 0;
-    if (it < items && (tn_next = item_len(it)) == 0) {
-        it = next_item(it);
-        if (it < items) tn_next = item_len(it);
-    }
+    uint32_t it = blockIdx.x, tn_next = 0, c_next = 0;
     uint2 pn[kRefineItems];
-    if (it < items) load_item(it, tn_next, pn);
+    if (it < items) {
+        advance(it, c_next);
+        load_item(it, c_next, tn_next, pn);
+    }
     while (it < items) {
-        const uint32_t c = it / tpc;  // chunk of this pass
+        const uint32_t c = c_next;  // chunk of this pass
         const uint32_t cg = chunk0 + c;              // chunk of the whole build
         const uint32_t part = cg / g.chunks_per_part;
         const uint32_t base_v = part * g.P + (cg % g.chunks_per_part) * (1u << g.shift);
@@ -300,10 +325,10 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
         uint2 p[kRefineItems];
 #pragma unroll
         for (int q = 0; q < kRefineItems; q++) p[q] = pn[q];
-        const uint32_t nxt = next_item(it);
+        const uint32_t nxt = it + gridDim.x;
         if (nxt < items) {
-            tn_next = item_len(nxt);
-            load_item(nxt, tn_next, pn);
+            advance(nxt, c_next);
+            load_item(nxt, c_next, tn_next, pn);
         }
         for (uint32_t b = threadIdx.x; b < S; b += kRefThreads) hist[b] = 0;
         __syncthreads();
@@ -595,8 +620,8 @@ void launch_refine(const Launch &L, const BucketGeom &g, uint32_t chunks, uint32
                    uint32_t sub_shift, const uint2 *pairs, const uint32_t *fill,
                    uint2 *pairs2, uint32_t *fill2, uint32_t cap2, Overflow ov, Ctl *ctl) {
     const uint32_t S = 1u << (g.shift - sub_shift);
-    const size_t smem1 =
-        ((3 * (size_t)S + kRefWarps + 1) & ~(size_t)1) * 4 + (size_t)kRefineTile * 8;
+    const size_t smem1 = ((3 * (size_t)S + kRefWarps + chunks + 1 + 1) & ~(size_t)1) * 4 +
+                         (size_t)kRefineTile * 8;
     smem_optin((const void *)k_refine_buckets);
     // items < 2^32: each holds up to 4096 of the pass's pairs, and the pair
     // storage of a pass is far below 2^44 pairs
