@@ -115,7 +115,7 @@ NCU_TRAFFIC = {
     # step: (source files, sha256 prefix, bytes per unit, where measured)
     "rounds": (("paper_1312_0526_gb300/csrc/peel.cu",
                 "paper_1312_0526_gb300/csrc/rounds_bucketed.cu",
-                "paper_1312_0526_gb300/csrc/build.cu"), "fca7234e879030d5", 325.74,
+                "paper_1312_0526_gb300/csrc/build.cu"), "c676189843cc709d", 325.51,
                "every round kernel (sorted round 0 and L_0, random k_round) of one peel at "
                "n = 3e7 (host round loop), scaled by peeled edges"),
 }

@@ -135,11 +135,17 @@ k_round0_emit(const unsigned long long *__restrict__ st, uint32_t m, uint32_t n,
 //               (part j, then 2^shift vertices of the part);
 //   !ENTRIES -- the ctl->ccur claims {g, v} of the flat list; chunks by edge
 //               (one part [0, P = n), 2^shift edges each).
-constexpr int kBucketThreads = 1024;
+#ifndef HPEEL_BUCKET_THREADS
+#define HPEEL_BUCKET_THREADS 512
+#endif
+#ifndef HPEEL_BUCKET_BLOCKS
+#define HPEEL_BUCKET_BLOCKS 2
+#endif
+constexpr int kBucketThreads = HPEEL_BUCKET_THREADS;
 constexpr int kBucketItems = 4 * kBucketThreads;  // items per tile (4 per thread)
 
 template <int R, bool ENTRIES>
-__global__ void __launch_bounds__(kBucketThreads)
+__global__ void __launch_bounds__(kBucketThreads, HPEEL_BUCKET_BLOCKS)
 k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
                const uint2 *__restrict__ claims, uint32_t claim_cap, BucketGeom g, uint32_t C,
                uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov, Ctl *ctl) {
@@ -573,7 +579,7 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     // claims of one round: at most the degree-1 vertices of round 0 (a
     // fraction lambda e^-lambda <= 1/e of the vertices for random graphs)
     p.claim_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0u, m * 38 / 100 + 4096);
-    p.regions = (uint32_t)std::max<int>(1, sms);  // one bucketing block per SM
+    p.regions = (uint32_t)std::max<int>(1, sms * HPEEL_BUCKET_BLOCKS);  // one wave of blocks
     // updates, by vertex: the build's chunks and sub-buckets
     p.vg = BucketGeom{(uint32_t)P, b.shift, b.chunks_per_part, 0, kFillShift};
     p.vchunks = b.chunks;
