@@ -432,14 +432,17 @@ void launch_round0(const Launch &L, uint32_t r, bool gen, const RoundParams *prm
 // lane-strided, and issues every atomic of its kRoundU edges before it
 // consumes any result: more memory requests in flight per thread.
 #ifndef HPEEL_ROUND_U
-#define HPEEL_ROUND_U 4
+#define HPEEL_ROUND_U 2
 #endif
 // r = 4 carries more registers per edge: two edges per thread
 template <int R>
 constexpr int round_u() { return R == 4 ? 2 : HPEEL_ROUND_U; }
 
+#ifndef HPEEL_ROUND_MIN_BLOCKS
+#define HPEEL_ROUND_MIN_BLOCKS 3
+#endif
 template <int R, bool GEN>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, HPEEL_ROUND_MIN_BLOCKS)
 k_round(const RoundParams *__restrict__ prm, cudaGraphConditionalHandle cond) {
     constexpr int kRoundU = round_u<R>();
     uint4 *__restrict__ Lw = prm->L;
