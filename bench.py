@@ -115,7 +115,7 @@ NCU_TRAFFIC = {
     # step: (source files, sha256 prefix, bytes per unit, where measured)
     "rounds": (("paper_1312_0526_gb300/csrc/peel.cu",
                 "paper_1312_0526_gb300/csrc/rounds_bucketed.cu",
-                "paper_1312_0526_gb300/csrc/build.cu"), "c676189843cc709d", 325.51,
+                "paper_1312_0526_gb300/csrc/build.cu"), "6bceb22fe8d56b6d", 324.96,
                "every round kernel (sorted round 0 and L_0, random k_round) of one peel at "
                "n = 3e7 (host round loop), scaled by peeled edges"),
 }
@@ -259,13 +259,12 @@ def roofline_of(prof, steps, n, m, st, round_loop):
     """Roofline of the step with the largest live CUDA-event total."""
     peak, peak_kind = measured_peaks()
     prof = dict(prof)
-    if round_loop == "host":
-        # the host loop times round 0, the sorted rounds and the random rounds
-        # apart; the byte model covers all of them, the graph loop's one scope
-        for part in ("round0", "rounds_sorted"):
-            if part in prof and "rounds" in prof:
-                c, t = prof.pop(part)[:2]
-                prof["rounds"] = [prof["rounds"][0] + c, prof["rounds"][1] + t]
+    # the host loop times round 0, the sorted rounds and the random rounds
+    # apart; the byte model covers all of them, as the graph loop's one scope
+    for part in ("round0", "rounds_sorted"):
+        if part in prof and "rounds" in prof:
+            c, t = prof.pop(part)[:2]
+            prof["rounds"] = [prof["rounds"][0] + c, prof["rounds"][1] + t]
     ranked = sorted(((v[1], k) for k, v in prof.items()), reverse=True)
     for tot_ms, name in ranked:
         model = byte_model(name, n, m, st)
