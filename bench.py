@@ -371,8 +371,8 @@ def peel_e2e(edges, m, ws, ref, steps, sync_all, max_over_ranks):
 
 def mphf_leg(n, steps, warmup, rank):
     """The MWHC MPHF build (hpeel_mphf_build: hash, incidence, peel,
-    canonical order, g assignment, rank directory) of n = 1e8 keys (BASELINE
-    configs[1]), keys device-resident; and end to end with each step's keys
+    canonical order, g assignment, rank directory) of n = 1e8 keys, keys
+    device-resident; and end to end with each step's keys
     copied from pinned host memory (double-buffered on a copy stream) and
     the g values and rank directory read back."""
     import numpy as np
@@ -471,7 +471,7 @@ def mphf_leg(n, steps, warmup, rank):
 
 
 def stress_leg(steps=2, warmup=1):
-    """The other plain-peel stress configurations (BASELINE configs[2]): n =
+    """The other plain-peel stress configurations: n =
     1e9 at gamma 1.222 (near the threshold, many rounds) and 1.20 (below it:
     a 2-core is left), and r = 4 at n = 1e8, gamma 1.30; hpeel_peel from
     device-resident edges."""
