@@ -116,7 +116,7 @@ NCU_TRAFFIC = {
     "rounds": (("paper_1312_0526_gb300/csrc/peel.cu",
                 "paper_1312_0526_gb300/csrc/rounds_bucketed.cu",
                 "paper_1312_0526_gb300/csrc/build.cu"), "6bceb22fe8d56b6d", 324.96,
-               "every round kernel (sorted round 0 and L_0, random k_round) of one peel at "
+               "every round kernel (sorted round 0 and L_0..L_2, random k_round) of one peel at "
                "n = 3e7 (host round loop), scaled by peeled edges"),
 }
 
