@@ -1219,7 +1219,7 @@ def main():
 
     e2e = None
     if "e2e" in legs:
-        e2e_steps = max(1, min(args.steps, 10))
+        e2e_steps = max(1, min(args.steps, 30))  # the copy pipeline fills once per run
         e2e_ms, same = peel_e2e(edges, m, ws, ref, e2e_steps, sync_all, max_over_ranks)
         e2e = {"value": aggregate_medges(n, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": 4 * R * n, "d2h_bytes_per_step": 8 * n,
