@@ -20,7 +20,7 @@
 // incidence lists one part at a time): position j's incidences are bucketed
 // and applied in pass j, so the buckets hold one incidence per edge instead
 // of r.  Capacities cover the expected load with a wide margin; an incidence
-// that finds its region full goes to an overflow list applied with direct
+// that finds its chunk's array full goes to an overflow list applied with direct
 // updates, and when that list is full as well the build reports it and is
 // redone with direct updates (same result), so any input is handled.
 #include <algorithm>
@@ -44,7 +44,7 @@ __device__ __forceinline__ uint32_t chunk_of(uint32_t v, uint32_t j, const Bucke
     return part * g.chunks_per_part + ((v - part * g.P) >> g.shift);
 }
 
-// An incidence that finds its region full goes to the overflow list, applied
+// An incidence that finds its chunk's array full goes to the overflow list, applied
 // after everything else; when the list itself is full the build fails with
 // kDevBuildOverflow and the host redoes it with direct updates.
 __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
@@ -222,11 +222,11 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
     }
 }
 
-// Refine: the pairs of each chunk (all its regions) are counting-sorted in
+// Refine: the pairs of each chunk's array are counting-sorted in
 // shared memory, a tile of kRefineTile slots at a time, into 2^(shift -
 // sub_shift) sub-buckets of 2^sub_shift vertices; each tile's run of a
 // sub-bucket is appended to it with one atomicAdd on its cursor.  One
-// resident wave of blocks strides over all (chunk, tile) items; the next
+// resident wave of blocks strides over the filled (chunk, tile) items; the next
 // item's pairs are loaded into registers while the current one is sorted
 // and written, so the load latency overlaps the work.
 #ifndef HPEEL_REFINE_THREADS

@@ -119,7 +119,7 @@ struct Overflow {
 };
 
 // Geometry of one bucketing: part size, log2 of the keys per chunk, chunks
-// per part, region capacity.
+// per part, chunk capacity, fill-counter stride.
 struct BucketGeom {
     uint32_t P;                // part size
     uint32_t shift;            // log2 of the vertices per chunk
@@ -170,7 +170,7 @@ struct SortedPlan {
     bool enabled;
     uint32_t min_edges, max_edges;  // layers deleted in sorted form
     uint32_t claim_cap;             // claims one round may make
-    uint32_t regions;               // blocks of the bucketing pass
+    uint32_t bucket_blocks;         // blocks of the bucketing pass
     BucketGeom vg;                  // updates by vertex (parts, chunks)
     uint32_t vchunks, vsub_shift, vsubs, vcap2;
     BucketGeom eg;                  // claims by edge (one part of n edges)

@@ -579,7 +579,7 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     // claims of one round: at most the degree-1 vertices of round 0 (a
     // fraction lambda e^-lambda <= 1/e of the vertices for random graphs)
     p.claim_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0u, m * 38 / 100 + 4096);
-    p.regions = (uint32_t)std::max<int>(1, sms * HPEEL_BUCKET_BLOCKS);  // one wave of blocks
+    p.bucket_blocks = (uint32_t)std::max<int>(1, sms * HPEEL_BUCKET_BLOCKS);  // one wave of blocks
     // updates, by vertex: the build's chunks and sub-buckets
     p.vg = BucketGeom{(uint32_t)P, b.shift, b.chunks_per_part, 0, kFillShift};
     p.vchunks = b.chunks;
@@ -589,7 +589,7 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     // (share: the part of the pairs that the largest chunk receives; a
     // part's last chunk is partial, so a full chunk gets more than an even
     // split)
-    auto region_cap = [&](uint64_t items, uint32_t per_item, double share) {
+    auto chunk_cap = [&](uint64_t items, uint32_t per_item, double share) {
         const uint64_t all = items * per_item;
         const double e = (double)all * std::min(1.0, share);
         return (uint32_t)std::min<uint64_t>((uint64_t)(e + 8.0 * std::sqrt(e + 1.0) + 64.0),
@@ -597,7 +597,7 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     };
     // a part holds about a third of the updates (0.4 leaves room for the
     // hinge positions' skew)
-    p.vg.cap = region_cap(p.max_edges, 2, 0.4 * (double)(1ull << b.shift) / (double)P);
+    p.vg.cap = chunk_cap(p.max_edges, 2, 0.4 * (double)(1ull << b.shift) / (double)P);
     const double e2 = 2.0 * p.max_edges * 0.4 * (double)(1ull << p.vsub_shift) / (double)P;
     p.vcap2 = (uint32_t)std::min<uint64_t>((uint64_t)(e2 + 8.0 * std::sqrt(e2 + 1.0) + 256.0),
                                            2ull * p.max_edges);
@@ -609,7 +609,7 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
                       kFillShift};
     p.echunks = p.eg.chunks_per_part;
     p.esubs = p.echunks << (p.eshift - p.esub);
-    p.eg.cap = region_cap(p.claim_cap, 1, (double)(1ull << p.eshift) / (double)n);
+    p.eg.cap = chunk_cap(p.claim_cap, 1, (double)(1ull << p.eshift) / (double)n);
     const double c2 = (double)p.claim_cap * (double)(1ull << p.esub) / (double)n;
     p.ecap2 = (uint32_t)std::min<uint64_t>((uint64_t)(c2 + 8.0 * std::sqrt(c2 + 1.0) + 256.0),
                                            p.claim_cap);
@@ -640,7 +640,7 @@ void launch_sorted_claims(const Launch &L, const SortedPlan &p, const SortedBufs
     BucketGeom eg = p.eg;
     set_smem((const void *)k_pairs_bucket<3, false>, p.bucket_smem);
     count_launch();
-    k_pairs_bucket<3, false><<<p.regions, kBucketThreads, p.bucket_smem, L.stream>>>(
+    k_pairs_bucket<3, false><<<p.bucket_blocks, kBucketThreads, p.bucket_smem, L.stream>>>(
         nullptr, nullptr, w.claims, p.claim_cap, eg, p.echunks, w.pairs, w.fill, none, ctl);
     launch_refine(L, eg, p.echunks, 0, p.esub, w.pairs, w.fill, w.pairs2, w.fill2,
                   p.ecap2, none, ctl);
@@ -676,7 +676,7 @@ void launch_sorted_round(const Launch &L, const SortedPlan &p, const SortedBufs 
     BucketGeom vg = p.vg;
     set_smem((const void *)k_pairs_bucket<3, true>, p.bucket_smem);
     count_launch();
-    k_pairs_bucket<3, true><<<p.regions, kBucketThreads, p.bucket_smem, L.stream>>>(
+    k_pairs_bucket<3, true><<<p.bucket_blocks, kBucketThreads, p.bucket_smem, L.stream>>>(
         Lst, loff, nullptr, 0, vg, p.vchunks, w.pairs, w.fill, none, ctl);
     launch_refine(L, vg, p.vchunks, 0, p.vsub_shift, w.pairs, w.fill, w.pairs2, w.fill2,
                   p.vcap2, none, ctl);
