@@ -82,7 +82,6 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
     uint32_t *cur = hist + Cp;        // C: the run's place in its chunk minus its stage slot
     uint32_t *toff = cur + Cp;        // C: start of the chunk's run in stage
     uint2 *stage = reinterpret_cast<uint2 *>(toff + Cp);  // R per edge (8-byte aligned: Cp even)
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 
     const uint64_t tiles = ((uint64_t)n + kTileEdges - 1) / kTileEdges;
     // the next tile's input (keys, or rows) is loaded while this one is
@@ -165,8 +164,10 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
             const uint32_t h = hist[c];
             cur[c] = h ? atomicAdd(fill + ((size_t)c << g.fill_shift), h) : 0u;
         }
-        // exclusive scan of hist -> toff (warp 0, 32 chunks per step)
-        if (warp == 0) {
+        // exclusive scan of hist -> toff (warp 0, 32 chunks per step; the
+        // other warps' cursor reservations are in flight meanwhile)
+        if (threadIdx.x < 32) {
+            const uint32_t lane = threadIdx.x;
             uint32_t run = 0;
             for (uint32_t c0 = 0; c0 < C; c0 += 32) {
                 const uint32_t c = c0 + lane;
@@ -333,17 +334,14 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
         for (uint32_t b = threadIdx.x; b < S; b += kRefThreads) hist[b] = 0;
         __syncthreads();
         uint32_t rk[kRefineItems];
-        bool ok[kRefineItems];
+        uint32_t bq[kRefineItems];  // sub-bucket of each pair, S for none
 #pragma unroll
         for (int q = 0; q < kRefineItems; q++) {
             const uint32_t i = (uint32_t)q * kRefThreads + threadIdx.x;
-            ok[q] = i < tn;
+            bq[q] = i < tn ? (p[q].x - base_v) >> sub_shift : S;
             // a pair outside the chunk (inconsistent input) is dropped with an error
-            if (ok[q] && ((p[q].x - base_v) >> sub_shift) >= S) {
-                raise_err(ctl, kDevBadVertex);
-                ok[q] = false;
-            }
-            rk[q] = ok[q] ? atomicAdd(&hist[(p[q].x - base_v) >> sub_shift], 1u) : 0u;
+            if (i < tn && bq[q] >= S) raise_err(ctl, kDevBadVertex);
+            rk[q] = bq[q] < S ? atomicAdd(&hist[bq[q]], 1u) : 0u;
         }
         __syncthreads();
         // reserve each sub-bucket's run with one atomicAdd on its cursor;
@@ -370,8 +368,15 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             }
             if (lane == 31) wsum[warp] = x;
             __syncthreads();
-            uint32_t run = x - loc;
-            for (uint32_t w = 0; w < warp; w++) run += wsum[w];
+            // the totals of the warps before this one: a shuffle prefix
+            uint32_t wx = lane < kRefWarps ? wsum[lane] : 0u;
+#pragma unroll
+            for (int d = 1; d < (int)kRefWarps; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wx, d);
+                if (lane >= (uint32_t)d) wx += y;
+            }
+            const uint32_t before = __shfl_sync(0xFFFFFFFFu, wx, (warp + 31u) & 31u);
+            uint32_t run = x - loc + (warp ? before : 0u);
             for (uint32_t q = 0; q < per; q++) {
                 const uint32_t b = b0 + q;
                 if (b < S) {
@@ -382,12 +387,8 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kRefineItems; q++) {
-            if (!ok[q]) continue;
-            const uint32_t b = (p[q].x - base_v) >> sub_shift;
-            const uint32_t slot = toff[b] + rk[q];
-            stage[slot] = p[q];
-        }
+        for (int q = 0; q < kRefineItems; q++)
+            if (bq[q] < S) stage[toff[bq[q]] + rk[q]] = p[q];
         // gbase[b] = cursor - first stage slot of the run: a staged pair at
         // slot k goes to position gbase[b] + k of its sub-bucket
 #pragma unroll

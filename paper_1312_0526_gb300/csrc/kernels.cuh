@@ -118,6 +118,46 @@ struct Overflow {
     uint32_t code = kDevBuildOverflow;
 };
 
+// Exclusive prefix sum of h[0 .. count) into out[0 .. count) by the whole
+// block (THREADS threads, each taking ceil(count / THREADS) consecutive
+// entries: a warp shuffle scan, then one over the warps' totals).  Every
+// thread calls it; the block is synchronised on return.
+template <int THREADS>
+__device__ __forceinline__ void block_scan_counts(const uint32_t *h, uint32_t *out,
+                                                  uint32_t count) {
+    constexpr int kW = THREADS / 32;
+    __shared__ uint32_t ws[kW];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t per = (count + THREADS - 1) / THREADS, c0 = threadIdx.x * per;
+    uint32_t loc = 0;
+    for (uint32_t q = 0; q < per; q++)
+        if (c0 + q < count) loc += h[c0 + q];
+    uint32_t x = loc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= (uint32_t)d) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    uint32_t wx = lane < (uint32_t)kW ? ws[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < kW; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wx, d);
+        if (lane >= (uint32_t)d) wx += y;
+    }
+    const uint32_t before = __shfl_sync(0xFFFFFFFFu, wx, (warp + 31u) & 31u);
+    uint32_t run = x - loc + (warp ? before : 0u);
+    for (uint32_t q = 0; q < per; q++) {
+        const uint32_t c = c0 + q;
+        if (c < count) {
+            out[c] = run;
+            run += h[c];
+        }
+    }
+    __syncthreads();
+}
+
 // Geometry of one bucketing: part size, log2 of the keys per chunk, chunks
 // per part, chunk capacity, fill-counter stride.
 struct BucketGeom {

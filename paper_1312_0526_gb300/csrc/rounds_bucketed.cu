@@ -156,7 +156,6 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
     uint32_t *cur = hist + Cp;                             // C: run's place - its stage slot
     uint32_t *toff = cur + Cp;                             // C: run's first stage slot
     uint2 *stage = reinterpret_cast<uint2 *>(toff + Cp);   // kPer per item (8-byte aligned)
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t i0, i1;
     if (ENTRIES) {
         const uint32_t t = *(volatile uint32_t *)&ctl->round;
@@ -215,22 +214,7 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
             const uint32_t h = hist[c];
             cur[c] = h ? atomicAdd(fill + ((size_t)c << g.fill_shift), h) : 0u;
         }
-        if (warp == 0) {  // exclusive scan of hist -> toff, 32 chunks per step
-            uint32_t run = 0;
-            for (uint32_t c0 = 0; c0 < C; c0 += 32) {
-                const uint32_t c = c0 + lane;
-                const uint32_t h = c < C ? hist[c] : 0u;
-                uint32_t x = h;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-                    if (lane >= (uint32_t)d) x += y;
-                }
-                if (c < C) toff[c] = run + x - h;
-                run += __shfl_sync(0xFFFFFFFFu, x, 31);
-            }
-        }
-        __syncthreads();
+        block_scan_counts<kBucketThreads>(hist, toff, C);  // exclusive scan of hist -> toff
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             if (!ok[q]) continue;
