@@ -31,10 +31,14 @@
 namespace hp {
 
 #ifndef HPEEL_RB_TILE
-#define HPEEL_RB_TILE 1024
+#define HPEEL_RB_TILE 2048
 #endif
 constexpr int kTileEdges = HPEEL_RB_TILE;  // edges per block step
-constexpr int kTileU = kTileEdges / kThreads;  // edges per thread and step
+#ifndef HPEEL_RB_THREADS
+#define HPEEL_RB_THREADS 512
+#endif
+constexpr int kRbThreads = HPEEL_RB_THREADS;     // threads of a record-pass block
+constexpr int kTileU = kTileEdges / kRbThreads;  // edges per thread and step
 
 // Chunk of vertex v at position j: chunks never straddle the parts of an
 // r-partite graph; a general graph (GEN) is one part [0, P = m).
@@ -56,11 +60,11 @@ __device__ __forceinline__ void overflow_push(uint2 p, Overflow ov, Ctl *ctl) {
 }
 
 #ifndef HPEEL_RB_MIN_BLOCKS
-#define HPEEL_RB_MIN_BLOCKS 4
+#define HPEEL_RB_MIN_BLOCKS 2
 #endif
 constexpr uint32_t kCurRegs = 2;  // chunk cursors per thread held in registers
 template <int R, bool FROM_KEYS, bool GEN>
-__global__ void __launch_bounds__(kThreads, HPEEL_RB_MIN_BLOCKS)
+__global__ void __launch_bounds__(kRbThreads, HPEEL_RB_MIN_BLOCKS)
 k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ rows,
                    uint32_t n, FastMod fm, uint64_t seed, const uint64_t *seed_dev, BucketGeom g,
                    uint4 *__restrict__ rec,
@@ -90,7 +94,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
     auto load_input = [&](uint64_t tile, uint32_t (&in)[kTileU][kWords]) {
 #pragma unroll
         for (int q = 0; q < kTileU; q++) {
-            const uint64_t e = tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x;
+            const uint64_t e = tile * kTileEdges + (uint64_t)q * kRbThreads + threadIdx.x;
 #pragma unroll
             for (int w = 0; w < kWords; w++) in[q][w] = 0;
             if (e < n) {
@@ -115,13 +119,13 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 #pragma unroll
             for (int w = 0; w < kWords; w++) in[q][w] = next_in[q][w];
         if (tile + gridDim.x < tiles) load_input(tile + gridDim.x, next_in);
-        for (uint32_t c = threadIdx.x; c < C; c += kThreads) hist[c] = 0;
+        for (uint32_t c = threadIdx.x; c < C; c += kRbThreads) hist[c] = 0;
         __syncthreads();
         uint32_t vv[kTileU][R], rank[kTileU][R];
         bool inc[kTileU];
 #pragma unroll
         for (int q = 0; q < kTileU; q++) {
-            const uint64_t e = tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x;
+            const uint64_t e = tile * kTileEdges + (uint64_t)q * kRbThreads + threadIdx.x;
             uint32_t v[4] = {0, 0, 0, 0};
             bool ok = e < n;
             if (ok) {
@@ -157,10 +161,10 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
         uint32_t gb[kCurRegs];
 #pragma unroll
         for (uint32_t q = 0; q < kCurRegs; q++) {
-            const uint32_t c = q * kThreads + threadIdx.x, h = c < C ? hist[c] : 0u;
+            const uint32_t c = q * kRbThreads + threadIdx.x, h = c < C ? hist[c] : 0u;
             gb[q] = h ? atomicAdd(fill + ((size_t)c << g.fill_shift), h) : 0u;
         }
-        for (uint32_t c = kCurRegs * kThreads + threadIdx.x; c < C; c += kThreads) {
+        for (uint32_t c = kCurRegs * kRbThreads + threadIdx.x; c < C; c += kRbThreads) {
             const uint32_t h = hist[c];
             cur[c] = h ? atomicAdd(fill + ((size_t)c << g.fill_shift), h) : 0u;
         }
@@ -186,7 +190,7 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
 #pragma unroll
         for (int q = 0; q < kTileU; q++) {
             if (!inc[q]) continue;
-            const uint32_t e = (uint32_t)(tile * kTileEdges + (uint64_t)q * kThreads + threadIdx.x);
+            const uint32_t e = (uint32_t)(tile * kTileEdges + (uint64_t)q * kRbThreads + threadIdx.x);
 #pragma unroll
             for (int j = 0; j < R; j++) {
                 if (!in_pass(j)) continue;
@@ -199,15 +203,15 @@ k_records_bucketed(const uint64_t *__restrict__ keys, const uint32_t *__restrict
         // (mod 2^32): staged pair k of chunk c goes to place cur[c] + k
 #pragma unroll
         for (uint32_t q = 0; q < kCurRegs; q++) {
-            const uint32_t c = q * kThreads + threadIdx.x;
+            const uint32_t c = q * kRbThreads + threadIdx.x;
             if (c < C) cur[c] = gb[q] - toff[c];
         }
-        for (uint32_t c = kCurRegs * kThreads + threadIdx.x; c < C; c += kThreads)
+        for (uint32_t c = kCurRegs * kRbThreads + threadIdx.x; c < C; c += kRbThreads)
             cur[c] -= toff[c];
         __syncthreads();
         // write the staged runs: consecutive slots -> consecutive addresses
         const uint32_t total = toff[C - 1] + hist[C - 1];
-        for (uint32_t k = threadIdx.x; k < total; k += kThreads) {
+        for (uint32_t k = threadIdx.x; k < total; k += kRbThreads) {
             const uint2 p = stage[k];
             // its chunk again, from the vertex (an r-partite graph's part
             // follows from the vertex id)
@@ -598,7 +602,7 @@ void launch_build_bucketed(const Launch &L, const BucketPlan &b, const uint64_t 
         auto kern = gen ? k_records_bucketed<RR, FK, true> : k_records_bucketed<RR, FK, false>; \
         smem_optin((const void *)kern);                                                      \
         count_launch();                                                                       \
-        kern<<<grid, kThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, seed_dev, g, rec,  \
+        kern<<<grid, kRbThreads, b.smem, L.stream>>>(keys, rows, n, fm, seed, seed_dev, g, rec,\
                                                    pairs, fill, ov, ctl, pass_part);          \
     } while (0)
     if (keys) {
