@@ -16,9 +16,9 @@
 //   scatter -- each warp ranks its 512 inputs in input order (the lanes
 //              holding the same bin, found with one ballot per bit of the
 //              bin, plus per-warp running counts), so equal keys keep the
-//              input order: the sort is stable.  The tile's ids are staged
-//              in shared memory in (bin, input) order, so each bin's run of
-//              the tile leaves as one contiguous, coalesced stretch.
+//              input order: the sort is stable.  The tile's inputs are
+//              staged in shared memory in (bin, input) order, so each bin's
+//              run of the tile leaves as one contiguous, coalesced stretch.
 #include "kernels.cuh"
 
 namespace hp {
@@ -31,19 +31,19 @@ __device__ __forceinline__ uint32_t emit_bin(uint32_t c, uint32_t base, uint32_t
 }
 
 // Lanes of the warp holding the same bin (valid lanes only): one ballot per
-// bit of the bin index (planes = bits of nbins - 1), instead of a match.
-__device__ __forceinline__ uint32_t bin_peers(uint32_t bin, bool valid, int planes) {
+// bit of the bin index, for a bin below 2^PLANES, instead of a match.  More
+// planes than the bins need give the same mask (the extra bits are 0 in
+// every lane).
+template <int PLANES>
+__device__ __forceinline__ uint32_t bin_peers(uint32_t bin, bool valid) {
     uint32_t m = __ballot_sync(0xFFFFFFFFu, valid);
-    for (int b = 0; b < planes; b++) {
+#pragma unroll
+    for (int b = 0; b < PLANES; b++) {
         const bool bit = (bin >> b) & 1u;
         const uint32_t x = __ballot_sync(0xFFFFFFFFu, bit);
         m &= bit ? x : ~x;
     }
     return valid ? m : 0u;
-}
-
-__device__ __forceinline__ int bin_planes(uint32_t nbins) {
-    return nbins > 1 ? 32 - __clz(nbins - 1) : 0;
 }
 
 __device__ __forceinline__ void emit_hist(const uint32_t *__restrict__ src, uint32_t count,
@@ -138,40 +138,56 @@ void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, cons
 #ifndef HPEEL_SCATTER_MIN_BLOCKS
 #define HPEEL_SCATTER_MIN_BLOCKS 4
 #endif
-__device__ __forceinline__ void emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
-                                             const uint32_t *__restrict__ claim, uint32_t base,
-                                             uint32_t core_key, uint32_t nbins,
-                                             const uint32_t *__restrict__ offs,
-                                             uint32_t *__restrict__ out) {
-    __shared__ uint32_t wc[kEmitWarps][kEmitBins];  // per warp and bin: count, then slot
-    __shared__ uint32_t obase[kEmitBins];            // output index of tile slot 0 of the bin
-    __shared__ uint32_t stage[kEmitTile];            // the tile's edge ids, ordered by bin
-    __shared__ uint8_t sbin[kEmitTile];              // bin of each staged id
+struct ScatterSmem {
+    uint32_t wc[kEmitWarps][kEmitBins];  // per warp and bin: count, then first slot
+    uint32_t obase[kEmitBins];           // output index of tile slot 0 of the bin
+    uint32_t stage[kEmitTile];           // (bin << 16) | tile index, ordered by bin
+};
+static_assert(kEmitTile <= 65536u && kEmitBins <= 65536u, "stage word packs bin and index");
+
+// One tile: each warp ranks its 512 inputs in input order.  The count pass
+// gives every input its rank among the warp's inputs of its bin (the warp's
+// running count of the bin before its group of 32, plus the peers in lower
+// lanes); after the scan the input goes to its bin's first slot for the
+// warp plus that rank, so equal keys keep the input order.
+template <int PLANES, bool SRC>
+__device__ __forceinline__ void emit_scatter_t(ScatterSmem &sm, const uint32_t *__restrict__ src,
+                                               uint32_t count, const uint32_t *__restrict__ claim,
+                                               uint32_t base, uint32_t core_key, uint32_t nbins,
+                                               const uint32_t *__restrict__ offs,
+                                               uint32_t *__restrict__ out) {
     const uint32_t tiles = (count + kEmitTile - 1) / kEmitTile;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     // bins past nbins hold no input: the counts and the scan stop at the
     // first multiple of 32 at or above nbins
     const uint32_t nb32 = (nbins + 31u) & ~31u;
-    for (uint32_t b = lane; b < nb32; b += 32) wc[warp][b] = 0;
+    uint32_t *wc = sm.wc[warp];
+    for (uint32_t b = lane; b < nb32; b += 32) wc[b] = 0;
     __syncwarp();
     // this warp's contiguous run of the tile, kEmitItems groups of 32
     const uint64_t t0 = (uint64_t)blockIdx.x * kEmitTile;
-    const uint64_t w0 = t0 + (uint64_t)warp * 32 * kEmitItems;
-    uint32_t bin[kEmitItems], eid[kEmitItems], peers[kEmitItems];
-    const int planes = bin_planes(nbins);
+    const uint32_t w0 = warp * 32u * kEmitItems;  // index in the tile
+    // br[g]: the input's bin, then (bin << 16) | rank; ~0 past the end
+    uint32_t br[kEmitItems];
 #pragma unroll
     for (int g = 0; g < kEmitItems; g++) {
-        const uint64_t i = w0 + (uint64_t)g * 32 + lane;
+        const uint64_t i = t0 + w0 + (uint32_t)g * 32u + lane;
         const bool valid = i < count;
-        eid[g] = valid ? (src ? src[i] : (uint32_t)i) : 0u;
-        bin[g] = valid ? emit_bin(claim[eid[g]], base, core_key, nbins) : 0xFFFFFFFFu;
+        const uint32_t e = valid ? (SRC ? src[i] : (uint32_t)i) : 0u;
+        br[g] = valid ? emit_bin(claim[e], base, core_key, nbins) : 0xFFFFFFFFu;
     }
 #pragma unroll
     for (int g = 0; g < kEmitItems; g++) {
-        const bool valid = bin[g] != 0xFFFFFFFFu;
-        peers[g] = bin_peers(valid ? bin[g] : 0u, valid, planes);
-        if (valid && lane == (uint32_t)(__ffs(peers[g]) - 1)) wc[warp][bin[g]] += __popc(peers[g]);
+        const uint32_t bin = br[g];
+        const bool valid = bin != 0xFFFFFFFFu;
+        const uint32_t peers = bin_peers<PLANES>(valid ? bin : 0u, valid);
+        const uint32_t below = __popc(peers & lt);
+        const uint32_t before = valid ? wc[bin] : 0u;
+        if (valid) br[g] = (bin << 16) | (before + below);  // rank < 512
+        __syncwarp();
+        // the lowest lane of each bin moves the bin's running count
+        if (valid && below == 0u) wc[bin] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -184,8 +200,8 @@ __device__ __forceinline__ void emit_scatter(const uint32_t *__restrict__ src, u
             uint32_t tot = 0;
 #pragma unroll
             for (int w = 0; w < kEmitWarps; w++) {
-                const uint32_t c = wc[w][b];
-                wc[w][b] = tot;  // exclusive over warps, relative to the bin start
+                const uint32_t c = sm.wc[w][b];
+                sm.wc[w][b] = tot;  // exclusive over warps, relative to the bin start
                 tot += c;
             }
             uint32_t x = tot;
@@ -196,31 +212,63 @@ __device__ __forceinline__ void emit_scatter(const uint32_t *__restrict__ src, u
             }
             const uint32_t start = run + x - tot;
 #pragma unroll
-            for (int w = 0; w < kEmitWarps; w++) wc[w][b] += start;
-            obase[b] = b < nbins ? offs[(uint64_t)b * tiles + blockIdx.x] - start : 0u;
+            for (int w = 0; w < kEmitWarps; w++) sm.wc[w][b] += start;
+            sm.obase[b] = b < nbins ? offs[(uint64_t)b * tiles + blockIdx.x] - start : 0u;
             run += __shfl_sync(0xFFFFFFFFu, x, 31);
         }
     }
     __syncthreads();
-    // stage the ids in bin order, input order inside a bin
+    // stage the inputs in bin order, input order inside a bin
 #pragma unroll
-    for (int g = 0; g < kEmitItems; g++) {
-        if (bin[g] != 0xFFFFFFFFu) {
-            const uint32_t slot = wc[warp][bin[g]] + __popc(peers[g] & lt);
-            stage[slot] = eid[g];
-            sbin[slot] = (uint8_t)bin[g];
-        }
-        __syncwarp();
-        if (bin[g] != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers[g]) - 1))
-            wc[warp][bin[g]] += __popc(peers[g]);
-        __syncwarp();
-    }
+    for (int g = 0; g < kEmitItems; g++)
+        if (br[g] != 0xFFFFFFFFu)
+            sm.stage[wc[br[g] >> 16] + (br[g] & 0xFFFFu)] =
+                (br[g] & 0xFFFF0000u) | (w0 + (uint32_t)g * 32u + lane);
     __syncthreads();
     // each bin's run of the tile is one contiguous stretch of the output:
     // consecutive threads write consecutive addresses
     const uint64_t left = (uint64_t)count - t0;
     const uint32_t tn = left < kEmitTile ? (uint32_t)left : kEmitTile;
-    for (uint32_t k = threadIdx.x; k < tn; k += kThreads) out[obase[sbin[k]] + k] = stage[k];
+#pragma unroll
+    for (int q = 0; q < kEmitItems; q++) {
+        const uint32_t k = (uint32_t)q * kThreads + threadIdx.x;
+        if (k < tn) {
+            const uint32_t s = sm.stage[k];
+            const uint64_t i = t0 + (s & 0xFFFFu);
+            out[sm.obase[s >> 16] + k] = SRC ? src[i] : (uint32_t)i;
+        }
+    }
+}
+
+// Ballot planes for the pass's bins (2, 4, 6, 7 or 8), and whether the
+// inputs are edge ids read from src or the tile's own indices.
+template <bool SRC>
+__device__ __forceinline__ void emit_scatter_src(ScatterSmem &sm, const uint32_t *src,
+                                                 uint32_t count, const uint32_t *claim,
+                                                 uint32_t base, uint32_t core_key, uint32_t nbins,
+                                                 const uint32_t *offs, uint32_t *out) {
+    if (nbins <= 4)
+        emit_scatter_t<2, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+    else if (nbins <= 16)
+        emit_scatter_t<4, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+    else if (nbins <= 64)
+        emit_scatter_t<6, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+    else if (nbins <= 128)
+        emit_scatter_t<7, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+    else
+        emit_scatter_t<8, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+}
+
+__device__ __forceinline__ void emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
+                                             const uint32_t *__restrict__ claim, uint32_t base,
+                                             uint32_t core_key, uint32_t nbins,
+                                             const uint32_t *__restrict__ offs,
+                                             uint32_t *__restrict__ out) {
+    __shared__ ScatterSmem sm;
+    if (src)
+        emit_scatter_src<true>(sm, src, count, claim, base, core_key, nbins, offs, out);
+    else
+        emit_scatter_src<false>(sm, src, count, claim, base, core_key, nbins, offs, out);
 }
 
 __global__ void __launch_bounds__(kThreads, HPEEL_SCATTER_MIN_BLOCKS)
