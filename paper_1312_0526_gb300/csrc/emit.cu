@@ -136,7 +136,7 @@ void launch_emit_hist(const Launch &L, const uint32_t *src, uint32_t count, cons
 }
 
 #ifndef HPEEL_SCATTER_MIN_BLOCKS
-#define HPEEL_SCATTER_MIN_BLOCKS 4
+#define HPEEL_SCATTER_MIN_BLOCKS 6
 #endif
 struct ScatterSmem {
     uint32_t wc[kEmitWarps][kEmitBins];  // per warp and bin: count, then first slot
