@@ -34,16 +34,16 @@ __device__ __forceinline__ uint32_t emit_bin(uint32_t c, uint32_t base, uint32_t
 // bit of the bin index, for a bin below 2^PLANES, instead of a match.  More
 // planes than the bins need give the same mask (the extra bits are 0 in
 // every lane).
-template <int PLANES>
+template <int PLANES, bool FULL>
 __device__ __forceinline__ uint32_t bin_peers(uint32_t bin, bool valid) {
-    uint32_t m = __ballot_sync(0xFFFFFFFFu, valid);
+    uint32_t m = FULL ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
 #pragma unroll
     for (int b = 0; b < PLANES; b++) {
         const bool bit = (bin >> b) & 1u;
         const uint32_t x = __ballot_sync(0xFFFFFFFFu, bit);
         m &= bit ? x : ~x;
     }
-    return valid ? m : 0u;
+    return FULL || valid ? m : 0u;
 }
 
 __device__ __forceinline__ void emit_hist(const uint32_t *__restrict__ src, uint32_t count,
@@ -149,8 +149,9 @@ static_assert(kEmitTile <= 65536u && kEmitBins <= 65536u, "stage word packs bin 
 // gives every input its rank among the warp's inputs of its bin (the warp's
 // running count of the bin before its group of 32, plus the peers in lower
 // lanes); after the scan the input goes to its bin's first slot for the
-// warp plus that rank, so equal keys keep the input order.
-template <int PLANES, bool SRC>
+// warp plus that rank, so equal keys keep the input order.  FULL: the tile
+// holds kEmitTile inputs (every tile but the last).
+template <int PLANES, bool SRC, bool FULL>
 __device__ __forceinline__ void emit_scatter_t(ScatterSmem &sm, const uint32_t *__restrict__ src,
                                                uint32_t count, const uint32_t *__restrict__ claim,
                                                uint32_t base, uint32_t core_key, uint32_t nbins,
@@ -173,7 +174,7 @@ __device__ __forceinline__ void emit_scatter_t(ScatterSmem &sm, const uint32_t *
 #pragma unroll
     for (int g = 0; g < kEmitItems; g++) {
         const uint64_t i = t0 + w0 + (uint32_t)g * 32u + lane;
-        const bool valid = i < count;
+        const bool valid = FULL || i < count;
         const uint32_t e = valid ? (SRC ? src[i] : (uint32_t)i) : 0u;
         br[g] = valid ? emit_bin(claim[e], base, core_key, nbins) : 0xFFFFFFFFu;
     }
@@ -181,7 +182,7 @@ __device__ __forceinline__ void emit_scatter_t(ScatterSmem &sm, const uint32_t *
     for (int g = 0; g < kEmitItems; g++) {
         const uint32_t bin = br[g];
         const bool valid = bin != 0xFFFFFFFFu;
-        const uint32_t peers = bin_peers<PLANES>(valid ? bin : 0u, valid);
+        const uint32_t peers = bin_peers<PLANES, FULL>(valid ? bin : 0u, valid);
         const uint32_t below = __popc(peers & lt);
         const uint32_t before = valid ? wc[bin] : 0u;
         if (valid) br[g] = (bin << 16) | (before + below);  // rank < 512
@@ -229,10 +230,10 @@ __device__ __forceinline__ void emit_scatter_t(ScatterSmem &sm, const uint32_t *
     // consecutive threads write consecutive addresses
     const uint64_t left = (uint64_t)count - t0;
     const uint32_t tn = left < kEmitTile ? (uint32_t)left : kEmitTile;
-#pragma unroll
+#pragma unroll 4
     for (int q = 0; q < kEmitItems; q++) {
         const uint32_t k = (uint32_t)q * kThreads + threadIdx.x;
-        if (k < tn) {
+        if (FULL || k < tn) {
             const uint32_t s = sm.stage[k];
             const uint64_t i = t0 + (s & 0xFFFFu);
             out[sm.obase[s >> 16] + k] = SRC ? src[i] : (uint32_t)i;
@@ -240,23 +241,24 @@ __device__ __forceinline__ void emit_scatter_t(ScatterSmem &sm, const uint32_t *
     }
 }
 
-// Ballot planes for the pass's bins (2, 4, 6, 7 or 8), and whether the
-// inputs are edge ids read from src or the tile's own indices.
-template <bool SRC>
+// Ballot planes for the pass's bins (2, 4, 6, 7 or 8), whether the inputs
+// are edge ids read from src or the tile's own indices, and whether the
+// tile is full.
+template <bool SRC, bool FULL>
 __device__ __forceinline__ void emit_scatter_src(ScatterSmem &sm, const uint32_t *src,
                                                  uint32_t count, const uint32_t *claim,
                                                  uint32_t base, uint32_t core_key, uint32_t nbins,
                                                  const uint32_t *offs, uint32_t *out) {
     if (nbins <= 4)
-        emit_scatter_t<2, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+        emit_scatter_t<2, SRC, FULL>(sm, src, count, claim, base, core_key, nbins, offs, out);
     else if (nbins <= 16)
-        emit_scatter_t<4, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+        emit_scatter_t<4, SRC, FULL>(sm, src, count, claim, base, core_key, nbins, offs, out);
     else if (nbins <= 64)
-        emit_scatter_t<6, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+        emit_scatter_t<6, SRC, FULL>(sm, src, count, claim, base, core_key, nbins, offs, out);
     else if (nbins <= 128)
-        emit_scatter_t<7, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+        emit_scatter_t<7, SRC, FULL>(sm, src, count, claim, base, core_key, nbins, offs, out);
     else
-        emit_scatter_t<8, SRC>(sm, src, count, claim, base, core_key, nbins, offs, out);
+        emit_scatter_t<8, SRC, FULL>(sm, src, count, claim, base, core_key, nbins, offs, out);
 }
 
 __device__ __forceinline__ void emit_scatter(const uint32_t *__restrict__ src, uint32_t count,
@@ -265,10 +267,19 @@ __device__ __forceinline__ void emit_scatter(const uint32_t *__restrict__ src, u
                                              const uint32_t *__restrict__ offs,
                                              uint32_t *__restrict__ out) {
     __shared__ ScatterSmem sm;
-    if (src)
-        emit_scatter_src<true>(sm, src, count, claim, base, core_key, nbins, offs, out);
-    else
-        emit_scatter_src<false>(sm, src, count, claim, base, core_key, nbins, offs, out);
+    const bool full = (uint64_t)(blockIdx.x + 1) * kEmitTile <= count;
+    if (src) {
+        if (full)
+            emit_scatter_src<true, true>(sm, src, count, claim, base, core_key, nbins, offs, out);
+        else
+            emit_scatter_src<true, false>(sm, src, count, claim, base, core_key, nbins, offs, out);
+    } else {
+        if (full)
+            emit_scatter_src<false, true>(sm, src, count, claim, base, core_key, nbins, offs, out);
+        else
+            emit_scatter_src<false, false>(sm, src, count, claim, base, core_key, nbins, offs,
+                                           out);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, HPEEL_SCATTER_MIN_BLOCKS)
