@@ -139,6 +139,61 @@ __device__ __forceinline__ void raise_err(Ctl *ctl, uint32_t code) {
     atomicCAS(&ctl->err, 0u, code);
 }
 
+// ------------------------------------------------------------ bulk copies --
+// One-dimensional TMA copies (cp.async.bulk) from global into shared memory,
+// completing on an mbarrier (one arrival: the thread that issues the copy
+// and sets the byte count).  Source, destination and size are multiples of
+// 16 bytes.  Waits are bounded: mbar_wait gives up after kMbarTries tries
+// (each try suspends the thread for a short, hardware-chosen time).
+constexpr uint32_t kMbarTries = 1u << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t arrivals) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(arrivals)
+                 : "memory");
+}
+// makes initialised mbarriers visible to the async proxy (before the first copy)
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// orders this thread's earlier shared-memory accesses before its later
+// async-proxy ones: a bulk copy into a buffer that the block just read
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n"
+        "  .reg .pred p;\n"
+        "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "  selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+// true once the phase with this parity has completed, false after kMbarTries
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kMbarTries; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // Mark bit in the degree half of a vertex record: set once the vertex has
 // degree 1 with its last edge claimed (round 0 scan, or the fall from 2 to 1).
 constexpr uint32_t kMark = 0x80000000u;

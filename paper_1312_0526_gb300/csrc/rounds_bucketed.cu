@@ -35,6 +35,7 @@
 // r = 3, r-partite graphs only.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -129,7 +130,9 @@ k_round0_emit(const unsigned long long *__restrict__ st, uint32_t m, uint32_t n,
 // One counting-sort pass: each block takes tiles of input items, sorts their
 // pairs by chunk in shared memory and appends each chunk's run to the chunk's
 // array (one atomicAdd per chunk and tile on its cursor; cursors one 128-byte
-// line apart, zeroed before the pass).  Items:
+// line apart, zeroed before the pass).  A tile's items are contiguous: one
+// bulk copy (TMA) brings them into one of two shared-memory buffers while the
+// block sorts the previous tile.  Items:
 //   ENTRIES  -- the entries of layer t = ctl->round, each giving the pairs
 //               {w, e} of its R - 1 non-hinge vertices; chunks by vertex
 //               (part j, then 2^shift vertices of the part);
@@ -143,6 +146,9 @@ k_round0_emit(const unsigned long long *__restrict__ st, uint32_t m, uint32_t n,
 #endif
 constexpr int kBucketThreads = HPEEL_BUCKET_THREADS;
 constexpr int kBucketItems = 4 * kBucketThreads;  // items per tile (4 per thread)
+// words of each per-chunk counter array (a multiple of 4: the arrays after
+// them stay 16-byte aligned)
+__host__ __device__ constexpr uint32_t bucket_counters(uint32_t C) { return (C + 3) & ~3u; }
 
 template <int R, bool ENTRIES>
 __global__ void __launch_bounds__(kBucketThreads, HPEEL_BUCKET_BLOCKS)
@@ -150,12 +156,15 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
                const uint2 *__restrict__ claims, uint32_t claim_cap, BucketGeom g, uint32_t C,
                uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov, Ctl *ctl) {
     constexpr int kPer = ENTRIES ? R - 1 : 1;
-    extern __shared__ uint32_t smem[];
-    const uint32_t Cp = (C + 1) & ~1u;
-    uint32_t *hist = smem;                                 // C: tile count per chunk
-    uint32_t *cur = hist + Cp;                             // C: run's place - its stage slot
-    uint32_t *toff = cur + Cp;                             // C: run's first stage slot
-    uint2 *stage = reinterpret_cast<uint2 *>(toff + Cp);   // kPer per item (8-byte aligned)
+    using In = typename std::conditional<ENTRIES, uint4, uint2>::type;  // one input item
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ uint64_t bar[2];
+    const uint32_t Cq = bucket_counters(C);
+    uint32_t *hist = smem;                                  // C: tile count per chunk
+    uint32_t *cur = hist + Cq;                              // C: run's place - its stage slot
+    uint32_t *toff = cur + Cq;                              // C: run's first stage slot
+    uint2 *stage = reinterpret_cast<uint2 *>(toff + Cq);    // kPer per item (16-byte aligned)
+    In *inbuf = reinterpret_cast<In *>(stage + 2 * kBucketItems);  // two tiles of input
     uint32_t i0, i1;
     if (ENTRIES) {
         const uint32_t t = *(volatile uint32_t *)&ctl->round;
@@ -166,6 +175,7 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
         i1 = min(*(volatile uint32_t *)&ctl->ccur, claim_cap);
     }
     if (i1 < i0) i1 = i0;
+    const In *in = (ENTRIES ? reinterpret_cast<const In *>(Lst) : reinterpret_cast<const In *>(claims)) + i0;
     auto chunk_of_key = [&](uint32_t x) -> uint32_t {
         if (ENTRIES) {
             const uint32_t j = part_of<R>(x, g.P);
@@ -174,37 +184,81 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
         return x >> g.shift;
     };
     const uint64_t tiles = ((uint64_t)(i1 - i0) + kBucketItems - 1) / kBucketItems;
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    auto tile_items = [&](uint64_t tile) -> uint32_t {
+        const uint64_t left = (uint64_t)(i1 - i0) - tile * kBucketItems;
+        return left < (uint64_t)kBucketItems ? (uint32_t)left : (uint32_t)kBucketItems;
+    };
+    // a tile's input arrives by one bulk copy of its first multiple of 16
+    // bytes (every item but a claim tile's odd last one, read directly)
+    auto bulk_bytes = [&](uint32_t tn) -> uint32_t { return (tn * (uint32_t)sizeof(In)) & ~15u; };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blockIdx.x < tiles) {
+        const uint32_t bytes = bulk_bytes(tile_items(blockIdx.x));
+        if (bytes) bulk_load(inbuf, in + (uint64_t)blockIdx.x * kBucketItems, bytes, &bar[0]);
+    }
+    uint32_t k = 0;  // this block's tiles so far: buffer k & 1, its use k >> 1
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, k++) {
+        const uint32_t buf = k & 1u;
+        // the next tile's input goes to the other buffer, which the block
+        // read in the previous tile (ended by a barrier)
+        const uint64_t next = tile + gridDim.x;
+        if (threadIdx.x == 0 && next < tiles) {
+            const uint32_t bytes = bulk_bytes(tile_items(next));
+            if (bytes) {
+                fence_proxy_async_smem();
+                bulk_load(inbuf + (size_t)(buf ^ 1u) * kBucketItems, in + next * kBucketItems,
+                          bytes, &bar[buf ^ 1u]);
+            }
+        }
         for (uint32_t c = threadIdx.x; c < C; c += kBucketThreads) hist[c] = 0;
-        __syncthreads();
+        const uint32_t tn = tile_items(tile);
+        const uint32_t nbulk = bulk_bytes(tn) / (uint32_t)sizeof(In);
+        const bool landed = nbulk == 0 || mbar_wait(&bar[buf], (k >> 1) & 1u);
+        if (!__syncthreads_and(landed)) {  // a copy that never lands: give up
+            if (threadIdx.x == 0) {
+                raise_err(ctl, kDevTimeout);
+                mbar_wait(&bar[buf], (k >> 1) & 1u);
+                if (next < tiles) mbar_wait(&bar[buf ^ 1u], ((k + 1) >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const In *tin = inbuf + (size_t)buf * kBucketItems;
+        const In *gin = in + tile * kBucketItems;
         uint2 pp[4][kPer];
         uint32_t ch[4][kPer], rank[4][kPer];
         bool ok[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const uint64_t i = i0 + tile * kBucketItems + (uint64_t)q * kBucketThreads + threadIdx.x;
-            ok[q] = i < i1;
+            const uint32_t li = (uint32_t)q * kBucketThreads + threadIdx.x;
+            ok[q] = li < tn;
 #pragma unroll
-            for (int k = 0; k < kPer; k++) pp[q][k] = make_uint2(0u, 0u);
+            for (int k2 = 0; k2 < kPer; k2++) pp[q][k2] = make_uint2(0u, 0u);
             if (ok[q]) {
-                if (ENTRIES) {
-                    const uint4 a = __ldcs(Lst + i);  // {v_hinge, v_a, v_b, e}
+                const In a = li < nbulk ? tin[li] : gin[li];
+                if constexpr (ENTRIES) {  // {v_hinge, v_a, v_b, e}
                     pp[q][0] = make_uint2(a.y, a.w);
                     if (kPer > 1) pp[q][kPer - 1] = make_uint2(a.z, a.w);
                 } else {
-                    pp[q][0] = __ldcs(claims + i);
+                    pp[q][0] = a;
                 }
             }
 #pragma unroll
-            for (int k = 0; k < kPer; k++) {
-                ch[q][k] = ok[q] ? chunk_of_key(pp[q][k].x) : 0u;
-                if (ch[q][k] >= C) {  // a key outside the geometry: inconsistent state
+            for (int k2 = 0; k2 < kPer; k2++) {
+                ch[q][k2] = ok[q] ? chunk_of_key(pp[q][k2].x) : 0u;
+                if (ch[q][k2] >= C) {  // a key outside the geometry: inconsistent state
                     raise_err(ctl, ENTRIES ? kDevBadVertex : kDevBadEdge);
                     ok[q] = false;
                 }
             }
 #pragma unroll
-            for (int k = 0; k < kPer; k++) rank[q][k] = ok[q] ? atomicAdd(&hist[ch[q][k]], 1u) : 0u;
+            for (int k2 = 0; k2 < kPer; k2++)
+                rank[q][k2] = ok[q] ? atomicAdd(&hist[ch[q][k2]], 1u) : 0u;
         }
         __syncthreads();
         // reserve each chunk's run; the result is awaited after the staging
@@ -219,9 +273,9 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
         for (int q = 0; q < 4; q++) {
             if (!ok[q]) continue;
 #pragma unroll
-            for (int k = 0; k < kPer; k++) {
-                const uint32_t slot = toff[ch[q][k]] + rank[q][k];
-                stage[slot] = pp[q][k];
+            for (int k2 = 0; k2 < kPer; k2++) {
+                const uint32_t slot = toff[ch[q][k2]] + rank[q][k2];
+                stage[slot] = pp[q][k2];
             }
         }
         // staged pair k of chunk c goes to place cur[c] + k (mod 2^32)
@@ -230,10 +284,10 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
             cur[c] -= toff[c];
         __syncthreads();
         const uint32_t total = toff[C - 1] + hist[C - 1];
-        for (uint32_t k = threadIdx.x; k < total; k += kBucketThreads) {
-            const uint2 p = stage[k];
+        for (uint32_t k2 = threadIdx.x; k2 < total; k2 += kBucketThreads) {
+            const uint2 p = stage[k2];
             const uint32_t c = chunk_of_key(p.x);  // its chunk again
-            const uint32_t pos = cur[c] + k;
+            const uint32_t pos = cur[c] + k2;
             if (pos < g.cap)
                 pairs[(uint64_t)c * g.cap + pos] = p;
             else
@@ -597,9 +651,11 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     const double c2 = (double)p.claim_cap * (double)(1ull << p.esub) / (double)n;
     p.ecap2 = (uint32_t)std::min<uint64_t>((uint64_t)(c2 + 8.0 * std::sqrt(c2 + 1.0) + 256.0),
                                            p.claim_cap);
-    // shared memory of the bucketing pass (counters of every chunk + a tile)
     const uint32_t C = std::max(p.vchunks, p.echunks);
-    p.bucket_smem = (size_t)3 * ((C + 1) & ~1u) * 4 + (size_t)kBucketItems * 2 * 8;
+    // shared memory of the bucketing pass: counters of every chunk, a tile's
+    // staged pairs and two tiles of input (16-byte entries at most)
+    p.bucket_smem = (size_t)3 * bucket_counters(C) * 4 + (size_t)kBucketItems * 2 * 8 +
+                    (size_t)2 * kBucketItems * 16;
     if (p.bucket_smem > (200u << 10)) return SortedPlan{};
     p.pairs_bytes = 8 * std::max<uint64_t>((uint64_t)p.vchunks * p.vg.cap,
                                            (uint64_t)p.echunks * p.eg.cap);
