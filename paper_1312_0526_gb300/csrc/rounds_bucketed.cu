@@ -156,6 +156,7 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
                const uint2 *__restrict__ claims, uint32_t claim_cap, BucketGeom g, uint32_t C,
                uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov, Ctl *ctl) {
     constexpr int kPer = ENTRIES ? R - 1 : 1;
+    static_assert(kPer <= 2, "the stage holds two pairs per item (r = 3)");
     using In = typename std::conditional<ENTRIES, uint4, uint2>::type;  // one input item
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ uint64_t bar[2];
