@@ -311,6 +311,11 @@ constexpr int kDelThreads = 512;
 // few hundred; 1024 keeps the block at 74 KB of shared memory (3 per SM)
 constexpr int kDelClaims = HPEEL_DEL_CLAIMS;
 constexpr int kDelU = 8;          // loads in flight per thread
+// updates from which a sub-bucket's records move by bulk copies
+#ifndef HPEEL_DEL_BULK
+#define HPEEL_DEL_BULK 512
+#endif
+constexpr uint32_t kDelBulk = HPEEL_DEL_BULK;
 
 __global__ void __launch_bounds__(kDelThreads)
 k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill2,
@@ -321,6 +326,7 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
     __shared__ uint2 cbuf[kDelClaims];
     __shared__ uint32_t s_cross[kDelThreads / 32];
     __shared__ uint32_t s_cnt, s_base;
+    __shared__ uint64_t dbar;
     const uint32_t nv = 1u << sub_shift;
     const uint32_t S = 1u << (g.shift - sub_shift);
     const uint32_t s = blockIdx.x;
@@ -332,38 +338,63 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
     const uint32_t cnt = min(fill2[s], cap2);
     if (cnt == 0) return;
     const uint32_t lim = min(nv, part_end - base_v);
-    for (uint32_t k = threadIdx.x; k < (nv + 31) / 32; k += kDelThreads) touched[k] = 0;
-    if (threadIdx.x == 0) s_cnt = 0;
+    // a sub-bucket with kDelBulk updates or more (a whole one, its records
+    // 16-byte aligned) takes all its records by one bulk copy and gives them
+    // back by one, instead of loading and storing the touched ones that a
+    // bitmap finds (which reads the updates twice)
+    const bool bulk = cnt >= kDelBulk && lim == nv && (base_v & 1u) == 0u;  // block-uniform
+    if (threadIdx.x == 0) {
+        s_cnt = 0;
+        if (bulk) {
+            mbar_init(&dbar, 1);
+            mbar_init_fence();
+        }
+    }
+    if (!bulk)
+        for (uint32_t k = threadIdx.x; k < (nv + 31) / 32; k += kDelThreads) touched[k] = 0;
     __syncthreads();
     const uint2 *src = pairs2 + (size_t)s * cap2;
-    // every loop keeps kDelU independent loads in flight per thread
-    for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += kDelU * kDelThreads) {
-        uint32_t k[kDelU];
-#pragma unroll
-        for (int u = 0; u < kDelU; u++) {
-            const uint32_t i = i0 + (uint32_t)u * kDelThreads;
-            k[u] = i < cnt ? __ldcg(src + i).x - base_v : 0xFFFFFFFFu;
+    if (bulk) {
+        if (threadIdx.x == 0) bulk_load(srec, st + base_v, nv * 8u, &dbar);
+        if (!__syncthreads_and(mbar_wait(&dbar, 0u))) {  // the copy never landed
+            if (threadIdx.x == 0) {
+                raise_err(ctl, kDevTimeout);
+                mbar_wait(&dbar, 0u);
+            }
+            __syncthreads();
+            return;
         }
-#pragma unroll
-        for (int u = 0; u < kDelU; u++)
-            if (k[u] < lim) atomicOr(&touched[k[u] >> 5], 1u << (k[u] & 31u));
     }
-    __syncthreads();
-    // only the touched records: a warp's loads cover 32 consecutive records
-    for (uint32_t k0 = threadIdx.x; k0 < lim; k0 += kDelU * kDelThreads) {
-        unsigned long long r[kDelU];
-        bool t[kDelU];
+    if (!bulk) {
+      // every loop keeps kDelU independent loads in flight per thread
+      for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += kDelU * kDelThreads) {
+          uint32_t k[kDelU];
 #pragma unroll
-        for (int u = 0; u < kDelU; u++) {
-            const uint32_t k = k0 + (uint32_t)u * kDelThreads;
-            t[u] = k < lim && ((touched[k >> 5] >> (k & 31u)) & 1u);
-            r[u] = t[u] ? __ldcg(st + base_v + k) : 0ull;
-        }
+          for (int u = 0; u < kDelU; u++) {
+              const uint32_t i = i0 + (uint32_t)u * kDelThreads;
+              k[u] = i < cnt ? __ldcg(src + i).x - base_v : 0xFFFFFFFFu;
+          }
 #pragma unroll
-        for (int u = 0; u < kDelU; u++)
-            if (t[u]) srec[k0 + (uint32_t)u * kDelThreads] = r[u];
+          for (int u = 0; u < kDelU; u++)
+              if (k[u] < lim) atomicOr(&touched[k[u] >> 5], 1u << (k[u] & 31u));
+      }
+      __syncthreads();
+      // only the touched records: a warp's loads cover 32 consecutive records
+      for (uint32_t k0 = threadIdx.x; k0 < lim; k0 += kDelU * kDelThreads) {
+          unsigned long long r[kDelU];
+          bool t[kDelU];
+#pragma unroll
+          for (int u = 0; u < kDelU; u++) {
+              const uint32_t k = k0 + (uint32_t)u * kDelThreads;
+              t[u] = k < lim && ((touched[k >> 5] >> (k & 31u)) & 1u);
+              r[u] = t[u] ? __ldcg(st + base_v + k) : 0ull;
+          }
+#pragma unroll
+          for (int u = 0; u < kDelU; u++)
+              if (t[u]) srec[k0 + (uint32_t)u * kDelThreads] = r[u];
+      }
+      __syncthreads();
     }
-    __syncthreads();
     // claims gather in shared memory and leave with one reservation on the
     // list cursor per block (a claim beyond the buffer reserves its own slot)
     uint32_t cross = 0;
@@ -405,6 +436,7 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
         }
       }
     }
+    if (bulk) fence_proxy_async_smem();  // this thread's shared atomics before the copy back
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t k = min(s_cnt, (uint32_t)kDelClaims);
@@ -418,8 +450,16 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
         for (uint32_t i = threadIdx.x; i < k; i += kDelThreads)
             if (b + i < claim_cap && b + i >= b) claims[b + i] = cbuf[i];
     }
-    for (uint32_t k = threadIdx.x; k < lim; k += kDelThreads)
-        if ((touched[k >> 5] >> (k & 31u)) & 1u) st[base_v + k] = srec[k];
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();  // the shared atomics before the copy's reads
+            bulk_store(st + base_v, srec, nv * 8u);
+            bulk_store_wait_read();
+        }
+    } else {
+        for (uint32_t k = threadIdx.x; k < lim; k += kDelThreads)
+            if ((touched[k >> 5] >> (k & 31u)) & 1u) st[base_v + k] = srec[k];
+    }
     const uint32_t wc = __reduce_add_sync(0xFFFFFFFFu, cross);
     if ((threadIdx.x & 31u) == 0) s_cross[threadIdx.x >> 5] = wc;
     __syncthreads();
