@@ -311,13 +311,19 @@ constexpr int kDelThreads = 512;
 // few hundred; 1024 keeps the block at 74 KB of shared memory (3 per SM)
 constexpr int kDelClaims = HPEEL_DEL_CLAIMS;
 constexpr int kDelU = 8;          // loads in flight per thread
+#ifndef HPEEL_DEL_PRE
+#define HPEEL_DEL_PRE 4
+#endif
+constexpr int kDelPre = HPEEL_DEL_PRE;  // updates per thread loaded beside a bulk copy
+static_assert(kDelPre >= 1 && kDelPre <= kDelU, "prefetched updates fit the first loop");
 // updates from which a sub-bucket's records move by bulk copies
 #ifndef HPEEL_DEL_BULK
 #define HPEEL_DEL_BULK 512
 #endif
 constexpr uint32_t kDelBulk = HPEEL_DEL_BULK;
 
-__global__ void __launch_bounds__(kDelThreads)
+// three blocks per SM, as many as their shared memory allows
+__global__ void __launch_bounds__(kDelThreads, 3)
 k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fill2,
                uint32_t cap2, BucketGeom g, uint32_t sub_shift, unsigned long long *__restrict__ st,
                uint32_t n, uint2 *__restrict__ claims, uint32_t claim_cap, Ctl *ctl) {
@@ -354,8 +360,16 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
         for (uint32_t k = threadIdx.x; k < (nv + 31) / 32; k += kDelThreads) touched[k] = 0;
     __syncthreads();
     const uint2 *src = pairs2 + (size_t)s * cap2;
+    // the bulk form's first updates (kDelPre per thread) load while its
+    // records arrive
+    uint2 pv0[kDelPre];
     if (bulk) {
         if (threadIdx.x == 0) bulk_load(srec, st + base_v, nv * 8u, &dbar);
+#pragma unroll
+        for (int u = 0; u < kDelPre; u++) {
+            const uint32_t i = threadIdx.x + (uint32_t)u * kDelThreads;
+            pv0[u] = i < cnt ? __ldcs(src + i) : make_uint2(0xFFFFFFFFu, 0u);  // {w, e}
+        }
         if (!__syncthreads_and(mbar_wait(&dbar, 0u))) {  // the copy never landed
             if (threadIdx.x == 0) {
                 raise_err(ctl, kDevTimeout);
@@ -400,10 +414,13 @@ k_delete_apply(const uint2 *__restrict__ pairs2, const uint32_t *__restrict__ fi
     uint32_t cross = 0;
     for (uint32_t i0 = threadIdx.x; i0 < cnt; i0 += kDelU * kDelThreads) {
       uint2 pv[kDelU];
+      const bool loaded = bulk && i0 == threadIdx.x;
 #pragma unroll
       for (int u = 0; u < kDelU; u++) {
           const uint32_t i = i0 + (uint32_t)u * kDelThreads;
-          pv[u] = i < cnt ? __ldcs(src + i) : make_uint2(0xFFFFFFFFu, 0u);  // {w, e}
+          pv[u] = loaded && u < kDelPre ? pv0[u < kDelPre ? u : 0]
+                  : i < cnt                 ? __ldcs(src + i)
+                                            : make_uint2(0xFFFFFFFFu, 0u);  // {w, e}
       }
 #pragma unroll
       for (int u = 0; u < kDelU; u++) {
