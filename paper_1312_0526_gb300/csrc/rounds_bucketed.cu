@@ -24,12 +24,13 @@
 //   updates -- the entries of the layer give their r - 1 DeleteEdge updates
 //              {vertex, edge}, bucketed by vertex range (chunks of a part,
 //              then sub-buckets of 2^sub_shift vertices); one block per
-//              sub-bucket loads the records of the vertices the round
-//              touches into shared memory, applies the updates there with
+//              sub-bucket brings its vertex records into shared memory (all
+//              of them by one bulk copy when it has many updates, else the
+//              ones the round touches), applies the updates there with
 //              64-bit shared atomics (degree and id sum in one word, as in
 //              global memory), lets every vertex that falls from degree 2 to
 //              1 claim its last edge for the next round, and writes the
-//              touched records back.
+//              records back.
 // A round runs in sorted form when its layer holds at least a set number of
 // edges; the rounds after the first one that does not run in random form.
 // r = 3, r-partite graphs only.
