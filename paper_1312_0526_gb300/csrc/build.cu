@@ -402,12 +402,15 @@ k_refine_buckets(const uint2 *__restrict__ pairs, const uint32_t *__restrict__ f
             if (b0 + q < S) gbase[b0 + q] -= toff[b0 + q];
         __syncthreads();
         const uint32_t total = toff[S - 1] + hist[S - 1];
+        // this chunk's sub-buckets: S * cap2 slots, below 2^32 (the plans
+        // check it), so a slot's index takes 32-bit arithmetic
+        uint2 *const cdst = pairs2 + (size_t)c * S * cap2;
         for (uint32_t k = threadIdx.x; k < total; k += kRefThreads) {
             const uint2 q = stage[k];
             const uint32_t b = (q.x - base_v) >> sub_shift;  // its sub-bucket, again
             const uint32_t pos = gbase[b] + k;
             if (pos < cap2)
-                pairs2[((size_t)c * S + b) * cap2 + pos] = q;
+                cdst[b * cap2 + pos] = q;
             else
                 overflow_push(q, ov, ctl);
         }
@@ -582,6 +585,10 @@ BucketPlan bucket_plan(uint64_t n, uint64_t m, uint32_t r, uint32_t parts, uint3
     b.pair2_bytes = (uint64_t)b.subs_pass * b.cap2 * 8;
     b.ovf_cap = (uint32_t)std::max<uint64_t>(1u << 16, n / 16);
     b.smem = (size_t)(3 * ((b.chunks + 1) & ~1u)) * 4 + (size_t)kTileEdges * r * 8;
+    // the refine indexes a chunk's sub-buckets with 32-bit arithmetic: a plan
+    // beyond that asks for more shared memory than any block has, so the
+    // caller builds without buckets
+    if ((uint64_t)b.cap2 << (shift - b.sub_shift) >= (1ull << 32)) b.smem = ~(size_t)0;
     b.parts = parts;
     return b;
 }

@@ -710,6 +710,10 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     const double c2 = (double)p.claim_cap * (double)(1ull << p.esub) / (double)n;
     p.ecap2 = (uint32_t)std::min<uint64_t>((uint64_t)(c2 + 8.0 * std::sqrt(c2 + 1.0) + 256.0),
                                            p.claim_cap);
+    // the refine indexes a chunk's sub-buckets with 32-bit arithmetic
+    if (((uint64_t)p.vcap2 << (p.vg.shift - p.vsub_shift)) >= (1ull << 32) ||
+        ((uint64_t)p.ecap2 << (p.eshift - p.esub)) >= (1ull << 32))
+        return SortedPlan{};
     const uint32_t C = std::max(p.vchunks, p.echunks);
     // shared memory of the bucketing pass: counters of every chunk, a tile's
     // staged pairs and two tiles of input (16-byte entries at most)
