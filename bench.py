@@ -115,7 +115,7 @@ NCU_TRAFFIC = {
     # step: (source files, sha256 prefix, bytes per unit, where measured)
     "rounds": (("paper_1312_0526_gb300/csrc/peel.cu",
                 "paper_1312_0526_gb300/csrc/rounds_bucketed.cu",
-                "paper_1312_0526_gb300/csrc/build.cu"), "35dbda0c991d9d0e", 339.63,
+                "paper_1312_0526_gb300/csrc/build.cu"), "9df1550ecb748c40", 339.63,
                "every round kernel (sorted round 0 and L_0..L_2, random k_round) of one peel at "
                "n = 3e7 (host round loop), scaled by peeled edges"),
 }

@@ -210,12 +210,13 @@ struct SortedPlan {
     bool enabled;
     uint32_t min_edges, max_edges;  // layers deleted in sorted form
     uint32_t claim_cap;             // claims one round may make
-    uint32_t bucket_blocks;         // blocks of the bucketing pass
+    uint32_t bucket_blocks;         // blocks of the bucketing pass (list entries)
+    uint32_t claim_bucket_blocks;   // blocks of the bucketing pass (claims)
     BucketGeom vg;                  // updates by vertex (parts, chunks)
     uint32_t vchunks, vsub_shift, vsubs, vcap2;
     BucketGeom eg;                  // claims by edge (one part of n edges)
     uint32_t eshift, esub, echunks, esubs, ecap2;
-    size_t bucket_smem;
+    size_t bucket_smem, claim_bucket_smem;
     uint64_t pairs_bytes, fill_bytes, pairs2_bytes, fill2_bytes, claims_bytes;
 };
 struct SortedBufs {

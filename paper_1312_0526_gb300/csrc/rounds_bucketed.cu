@@ -145,14 +145,26 @@ k_round0_emit(const unsigned long long *__restrict__ st, uint32_t m, uint32_t n,
 #ifndef HPEEL_BUCKET_BLOCKS
 #define HPEEL_BUCKET_BLOCKS 2
 #endif
+// the claims' pass stages one pair per item from 8-byte items: more blocks fit
+#ifndef HPEEL_CLAIM_BUCKET_BLOCKS
+#define HPEEL_CLAIM_BUCKET_BLOCKS 3
+#endif
 constexpr int kBucketThreads = HPEEL_BUCKET_THREADS;
 constexpr int kBucketItems = 4 * kBucketThreads;  // items per tile (4 per thread)
 // words of each per-chunk counter array (a multiple of 4: the arrays after
 // them stay 16-byte aligned)
 __host__ __device__ constexpr uint32_t bucket_counters(uint32_t C) { return (C + 3) & ~3u; }
 
+// shared memory of one pass: counters of every chunk, a tile's staged pairs
+// and two tiles of input
+__host__ __device__ constexpr size_t bucket_smem_bytes(uint32_t C, bool entries) {
+    return (size_t)3 * bucket_counters(C) * 4 + (size_t)kBucketItems * (entries ? 2 : 1) * 8 +
+           (size_t)2 * kBucketItems * (entries ? 16 : 8);
+}
+
 template <int R, bool ENTRIES>
-__global__ void __launch_bounds__(kBucketThreads, HPEEL_BUCKET_BLOCKS)
+__global__ void __launch_bounds__(kBucketThreads,
+                                  ENTRIES ? HPEEL_BUCKET_BLOCKS : HPEEL_CLAIM_BUCKET_BLOCKS)
 k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
                const uint2 *__restrict__ claims, uint32_t claim_cap, BucketGeom g, uint32_t C,
                uint2 *__restrict__ pairs, uint32_t *__restrict__ fill, Overflow ov, Ctl *ctl) {
@@ -166,7 +178,7 @@ k_pairs_bucket(const uint4 *__restrict__ Lst, const uint32_t *__restrict__ loff,
     uint32_t *cur = hist + Cq;                              // C: run's place - its stage slot
     uint32_t *toff = cur + Cq;                              // C: run's first stage slot
     uint2 *stage = reinterpret_cast<uint2 *>(toff + Cq);    // kPer per item (16-byte aligned)
-    In *inbuf = reinterpret_cast<In *>(stage + 2 * kBucketItems);  // two tiles of input
+    In *inbuf = reinterpret_cast<In *>(stage + kPer * kBucketItems);  // two tiles of input
     uint32_t i0, i1;
     if (ENTRIES) {
         const uint32_t t = *(volatile uint32_t *)&ctl->round;
@@ -677,6 +689,7 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
     // fraction lambda e^-lambda <= 1/e of the vertices for random graphs)
     p.claim_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0u, m * 38 / 100 + 4096);
     p.bucket_blocks = (uint32_t)std::max<int>(1, sms * HPEEL_BUCKET_BLOCKS);  // one wave of blocks
+    p.claim_bucket_blocks = (uint32_t)std::max<int>(1, sms * HPEEL_CLAIM_BUCKET_BLOCKS);
     // updates, by vertex: the build's chunks and sub-buckets
     p.vg = BucketGeom{(uint32_t)P, b.shift, b.chunks_per_part, 0, kFillShift};
     p.vchunks = b.chunks;
@@ -715,10 +728,8 @@ SortedPlan sorted_plan(uint64_t n, uint64_t m, uint32_t r, const BucketPlan &b, 
         ((uint64_t)p.ecap2 << (p.eshift - p.esub)) >= (1ull << 32))
         return SortedPlan{};
     const uint32_t C = std::max(p.vchunks, p.echunks);
-    // shared memory of the bucketing pass: counters of every chunk, a tile's
-    // staged pairs and two tiles of input (16-byte entries at most)
-    p.bucket_smem = (size_t)3 * bucket_counters(C) * 4 + (size_t)kBucketItems * 2 * 8 +
-                    (size_t)2 * kBucketItems * 16;
+    p.bucket_smem = bucket_smem_bytes(C, true);
+    p.claim_bucket_smem = bucket_smem_bytes(C, false);
     if (p.bucket_smem > (200u << 10)) return SortedPlan{};
     p.pairs_bytes = 8 * std::max<uint64_t>((uint64_t)p.vchunks * p.vg.cap,
                                            (uint64_t)p.echunks * p.eg.cap);
@@ -741,9 +752,10 @@ void launch_sorted_claims(const Launch &L, const SortedPlan &p, const SortedBufs
     cudaMemsetAsync(w.fill, 0, 4 * ((size_t)p.echunks << kFillShift), L.stream);
     cudaMemsetAsync(w.fill2, 0, 4 * (size_t)p.esubs, L.stream);
     BucketGeom eg = p.eg;
-    set_smem((const void *)k_pairs_bucket<3, false>, p.bucket_smem);
+    set_smem((const void *)k_pairs_bucket<3, false>, p.claim_bucket_smem);
     count_launch();
-    k_pairs_bucket<3, false><<<p.bucket_blocks, kBucketThreads, p.bucket_smem, L.stream>>>(
+    k_pairs_bucket<3, false><<<p.claim_bucket_blocks, kBucketThreads, p.claim_bucket_smem,
+                               L.stream>>>(
         nullptr, nullptr, w.claims, p.claim_cap, eg, p.echunks, w.pairs, w.fill, none, ctl);
     launch_refine(L, eg, p.echunks, 0, p.esub, w.pairs, w.fill, w.pairs2, w.fill2,
                   p.ecap2, none, ctl);
